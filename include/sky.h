@@ -1,0 +1,173 @@
+/*
+ * libsky: C ABI of the GB300 (sm_103a) damped-gradient Skyrme-DFT hot path
+ * (Afibuzzaman, Schuetrumpf, Aktulga, arXiv 1610.07522).
+ *
+ * One iteration (Fig. 1, steps 2-5) is the sequence
+ *   sky_apply_h(psi) -> sky_damped_step -> sky_apply_h(phi) -> sky_overlap (x2)
+ *   -> sky_orthonormalize -> sky_subspace_diag -> sky_rotate
+ *   -> sky_densities (per species) -> sky_mean_fields -> sky_energy,
+ * with sky_sp_spread giving the convergence measure of Eq. convergence.
+ *
+ * Conventions shared by every entry point
+ *   - All array arguments are DEVICE pointers owned by the caller.  No entry
+ *     point frees or retains them past the call.
+ *   - Every call is enqueued on the context's CUDA stream and returns without
+ *     waiting.  The return value reports argument and launch errors.  Errors
+ *     found on the device (SKY_ENOTPD, SKY_ENOCONV, SKY_ETIMEOUT, SKY_ENAN)
+ *     are recorded in a device status word that sky_sync() returns and clears.
+ *   - Grid: nx, ny, nz points with spacing dx (fm), periodic, x_a = a*dx.
+ *     G = nx*ny*nz.  A spinor is 2 spin components of G points; V = 2G
+ *     (Sec. 3.1, "psi(V,A)").
+ *   - Spinor arrays: [I][2][nz][ny][nx] complex, x fastest, interleaved
+ *     (re, im), in the context precision: double2 for SKY_F64, float2 for
+ *     SKY_F32.  Consecutive states are V complex values apart.
+ *   - Field arrays (rho, tau, divJ, U, B): [nz][ny][nx] double.  Vector
+ *     fields (J, W): [3][nz][ny][nx] double, components x, y, z.
+ *   - I x I matrices: row-major double2, element (a, b) at [a*I + b].
+ *   - I must satisfy 0 <= I <= max_states given to sky_init; I == 0 is a no-op.
+ *   - Units: MeV and fm.
+ */
+#ifndef SKY_H
+#define SKY_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sky_ctx sky_ctx;
+
+typedef enum {
+  SKY_OK = 0,
+  SKY_EINVAL = 1,       /* bad argument (null pointer, size out of range)        */
+  SKY_ENOMEM = 2,       /* device allocation failed in sky_init                  */
+  SKY_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed           */
+  SKY_ENOTPD = 4,       /* overlap matrix not positive definite (dependent phi)  */
+  SKY_ENOCONV = 5,      /* Jacobi eigensolver hit its sweep limit                */
+  SKY_ETIMEOUT = 6,     /* a bounded device-side wait gave up                    */
+  SKY_ENAN = 7,         /* NaN or Inf in the energy                              */
+  SKY_EUNSUPPORTED = 8  /* grid size or precision not built into this library   */
+} sky_status;
+
+typedef enum {
+  SKY_F64 = 0,          /* complex double spinors, FP64 everywhere               */
+  SKY_F32 = 1           /* complex float spinors; matrices and sums FP64         */
+} sky_prec;
+
+/* Skyrme parameters (Eq. Skyrme; the paper fits them without printing them).
+ * t0 [MeV fm^3], t1, t2 [MeV fm^5], t3 [MeV fm^(3+3 alpha)], x0..x3, alpha,
+ * W0 [MeV fm^5], hb2m_n/hb2m_p = hbar^2/2m [MeV fm^2], e2 = e^2 [MeV fm];
+ * coulomb != 0 adds the FFT-Poisson Coulomb potential to the protons
+ * (Sec. 2.2). */
+typedef struct {
+  double t0, t1, t2, t3;
+  double x0, x1, x2, x3;
+  double alpha, W0;
+  double hb2m_n, hb2m_p, e2;
+  int coulomb;
+} sky_skyrme;
+
+/* Create a context for one grid.  grid[3] = (nx, ny, nz), each from the sizes
+ * sky_supported_size() accepts for the precision; dx[3] in fm; twist[3] is the
+ * Bloch phase theta in [-pi, pi) per direction (NULL = 0), so derivatives use
+ * k + theta/L; max_states bounds I in every later call and sizes the scratch
+ * memory the context owns; stream is a cudaStream_t (NULL = legacy default
+ * stream).  The device is the current CUDA device.  On success *out owns
+ * device memory until sky_destroy.  Returns SKY_EINVAL / SKY_EUNSUPPORTED /
+ * SKY_ENOMEM / SKY_ECUDA on failure with *out = NULL. */
+sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3],
+                    const sky_skyrme* params, const double twist[3],
+                    sky_prec prec, int max_states, void* stream);
+
+/* Free everything the context owns (waits for its stream first). */
+sky_status sky_destroy(sky_ctx* ctx);
+
+/* Change the stream later calls are enqueued on. */
+sky_status sky_set_stream(sky_ctx* ctx, void* stream);
+
+/* Wait for the context's stream; return and clear the device status word. */
+sky_status sky_sync(sky_ctx* ctx);
+
+/* Human-readable text of the last error the context saw (never NULL). */
+const char* sky_last_error(const sky_ctx* ctx);
+
+/* 1 if an axis of n points is built for precision prec, else 0. */
+int sky_supported_size(int n, sky_prec prec);
+
+/* ---- Step 2: single-particle Hamiltonian (Sec. 2.1-2.2, Eq. Schroedinger) --
+ * hpsi = h psi for I states, h = U - sum_j d_j B d_j
+ *        - (i/2) sum_ijk eps_ijk [W_i sigma_k d_j + d_j W_i sigma_k],
+ * every derivative spectral along its axis with k + theta/L (Nyquist kept).
+ * U, B: [G]; W: [3][G] (one species' mean field).  psi, hpsi: [I][2][G]
+ * spinors, must not overlap.  eps (nullable, [I]) receives <psi|h|psi>,
+ * hnorm2 (nullable, [I]) receives <h psi|h psi> (= <psi|h^2|psi>), both
+ * with the volume element dx^3.  Stored as the paper's hampsi (Sec. 3.4). */
+sky_status sky_apply_h(sky_ctx* ctx, const double* U, const double* B, const double* W,
+                       const void* psi, void* hpsi, int I, double* eps, double* hnorm2);
+
+/* ---- Step 2: damped gradient step (Eq. dampstep) ---------------------------
+ * phi = psi - x0 * P (hpsi - eps psi), P = 1/(E0 + hb2m_q |k + theta/L|^2)
+ * diagonal in momentum space (hb2m_q of species q = 0 neutrons, 1 protons).
+ * psi, hpsi, phi: [I][2][G]; phi must not overlap psi or hpsi; eps: [I].
+ * x0 dimensionless step (the paper's delta), E0 in MeV.
+ * w must be NULL (a per-voxel damping weight is not built). */
+sky_status sky_damped_step(sky_ctx* ctx, int q, const void* psi, const void* hpsi,
+                           const double* eps, void* phi, int I, double x0, double E0,
+                           const float* w);
+
+/* ---- Step 3a: overlap / Hamiltonian matrix (Eqs. normmatrix, hammatrix) ----
+ * X[a*I + b] = <a_a | b_b> = dx^3 sum_v conj(a_a[v]) b_b[v] for a >= b, and
+ * X[b*I + a] = conj(X[a*I + b]) (only the lower triangle is formed, Fig. 3).
+ * S = sky_overlap(phi, phi), H = sky_overlap(phi, h phi).  X: [I*I]. */
+sky_status sky_overlap(sky_ctx* ctx, const void* a, const void* b, int I, double* X);
+
+/* ---- Step 3c: Loewdin orthonormalisation (Eqs. Loewedin, orthmatvec) ------
+ * C = S^{-1/2} = X Lambda^{-1/2} X^H from the eigendecomposition of the
+ * Hermitian overlap S [I*I].  C: [I*I], may not alias S.  A non-positive
+ * eigenvalue sets SKY_ENOTPD on the device. */
+sky_status sky_orthonormalize(sky_ctx* ctx, const double* S, int I, double* C);
+
+/* ---- Steps 3b, 3d: diagonalisation and combination (Sec. 3.3.2-3.3.3) -----
+ * Exact Rayleigh-Ritz in the Loewdin basis: H' = C^H H C = Z Lambda Z^H
+ * (Lambda ascending), M = C Z.  H, C, M: [I*I]; eps: [I] receives Lambda.
+ * The new states are psi_a = sum_b M[b*I + a] phi_b (sky_rotate). */
+sky_status sky_subspace_diag(sky_ctx* ctx, const double* H, const double* C, int I,
+                             double* M, double* eps);
+
+/* ---- Step 3e: recombination (Sec. 3.3.3, Fig. 3) ---------------------------
+ * psi_out[a] = sum_b M[b*I + a] phi[b] for all V entries.  phi, psi_out:
+ * [I][2][G] and must not overlap.  Also the Loewdin application of
+ * Eq. orthmatvec when M = C. */
+sky_status sky_rotate(sky_ctx* ctx, const void* phi, const double* M, int I, void* psi_out);
+
+/* ---- Step 4a: densities (Eqs. rho, curr, tau; all v^2 = 1) -----------------
+ * For the I states of one species: rho = sum |psi|^2, tau = sum |d psi|^2,
+ * J_i = sum Re[-i eps_ijk psi^+ sigma_k d_j psi], divJ = sum_i d_i J_i
+ * (spectral, real part).  rho, tau, divJ: [G]; J: [3][G] or NULL. */
+sky_status sky_densities(sky_ctx* ctx, const void* psi, int I, double* rho, double* tau,
+                         double* J, double* divJ);
+
+/* ---- Step 4b: mean field (Eq. Skyrme, Sec. 2.2) ----------------------------
+ * Both species at once (the only neutron-proton coupling, Sec. 3.2).
+ * rho, tau, divJ: [2][G] (neutrons then protons).  U, B: [2][G]; W: [2][3][G].
+ * U_q = dE/drho_q (Coulomb added to protons when enabled), B_q = dE/dtau_q,
+ * W_q = dE/dJ_q of the isoscalar/isovector Skyrme functional. */
+sky_status sky_mean_fields(sky_ctx* ctx, const double* rho, const double* tau,
+                           const double* divJ, double* U, double* B, double* W);
+
+/* ---- Step 5: energy (Eq. Skyrme; Coulomb by FFT Poisson) -------------------
+ * out[8] (device doubles): total E, kinetic, rho^2 (+density dependent),
+ * rho tau, rho Delta rho, rho div J, Coulomb, particle number A = int rho.
+ * A NaN or Inf total sets SKY_ENAN. */
+sky_status sky_energy(sky_ctx* ctx, const double* rho, const double* tau,
+                      const double* divJ, double* out);
+
+/* ---- Step 5: convergence measure (Eq. convergence) -------------------------
+ * out[0] = sqrt( sum_a (hnorm2[a] - eps[a]^2) / A ), out[1] = sum_a eps[a],
+ * over A states (pass both species' arrays back to back). */
+sky_status sky_sp_spread(sky_ctx* ctx, const double* eps, const double* hnorm2, int A,
+                         double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SKY_H */

@@ -1,0 +1,172 @@
+"""Thin ctypes binding of libsky (include/sky.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Array
+arguments may be torch tensors (their ``data_ptr()`` is passed), raw integer
+device addresses, or None for nullable pointers.  A non-OK status raises
+``SkyError``.  There is no fallback: if the library is missing, ``lib()``
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+SKY_OK, SKY_EINVAL, SKY_ENOMEM, SKY_ECUDA, SKY_ENOTPD, SKY_ENOCONV, SKY_ETIMEOUT, SKY_ENAN, SKY_EUNSUPPORTED = range(9)
+STATUS_NAMES = ["SKY_OK", "SKY_EINVAL", "SKY_ENOMEM", "SKY_ECUDA", "SKY_ENOTPD",
+                "SKY_ENOCONV", "SKY_ETIMEOUT", "SKY_ENAN", "SKY_EUNSUPPORTED"]
+SKY_F64, SKY_F32 = 0, 1
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+
+class SkySkyrme(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("t0", "t1", "t2", "t3", "x0", "x1", "x2", "x3", "alpha", "W0",
+                 "hb2m_n", "hb2m_p", "e2")] + [("coulomb", ctypes.c_int)]
+
+
+class SkyError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+
+
+_SIGNATURES = {
+    "sky_init": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_D),
+                      ctypes.POINTER(SkySkyrme), ctypes.POINTER(_D), _I, _I, _P]),
+    "sky_destroy": (_I, [_P]),
+    "sky_set_stream": (_I, [_P, _P]),
+    "sky_sync": (_I, [_P]),
+    "sky_last_error": (ctypes.c_char_p, [_P]),
+    "sky_supported_size": (_I, [_I, _I]),
+    "sky_apply_h": (_I, [_P, _P, _P, _P, _P, _P, _I, _P, _P]),
+    "sky_damped_step": (_I, [_P, _I, _P, _P, _P, _P, _I, _D, _D, _P]),
+    "sky_overlap": (_I, [_P, _P, _P, _I, _P]),
+    "sky_orthonormalize": (_I, [_P, _P, _I, _P]),
+    "sky_subspace_diag": (_I, [_P, _P, _P, _I, _P, _P]),
+    "sky_rotate": (_I, [_P, _P, _P, _I, _P]),
+    "sky_densities": (_I, [_P, _P, _I, _P, _P, _P, _P]),
+    "sky_mean_fields": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "sky_energy": (_I, [_P, _P, _P, _P, _P]),
+    "sky_sp_spread": (_I, [_P, _P, _P, _I, _P]),
+}
+
+_LIB = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libsky.so (built in-tree by ``build.build()``); raise if absent."""
+    global _LIB
+    if _LIB is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsky is not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _check(ctx, st):
+    if st != SKY_OK:
+        msg = lib().sky_last_error(ctx).decode() if ctx else ""
+        raise SkyError(st, msg)
+
+
+def skyrme_struct(params, coulomb):
+    s = SkySkyrme()
+    for k in ("t0", "t1", "t2", "t3", "x0", "x1", "x2", "x3", "alpha", "W0", "hb2m_n", "hb2m_p", "e2"):
+        setattr(s, k, float(params[k]))
+    s.coulomb = 1 if coulomb else 0
+    return s
+
+
+def sky_init(grid, dx, params, coulomb, twist=(0.0, 0.0, 0.0), prec=SKY_F64, max_states=1, stream=0):
+    ctx = _P()
+    g = (_I * 3)(*[int(v) for v in grid])
+    d = (_D * 3)(*[float(v) for v in dx])
+    t = (_D * 3)(*[float(v) for v in twist])
+    s = skyrme_struct(params, coulomb)
+    st = lib().sky_init(ctypes.byref(ctx), g, d, ctypes.byref(s), t, int(prec), int(max_states),
+                        _P(stream) if stream else None)
+    if st != SKY_OK:
+        raise SkyError(st, "sky_init failed")
+    return ctx
+
+
+def sky_destroy(ctx):
+    _check(None, lib().sky_destroy(ctx))
+
+
+def sky_set_stream(ctx, stream):
+    _check(ctx, lib().sky_set_stream(ctx, _P(stream) if stream else None))
+
+
+def sky_sync(ctx):
+    _check(ctx, lib().sky_sync(ctx))
+
+
+def sky_supported_size(n, prec):
+    return bool(lib().sky_supported_size(int(n), int(prec)))
+
+
+def sky_apply_h(ctx, U, B, W, psi, hpsi, I, eps=None, hnorm2=None):
+    _check(ctx, lib().sky_apply_h(ctx, _ptr(U), _ptr(B), _ptr(W), _ptr(psi), _ptr(hpsi), int(I),
+                                  _ptr(eps), _ptr(hnorm2)))
+
+
+def sky_damped_step(ctx, q, psi, hpsi, eps, phi, I, x0, E0, w=None):
+    _check(ctx, lib().sky_damped_step(ctx, int(q), _ptr(psi), _ptr(hpsi), _ptr(eps), _ptr(phi),
+                                      int(I), float(x0), float(E0), _ptr(w)))
+
+
+def sky_overlap(ctx, a, b, I, X):
+    _check(ctx, lib().sky_overlap(ctx, _ptr(a), _ptr(b), int(I), _ptr(X)))
+
+
+def sky_orthonormalize(ctx, S, I, C):
+    _check(ctx, lib().sky_orthonormalize(ctx, _ptr(S), int(I), _ptr(C)))
+
+
+def sky_subspace_diag(ctx, H, C, I, M, eps):
+    _check(ctx, lib().sky_subspace_diag(ctx, _ptr(H), _ptr(C), int(I), _ptr(M), _ptr(eps)))
+
+
+def sky_rotate(ctx, phi, M, I, psi_out):
+    _check(ctx, lib().sky_rotate(ctx, _ptr(phi), _ptr(M), int(I), _ptr(psi_out)))
+
+
+def sky_densities(ctx, psi, I, rho, tau, J, divJ):
+    _check(ctx, lib().sky_densities(ctx, _ptr(psi), int(I), _ptr(rho), _ptr(tau), _ptr(J), _ptr(divJ)))
+
+
+def sky_mean_fields(ctx, rho, tau, divJ, U, B, W):
+    _check(ctx, lib().sky_mean_fields(ctx, _ptr(rho), _ptr(tau), _ptr(divJ), _ptr(U), _ptr(B), _ptr(W)))
+
+
+def sky_energy(ctx, rho, tau, divJ, out):
+    _check(ctx, lib().sky_energy(ctx, _ptr(rho), _ptr(tau), _ptr(divJ), _ptr(out)))
+
+
+def sky_sp_spread(ctx, eps, hnorm2, A, out):
+    _check(ctx, lib().sky_sp_spread(ctx, _ptr(eps), _ptr(hnorm2), int(A), _ptr(out)))

@@ -1,0 +1,247 @@
+// Complex contractions of step 3 (Sec. 3.3): the overlap and Hamiltonian
+// matrices X = <a|b> (Eqs. normmatrix, hammatrix; lower triangle only, as in
+// Fig. 3), the recombination psi = phi M (Sec. 3.3.3) and small I x I
+// products for the Loewdin and Rayleigh-Ritz factors.  FP64 FMA on the CUDA
+// cores; FP32 spinors are widened on load.
+#include "sky_internal.cuh"
+
+namespace sky {
+
+constexpr int BM = 32, BN = 32, BK = 16;   // tile of 32 x 32 complex outputs
+
+__device__ __forceinline__ double2 ld2(const double2* p) { return *p; }
+__device__ __forceinline__ double2 ld2(const float2* p) { const float2 v = *p; return make_double2(v.x, v.y); }
+
+// ---------------------------------------------------------------- overlap
+// Lower-triangle tile t -> (ti, tj), ti >= tj.
+__device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
+  int i = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  while (i * (i + 1) / 2 > t) --i;
+  ti = i;
+  tj = t - i * (i + 1) / 2;
+}
+
+// part[split][a][b] = sum_{v in split} conj(A[a][v]) Bm[b][v] for the lower tiles.
+template <typename S>
+__global__ void __launch_bounds__(256) k_overlap(const S* __restrict__ A, const S* __restrict__ Bm,
+                                                 int I, long long V, long long kchunk,
+                                                 double2* __restrict__ part) {
+  __shared__ double2 As[BK][BM + 1];
+  __shared__ double2 Bs[BK][BN + 1];
+  int ti, tj;
+  tri_tile(blockIdx.x, ti, tj);
+  const int r0 = ti * BM, c0 = tj * BN;
+  const long long kb = (long long)blockIdx.y * kchunk;
+  const long long ke = (kb + kchunk) < V ? (kb + kchunk) : V;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int lrow = tid >> 3, lk = (tid & 7) * 2;   // loader: 32 rows x 16 k
+  double2 acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  for (long long k0 = kb; k0 < ke; k0 += BK) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const long long k = k0 + lk + u;
+      const int ra = r0 + lrow, rb = c0 + lrow;
+      As[lk + u][lrow] = (ra < I && k < ke) ? ld2(A + (long long)ra * V + k) : make_double2(0.0, 0.0);
+      Bs[lk + u][lrow] = (rb < I && k < ke) ? ld2(Bm + (long long)rb * V + k) : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const double2 a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+      const double2 b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      acc[0][0] = acc[0][0] + cmulc(a0, b0);
+      acc[0][1] = acc[0][1] + cmulc(a0, b1);
+      acc[1][0] = acc[1][0] + cmulc(a1, b0);
+      acc[1][1] = acc[1][1] + cmulc(a1, b1);
+    }
+    __syncthreads();
+  }
+  double2* dst = part + (long long)blockIdx.y * I * I;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = r0 + ty * 2 + i, cc = c0 + tx * 2 + j;
+      if (r < I && cc < I && r >= cc) dst[(long long)r * I + cc] = acc[i][j];
+    }
+}
+
+// X[a][b] = dV sum_split part (a >= b); X[b][a] = conj(X[a][b]).
+__global__ void k_overlap_reduce(const double2* part, int nsplit, int I, double dV, double2* X) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)I * I) return;
+  const int a = (int)(e / I), b = (int)(e % I);
+  if (a < b) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int k = 0; k < nsplit; ++k) s = s + part[(long long)k * I * I + e];
+  s = dV * s;
+  X[(long long)a * I + b] = s;
+  if (a != b) X[(long long)b * I + a] = conjx(s);
+}
+
+static int overlap_splits(int I, long long V, int num_sms, int* ntiles_out) {
+  const int nt = (I + BM - 1) / BM;
+  const int ntiles = nt * (nt + 1) / 2;
+  const long long kblocks = (V + BK - 1) / BK;
+  long long want = (4LL * num_sms + ntiles - 1) / ntiles;
+  if (want > kblocks) want = kblocks;
+  if (want < 1) want = 1;
+  if (ntiles_out) *ntiles_out = ntiles;
+  return (int)want;
+}
+
+size_t overlap_partial_elems(int I, long long V, int num_sms) {
+  return (size_t)overlap_splits(I, V, num_sms, nullptr) * (size_t)I * (size_t)I;
+}
+
+sky_status overlap_impl(Ctx* c, const void* a, const void* b, int I, double2* X) {
+  const long long V = 2LL * c->G;
+  int ntiles;
+  const int nsplit = overlap_splits(I, V, c->num_sms, &ntiles);
+  const long long kblocks = (V + BK - 1) / BK;
+  const long long kchunk = ((kblocks + nsplit - 1) / nsplit) * BK;
+  const int nsplit_eff = (int)((V + kchunk - 1) / kchunk);
+  if ((size_t)nsplit_eff * I * I > c->gpart_elems)
+    return set_err(c, SKY_EINVAL, "overlap scratch too small for I=%d", I);
+  dim3 grid(ntiles, nsplit_eff);
+  if (c->prec == SKY_F64)
+    k_overlap<double2><<<grid, 256, 0, c->stream>>>((const double2*)a, (const double2*)b, I, V,
+                                                    kchunk, c->d_gpart);
+  else
+    k_overlap<float2><<<grid, 256, 0, c->stream>>>((const float2*)a, (const float2*)b, I, V,
+                                                   kchunk, c->d_gpart);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(c, e, "overlap");
+  k_overlap_reduce<<<div_up((long long)I * I, 256), 256, 0, c->stream>>>(c->d_gpart, nsplit_eff, I,
+                                                                       c->dV, X);
+  return cuda_check(c, cudaGetLastError(), "overlap reduce");
+}
+
+// ---------------------------------------------------------------- rotate
+// out[a][v] = sum_b M[b][a] phi[b][v]; tile rows a (32) x columns v (32).
+template <typename S>
+__global__ void __launch_bounds__(256) k_rotate(const S* __restrict__ phi, const double2* __restrict__ M,
+                                                int I, long long V, S* __restrict__ out) {
+  __shared__ double2 As[BK][BM + 1];
+  __shared__ double2 Bs[BK][BN + 1];
+  const int r0 = blockIdx.y * BM;
+  const long long v0 = (long long)blockIdx.x * BN;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  double2 acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < I; k0 += BK) {
+    // 16 k x 32 entries per operand, 2 per thread, contiguous along the tile row
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid * 2 + u;
+      const int kk = e >> 5, col = e & 31;
+      const int k = k0 + kk;
+      const int a = r0 + col;
+      const long long v = v0 + col;
+      As[kk][col] = (k < I && a < I) ? M[(long long)k * I + a] : make_double2(0.0, 0.0);
+      Bs[kk][col] = (k < I && v < V) ? ld2(phi + (long long)k * V + v) : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const double2 a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+      const double2 b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      acc[0][0] = acc[0][0] + cmul(a0, b0);
+      acc[0][1] = acc[0][1] + cmul(a0, b1);
+      acc[1][0] = acc[1][0] + cmul(a1, b0);
+      acc[1][1] = acc[1][1] + cmul(a1, b1);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = r0 + ty * 2 + i;
+      const long long v = v0 + tx * 2 + j;
+      if (r < I && v < V) {
+        if constexpr (std::is_same<S, double2>::value)
+          out[(long long)r * V + v] = acc[i][j];
+        else
+          out[(long long)r * V + v] = make_float2((float)acc[i][j].x, (float)acc[i][j].y);
+      }
+    }
+}
+
+sky_status rotate_impl(Ctx* c, const void* phi, const double2* M, int I, void* out) {
+  const long long V = 2LL * c->G;
+  dim3 grid(div_up(V, BN), div_up(I, BM));
+  if (c->prec == SKY_F64)
+    k_rotate<double2><<<grid, 256, 0, c->stream>>>((const double2*)phi, M, I, V, (double2*)out);
+  else
+    k_rotate<float2><<<grid, 256, 0, c->stream>>>((const float2*)phi, M, I, V, (float2*)out);
+  return cuda_check(c, cudaGetLastError(), "rotate");
+}
+
+// ---------------------------------------------------------------- small GEMM
+// C = opA(A) opB(B), n x n row-major; op = identity or conjugate transpose.
+template <bool AH, bool BH>
+__global__ void __launch_bounds__(256) k_zgemm(const double2* __restrict__ A,
+                                               const double2* __restrict__ B,
+                                               double2* __restrict__ C, int n) {
+  __shared__ double2 As[BK][BM + 1];
+  __shared__ double2 Bs[BK][BN + 1];
+  const int r0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  double2 acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < n; k0 += BK) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid * 2 + u;
+      const int kk = e >> 5, col = e & 31;
+      const int k = k0 + kk, r = r0 + col, cc = c0 + col;
+      double2 av = make_double2(0.0, 0.0), bv = make_double2(0.0, 0.0);
+      if (k < n && r < n) av = AH ? conjx(A[(long long)k * n + r]) : A[(long long)r * n + k];
+      if (k < n && cc < n) bv = BH ? conjx(B[(long long)cc * n + k]) : B[(long long)k * n + cc];
+      As[kk][col] = av;
+      Bs[kk][col] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const double2 a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+      const double2 b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      acc[0][0] = acc[0][0] + cmul(a0, b0);
+      acc[0][1] = acc[0][1] + cmul(a0, b1);
+      acc[1][0] = acc[1][0] + cmul(a1, b0);
+      acc[1][1] = acc[1][1] + cmul(a1, b1);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int r = r0 + ty * 2 + i, cc = c0 + tx * 2 + j;
+      if (r < n && cc < n) C[(long long)r * n + cc] = acc[i][j];
+    }
+}
+
+sky_status zgemm_small(Ctx* c, bool ah, bool bh, const double2* A, const double2* B, double2* C,
+                       int n) {
+  dim3 grid(div_up(n, BN), div_up(n, BM));
+  if (!ah && !bh) k_zgemm<false, false><<<grid, 256, 0, c->stream>>>(A, B, C, n);
+  else if (ah && !bh) k_zgemm<true, false><<<grid, 256, 0, c->stream>>>(A, B, C, n);
+  else if (!ah && bh) k_zgemm<false, true><<<grid, 256, 0, c->stream>>>(A, B, C, n);
+  else k_zgemm<true, true><<<grid, 256, 0, c->stream>>>(A, B, C, n);
+  return cuda_check(c, cudaGetLastError(), "zgemm");
+}
+
+}  // namespace sky

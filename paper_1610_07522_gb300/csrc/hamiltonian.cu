@@ -1,0 +1,411 @@
+// Single-particle Hamiltonian (Sec. 2.1-2.2), damped gradient step
+// (Eq. dampstep) and densities (Eqs. rho, curr, tau) for batched spinors.
+//
+// h psi is evaluated in the rearranged but identical form
+//   h psi = U psi - (i/2) sum_j A_j (d_j psi) + sum_j d_j F_j,
+//   F_j   = -B d_j psi - (i/2) A_j psi,   A_j = (sigma x W)_j,
+// which follows from eps_ijk W_i sigma_k = (sigma x W)_j.  The passes are
+//   1. G_j = d_j psi               (one 1D spectral pass per axis)
+//   2. L = U psi - (i/2) sum A_j G_j -> hpsi;  F_j -> in place of G_j
+//   3. F_j <- d_j F_j              (one pass per axis, in place)
+//   4. hpsi = L + sum_j F_j, with <psi|h psi> and |h psi|^2 per block.
+#include "fft_lines.cuh"
+
+namespace sky {
+
+sky_status upload_twiddles_hamiltonian(Ctx* c) {
+  return cuda_check(c, upload_twiddles_this_unit(), "twiddle upload (hamiltonian)");
+}
+
+// ------------------------------------------------------------ line ops
+// out = d_axis in  (i (k + theta/L) / N after the forward transform)
+template <typename T> struct OpDeriv {
+  static constexpr bool kFwd = true, kInv = true;
+  const cx<T>* in; cx<T>* out; const T* k; T inv_n; long long G;
+  __device__ __forceinline__ cx<T> load(long long b, int i) const { return in[b * G + i]; }
+  __device__ __forceinline__ void mid(cx<T>& v, long long, int, int m) const {
+    const T kk = k[m] * inv_n;
+    v = mkc<T>(-kk * v.y, kk * v.x);
+  }
+  __device__ __forceinline__ void store(long long b, int i, cx<T> v) const { out[b * G + i] = v; }
+};
+
+// Damped step, z pass: r = hpsi - eps psi, forward along z, into phi.
+template <typename T> struct OpDampZFwd {
+  static constexpr bool kFwd = true, kInv = false;
+  const cx<T>* psi; const cx<T>* hpsi; const double* eps; cx<T>* phi; long long G;
+  __device__ __forceinline__ cx<T> load(long long b, int i) const {
+    const T e = (T)eps[b >> 1];
+    const cx<T> h = hpsi[b * G + i], p = psi[b * G + i];
+    return mkc<T>(h.x - e * p.x, h.y - e * p.y);
+  }
+  __device__ __forceinline__ void mid(cx<T>&, long long, int, int) const {}
+  __device__ __forceinline__ void store(long long b, int i, cx<T> v) const { phi[b * G + i] = v; }
+};
+// Plain forward or inverse pass in place.
+template <typename T, bool INV> struct OpPass {
+  static constexpr bool kFwd = !INV, kInv = INV;
+  cx<T>* a; long long G;
+  __device__ __forceinline__ cx<T> load(long long b, int i) const { return a[b * G + i]; }
+  __device__ __forceinline__ void mid(cx<T>&, long long, int, int) const {}
+  __device__ __forceinline__ void store(long long b, int i, cx<T> v) const { a[b * G + i] = v; }
+};
+// Damped step, x pass: forward, times x0 / (G (E0 + T(k))), inverse.
+template <typename T> struct OpDampX {
+  static constexpr bool kFwd = true, kInv = true;
+  cx<T>* a; const double* P; T scale; long long G;
+  __device__ __forceinline__ cx<T> load(long long b, int i) const { return a[b * G + i]; }
+  __device__ __forceinline__ void mid(cx<T>& v, long long, int i, int) const {
+    const T f = (T)P[i] * scale;
+    v = mkc<T>(f * v.x, f * v.y);
+  }
+  __device__ __forceinline__ void store(long long b, int i, cx<T> v) const { a[b * G + i] = v; }
+};
+// Damped step, z pass: inverse along z, phi = psi - result.
+template <typename T> struct OpDampZInv {
+  static constexpr bool kFwd = false, kInv = true;
+  const cx<T>* psi; cx<T>* phi; long long G;
+  __device__ __forceinline__ cx<T> load(long long b, int i) const { return phi[b * G + i]; }
+  __device__ __forceinline__ void mid(cx<T>&, long long, int, int) const {}
+  __device__ __forceinline__ void store(long long b, int i, cx<T> v) const {
+    phi[b * G + i] = psi[b * G + i] - v;
+  }
+};
+
+template <typename T> const T* kt_of(const Ctx* c, int axis);
+template <> const double* kt_of<double>(const Ctx* c, int axis) { return c->d_kt[axis]; }
+template <> const float* kt_of<float>(const Ctx* c, int axis) { return c->d_ktf[axis]; }
+
+// G_j = d_j src for the three axes; nb = number of 3D arrays.
+template <typename T>
+static cudaError_t gradient_passes(Ctx* c, const cx<T>* src, cx<T>* const dst[3], long long nb) {
+  const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
+  const long long G = c->G;
+  cudaError_t e;
+  for (int ax = 0; ax < 3; ++ax) {
+    OpDeriv<T> op{src, dst[ax], kt_of<T>(c, ax), (T)(1.0 / c->n[ax]), G};
+    auto go = [&](auto NC) -> cudaError_t {
+      constexpr int N = decltype(NC)::value;
+      if (ax == 0) return launch_line<T, N, 0>(op, nx, ny, nz, nb, c->stream);
+      if (ax == 1) return launch_line<T, N, 1>(op, nx, ny, nz, nb, c->stream);
+      return launch_line<T, N, 2>(op, nx, ny, nz, nb, c->stream);
+    };
+    e = dispatch_n<std::is_same<T, float>::value>(c->n[ax], go);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------ apply_h kernels
+// Spin-orbit matrices A_j = (sigma x W)_j acting on a spinor (v0, v1):
+//   A_x v = (-Wy v0 - i Wz v1,  i Wz v0 + Wy v1)
+//   A_y v = ( Wx v0 -   Wz v1,   -Wz v0 - Wx v1)
+//   A_z v = ((Wy + i Wx) v1,    (Wy - i Wx) v0)
+template <typename T>
+__device__ __forceinline__ void apply_A(int j, T wx, T wy, T wz, cx<T> v0, cx<T> v1,
+                                        cx<T>& o0, cx<T>& o1) {
+  if (j == 0) {
+    o0 = (-wy) * v0 + wz * mul_mi(v1);
+    o1 = wz * mul_i(v0) + wy * v1;
+  } else if (j == 1) {
+    o0 = wx * v0 - wz * v1;
+    o1 = (-wz) * v0 - wx * v1;
+  } else {
+    o0 = wy * v1 + wx * mul_i(v1);
+    o1 = wy * v0 + wx * mul_mi(v0);
+  }
+}
+
+// Pass 2: L -> hpsi, F_j -> G_j (in place).  grid.y = state within chunk.
+template <typename T>
+__global__ void __launch_bounds__(256) k_h_local(const cx<T>* __restrict__ psi, cx<T>* g0,
+                                                 cx<T>* g1, cx<T>* g2, cx<T>* __restrict__ hpsi,
+                                                 const double* __restrict__ U,
+                                                 const double* __restrict__ B,
+                                                 const double* __restrict__ W, int G) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= G) return;
+  const long long o0 = (long long)blockIdx.y * 2 * G + p, o1 = o0 + G;
+  const cx<T> a0 = psi[o0], a1 = psi[o1];
+  const T u = (T)U[p], bb = (T)B[p];
+  const T wx = (T)W[p], wy = (T)W[G + p], wz = (T)W[2 * G + p];
+  cx<T>* gs[3] = {g0, g1, g2};
+  cx<T> L0 = u * a0, L1 = u * a1;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const cx<T> d0 = gs[j][o0], d1 = gs[j][o1];
+    cx<T> t0, t1;
+    apply_A<T>(j, wx, wy, wz, d0, d1, t0, t1);     // A_j G_j
+    L0 = L0 + (T)0.5 * mul_mi(t0);                  // - (i/2) A_j G_j
+    L1 = L1 + (T)0.5 * mul_mi(t1);
+    apply_A<T>(j, wx, wy, wz, a0, a1, t0, t1);     // A_j psi
+    gs[j][o0] = (-bb) * d0 + (T)0.5 * mul_mi(t0);   // F_j = -B G_j - (i/2) A_j psi
+    gs[j][o1] = (-bb) * d1 + (T)0.5 * mul_mi(t1);
+  }
+  hpsi[o0] = L0;
+  hpsi[o1] = L1;
+}
+
+// Deterministic block sum of two doubles (blockDim.x == kRedBlock).
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double sa[kRedBlock / 32], sb[kRedBlock / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sa[w] = a; sb[w] = b; }
+  __syncthreads();
+  if (w == 0) {
+    a = (l < kRedBlock / 32) ? sa[l] : 0.0;
+    b = (l < kRedBlock / 32) ? sb[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+  }
+}
+
+// Pass 4: hpsi = L + F_x + F_y + F_z; partial <psi|h psi>, |h psi|^2.
+template <typename T>
+__global__ void __launch_bounds__(kRedBlock) k_h_sum(const cx<T>* __restrict__ psi,
+                                                     const cx<T>* __restrict__ g0,
+                                                     const cx<T>* __restrict__ g1,
+                                                     const cx<T>* __restrict__ g2,
+                                                     cx<T>* __restrict__ hpsi, int G,
+                                                     double* part, int nblk, int state0) {
+  const long long base = (long long)blockIdx.y * 2 * G;
+  double e = 0.0, n2 = 0.0;
+  for (int p = blockIdx.x * kRedBlock + threadIdx.x; p < 2 * G; p += nblk * kRedBlock) {
+    const long long o = base + p;
+    const cx<T> h = hpsi[o] + g0[o] + g1[o] + g2[o];
+    hpsi[o] = h;
+    const double2 hd = to_d2(h), pd = to_d2(psi[o]);
+    e += pd.x * hd.x + pd.y * hd.y;
+    n2 += hd.x * hd.x + hd.y * hd.y;
+  }
+  block_sum2(e, n2);
+  if (threadIdx.x == 0) {
+    double* dst = part + ((long long)(state0 + blockIdx.y) * nblk + blockIdx.x) * 2;
+    dst[0] = e;
+    dst[1] = n2;
+  }
+}
+
+// Per-state totals of the partial sums, times dV.
+__global__ void k_state_totals(const double* part, int nblk, int I, double dV,
+                               double* eps, double* hn2) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= I) return;
+  double a = 0.0, b = 0.0;
+  for (int k = 0; k < nblk; ++k) {
+    a += part[((long long)s * nblk + k) * 2];
+    b += part[((long long)s * nblk + k) * 2 + 1];
+  }
+  if (eps) eps[s] = dV * a;
+  if (hn2) hn2[s] = dV * b;
+}
+
+template <typename T>
+static sky_status apply_h_t(Ctx* c, const double* U, const double* B, const double* W,
+                            const cx<T>* psi, cx<T>* hpsi, int I, double* eps, double* hn2) {
+  const long long G = c->G, V = 2 * G;
+  cx<T>* scr = static_cast<cx<T>*>(c->d_gscr);
+  const long long cstride = (long long)c->chunk * V;
+  cx<T>* g[3] = {scr, scr + cstride, scr + 2 * cstride};
+  for (int s0 = 0; s0 < I; s0 += c->chunk) {
+    const int ns = (I - s0) < c->chunk ? (I - s0) : c->chunk;
+    const cx<T>* ps = psi + (long long)s0 * V;
+    cx<T>* hs = hpsi + (long long)s0 * V;
+    cudaError_t e = gradient_passes<T>(c, ps, g, 2LL * ns);
+    if (e != cudaSuccess) return cuda_check(c, e, "apply_h gradient");
+    dim3 grid(div_up(G, 256), ns);
+    k_h_local<T><<<grid, 256, 0, c->stream>>>(ps, g[0], g[1], g[2], hs, U, B, W, (int)G);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "apply_h local");
+    // pass 3: F_j <- d_j F_j in place, one axis per array
+    const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
+    for (int ax = 0; ax < 3; ++ax) {
+      OpDeriv<T> op{g[ax], g[ax], kt_of<T>(c, ax), (T)(1.0 / c->n[ax]), G};
+      auto go = [&](auto NC) -> cudaError_t {
+        constexpr int N = decltype(NC)::value;
+        if (ax == 0) return launch_line<T, N, 0>(op, nx, ny, nz, 2LL * ns, c->stream);
+        if (ax == 1) return launch_line<T, N, 1>(op, nx, ny, nz, 2LL * ns, c->stream);
+        return launch_line<T, N, 2>(op, nx, ny, nz, 2LL * ns, c->stream);
+      };
+      e = dispatch_n<std::is_same<T, float>::value>(c->n[ax], go);
+      if (e != cudaSuccess) return cuda_check(c, e, "apply_h divergence");
+    }
+    dim3 g4(c->red_nblk, ns);
+    k_h_sum<T><<<g4, kRedBlock, 0, c->stream>>>(ps, g[0], g[1], g[2], hs, (int)G, c->d_red,
+                                                c->red_nblk, s0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "apply_h sum");
+  }
+  if (eps || hn2) {
+    k_state_totals<<<div_up(I, 128), 128, 0, c->stream>>>(c->d_red, c->red_nblk, I, c->dV,
+                                                          eps, hn2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(c, e, "apply_h totals");
+  }
+  return SKY_OK;
+}
+
+sky_status apply_h_impl(Ctx* c, const double* U, const double* B, const double* W,
+                        const void* psi, void* hpsi, int I, double* eps, double* hn2) {
+  if (c->prec == SKY_F64)
+    return apply_h_t<double>(c, U, B, W, (const double2*)psi, (double2*)hpsi, I, eps, hn2);
+  return apply_h_t<float>(c, U, B, W, (const float2*)psi, (float2*)hpsi, I, eps, hn2);
+}
+
+// ------------------------------------------------------------ damped step
+__global__ void k_damp_table(double* P, const double* kx, const double* ky, const double* kz,
+                             int nx, int ny, int nz, double hb2m, double E0) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nx * ny * nz) return;
+  const int x = p % nx, y = (p / nx) % ny, z = p / (nx * ny);
+  const double k2 = kx[x] * kx[x] + ky[y] * ky[y] + kz[z] * kz[z];
+  P[p] = 1.0 / (E0 + hb2m * k2);
+}
+
+template <typename T>
+static sky_status damped_t(Ctx* c, int q, const cx<T>* psi, const cx<T>* hpsi,
+                           const double* eps, cx<T>* phi, int I, double x0, double E0) {
+  const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
+  const long long G = c->G;
+  cudaError_t e;
+  if (!(c->damp_E0[q] == E0)) {
+    k_damp_table<<<div_up(G, 256), 256, 0, c->stream>>>(c->d_damp[q], c->d_kt[0], c->d_kt[1],
+                                                        c->d_kt[2], nx, ny, nz, c->cp.hb2m[q], E0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "damping table");
+    c->damp_E0[q] = E0;
+  }
+  const long long nb = 2LL * I;
+  OpDampZFwd<T> o1{psi, hpsi, eps, phi, G};
+  OpPass<T, false> o2{phi, G};
+  OpDampX<T> o3{phi, c->d_damp[q], (T)(x0 / (double)G), G};
+  OpPass<T, true> o4{phi, G};
+  OpDampZInv<T> o5{psi, phi, G};
+  constexpr bool L = std::is_same<T, float>::value;
+  e = dispatch_n<L>(nz, [&](auto NC) { return launch_line<T, decltype(NC)::value, 2>(o1, nx, ny, nz, nb, c->stream); });
+  if (e == cudaSuccess)
+    e = dispatch_n<L>(ny, [&](auto NC) { return launch_line<T, decltype(NC)::value, 1>(o2, nx, ny, nz, nb, c->stream); });
+  if (e == cudaSuccess)
+    e = dispatch_n<L>(nx, [&](auto NC) { return launch_line<T, decltype(NC)::value, 0>(o3, nx, ny, nz, nb, c->stream); });
+  if (e == cudaSuccess)
+    e = dispatch_n<L>(ny, [&](auto NC) { return launch_line<T, decltype(NC)::value, 1>(o4, nx, ny, nz, nb, c->stream); });
+  if (e == cudaSuccess)
+    e = dispatch_n<L>(nz, [&](auto NC) { return launch_line<T, decltype(NC)::value, 2>(o5, nx, ny, nz, nb, c->stream); });
+  return e == cudaSuccess ? SKY_OK : cuda_check(c, e, "damped step");
+}
+
+sky_status damped_step_impl(Ctx* c, int q, const void* psi, const void* hpsi,
+                            const double* eps, void* phi, int I, double x0, double E0) {
+  if (c->prec == SKY_F64)
+    return damped_t<double>(c, q, (const double2*)psi, (const double2*)hpsi, eps,
+                            (double2*)phi, I, x0, E0);
+  return damped_t<float>(c, q, (const float2*)psi, (const float2*)hpsi, eps, (float2*)phi, I,
+                         x0, E0);
+}
+
+// ------------------------------------------------------------ densities
+// Partial rho, tau, J over the states of one split:
+//   M_kj = psi^+ sigma_k G_j, J_x = Im M_zy - Im M_yz, J_y = Im M_xz - Im M_zx,
+//   J_z = Im M_yx - Im M_xy  (J_i = sum_jk eps_ijk Re[-i M_kj] = sum eps_ijk Im M_kj).
+template <typename T>
+__global__ void __launch_bounds__(128) k_dens_accum(const cx<T>* __restrict__ psi,
+                                                    const cx<T>* __restrict__ g0,
+                                                    const cx<T>* __restrict__ g1,
+                                                    const cx<T>* __restrict__ g2, int G, int ns,
+                                                    int per_split, double* part) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= G) return;
+  const int s_beg = blockIdx.y * per_split;
+  const int s_end = (s_beg + per_split) < ns ? (s_beg + per_split) : ns;
+  double rho = 0, tau = 0, jx = 0, jy = 0, jz = 0;
+  const cx<T>* gs[3] = {g0, g1, g2};
+  for (int s = s_beg; s < s_end; ++s) {
+    const long long o0 = (long long)s * 2 * G + p, o1 = o0 + G;
+    const double2 a0 = to_d2(psi[o0]), a1 = to_d2(psi[o1]);
+    rho += a0.x * a0.x + a0.y * a0.y + a1.x * a1.x + a1.y * a1.y;
+    double imx[3], imy[3], imz[3];   // Im M_{x,j}, Im M_{y,j}, Im M_{z,j}
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double2 d0 = to_d2(gs[j][o0]), d1 = to_d2(gs[j][o1]);
+      tau += d0.x * d0.x + d0.y * d0.y + d1.x * d1.x + d1.y * d1.y;
+      const double2 c01 = cmulc(a0, d1), c10 = cmulc(a1, d0);   // conj(a0) d1, conj(a1) d0
+      const double2 c00 = cmulc(a0, d0), c11 = cmulc(a1, d1);
+      imx[j] = c01.y + c10.y;
+      imy[j] = c10.x - c01.x;
+      imz[j] = c00.y - c11.y;
+    }
+    jx += imz[1] - imy[2];
+    jy += imx[2] - imz[0];
+    jz += imy[0] - imx[1];
+  }
+  double* dst = part + (long long)blockIdx.y * 5 * G;
+  dst[p] = rho;
+  dst[G + p] = tau;
+  dst[2 * G + p] = jx;
+  dst[3 * G + p] = jy;
+  dst[4 * G + p] = jz;
+}
+
+// Sum the splits in order; accumulate onto the outputs after the first chunk.
+__global__ void k_dens_reduce(const double* part, int nsplit, int G, int accumulate,
+                              double* rho, double* tau, double* J) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= G) return;
+  double v[5] = {0, 0, 0, 0, 0};
+  for (int s = 0; s < nsplit; ++s)
+#pragma unroll
+    for (int f = 0; f < 5; ++f) v[f] += part[((long long)s * 5 + f) * G + p];
+  if (accumulate) {
+    rho[p] += v[0]; tau[p] += v[1];
+    J[p] += v[2]; J[G + p] += v[3]; J[2 * G + p] += v[4];
+  } else {
+    rho[p] = v[0]; tau[p] = v[1];
+    J[p] = v[2]; J[G + p] = v[3]; J[2 * G + p] = v[4];
+  }
+}
+
+sky_status field_divergence(Ctx* c, const double* J, double* divJ);  // fields.cu
+
+template <typename T>
+static sky_status densities_t(Ctx* c, const cx<T>* psi, int I, double* rho, double* tau,
+                              double* J, double* divJ) {
+  const long long G = c->G, V = 2 * G;
+  cx<T>* scr = static_cast<cx<T>*>(c->d_gscr);
+  const long long cstride = (long long)c->chunk * V;
+  cx<T>* g[3] = {scr, scr + cstride, scr + 2 * cstride};
+  double* Jout = J ? J : c->d_ftmp + 13 * G;   // [3][G] temporaries when J not wanted
+  if (I == 0) {
+    cudaMemsetAsync(rho, 0, G * sizeof(double), c->stream);
+    cudaMemsetAsync(tau, 0, G * sizeof(double), c->stream);
+    cudaMemsetAsync(Jout, 0, 3 * G * sizeof(double), c->stream);
+  }
+  for (int s0 = 0; s0 < I; s0 += c->chunk) {
+    const int ns = (I - s0) < c->chunk ? (I - s0) : c->chunk;
+    const cx<T>* ps = psi + (long long)s0 * V;
+    cudaError_t e = gradient_passes<T>(c, ps, g, 2LL * ns);
+    if (e != cudaSuccess) return cuda_check(c, e, "densities gradient");
+    const int per = (ns + kDensSplits - 1) / kDensSplits;
+    const int nsplit = (ns + per - 1) / per;
+    dim3 grid(div_up(G, 128), nsplit);
+    k_dens_accum<T><<<grid, 128, 0, c->stream>>>(ps, g[0], g[1], g[2], (int)G, ns, per, c->d_dpart);
+    k_dens_reduce<<<div_up(G, 256), 256, 0, c->stream>>>(c->d_dpart, nsplit, (int)G, s0 > 0, rho,
+                                                         tau, Jout);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "densities accumulate");
+  }
+  if (divJ) return field_divergence(c, Jout, divJ);
+  return SKY_OK;
+}
+
+sky_status densities_impl(Ctx* c, const void* psi, int I, double* rho, double* tau, double* J,
+                          double* divJ) {
+  if (c->prec == SKY_F64)
+    return densities_t<double>(c, (const double2*)psi, I, rho, tau, J, divJ);
+  return densities_t<float>(c, (const float2*)psi, I, rho, tau, J, divJ);
+}
+
+}  // namespace sky

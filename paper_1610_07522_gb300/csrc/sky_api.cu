@@ -1,0 +1,332 @@
+// C ABI of libsky: context creation (wavenumber tables, scratch sized for
+// max_states), argument checks and dispatch to the kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "sky_internal.cuh"
+
+namespace sky {
+
+sky_status set_err(Ctx* c, sky_status s, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return s;
+}
+
+sky_status cuda_check(Ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return SKY_OK;
+  return set_err(c, SKY_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+sky_status build_coulomb_table(Ctx* c);   // fields.cu
+
+static bool size_ok(int n, sky_prec p) {
+  switch (n) {
+    case 8: case 12: case 16: case 20: case 24: case 32: return true;
+    case 48: case 64: return p == SKY_F32;
+    default: return false;
+  }
+}
+
+static Couplings couplings(const sky_skyrme& p) {
+  Couplings c;
+  c.rho[0] = 3.0 * p.t0 / 8.0;
+  c.rho[1] = -p.t0 * (0.5 + p.x0) / 4.0;
+  c.rhoa[0] = p.t3 / 16.0;
+  c.rhoa[1] = -p.t3 * (0.5 + p.x3) / 24.0;
+  c.tau[0] = 3.0 * p.t1 / 16.0 + p.t2 * (1.25 + p.x2) / 4.0;
+  c.tau[1] = -p.t1 * (0.5 + p.x1) / 8.0 + p.t2 * (0.5 + p.x2) / 8.0;
+  c.drho[0] = -9.0 * p.t1 / 64.0 + p.t2 * (1.25 + p.x2) / 16.0;
+  c.drho[1] = 3.0 * p.t1 * (0.5 + p.x1) / 32.0 + p.t2 * (0.5 + p.x2) / 32.0;
+  c.nJ[0] = -0.75 * p.W0;
+  c.nJ[1] = -0.25 * p.W0;
+  c.alpha = p.alpha;
+  c.hb2m[0] = p.hb2m_n;
+  c.hb2m[1] = p.hb2m_p;
+  c.e2 = p.e2;
+  c.coulomb = p.coulomb;
+  return c;
+}
+
+template <typename T>
+static sky_status dalloc(Ctx* c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return set_err(c, SKY_ENOMEM, "cudaMalloc of %zu bytes failed", count * sizeof(T));
+  }
+  return SKY_OK;
+}
+
+static void free_all(Ctx* c) {
+  void* ptrs[] = {c->d_status, c->d_kt[0], c->d_kt[1], c->d_kt[2], c->d_ktf[0], c->d_ktf[1],
+                  c->d_ktf[2], c->d_kp[0], c->d_kp[1], c->d_kp[2], c->d_damp[0], c->d_damp[1],
+                  c->d_coul, c->d_gscr, c->d_red, c->d_dpart, c->d_ftmp, c->d_fcx, c->d_gpart,
+                  c->d_eigA[0], c->d_eigA[1], c->d_eigV, c->d_eigw, c->d_eigpart, c->d_bar,
+                  c->d_eigres, c->d_small[0], c->d_small[1], c->d_small[2]};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+static size_t scratch_budget() {
+  const char* s = getenv("SKY_SCRATCH_MB");
+  if (s && atol(s) > 0) return (size_t)atol(s) << 20;
+  return (size_t)2048 << 20;
+}
+
+}  // namespace sky
+
+using namespace sky;
+
+extern "C" {
+
+int sky_supported_size(int n, sky_prec prec) { return size_ok(n, prec) ? 1 : 0; }
+
+sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const sky_skyrme* params,
+                    const double twist[3], sky_prec prec, int max_states, void* stream) {
+  if (!out) return SKY_EINVAL;
+  *out = nullptr;
+  if (!grid || !dx || !params || max_states < 0) return SKY_EINVAL;
+  if (prec != SKY_F64 && prec != SKY_F32) return SKY_EUNSUPPORTED;
+  for (int j = 0; j < 3; ++j) {
+    if (!size_ok(grid[j], prec)) return SKY_EUNSUPPORTED;
+    if (!(dx[j] > 0.0)) return SKY_EINVAL;
+  }
+  sky_ctx* c = new (std::nothrow) sky_ctx();
+  if (!c) return SKY_ENOMEM;
+  std::memset(static_cast<Ctx*>(c), 0, sizeof(Ctx));
+  c->stream = (cudaStream_t)stream;
+  c->prec = prec;
+  c->max_states = max_states;
+  c->csize = prec == SKY_F64 ? 16 : 8;
+  c->G = 1;
+  for (int j = 0; j < 3; ++j) {
+    c->n[j] = grid[j];
+    c->dx[j] = dx[j];
+    c->L[j] = grid[j] * dx[j];
+    c->theta[j] = twist ? twist[j] : 0.0;
+    c->G *= grid[j];
+  }
+  c->dV = dx[0] * dx[1] * dx[2];
+  c->cp = couplings(*params);
+  c->damp_E0[0] = c->damp_E0[1] = NAN;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return SKY_ECUDA;
+  }
+  const long long G = c->G, V = 2 * G;
+  const int Imax = max_states > 0 ? max_states : 1;
+  const int m = Imax + (Imax & 1);
+  size_t per_state = (size_t)3 * V * c->csize;
+  size_t chunk = scratch_budget() / per_state;
+  if (chunk < 1) chunk = 1;
+  if (chunk > (size_t)Imax) chunk = Imax;
+  c->chunk = (int)chunk;
+  c->red_nblk = (int)((2 * G + 4095) / 4096);
+  if (c->red_nblk < 1) c->red_nblk = 1;
+  if (c->red_nblk > 64) c->red_nblk = 64;
+  size_t gpart = 0;
+  for (int I = 1; I <= Imax; ++I) {
+    const size_t need = overlap_partial_elems(I, V, c->num_sms);
+    if (need > gpart) gpart = need;
+  }
+  c->gpart_elems = gpart;
+
+  sky_status s = SKY_OK;
+#define ALLOC(ptr, n) if (s == SKY_OK) s = dalloc(c, &(ptr), (size_t)(n))
+  ALLOC(c->d_status, 1);
+  for (int j = 0; j < 3; ++j) {
+    ALLOC(c->d_kt[j], grid[j]);
+    ALLOC(c->d_ktf[j], grid[j]);
+    ALLOC(c->d_kp[j], grid[j]);
+  }
+  ALLOC(c->d_damp[0], G);
+  ALLOC(c->d_damp[1], G);
+  ALLOC(c->d_coul, G);
+  if (s == SKY_OK) {
+    void* p = nullptr;
+    e = cudaMalloc(&p, chunk * per_state);
+    if (e != cudaSuccess) { cudaGetLastError(); s = set_err(c, SKY_ENOMEM, "scratch allocation failed"); }
+    c->d_gscr = p;
+  }
+  ALLOC(c->d_red, (size_t)Imax * c->red_nblk * 2);
+  ALLOC(c->d_dpart, (size_t)kDensSplits * 5 * G);
+  ALLOC(c->d_ftmp, (size_t)16 * G);
+  ALLOC(c->d_fcx, G);
+  ALLOC(c->d_gpart, gpart);
+  ALLOC(c->d_eigA[0], (size_t)m * m);
+  ALLOC(c->d_eigA[1], (size_t)m * m);
+  ALLOC(c->d_eigV, (size_t)m * m);
+  ALLOC(c->d_eigw, m);
+  ALLOC(c->d_bar, 2);
+  ALLOC(c->d_eigres, 1);
+  for (int k = 0; k < 3; ++k) ALLOC(c->d_small[k], (size_t)Imax * Imax);
+  if (s == SKY_OK) {
+    c->eig_grid = jacobi_max_grid(c);
+    ALLOC(c->d_eigpart, (size_t)2 * c->eig_grid);
+  }
+#undef ALLOC
+  if (s == SKY_OK) {
+    // wavenumbers in FFT order: index a -> m = a (a < (n+1)/2) or a - n
+    for (int j = 0; j < 3 && s == SKY_OK; ++j) {
+      const int n = grid[j];
+      double* kt = new double[n];
+      double* kp = new double[n];
+      float* kf = new float[n];
+      for (int a = 0; a < n; ++a) {
+        const int mm = (a < (n + 1) / 2) ? a : a - n;
+        kp[a] = 2.0 * M_PI * mm / c->L[j];
+        kt[a] = kp[a] + c->theta[j] / c->L[j];
+        kf[a] = (float)kt[a];
+      }
+      e = cudaMemcpy(c->d_kt[j], kt, n * sizeof(double), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(c->d_kp[j], kp, n * sizeof(double), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(c->d_ktf[j], kf, n * sizeof(float), cudaMemcpyHostToDevice);
+      delete[] kt; delete[] kp; delete[] kf;
+      s = cuda_check(c, e, "wavenumber upload");
+    }
+  }
+  if (s == SKY_OK) s = cuda_check(c, cudaMemset(c->d_status, 0, sizeof(int)), "status reset");
+  if (s == SKY_OK) s = cuda_check(c, cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned)), "barrier reset");
+  if (s == SKY_OK) s = upload_twiddles_hamiltonian(c);
+  if (s == SKY_OK) s = upload_twiddles_fields(c);
+  if (s == SKY_OK) s = build_coulomb_table(c);
+  if (s == SKY_OK) s = cuda_check(c, cudaStreamSynchronize(c->stream), "init sync");
+  if (s != SKY_OK) {
+    free_all(c);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return SKY_OK;
+}
+
+sky_status sky_destroy(sky_ctx* c) {
+  if (!c) return SKY_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+  return SKY_OK;
+}
+
+sky_status sky_set_stream(sky_ctx* c, void* stream) {
+  if (!c) return SKY_EINVAL;
+  c->stream = (cudaStream_t)stream;
+  return SKY_OK;
+}
+
+sky_status sky_sync(sky_ctx* c) {
+  if (!c) return SKY_EINVAL;
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "sync");
+  if (st) {
+    cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+    cudaStreamSynchronize(c->stream);
+    const sky_status order[] = {SKY_ETIMEOUT, SKY_ENOTPD, SKY_ENOCONV, SKY_ENAN};
+    for (sky_status k : order)
+      if (st & SKY_STATUS_BIT(k))
+        return set_err(c, k, "device status word 0x%x", st);
+  }
+  return SKY_OK;
+}
+
+const char* sky_last_error(const sky_ctx* c) { return c ? c->err : "null context"; }
+
+#define CHECK_CTX()                                     \
+  if (!c) return SKY_EINVAL;                            \
+  if (I < 0 || I > c->max_states)                       \
+    return set_err(c, SKY_EINVAL, "I=%d outside [0, %d]", I, c->max_states)
+
+sky_status sky_apply_h(sky_ctx* c, const double* U, const double* B, const double* W,
+                       const void* psi, void* hpsi, int I, double* eps, double* hnorm2) {
+  CHECK_CTX();
+  if (I == 0) return SKY_OK;
+  if (!U || !B || !W || !psi || !hpsi) return set_err(c, SKY_EINVAL, "apply_h: null pointer");
+  if (psi == hpsi) return set_err(c, SKY_EINVAL, "apply_h: psi and hpsi must differ");
+  return apply_h_impl(c, U, B, W, psi, hpsi, I, eps, hnorm2);
+}
+
+sky_status sky_damped_step(sky_ctx* c, int q, const void* psi, const void* hpsi, const double* eps,
+                           void* phi, int I, double x0, double E0, const float* w) {
+  CHECK_CTX();
+  if (I == 0) return SKY_OK;
+  if (q != 0 && q != 1) return set_err(c, SKY_EINVAL, "damped_step: q must be 0 or 1");
+  if (!psi || !hpsi || !eps || !phi) return set_err(c, SKY_EINVAL, "damped_step: null pointer");
+  if (w) return set_err(c, SKY_EUNSUPPORTED, "damped_step: per-voxel weight not built");
+  if (phi == psi || phi == hpsi) return set_err(c, SKY_EINVAL, "damped_step: phi must be a separate buffer");
+  return damped_step_impl(c, q, psi, hpsi, eps, phi, I, x0, E0);
+}
+
+sky_status sky_overlap(sky_ctx* c, const void* a, const void* b, int I, double* X) {
+  CHECK_CTX();
+  if (I == 0) return SKY_OK;
+  if (!a || !b || !X) return set_err(c, SKY_EINVAL, "overlap: null pointer");
+  return overlap_impl(c, a, b, I, (double2*)X);
+}
+
+sky_status sky_orthonormalize(sky_ctx* c, const double* S, int I, double* C) {
+  CHECK_CTX();
+  if (I == 0) return SKY_OK;
+  if (!S || !C || S == C) return set_err(c, SKY_EINVAL, "orthonormalize: bad pointers");
+  return lowdin_impl(c, (const double2*)S, I, (double2*)C);
+}
+
+sky_status sky_subspace_diag(sky_ctx* c, const double* H, const double* C, int I, double* M,
+                             double* eps) {
+  CHECK_CTX();
+  if (I == 0) return SKY_OK;
+  if (!H || !C || !M || !eps) return set_err(c, SKY_EINVAL, "subspace_diag: null pointer");
+  return subspace_impl(c, (const double2*)H, (const double2*)C, I, (double2*)M, eps);
+}
+
+sky_status sky_rotate(sky_ctx* c, const void* phi, const double* M, int I, void* psi_out) {
+  CHECK_CTX();
+  if (I == 0) return SKY_OK;
+  if (!phi || !M || !psi_out) return set_err(c, SKY_EINVAL, "rotate: null pointer");
+  if (phi == psi_out) return set_err(c, SKY_EINVAL, "rotate: output must not alias phi");
+  return rotate_impl(c, phi, (const double2*)M, I, psi_out);
+}
+
+sky_status sky_densities(sky_ctx* c, const void* psi, int I, double* rho, double* tau, double* J,
+                         double* divJ) {
+  CHECK_CTX();
+  if ((!psi && I > 0) || !rho || !tau || !divJ) return set_err(c, SKY_EINVAL, "densities: null pointer");
+  return densities_impl(c, psi, I, rho, tau, J, divJ);
+}
+
+sky_status sky_mean_fields(sky_ctx* c, const double* rho, const double* tau, const double* divJ,
+                           double* U, double* B, double* W) {
+  if (!c) return SKY_EINVAL;
+  if (!rho || !tau || !divJ || !U || !B || !W) return set_err(c, SKY_EINVAL, "mean_fields: null pointer");
+  return mean_fields_impl(c, rho, tau, divJ, U, B, W);
+}
+
+sky_status sky_energy(sky_ctx* c, const double* rho, const double* tau, const double* divJ,
+                      double* out) {
+  if (!c) return SKY_EINVAL;
+  if (!rho || !tau || !divJ || !out) return set_err(c, SKY_EINVAL, "energy: null pointer");
+  return energy_impl(c, rho, tau, divJ, out);
+}
+
+sky_status sky_sp_spread(sky_ctx* c, const double* eps, const double* hnorm2, int A, double* out) {
+  if (!c) return SKY_EINVAL;
+  if (A < 0 || (A > 0 && (!eps || !hnorm2)) || !out) return set_err(c, SKY_EINVAL, "sp_spread: bad arguments");
+  return sp_spread_impl(c, eps, hnorm2, A, out);
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+// Internal definitions shared by the libsky translation units: complex
+// helpers, the context structure, status plumbing and launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <type_traits>
+
+#include "sky.h"
+
+namespace sky {
+
+// ----------------------------------------------------------------- complex
+template <typename T> struct CxT;
+template <> struct CxT<double> { using type = double2; };
+template <> struct CxT<float> { using type = float2; };
+template <typename T> using cx = typename CxT<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cx<T> mkc(T a, T b) {
+  cx<T> r; r.x = a; r.y = b; return r;
+}
+#define SKY_CX_OPS(V, S)                                                              \
+  __host__ __device__ __forceinline__ V operator+(V a, V b) { V r; r.x = a.x + b.x; r.y = a.y + b.y; return r; } \
+  __host__ __device__ __forceinline__ V operator-(V a, V b) { V r; r.x = a.x - b.x; r.y = a.y - b.y; return r; } \
+  __host__ __device__ __forceinline__ V operator-(V a) { V r; r.x = -a.x; r.y = -a.y; return r; }              \
+  __host__ __device__ __forceinline__ V operator*(S s, V a) { V r; r.x = s * a.x; r.y = s * a.y; return r; }    \
+  __host__ __device__ __forceinline__ V cmul(V a, V b) { V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r; } \
+  __host__ __device__ __forceinline__ V cmulc(V a, V b) { V r; r.x = a.x * b.x + a.y * b.y; r.y = a.x * b.y - a.y * b.x; return r; } \
+  __host__ __device__ __forceinline__ V conjx(V a) { V r; r.x = a.x; r.y = -a.y; return r; }                   \
+  __host__ __device__ __forceinline__ V mul_i(V a) { V r; r.x = -a.y; r.y = a.x; return r; }                    \
+  __host__ __device__ __forceinline__ V mul_mi(V a) { V r; r.x = a.y; r.y = -a.x; return r; }
+SKY_CX_OPS(double2, double)
+SKY_CX_OPS(float2, float)
+#undef SKY_CX_OPS
+// cmulc(a, b) = conj(a) * b.
+
+__device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+template <typename T> __device__ __forceinline__ cx<T> from_d2(double2 a);
+template <> __device__ __forceinline__ double2 from_d2<double>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 from_d2<float>(double2 a) {
+  return make_float2((float)a.x, (float)a.y);
+}
+
+// ----------------------------------------------------------------- context
+// Isoscalar (index 0) / isovector (index 1) Skyrme couplings, host-computed.
+struct Couplings {
+  double rho[2], rhoa[2], tau[2], drho[2], nJ[2];
+  double alpha, hb2m[2], e2;
+  int coulomb;
+};
+
+struct Ctx;  // defined below; sky_ctx is an alias at the C boundary
+
+constexpr int kDensSplits = 8;     // state splits of the density accumulation
+constexpr int kRedBlock = 256;     // threads of the per-state reduction blocks
+
+struct Ctx {
+  // geometry
+  int n[3];
+  double dx[3], L[3], theta[3];
+  int G;
+  double dV;
+  sky_prec prec;
+  int max_states;
+  int csize;            // bytes per complex spinor entry
+  Couplings cp;
+  cudaStream_t stream;
+  int device, num_sms;
+  // device memory owned by the context
+  int* d_status;                    // device status word (sky_status bits)
+  double* d_kt[3];                  // twisted wavenumbers k + theta/L (FP64)
+  float* d_ktf[3];                  // the same in FP32
+  double* d_kp[3];                  // plain wavenumbers (real fields)
+  double* d_damp[2];                // 1 / (E0 + hb2m_q |k + theta/L|^2), [G]
+  double damp_E0[2];                // E0 the tables were built for (NaN = none)
+  double* d_coul;                   // 4 pi e^2 / |k|^2 (0 at k = 0), [G]
+  void* d_gscr;                     // derivative scratch: 3 * chunk * V complex
+  int chunk;                        // states per apply_h / densities chunk
+  double* d_red;                    // per-state partial sums [max_states][nblk][2]
+  int red_nblk;                     // reduction blocks per state
+  double* d_dpart;                  // density partials [kDensSplits][5][G]
+  double* d_ftmp;                   // field temporaries [16][G]
+  double2* d_fcx;                   // complex field scratch [G]
+  double2* d_gpart;                 // split-K partials of sky_overlap
+  size_t gpart_elems;
+  double2* d_eigA[2];               // Jacobi ping-pong matrices [m*m]
+  double2* d_eigV;                  // Jacobi rotations accumulated [m*m]
+  double* d_eigw;                   // eigenvalues [m]
+  double* d_eigpart;                // per-block partial norms
+  unsigned* d_bar;                  // grid barrier {count, generation}
+  int* d_eigres;                    // which ping-pong buffer holds the result
+  int eig_grid;                     // co-resident blocks of the Jacobi kernel
+  double2* d_small[3];              // I x I temporaries
+  char err[256];
+};
+
+// ----------------------------------------------------------------- status
+#define SKY_STATUS_BIT(s) (1 << (int)(s))
+
+__device__ __forceinline__ void flag_status(int* st, sky_status s) {
+  atomicOr(st, SKY_STATUS_BIT(s));
+}
+
+sky_status set_err(Ctx* c, sky_status s, const char* fmt, ...);
+sky_status cuda_check(Ctx* c, cudaError_t e, const char* what);
+
+inline unsigned div_up(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// Host-side entry points of the other translation units.
+sky_status upload_twiddles_hamiltonian(Ctx* c);
+sky_status upload_twiddles_fields(Ctx* c);
+sky_status apply_h_impl(Ctx* c, const double* U, const double* B, const double* W,
+                        const void* psi, void* hpsi, int I, double* eps, double* hn2);
+sky_status damped_step_impl(Ctx* c, int q, const void* psi, const void* hpsi,
+                            const double* eps, void* phi, int I, double x0, double E0);
+sky_status densities_impl(Ctx* c, const void* psi, int I, double* rho, double* tau,
+                          double* J, double* divJ);
+sky_status mean_fields_impl(Ctx* c, const double* rho, const double* tau,
+                            const double* divJ, double* U, double* B, double* W);
+sky_status energy_impl(Ctx* c, const double* rho, const double* tau, const double* divJ,
+                       double* out);
+sky_status sp_spread_impl(Ctx* c, const double* eps, const double* hn2, int A, double* out);
+sky_status overlap_impl(Ctx* c, const void* a, const void* b, int I, double2* X);
+sky_status rotate_impl(Ctx* c, const void* phi, const double2* M, int I, void* out);
+sky_status zgemm_small(Ctx* c, bool ah, bool bh, const double2* A, const double2* B,
+                       double2* C, int n);
+sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z);
+sky_status lowdin_impl(Ctx* c, const double2* S, int I, double2* C);
+sky_status subspace_impl(Ctx* c, const double2* H, const double2* C, int I, double2* M,
+                         double* eps);
+int jacobi_max_grid(Ctx* c);
+size_t overlap_partial_elems(int I, long long V, int num_sms);
+
+}  // namespace sky
+
+struct sky_ctx : public sky::Ctx {};

@@ -1,0 +1,151 @@
+"""Driver of the damped-gradient iteration (Fig. 1) through the libsky C ABI.
+
+PyTorch provides device memory and the stream; every arithmetic step is a
+libsky call.  One ``step()`` is one full iteration for both species:
+steps 2-3 per species (h psi, damped step, h phi, matrices, Loewdin and
+Rayleigh-Ritz, recombination), then the densities of both species, the new
+mean field and the energy (steps 4-5).
+
+Buffers per species q: ``psi`` (orthonormal states), ``phi`` (damped
+states), ``h`` (h psi, then h phi); matrices S, H, C, M; the mean field
+U, B, W and densities rho, tau, J, divJ of both species.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+class Solver:
+    def __init__(self, workload, prec=B.SKY_F64, device="cuda:0", max_states=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (there is no CPU path)")
+        self.w = workload
+        self.device = torch.device(device)
+        self.prec = prec
+        self.cdtype = torch.complex128 if prec == B.SKY_F64 else torch.complex64
+        nx, ny, nz = workload.grid
+        self.shape = (nz, ny, nx)
+        self.G = nx * ny * nz
+        self.I = (workload.N, workload.Z)
+        self.A = workload.N + workload.Z
+        Imax = max_states or max(self.I)
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.current_stream(self.device)
+            self.ctx = B.sky_init(workload.grid, workload.dx, workload.params, workload.coulomb,
+                                  workload.twist, prec, Imax, self.stream.cuda_stream)
+        dev, G = self.device, self.G
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.psi = [torch.zeros((I, 2) + self.shape, dtype=self.cdtype, device=dev) for I in self.I]
+        self.phi = [torch.zeros_like(p) for p in self.psi]
+        self.h = [torch.zeros_like(p) for p in self.psi]
+        self.U = torch.zeros((2, G), **f64)
+        self.Bf = torch.zeros((2, G), **f64)
+        self.W = torch.zeros((2, 3, G), **f64)
+        self.rho = torch.zeros((2, G), **f64)
+        self.tau = torch.zeros((2, G), **f64)
+        self.J = torch.zeros((2, 3, G), **f64)
+        self.divJ = torch.zeros((2, G), **f64)
+        mat = lambda I: torch.zeros((I, I), dtype=torch.complex128, device=dev)
+        self.S = [mat(I) for I in self.I]
+        self.H = [mat(I) for I in self.I]
+        self.C = [mat(I) for I in self.I]
+        self.M = [mat(I) for I in self.I]
+        self.eps = torch.zeros(self.A, **f64)
+        self.hn2 = torch.zeros(self.A, **f64)
+        self.lam = torch.zeros(self.A, **f64)
+        self.eout = torch.zeros(8, **f64)
+        self.spread = torch.zeros(2, **f64)
+        self.off = (0, workload.N)
+
+    # ------------------------------------------------------------ set-up
+    def _orthonormalize_into_psi(self, q):
+        """psi = Loewdin(phi) (Eqs. Loewedin, orthmatvec), phi holding raw states."""
+        I = self.I[q]
+        B.sky_overlap(self.ctx, self.phi[q], self.phi[q], I, self.S[q])
+        B.sky_orthonormalize(self.ctx, self.S[q], I, self.C[q])
+        B.sky_rotate(self.ctx, self.phi[q], self.C[q], I, self.psi[q])
+
+    def load(self, psi0, rho0=None, tau0=None):
+        """Fig. 1 step 1 from host arrays: orthonormalise the trial states; the
+        mean field from their densities or from given initial densities."""
+        for q in range(2):
+            self.phi[q].copy_(torch.from_numpy(np.ascontiguousarray(psi0[q])).to(self.cdtype))
+            self._orthonormalize_into_psi(q)
+        if rho0 is None:
+            self.densities()
+        else:
+            self.rho.copy_(torch.from_numpy(np.asarray(rho0).reshape(2, -1)))
+            self.tau.copy_(torch.from_numpy(np.asarray(tau0).reshape(2, -1)))
+            self.divJ.zero_()
+        B.sky_mean_fields(self.ctx, self.rho, self.tau, self.divJ, self.U, self.Bf, self.W)
+        B.sky_sync(self.ctx)
+
+    # ------------------------------------------------------------ iteration
+    def densities(self):
+        for q in range(2):
+            B.sky_densities(self.ctx, self.psi[q], self.I[q], self.rho[q], self.tau[q], self.J[q],
+                            self.divJ[q])
+
+    def species_step(self, q):
+        """Steps 2-3 for species q."""
+        I, o = self.I[q], self.off[q]
+        ctx = self.ctx
+        B.sky_apply_h(ctx, self.U[q], self.Bf[q], self.W[q], self.psi[q], self.h[q], I,
+                      self.eps[o:o + I], self.hn2[o:o + I])
+        B.sky_damped_step(ctx, q, self.psi[q], self.h[q], self.eps[o:o + I], self.phi[q], I,
+                          self.w.x0, self.w.E0)
+        B.sky_apply_h(ctx, self.U[q], self.Bf[q], self.W[q], self.phi[q], self.h[q], I)
+        B.sky_overlap(ctx, self.phi[q], self.phi[q], I, self.S[q])
+        B.sky_overlap(ctx, self.phi[q], self.h[q], I, self.H[q])
+        B.sky_orthonormalize(ctx, self.S[q], I, self.C[q])
+        B.sky_subspace_diag(ctx, self.H[q], self.C[q], I, self.M[q], self.lam[o:o + I])
+        B.sky_rotate(ctx, self.phi[q], self.M[q], I, self.psi[q])
+
+    def step(self, frozen=False):
+        """One full iteration (Fig. 1 steps 2-5); enqueued, not synchronised."""
+        for q in range(2):
+            self.species_step(q)
+        B.sky_sp_spread(self.ctx, self.eps, self.hn2, self.A, self.spread)
+        self.densities()
+        if not frozen:
+            B.sky_mean_fields(self.ctx, self.rho, self.tau, self.divJ, self.U, self.Bf, self.W)
+        B.sky_energy(self.ctx, self.rho, self.tau, self.divJ, self.eout)
+
+    def sync(self):
+        B.sky_sync(self.ctx)
+
+    def energy(self):
+        """Host copy of (E, delta_eps) after synchronising."""
+        self.sync()
+        e = self.eout.cpu().numpy()
+        return float(e[0]), float(self.spread[0].item()), e
+
+    def run(self, maxit=None, tol=None, callback=None):
+        """Iterate until |E_n/A - E_{n-1}/A| < tol or maxit; returns history."""
+        maxit = self.w.maxit if maxit is None else maxit
+        tol = self.w.tol if tol is None else tol
+        hist, E_prev = [], None
+        for it in range(maxit):
+            self.step()
+            E, de, _ = self.energy()
+            hist.append({"it": it, "E": E, "delta_eps": de})
+            if callback:
+                callback(it, hist[-1])
+            if E_prev is not None and abs(E - E_prev) / self.A < tol:
+                return hist, True
+            E_prev = E
+        return hist, False
+
+    def close(self):
+        if self.ctx:
+            B.sky_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

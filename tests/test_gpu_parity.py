@@ -1,0 +1,323 @@
+"""Parity of every libsky entry point with the FP64 CPU oracle (GPU).
+
+All inputs come from the seeded generators; both sides receive the same
+arrays.  Tolerances (FP64 form): per-call results element by element within
+1e-12 of the largest magnitude (FFT and GEMM rounding, a few ulp times
+log N growth); single-particle energies within 1e-9 MeV and total energies
+within 1e-10 relative, as stated for the FP64 form.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_1610_07522_gb300 import binding as B
+from paper_1610_07522_gb300 import inputs as IN
+
+pytestmark = pytest.mark.gpu
+
+P = dict(IN.SLY4)
+REL = 1e-12
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def relerr(got, want):
+    return float(np.max(np.abs(got - want)) / max(np.max(np.abs(want)), 1e-300))
+
+
+class Ctx:
+    def __init__(self, grid, dx=(1.0, 1.0, 1.0), twist=(0.0, 0.0, 0.0), coulomb=False,
+                 max_states=64, prec=B.SKY_F64):
+        self.grid = O.Grid(grid, dx, twist)
+        self.ctx = B.sky_init(grid, dx, P, coulomb, twist, prec, max_states,
+                              torch.cuda.current_stream().cuda_stream)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        B.sky_sync(self.ctx)
+        B.sky_destroy(self.ctx)
+
+
+CASES = [
+    ((8, 8, 8), (1.0, 1.0, 1.0), (0.0, 0.0, 0.0)),
+    ((16, 16, 16), (1.0, 1.0, 1.0), (0.0, 0.0, 0.0)),
+    ((24, 24, 24), (1.0, 1.0, 1.0), (0.0, 0.0, 0.0)),
+    ((12, 16, 20), (0.9, 1.1, 1.0), (0.3, -1.2, 2.0)),
+    ((32, 8, 24), (1.0, 1.0, 1.0), (-2.0, 0.5, 0.0)),
+]
+
+
+def _fields(grid, rng):
+    U = IN.random_smooth_field(grid.n, rng, -40.0, 30.0)
+    Bf = IN.random_smooth_field(grid.n, rng, 20.0, 6.0)
+    W = np.stack([IN.random_smooth_field(grid.n, rng, 0.0, 10.0) for _ in range(3)])
+    return U, Bf, W
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_apply_h(case):
+    rng = np.random.default_rng(1)
+    with Ctx(*case) as c:
+        g = c.grid
+        I = 5
+        psi = IN.random_spinors(g.n, I, rng)
+        U, Bf, W = _fields(g, rng)
+        want = O.apply_h(psi, U, Bf, W, g)
+        eps_w, hn2_w = O.sp_energies(psi, want, g)
+        d_psi, d_h = dev(psi), torch.zeros(psi.shape, dtype=torch.complex128, device="cuda:0")
+        eps, hn2 = torch.zeros(I, dtype=torch.float64, device="cuda:0"), torch.zeros(I, dtype=torch.float64, device="cuda:0")
+        B.sky_apply_h(c.ctx, dev(U), dev(Bf), dev(W), d_psi, d_h, I, eps, hn2)
+        B.sky_sync(c.ctx)
+        assert relerr(host(d_h), want) < REL
+        assert relerr(host(eps), eps_w) < REL
+        assert relerr(host(hn2), hn2_w) < REL
+
+
+def test_apply_h_ragged_chunks(monkeypatch):
+    """Scratch limited to 1 MiB: the 16^3 states run in chunks of 2, 2, 2, 1."""
+    monkeypatch.setenv("SKY_SCRATCH_MB", "1")
+    rng = np.random.default_rng(2)
+    with Ctx((16, 16, 16), twist=(0.2, 0.4, -0.6)) as c:
+        g = c.grid
+        I = 7
+        psi = IN.random_spinors(g.n, I, rng)
+        U, Bf, W = _fields(g, rng)
+        want = O.apply_h(psi, U, Bf, W, g)
+        d_h = torch.zeros(psi.shape, dtype=torch.complex128, device="cuda:0")
+        eps = torch.zeros(I, dtype=torch.float64, device="cuda:0")
+        B.sky_apply_h(c.ctx, dev(U), dev(Bf), dev(W), dev(psi), d_h, I, eps, None)
+        assert relerr(host(d_h), want) < REL
+        assert relerr(host(eps), O.sp_energies(psi, want, g)[0]) < REL
+        rho_w, tau_w, J_w, dJ_w = O.densities(psi, g)
+        rho, tau = torch.zeros(g.G, dtype=torch.float64, device="cuda:0"), torch.zeros(g.G, dtype=torch.float64, device="cuda:0")
+        J, dJ = torch.zeros(3 * g.G, dtype=torch.float64, device="cuda:0"), torch.zeros(g.G, dtype=torch.float64, device="cuda:0")
+        B.sky_densities(c.ctx, dev(psi), I, rho, tau, J, dJ)
+        assert relerr(host(rho), rho_w.ravel()) < REL
+        assert relerr(host(tau), tau_w.ravel()) < REL
+        assert relerr(host(J), J_w.ravel()) < REL
+
+
+@pytest.mark.parametrize("case", CASES[1:4])
+def test_damped_step(case):
+    rng = np.random.default_rng(3)
+    with Ctx(*case) as c:
+        g = c.grid
+        I = 3
+        psi = IN.random_spinors(g.n, I, rng)
+        hpsi = IN.random_spinors(g.n, I, rng) * 30.0
+        eps = rng.uniform(-40, 10, I)
+        for q in (0, 1):
+            want = O.damped_step(psi, hpsi, eps, g, P["hb2m_n" if q == 0 else "hb2m_p"], 0.45, 100.0)
+            phi = torch.zeros(psi.shape, dtype=torch.complex128, device="cuda:0")
+            B.sky_damped_step(c.ctx, q, dev(psi), dev(hpsi), dev(eps), phi, I, 0.45, 100.0)
+            assert relerr(host(phi), want) < REL
+        # a second E0 rebuilds the cached preconditioner table
+        want = O.damped_step(psi, hpsi, eps, g, P["hb2m_n"], 0.3, 60.0)
+        phi = torch.zeros(psi.shape, dtype=torch.complex128, device="cuda:0")
+        B.sky_damped_step(c.ctx, 0, dev(psi), dev(hpsi), dev(eps), phi, I, 0.3, 60.0)
+        assert relerr(host(phi), want) < REL
+
+
+@pytest.mark.parametrize("I", [1, 2, 31, 37, 70])
+def test_overlap(I):
+    rng = np.random.default_rng(4 + I)
+    with Ctx((16, 16, 16), max_states=80) as c:
+        g = c.grid
+        a = IN.random_spinors(g.n, I, rng)
+        b = IN.random_spinors(g.n, I, rng)
+        X = torch.zeros((I, I), dtype=torch.complex128, device="cuda:0")
+        B.sky_overlap(c.ctx, dev(a), dev(b), I, X)
+        assert relerr(host(X), O.overlap(a, b, g)) < REL
+        B.sky_overlap(c.ctx, dev(a), dev(a), I, X)
+        assert relerr(host(X), O.overlap(a, a, g)) < REL
+
+
+def _phi_h(g, I, rng):
+    phi = IN.random_superpositions(g.n, g.dx, I, rng) / np.sqrt(g.L[0] * g.L[1] * g.L[2]) * 3
+    U, Bf, W = _fields(g, rng)
+    return phi, O.apply_h(phi, U, Bf, W, g)
+
+
+@pytest.mark.parametrize("I", [1, 2, 5, 16, 33])
+def test_loewdin_and_rayleigh_ritz(I):
+    rng = np.random.default_rng(10 + I)
+    with Ctx((16, 16, 16)) as c:
+        g = c.grid
+        phi, hphi = _phi_h(g, I, rng)
+        S, H = O.overlap(phi, phi, g), O.overlap(phi, hphi, g)
+        C_w = O.loewdin(S)
+        M_w, lam_w = O.rayleigh_ritz(S, H)
+        dS, dH = dev(S), dev(H)
+        C = torch.zeros_like(dS)
+        M = torch.zeros_like(dS)
+        lam = torch.zeros(I, dtype=torch.float64, device="cuda:0")
+        B.sky_orthonormalize(c.ctx, dS, I, C)
+        B.sky_subspace_diag(c.ctx, dH, C, I, M, lam)
+        B.sky_sync(c.ctx)
+        Cg, Mg, lg = host(C), host(M), host(lam)
+        assert relerr(Cg, C_w) < 1e-11
+        assert np.max(np.abs(lg - lam_w)) < 1e-9
+        assert np.max(np.abs(Mg.conj().T @ S @ Mg - np.eye(I))) < 1e-11
+        assert np.max(np.abs(Mg.conj().T @ H @ Mg - np.diag(lam_w))) < 1e-9 * max(1.0, np.max(np.abs(lam_w)))
+        # Ritz vectors agree up to a phase per (non-degenerate) column
+        for j in range(I):
+            k = int(np.argmax(np.abs(M_w[:, j])))
+            ph = Mg[k, j] / M_w[k, j]
+            assert abs(abs(ph) - 1) < 1e-9
+            assert np.max(np.abs(Mg[:, j] - ph * M_w[:, j])) < 1e-8 * np.max(np.abs(M_w[:, j]))
+
+
+def test_rotate():
+    rng = np.random.default_rng(5)
+    for I in (1, 3, 40):
+        with Ctx((16, 16, 16)) as c:
+            phi = IN.random_spinors(c.grid.n, I, rng)
+            M = rng.standard_normal((I, I)) + 1j * rng.standard_normal((I, I))
+            out = torch.zeros(phi.shape, dtype=torch.complex128, device="cuda:0")
+            B.sky_rotate(c.ctx, dev(phi), dev(M), I, out)
+            assert relerr(host(out), O.rotate(phi, M)) < REL
+
+
+@pytest.mark.parametrize("case", CASES[1:])
+def test_densities(case):
+    rng = np.random.default_rng(6)
+    with Ctx(*case) as c:
+        g = c.grid
+        I = 9
+        psi = O.orthonormalize(IN.random_superpositions(g.n, g.dx, I, rng), g)
+        rho_w, tau_w, J_w, dJ_w = O.densities(psi, g)
+        z = lambda n: torch.zeros(n, dtype=torch.float64, device="cuda:0")
+        rho, tau, J, dJ = z(g.G), z(g.G), z(3 * g.G), z(g.G)
+        B.sky_densities(c.ctx, dev(psi), I, rho, tau, J, dJ)
+        assert relerr(host(rho), rho_w.ravel()) < REL
+        assert relerr(host(tau), tau_w.ravel()) < REL
+        assert relerr(host(J), J_w.ravel()) < REL
+        assert relerr(host(dJ), dJ_w.ravel()) < 1e-11
+        B.sky_densities(c.ctx, dev(psi), I, rho, tau, None, dJ)
+        assert relerr(host(dJ), dJ_w.ravel()) < 1e-11
+        B.sky_densities(c.ctx, dev(psi), 0, rho, tau, J, dJ)     # no states: zero fields
+        assert np.all(host(rho) == 0) and np.all(host(dJ) == 0)
+
+
+@pytest.mark.parametrize("coulomb", [False, True])
+@pytest.mark.parametrize("case", [CASES[2], CASES[3]])
+def test_mean_fields_and_energy(case, coulomb):
+    rng = np.random.default_rng(7)
+    with Ctx(*case, coulomb=coulomb) as c:
+        g = c.grid
+        ds = [O.densities(O.orthonormalize(IN.random_superpositions(g.n, g.dx, I, rng), g), g) for I in (6, 4)]
+        rho = np.stack([d[0] for d in ds]); tau = np.stack([d[1] for d in ds]); dJ = np.stack([d[3] for d in ds])
+        U_w, B_w, W_w = O.mean_fields(rho, tau, dJ, P, g, coulomb)
+        E_w = O.energy(rho, tau, dJ, P, g, coulomb)
+        U = torch.zeros((2, g.G), dtype=torch.float64, device="cuda:0")
+        Bf = torch.zeros_like(U)
+        W = torch.zeros((2, 3, g.G), dtype=torch.float64, device="cuda:0")
+        out = torch.zeros(8, dtype=torch.float64, device="cuda:0")
+        B.sky_mean_fields(c.ctx, dev(rho), dev(tau), dev(dJ), U, Bf, W)
+        B.sky_energy(c.ctx, dev(rho), dev(tau), dev(dJ), out)
+        B.sky_sync(c.ctx)
+        assert relerr(host(U), U_w.reshape(2, -1)) < 1e-11
+        assert relerr(host(Bf), B_w.reshape(2, -1)) < REL
+        assert relerr(host(W), W_w.reshape(2, 3, -1)) < 1e-11
+        e = host(out)
+        keys = ["total", "kin", "rho", "tau", "drho", "nJ", "coul", "A"]
+        for i, k in enumerate(keys):
+            assert abs(e[i] - E_w[k]) <= 1e-11 * max(1.0, abs(E_w[k])), (k, e[i], E_w[k])
+
+
+def test_sp_spread():
+    rng = np.random.default_rng(8)
+    eps = rng.uniform(-50, 0, 400)
+    hn2 = eps ** 2 + rng.uniform(0, 3, 400)
+    with Ctx((8, 8, 8)) as c:
+        out = torch.zeros(2, dtype=torch.float64, device="cuda:0")
+        B.sky_sp_spread(c.ctx, dev(eps), dev(hn2), 400, out)
+        got = host(out)
+    assert abs(got[0] - O.convergence_measure([eps], [hn2])) < 1e-12 * got[0]
+    assert abs(got[1] - eps.sum()) < 1e-12 * abs(eps.sum())
+
+
+def test_status_reporting():
+    with Ctx((8, 8, 8), max_states=4) as c:
+        # I beyond max_states is refused before anything is enqueued
+        X = torch.zeros((5, 5), dtype=torch.complex128, device="cuda:0")
+        with pytest.raises(B.SkyError) as ei:
+            B.sky_overlap(c.ctx, X, X, 5, X)
+        assert ei.value.status == B.SKY_EINVAL
+        with pytest.raises(B.SkyError):
+            B.sky_rotate(c.ctx, X, X, 2, X)            # output aliases input
+        # I == 0 is a no-op
+        B.sky_apply_h(c.ctx, X, X, X, X, X.view(-1)[1:], 0)
+        # two identical states: overlap singular -> SKY_ENOTPD from the device
+        S = dev(np.array([[1.0, 1.0], [1.0, 1.0]], dtype=complex))
+        C = torch.zeros_like(S)
+        B.sky_orthonormalize(c.ctx, S, 2, C)
+        with pytest.raises(B.SkyError) as ei:
+            B.sky_sync(c.ctx)
+        assert ei.value.status == B.SKY_ENOTPD
+        B.sky_sync(c.ctx)                              # status word cleared
+
+
+def _gpu_run(w, inp, nit):
+    from paper_1610_07522_gb300.solver import Solver
+    s = Solver(w, prec=B.SKY_F64)
+    s.load(inp["psi0"], inp.get("rho0"), inp.get("tau0"))
+    recs = []
+    for _ in range(nit):
+        s.step()
+        E, de, parts = s.energy()
+        lam = host(s.lam)
+        recs.append({"E": E, "delta_eps": de, "lam": [np.sort(lam[:w.N]), np.sort(lam[w.N:])],
+                     "rho": host(s.rho).copy()})
+    s.close()
+    return recs
+
+
+def _oracle_run(w, inp, nit):
+    g = O.Grid(w.grid, w.dx, w.twist)
+    st = O.initial_state(inp["psi0"], g, w.params, w.coulomb, inp.get("rho0"), inp.get("tau0"))
+    return [O.iterate(st, g, w.params, w.coulomb, w.x0, w.E0) for _ in range(nit)]
+
+
+def _compare_runs(gpu, ora, e_rel=1e-10, lam_abs=1e-9, rho_rel=1e-10):
+    for k, (a, b) in enumerate(zip(gpu, ora)):
+        assert abs(a["E"] - b["E"]) <= e_rel * abs(b["E"]), (k, a["E"], b["E"])
+        assert abs(a["delta_eps"] - b["delta_eps"]) <= 1e-8 * max(1.0, b["delta_eps"]), k
+        for q in range(2):
+            assert np.max(np.abs(a["lam"][q] - np.sort(b["lam"][q]))) < lam_abs, k
+        assert relerr(a["rho"], b["rho"].reshape(2, -1)) < rho_rel, k
+
+
+def test_iterations_16cubed_16n16p():
+    """The 16^3, 16 n + 16 p workload: 12 full iterations against the oracle."""
+    w = IN.WORKLOADS["sly4_16cubed_16n16p_fp64"]
+    inp = IN.make_inputs(w)
+    _compare_runs(_gpu_run(w, inp, 12), _oracle_run(w, inp, 12))
+
+
+def test_iterations_twisted_coulomb_small():
+    w = IN.Workload(name="t", grid=(12, 16, 8), dx=(1.0, 0.9, 1.2), N=9, Z=7, coulomb=True,
+                    twist=(1.0, -0.5, 2.2), init="blobs", seed=33)
+    inp = IN.make_inputs(w)
+    _compare_runs(_gpu_run(w, inp, 6), _oracle_run(w, inp, 6))
+
+
+def test_iterations_24cubed_280n120p_coulomb():
+    """The full-size 24^3, 280 n + 120 p Coulomb workload: 2 iterations (the
+    oracle takes ~30 s per iteration)."""
+    w = IN.WORKLOADS["sly4_24cubed_280n120p_coulomb_fp64"]
+    inp = IN.make_inputs(w)
+    _compare_runs(_gpu_run(w, inp, 2), _oracle_run(w, inp, 2))
