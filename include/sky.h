@@ -93,6 +93,10 @@ const char* sky_last_error(const sky_ctx* ctx);
 /* 1 if an axis of n points is built for precision prec, else 0. */
 int sky_supported_size(int n, sky_prec prec);
 
+/* Number of CUDA kernels this process has enqueued through libsky so far
+ * (all contexts); for launch accounting by callers. */
+unsigned long long sky_kernel_launches(void);
+
 /* ---- Step 2: single-particle Hamiltonian (Sec. 2.1-2.2, Eq. Schroedinger) --
  * hpsi = h psi for I states, h = U - sum_j d_j B d_j
  *        - (i/2) sum_ijk eps_ijk [W_i sigma_k d_j + d_j W_i sigma_k],

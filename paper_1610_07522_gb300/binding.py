@@ -44,6 +44,7 @@ _SIGNATURES = {
     "sky_sync": (_I, [_P]),
     "sky_last_error": (ctypes.c_char_p, [_P]),
     "sky_supported_size": (_I, [_I, _I]),
+    "sky_kernel_launches": (ctypes.c_ulonglong, []),
     "sky_apply_h": (_I, [_P, _P, _P, _P, _P, _P, _I, _P, _P]),
     "sky_damped_step": (_I, [_P, _I, _P, _P, _P, _P, _I, _D, _D, _P]),
     "sky_overlap": (_I, [_P, _P, _P, _I, _P]),
@@ -128,6 +129,10 @@ def sky_sync(ctx):
 
 def sky_supported_size(n, prec):
     return bool(lib().sky_supported_size(int(n), int(prec)))
+
+
+def sky_kernel_launches():
+    return int(lib().sky_kernel_launches())
 
 
 def sky_apply_h(ctx, U, B, W, psi, hpsi, I, eps=None, hnorm2=None):

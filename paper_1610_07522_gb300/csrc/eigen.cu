@@ -270,7 +270,7 @@ sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z) {
   const int m = I + (I & 1);
   k_jacobi_init<<<div_up((long long)m * m, 256), 256, 0, c->stream>>>(A, I, m, c->d_eigA[0],
                                                                       c->d_eigV, c->d_bar,
-                                                                      c->d_eigres);
+                                                                      c->d_eigres); note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(c, e, "jacobi init");
   if (m >= 2) {
@@ -285,12 +285,13 @@ sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z) {
     a.max_sweeps = 60;
     a.part = c->d_eigpart; a.bar = c->d_bar; a.status = c->d_status; a.result = c->d_eigres;
     void* args[] = {&a};
+    note_launch();
     e = cudaLaunchCooperativeKernel((const void*)k_jacobi, dim3(grid), dim3(kJacThreads), args, 0,
                                     c->stream);
     if (e != cudaSuccess) return cuda_check(c, e, "jacobi");
   }
   k_jacobi_finish<<<div_up(I, 128), 128, 0, c->stream>>>(c->d_eigA[0], c->d_eigA[1], c->d_eigV,
-                                                        c->d_eigres, I, m, w, Z);
+                                                        c->d_eigres, I, m, w, Z); note_launch();
   return cuda_check(c, cudaGetLastError(), "jacobi finish");
 }
 
@@ -326,7 +327,7 @@ sky_status lowdin_impl(Ctx* c, const double2* S, int I, double2* C) {
   sky_status st = eigh_impl(c, S, I, c->d_eigw, X);
   if (st != SKY_OK) return st;
   k_inv_sqrt_cols<<<div_up((long long)I * I, 256), 256, 0, c->stream>>>(X, c->d_eigw, I, Y,
-                                                                       c->d_status);
+                                                                       c->d_status); note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(c, e, "loewdin scale");
   return zgemm_small(c, false, true, Y, X, C, I);   // C = Y X^H
@@ -341,7 +342,7 @@ sky_status subspace_impl(Ctx* c, const double2* H, const double2* C, int I, doub
   sky_status st = zgemm_small(c, true, false, C, H, T1, I);   // C^H H
   if (st == SKY_OK) st = zgemm_small(c, false, false, T1, C, Hp, I);   // (C^H H) C
   if (st != SKY_OK) return st;
-  k_hermitize<<<div_up((long long)I * I, 256), 256, 0, c->stream>>>(Hp, I);
+  k_hermitize<<<div_up((long long)I * I, 256), 256, 0, c->stream>>>(Hp, I); note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(c, e, "hermitize");
   st = eigh_impl(c, Hp, I, eps, Z);

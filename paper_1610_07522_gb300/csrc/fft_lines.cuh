@@ -261,9 +261,9 @@ inline cudaError_t launch_line(const Op& op, int nx, int ny, int nz, long long n
                                            (int)smem);
       if (e != cudaSuccess) return e;
     }
-    k_line_x<T, N, Op><<<div_up(g.nlines, kLinesX), kLinesX, smem, s>>>(op, g);
+    k_line_x<T, N, Op><<<div_up(g.nlines, kLinesX), kLinesX, smem, s>>>(op, g); note_launch();
   } else {
-    k_line_yz<T, N, AXIS, Op><<<div_up(g.nlines, kLineThreads), kLineThreads, 0, s>>>(op, g);
+    k_line_yz<T, N, AXIS, Op><<<div_up(g.nlines, kLineThreads), kLineThreads, 0, s>>>(op, g); note_launch();
   }
   return cudaGetLastError();
 }

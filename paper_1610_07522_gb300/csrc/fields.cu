@@ -118,7 +118,7 @@ __global__ void k_coul_table(double* Pc, const double* kx, const double* ky, con
 sky_status build_coulomb_table(Ctx* c) {
   k_coul_table<<<div_up(c->G, 256), 256, 0, c->stream>>>(c->d_coul, c->d_kp[0], c->d_kp[1],
                                                          c->d_kp[2], c->n[0], c->n[1], c->n[2],
-                                                         c->cp.e2);
+                                                         c->cp.e2); note_launch();
   return cuda_check(c, cudaGetLastError(), "coulomb table");
 }
 
@@ -127,7 +127,7 @@ static sky_status field_prep(Ctx* c, const double* rho, bool need_grad) {
   const long long G = c->G;
   double* f = c->d_ftmp;
   cudaError_t e;
-  k_isospin<<<div_up(G, 256), 256, 0, c->stream>>>(rho, f, (int)G);
+  k_isospin<<<div_up(G, 256), 256, 0, c->stream>>>(rho, f, (int)G); note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "isospin");
   if ((e = real_op_sum(c, f, f + 2 * G, 2, 1)) != cudaSuccess) return cuda_check(c, e, "laplacian");
   if (need_grad) {
@@ -194,7 +194,7 @@ sky_status mean_fields_impl(Ctx* c, const double* rho, const double* tau, const 
   sky_status s = field_prep(c, rho, true);
   if (s != SKY_OK) return s;
   k_mean_fields<<<div_up(c->G, 256), 256, 0, c->stream>>>(c->cp, tau, divJ, c->d_ftmp, c->G, U,
-                                                          B, W);
+                                                          B, W); note_launch();
   return cuda_check(c, cudaGetLastError(), "mean fields");
 }
 
@@ -263,8 +263,8 @@ sky_status energy_impl(Ctx* c, const double* rho, const double* tau, const doubl
   if (s != SKY_OK) return s;
   const int nblk = 64;
   double* part = c->d_ftmp + 11 * (long long)c->G;
-  k_energy_parts<<<nblk, kEnBlock, 0, c->stream>>>(c->cp, rho, tau, divJ, c->d_ftmp, c->G, part);
-  k_energy_final<<<1, 32, 0, c->stream>>>(part, nblk, c->dV, out, c->d_status);
+  k_energy_parts<<<nblk, kEnBlock, 0, c->stream>>>(c->cp, rho, tau, divJ, c->d_ftmp, c->G, part); note_launch();
+  k_energy_final<<<1, 32, 0, c->stream>>>(part, nblk, c->dV, out, c->d_status); note_launch();
   return cuda_check(c, cudaGetLastError(), "energy");
 }
 
@@ -292,7 +292,7 @@ __global__ void k_sp_spread(const double* eps, const double* hn2, int A, double*
 }
 
 sky_status sp_spread_impl(Ctx* c, const double* eps, const double* hn2, int A, double* out) {
-  k_sp_spread<<<1, 1024, 0, c->stream>>>(eps, hn2, A, out);
+  k_sp_spread<<<1, 1024, 0, c->stream>>>(eps, hn2, A, out); note_launch();
   return cuda_check(c, cudaGetLastError(), "sp spread");
 }
 

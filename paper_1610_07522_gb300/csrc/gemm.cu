@@ -115,10 +115,11 @@ sky_status overlap_impl(Ctx* c, const void* a, const void* b, int I, double2* X)
   else
     k_overlap<float2><<<grid, 256, 0, c->stream>>>((const float2*)a, (const float2*)b, I, V,
                                                    kchunk, c->d_gpart);
+  note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(c, e, "overlap");
   k_overlap_reduce<<<div_up((long long)I * I, 256), 256, 0, c->stream>>>(c->d_gpart, nsplit_eff, I,
-                                                                       c->dV, X);
+                                                                       c->dV, X); note_launch();
   return cuda_check(c, cudaGetLastError(), "overlap reduce");
 }
 
@@ -183,6 +184,7 @@ sky_status rotate_impl(Ctx* c, const void* phi, const double2* M, int I, void* o
     k_rotate<double2><<<grid, 256, 0, c->stream>>>((const double2*)phi, M, I, V, (double2*)out);
   else
     k_rotate<float2><<<grid, 256, 0, c->stream>>>((const float2*)phi, M, I, V, (float2*)out);
+  note_launch();
   return cuda_check(c, cudaGetLastError(), "rotate");
 }
 
@@ -241,6 +243,7 @@ sky_status zgemm_small(Ctx* c, bool ah, bool bh, const double2* A, const double2
   else if (ah && !bh) k_zgemm<true, false><<<grid, 256, 0, c->stream>>>(A, B, C, n);
   else if (!ah && bh) k_zgemm<false, true><<<grid, 256, 0, c->stream>>>(A, B, C, n);
   else k_zgemm<true, true><<<grid, 256, 0, c->stream>>>(A, B, C, n);
+  note_launch();
   return cuda_check(c, cudaGetLastError(), "zgemm");
 }
 

@@ -222,7 +222,7 @@ static sky_status apply_h_t(Ctx* c, const double* U, const double* B, const doub
     cudaError_t e = gradient_passes<T>(c, ps, g, 2LL * ns);
     if (e != cudaSuccess) return cuda_check(c, e, "apply_h gradient");
     dim3 grid(div_up(G, 256), ns);
-    k_h_local<T><<<grid, 256, 0, c->stream>>>(ps, g[0], g[1], g[2], hs, U, B, W, (int)G);
+    k_h_local<T><<<grid, 256, 0, c->stream>>>(ps, g[0], g[1], g[2], hs, U, B, W, (int)G); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "apply_h local");
     // pass 3: F_j <- d_j F_j in place, one axis per array
     const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
@@ -239,12 +239,12 @@ static sky_status apply_h_t(Ctx* c, const double* U, const double* B, const doub
     }
     dim3 g4(c->red_nblk, ns);
     k_h_sum<T><<<g4, kRedBlock, 0, c->stream>>>(ps, g[0], g[1], g[2], hs, (int)G, c->d_red,
-                                                c->red_nblk, s0);
+                                                c->red_nblk, s0); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "apply_h sum");
   }
   if (eps || hn2) {
     k_state_totals<<<div_up(I, 128), 128, 0, c->stream>>>(c->d_red, c->red_nblk, I, c->dV,
-                                                          eps, hn2);
+                                                          eps, hn2); note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(c, e, "apply_h totals");
   }
@@ -276,7 +276,7 @@ static sky_status damped_t(Ctx* c, int q, const cx<T>* psi, const cx<T>* hpsi,
   cudaError_t e;
   if (!(c->damp_E0[q] == E0)) {
     k_damp_table<<<div_up(G, 256), 256, 0, c->stream>>>(c->d_damp[q], c->d_kt[0], c->d_kt[1],
-                                                        c->d_kt[2], nx, ny, nz, c->cp.hb2m[q], E0);
+                                                        c->d_kt[2], nx, ny, nz, c->cp.hb2m[q], E0); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "damping table");
     c->damp_E0[q] = E0;
   }
@@ -392,9 +392,9 @@ static sky_status densities_t(Ctx* c, const cx<T>* psi, int I, double* rho, doub
     const int per = (ns + kDensSplits - 1) / kDensSplits;
     const int nsplit = (ns + per - 1) / per;
     dim3 grid(div_up(G, 128), nsplit);
-    k_dens_accum<T><<<grid, 128, 0, c->stream>>>(ps, g[0], g[1], g[2], (int)G, ns, per, c->d_dpart);
+    k_dens_accum<T><<<grid, 128, 0, c->stream>>>(ps, g[0], g[1], g[2], (int)G, ns, per, c->d_dpart); note_launch();
     k_dens_reduce<<<div_up(G, 256), 256, 0, c->stream>>>(c->d_dpart, nsplit, (int)G, s0 > 0, rho,
-                                                         tau, Jout);
+                                                         tau, Jout); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "densities accumulate");
   }
   if (divJ) return field_divergence(c, Jout, divJ);

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "sky_internal.cuh"
@@ -84,6 +85,9 @@ static size_t scratch_budget() {
   return (size_t)2048 << 20;
 }
 
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 }  // namespace sky
 
 using namespace sky;
@@ -91,6 +95,8 @@ using namespace sky;
 extern "C" {
 
 int sky_supported_size(int n, sky_prec prec) { return size_ok(n, prec) ? 1 : 0; }
+
+unsigned long long sky_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const sky_skyrme* params,
                     const double twist[3], sky_prec prec, int max_states, void* stream) {

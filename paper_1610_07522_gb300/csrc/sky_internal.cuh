@@ -106,6 +106,9 @@ __device__ __forceinline__ void flag_status(int* st, sky_status s) {
 sky_status set_err(Ctx* c, sky_status s, const char* fmt, ...);
 sky_status cuda_check(Ctx* c, cudaError_t e, const char* what);
 
+// Process-wide count of kernels enqueued by the library.
+void note_launch(unsigned n = 1);
+
 inline unsigned div_up(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
 // Host-side entry points of the other translation units.

@@ -59,6 +59,7 @@ class Solver:
         self.eout = torch.zeros(8, **f64)
         self.spread = torch.zeros(2, **f64)
         self.off = (0, workload.N)
+        self.overlap_events = None   # list to collect (I, start, end) CUDA events, or None
 
     # ------------------------------------------------------------ set-up
     def _orthonormalize_into_psi(self, q):
@@ -98,8 +99,16 @@ class Solver:
         B.sky_damped_step(ctx, q, self.psi[q], self.h[q], self.eps[o:o + I], self.phi[q], I,
                           self.w.x0, self.w.E0)
         B.sky_apply_h(ctx, self.U[q], self.Bf[q], self.W[q], self.phi[q], self.h[q], I)
-        B.sky_overlap(ctx, self.phi[q], self.phi[q], I, self.S[q])
-        B.sky_overlap(ctx, self.phi[q], self.h[q], I, self.H[q])
+        for X, rhs in ((self.S[q], self.phi[q]), (self.H[q], self.h[q])):
+            if self.overlap_events is None:
+                B.sky_overlap(ctx, self.phi[q], rhs, I, X)
+            else:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(self.stream)
+                B.sky_overlap(ctx, self.phi[q], rhs, I, X)
+                e1.record(self.stream)
+                self.overlap_events.append((I, e0, e1))
         B.sky_orthonormalize(ctx, self.S[q], I, self.C[q])
         B.sky_subspace_diag(ctx, self.H[q], self.C[q], I, self.M[q], self.lam[o:o + I])
         B.sky_rotate(ctx, self.phi[q], self.M[q], I, self.psi[q])
@@ -113,6 +122,19 @@ class Solver:
         if not frozen:
             B.sky_mean_fields(self.ctx, self.rho, self.tau, self.divJ, self.U, self.Bf, self.W)
         B.sky_energy(self.ctx, self.rho, self.tau, self.divJ, self.eout)
+
+    def step_host(self, host, eout_host):
+        """One iteration from host state: copy psi and the mean field in from
+        pinned host tensors, iterate, copy the energies back (end to end)."""
+        for q in range(2):
+            self.psi[q].copy_(host["psi"][q], non_blocking=True)
+        self.U.copy_(host["U"], non_blocking=True)
+        self.Bf.copy_(host["B"], non_blocking=True)
+        self.W.copy_(host["W"], non_blocking=True)
+        self.step()
+        eout_host.copy_(self.eout, non_blocking=True)
+        self.sync()
+        return eout_host
 
     def sync(self):
         B.sky_sync(self.ctx)
