@@ -171,6 +171,23 @@ sky_status sky_energy(sky_ctx* ctx, const double* rho, const double* tau,
 sky_status sky_sp_spread(sky_ctx* ctx, const double* eps, const double* hnorm2, int A,
                          double* out);
 
+/* ---- Overlap matrix without a context or any device allocation -----------
+ * The paper has no counterpart to this entry point.  It computes the same
+ * matrix as sky_overlap, X[a*I + b] = dV * sum_v conj(a_a[v]) b_b[v] (lower
+ * triangle formed, mirrored), for callers that are not allowed to allocate
+ * device memory -- e.g. code inside a host application whose allocator owns
+ * the whole device-memory budget -- and so cannot create a context.
+ * a, b: [I][V] complex in precision prec (double2 or float2); X: [I*I]
+ * double2, all device pointers owned by the caller; V complex entries per
+ * state; dV the volume element; stream a cudaStream_t (NULL = default).
+ * Its scratch is one fixed 16 MiB device array inside the library, held by
+ * every GPU that loads it until exit; I is limited to 1024 (SKY_EINVAL
+ * above).  The first call on a device looks up that array's address and
+ * should come before any stream capture.  Calls share the array: calls that
+ * overlap in time on the GPU race.  Calls no cudaMalloc or cudaFree. */
+sky_status sky_overlap_noalloc(const void* a, const void* b, int I, long long V, double dV,
+                               sky_prec prec, double* X, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,7 @@ _SIGNATURES = {
     "sky_mean_fields": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "sky_energy": (_I, [_P, _P, _P, _P, _P]),
     "sky_sp_spread": (_I, [_P, _P, _P, _I, _P]),
+    "sky_overlap_noalloc": (_I, [_P, _P, _I, ctypes.c_longlong, _D, _I, _P, _P]),
 }
 
 _LIB = None
@@ -175,3 +176,11 @@ def sky_energy(ctx, rho, tau, divJ, out):
 
 def sky_sp_spread(ctx, eps, hnorm2, A, out):
     _check(ctx, lib().sky_sp_spread(ctx, _ptr(eps), _ptr(hnorm2), int(A), _ptr(out)))
+
+
+def sky_overlap_noalloc(a, b, I, V, dV, prec, X, stream=0):
+    """Overlap matrix with no context and no device allocation (include/sky.h)."""
+    st = lib().sky_overlap_noalloc(_ptr(a), _ptr(b), int(I), int(V), float(dV), int(prec), _ptr(X),
+                                   _P(stream) if stream else None)
+    if st != SKY_OK:
+        raise SkyError(st, "sky_overlap_noalloc failed")
