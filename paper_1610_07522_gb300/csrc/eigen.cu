@@ -16,61 +16,79 @@
 
 namespace sky {
 
-constexpr int kJacThreads = 256;
-constexpr int kJacTile = 16;                  // 16 x 16 work items per tile
-constexpr long long kBarrierSpins = 20000000; // x ~64 ns: bounded wait per barrier
+constexpr int kJacThreads = 512;
+constexpr long long kBarrierSpins = 40000000; // x ~32 ns: bounded wait per barrier
 
-struct Rot {
-  double c, s;    // real rotation
-  double2 e;      // phase of A_pq (unit modulus)
+// Rotation of one index pair (p, q) in one round.  J = D R with D removing the
+// phase of A_pq and R the real Jacobi rotation:
+//   J = [[c, s], [-s ce, c ce]],  ce = e^{-i arg A_pq};   J^H = [[c, -s e], [s, c e]].
+// dp, dq are the new diagonal entries; id marks a rotation skipped because
+// |A_pq| is below the threshold (then J = 1).
+struct JRot {
+  double c, s;
+  double2 ce;
+  double dp, dq;
+  int p, q, id, pad;
 };
 
-// Round-robin pairing: L_r[0] = 0, L_r[i] = 1 + ((i - 1 + r) mod (m - 1)).
+// Round-robin pairing: L_r[0] = 0, L_r[i] = 1 + ((i - 1 + r) mod (m - 1));
+// pair k of round r is (L_r[k], L_r[m-1-k]), returned with p < q.
 __device__ __forceinline__ void pair_of(int k, int r, int m, int& p, int& q) {
-  const int i = k, j = m - 1 - k;
-  p = (i == 0) ? 0 : 1 + ((i - 1 + r) % (m - 1));
+  const int j = m - 1 - k;
+  p = (k == 0) ? 0 : 1 + ((k - 1 + r) % (m - 1));
   q = 1 + ((j - 1 + r) % (m - 1));
   if (p > q) { const int t = p; p = q; q = t; }
 }
+// Inverse: the pair index of index i in round r.
+__device__ __forceinline__ int pair_index(int i, int r, int m) {
+  if (i == 0) return 0;
+  const int pos = ((i - 1 - r) % (m - 1) + (m - 1)) % (m - 1) + 1;
+  return pos < m / 2 ? pos : m - 1 - pos;
+}
 
-__device__ __forceinline__ Rot make_rot(const double2* A, int m, int n, int p, int q) {
-  Rot R;
-  R.c = 1.0; R.s = 0.0; R.e = make_double2(1.0, 0.0);
+__device__ __forceinline__ JRot make_rot(double app, double aqq, double2 z, int p, int q, int n,
+                                         double thr) {
+  JRot R;
+  R.c = 1.0; R.s = 0.0; R.ce = make_double2(1.0, 0.0);
+  R.dp = app; R.dq = aqq; R.p = p; R.q = q; R.id = 1; R.pad = 0;
   if (p >= n || q >= n) return R;   // padding index: identity
-  const double2 z = A[(long long)p * m + q];
   const double az = hypot(z.x, z.y);
-  if (az == 0.0) return R;
-  const double app = A[(long long)p * m + p].x, aqq = A[(long long)q * m + q].x;
+  if (!(az > thr)) return R;
   const double th = (aqq - app) / (2.0 * az);
   double t;
   if (fabs(th) > 1e150) t = 0.5 / th;
   else t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
   R.c = 1.0 / sqrt(t * t + 1.0);
   R.s = t * R.c;
-  R.e = make_double2(z.x / az, z.y / az);
+  R.ce = make_double2(z.x / az, -z.y / az);
+  R.dp = app - t * az;
+  R.dq = aqq + t * az;
+  R.id = 0;
   return R;
 }
 
-// J = [[c, s], [-s conj(e), c conj(e)]];  J^H = [[c, -s e], [s, c e]].
-__device__ __forceinline__ void block_update(const Rot& R1, const Rot& R2, double2 b00,
-                                             double2 b01, double2 b10, double2 b11,
-                                             double2& o00, double2& o01, double2& o10,
-                                             double2& o11) {
-  const double2 ce2 = conjx(R2.e);
-  // T = B J2
-  const double2 t00 = R2.c * b00 - R2.s * cmul(b01, ce2);
-  const double2 t01 = R2.s * b00 + R2.c * cmul(b01, ce2);
-  const double2 t10 = R2.c * b10 - R2.s * cmul(b11, ce2);
-  const double2 t11 = R2.s * b10 + R2.c * cmul(b11, ce2);
-  // B' = J1^H T
-  o00 = R1.c * t00 - R1.s * cmul(R1.e, t10);
-  o01 = R1.c * t01 - R1.s * cmul(R1.e, t11);
-  o10 = R1.s * t00 + R1.c * cmul(R1.e, t10);
-  o11 = R1.s * t01 + R1.c * cmul(R1.e, t11);
+// Column b of (B J2) for the 2x2 block B = [[b00, b01], [b10, b11]].
+__device__ __forceinline__ void right_col(const JRot& R2, int col, double2 b00, double2 b01,
+                                          double2 b10, double2 b11, double2& t0, double2& t1) {
+  if (col == 0) {
+    const double2 f = (-R2.s) * R2.ce;            // J2[1][0]
+    t0 = R2.c * b00 + cmul(b01, f);
+    t1 = R2.c * b10 + cmul(b11, f);
+  } else {
+    const double2 f = R2.c * R2.ce;               // J2[1][1]
+    t0 = R2.s * b00 + cmul(b01, f);
+    t1 = R2.s * b10 + cmul(b11, f);
+  }
+}
+// Row a of J1^H applied to the column (t0, t1).
+__device__ __forceinline__ double2 left_row(const JRot& R1, int row, double2 t0, double2 t1) {
+  const double2 e = conjx(R1.ce);
+  if (row == 0) return R1.c * t0 - R1.s * cmul(e, t1);
+  return R1.s * t0 + R1.c * cmul(e, t1);
 }
 
-// Sense-free generation barrier over all blocks of a cooperative launch,
-// with a bounded spin.  Returns false (and flags SKY_ETIMEOUT) on timeout.
+// Generation barrier over all blocks of a cooperative launch with a bounded
+// spin.  Returns false (and flags SKY_ETIMEOUT) when it gives up.
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* status) {
   __shared__ int s_ok;
   __syncthreads();
@@ -92,7 +110,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* status) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     __threadfence();
@@ -104,128 +122,178 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* status) {
 
 struct JacArgs {
   double2* A0; double2* A1; double2* V;
+  JRot* R0; JRot* R1;   // rotations of the current / next round, [m/2] each
   int n, m;
   double tol;
   int max_sweeps;
-  double* part;       // [gridDim.x][2]
+  double* part;         // [gridDim.x][2]
   unsigned* bar;
   int* status;
-  int* result;        // 0: A0 holds the result, 1: A1
+  int* result;          // 0: A0 holds the result, 1: A1
+  const int* run;       // device gate: skip the whole solve when *run == 0
 };
 
+__device__ __forceinline__ void block_norms(double off, double tot, double* part) {
+  __shared__ double s_red[2][kJacThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    off += __shfl_down_sync(0xffffffffu, off, o);
+    tot += __shfl_down_sync(0xffffffffu, tot, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_red[0][threadIdx.x >> 5] = off;
+    s_red[1][threadIdx.x >> 5] = tot;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int w = 0; w < kJacThreads / 32; ++w) { x += s_red[0][w]; y += s_red[1][w]; }
+    part[2 * blockIdx.x] = x;
+    part[2 * blockIdx.x + 1] = y;
+  }
+}
+
+// Every block sums the partial norms in the same order: same decision everywhere.
+__device__ __forceinline__ bool decide_stop(const JacArgs& a, int sweep, double* thr) {
+  __shared__ int s_stop;
+  __shared__ double s_thr;
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) { x += a.part[2 * b]; y += a.part[2 * b + 1]; }
+    int stop = (x <= a.tol * a.tol * y) || (y == 0.0);
+    if (!stop && sweep >= a.max_sweeps) {
+      flag_status(a.status, SKY_ENOCONV);
+      stop = 1;
+    }
+    s_stop = stop;
+    s_thr = 1e-19 * sqrt(y);     // rotations below this change nothing measurable
+  }
+  __syncthreads();
+  *thr = s_thr;
+  return s_stop != 0;
+}
+
 __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacArgs a) {
+  if (a.run && *a.run == 0) return;   // uniform across the grid: no barrier is entered
   const int m = a.m, n = a.n, h = m / 2;
+  const int gtid = blockIdx.x * kJacThreads + threadIdx.x;
+  const int gsz = gridDim.x * kJacThreads;
   double2* cur = a.A0;
   double2* nxt = a.A1;
+  JRot* Rc = a.R0;
+  JRot* Rn = a.R1;
   int which = 0;
-  __shared__ Rot s_r1[kJacTile], s_r2[kJacTile];
-  __shared__ double s_red[2][kJacThreads / 32];
-  const int ntA = (h + kJacTile - 1) / kJacTile;          // pair tiles per side
-  const int ntV = (m + kJacTile - 1) / kJacTile;          // row tiles of V
-  const int tilesA = ntA * ntA, tilesV = ntV * ntA;
-  for (int sweep = 0;; ++sweep) {
-    // off-diagonal and total Frobenius norms of cur
+  // prologue: norms of the input
+  {
     double off = 0.0, tot = 0.0;
-    for (long long e = (long long)blockIdx.x * kJacThreads + threadIdx.x; e < (long long)n * n;
-         e += (long long)gridDim.x * kJacThreads) {
-      const int i = (int)(e / n), j = (int)(e % n);
+    for (int e = gtid; e < n * n; e += gsz) {
+      const int i = e / n, j = e % n;
       const double2 v = cur[(long long)i * m + j];
-      const double w = v.x * v.x + v.y * v.y;
-      tot += w;
-      if (i != j) off += w;
+      const double w2 = v.x * v.x + v.y * v.y;
+      tot += w2;
+      if (i != j) off += w2;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_down_sync(0xffffffffu, off, o);
-      tot += __shfl_down_sync(0xffffffffu, tot, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      s_red[0][threadIdx.x >> 5] = off;
-      s_red[1][threadIdx.x >> 5] = tot;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double x = 0.0, y = 0.0;
-      for (int w = 0; w < kJacThreads / 32; ++w) { x += s_red[0][w]; y += s_red[1][w]; }
-      a.part[2 * blockIdx.x] = x;
-      a.part[2 * blockIdx.x + 1] = y;
-    }
-    if (!grid_barrier(a.bar, a.status)) return;
-    __shared__ int s_stop;
-    if (threadIdx.x == 0) {
-      double x = 0.0, y = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b) { x += a.part[2 * b]; y += a.part[2 * b + 1]; }
-      int stop = (x <= a.tol * a.tol * y) || (y == 0.0);
-      if (!stop && sweep >= a.max_sweeps) {
-        flag_status(a.status, SKY_ENOCONV);
-        stop = 1;
-      }
-      s_stop = stop;
-    }
-    __syncthreads();
-    if (s_stop) break;
-    // the partial norms are rewritten next sweep only after everyone read them
-    if (!grid_barrier(a.bar, a.status)) return;
+    block_norms(off, tot, a.part);
+  }
+  if (!grid_barrier(a.bar, a.status)) return;
+  double thr;
+  bool stop = decide_stop(a, 0, &thr);
+  // rotations of round 0
+  for (int k = gtid; k < h; k += gsz) {
+    int p, q;
+    pair_of(k, 0, m, p, q);
+    Rc[k] = make_rot(cur[(long long)p * m + p].x, cur[(long long)q * m + q].x,
+                     cur[(long long)p * m + q], p, q, n, thr);
+  }
+  if (!grid_barrier(a.bar, a.status)) return;
+  const int nblk = h * h, nV = m * h;
+  for (int sweep = 1; !stop; ++sweep) {
     for (int r = 0; r < m - 1; ++r) {
-      for (int t = blockIdx.x; t < tilesA + tilesV; t += gridDim.x) {
-        int k1b, k2b, rowb = 0;
-        const bool isA = t < tilesA;
-        if (isA) { k1b = (t / ntA) * kJacTile; k2b = (t % ntA) * kJacTile; }
-        else { const int u = t - tilesA; rowb = (u / ntA) * kJacTile; k2b = (u % ntA) * kJacTile; k1b = 0; }
-        __syncthreads();
-        if (threadIdx.x < kJacTile) {
-          const int k = k2b + threadIdx.x;
-          if (k < h) { int p, q; pair_of(k, r, m, p, q); s_r2[threadIdx.x] = make_rot(cur, m, n, p, q); }
-        } else if (isA && threadIdx.x < 2 * kJacTile) {
-          const int k = k1b + threadIdx.x - kJacTile;
-          if (k < h) { int p, q; pair_of(k, r, m, p, q); s_r1[threadIdx.x - kJacTile] = make_rot(cur, m, n, p, q); }
-        }
-        __syncthreads();
-        const int ia = threadIdx.x / kJacTile, ib = threadIdx.x % kJacTile;
-        if (isA) {
-          const int k1 = k1b + ia, k2 = k2b + ib;
-          if (k1 < h && k2 < h) {
-            int p1, q1, p2, q2;
-            pair_of(k1, r, m, p1, q1);
-            pair_of(k2, r, m, p2, q2);
-            const Rot& R1 = s_r1[ia];
-            const Rot& R2 = s_r2[ib];
-            double2 o00, o01, o10, o11;
-            if (k1 == k2 && p1 < n && q1 < n && (R1.s != 0.0 || R1.e.y != 0.0 || R1.e.x != 1.0)) {
-              // diagonal block: exact result of the 2x2 diagonalisation
-              const double2 z = cur[(long long)p1 * m + q1];
-              const double az = hypot(z.x, z.y);
-              const double t = R1.s / R1.c;
-              o00 = make_double2(cur[(long long)p1 * m + p1].x - t * az, 0.0);
-              o11 = make_double2(cur[(long long)q1 * m + q1].x + t * az, 0.0);
-              o01 = make_double2(0.0, 0.0);
-              o10 = o01;
-            } else {
-              block_update(R1, R2, cur[(long long)p1 * m + p2], cur[(long long)p1 * m + q2],
-                           cur[(long long)q1 * m + p2], cur[(long long)q1 * m + q2], o00, o01, o10,
-                           o11);
-            }
-            nxt[(long long)p1 * m + p2] = o00;
-            nxt[(long long)p1 * m + q2] = o01;
-            nxt[(long long)q1 * m + p2] = o10;
-            nxt[(long long)q1 * m + q2] = o11;
+      const bool last = (r == m - 2);
+      const int rn = last ? 0 : r + 1;
+      double off = 0.0, tot = 0.0;
+      for (int w = gtid; w < nblk + nV + h; w += gsz) {
+        if (w < nblk) {
+          // 2x2 block (P1 rows, P2 columns): B' = J1^H B J2 into the other buffer
+          const JRot& R1 = Rc[w / h];
+          const JRot& R2 = Rc[w % h];
+          const long long i00 = (long long)R1.p * m + R2.p, i01 = (long long)R1.p * m + R2.q;
+          const long long i10 = (long long)R1.q * m + R2.p, i11 = (long long)R1.q * m + R2.q;
+          double2 o00, o01, o10, o11;
+          if (R1.id && R2.id) {
+            o00 = cur[i00]; o01 = cur[i01]; o10 = cur[i10]; o11 = cur[i11];
+          } else if (w / h == w % h) {
+            o00 = make_double2(R1.dp, 0.0); o11 = make_double2(R1.dq, 0.0);
+            o01 = make_double2(0.0, 0.0); o10 = o01;
+          } else {
+            const double2 b00 = cur[i00], b01 = cur[i01], b10 = cur[i10], b11 = cur[i11];
+            double2 t0, t1;
+            right_col(R2, 0, b00, b01, b10, b11, t0, t1);
+            o00 = left_row(R1, 0, t0, t1);
+            o10 = left_row(R1, 1, t0, t1);
+            right_col(R2, 1, b00, b01, b10, b11, t0, t1);
+            o01 = left_row(R1, 0, t0, t1);
+            o11 = left_row(R1, 1, t0, t1);
+          }
+          nxt[i00] = o00; nxt[i01] = o01; nxt[i10] = o10; nxt[i11] = o11;
+          if (last) {
+            const double w00 = o00.x * o00.x + o00.y * o00.y, w01 = o01.x * o01.x + o01.y * o01.y;
+            const double w10 = o10.x * o10.x + o10.y * o10.y, w11 = o11.x * o11.x + o11.y * o11.y;
+            tot += w00 + w01 + w10 + w11;
+            off += (R1.p != R2.p ? w00 : 0.0) + (R1.p != R2.q ? w01 : 0.0) +
+                   (R1.q != R2.p ? w10 : 0.0) + (R1.q != R2.q ? w11 : 0.0);
+          }
+        } else if (w < nblk + nV) {
+          // accumulate the rotation into row `row` of V (in place)
+          const int u = w - nblk, row = u / h;
+          const JRot& R = Rc[u % h];
+          if (!R.id) {
+            double2* vr = a.V + (long long)row * m;
+            const double2 vp = vr[R.p], vq = vr[R.q];
+            vr[R.p] = R.c * vp + cmul(vq, (-R.s) * R.ce);
+            vr[R.q] = R.s * vp + cmul(vq, R.c * R.ce);
           }
         } else {
-          const int row = rowb + ia, k = k2b + ib;
-          if (row < m && k < h) {
-            int p, q;
-            pair_of(k, r, m, p, q);
-            const Rot& R = s_r2[ib];
-            const double2 vp = a.V[(long long)row * m + p], vq = a.V[(long long)row * m + q];
-            const double2 ce = conjx(R.e);
-            a.V[(long long)row * m + p] = R.c * vp - R.s * cmul(vq, ce);
-            a.V[(long long)row * m + q] = R.s * vp + R.c * cmul(vq, ce);
+          // rotation of pair k of the next round from this round's result,
+          // recomputed here from the old blocks (no extra barrier)
+          const int k = w - nblk - nV;
+          int p, q;
+          pair_of(k, rn, m, p, q);
+          const JRot& Rp = Rc[pair_index(p, r, m)];
+          const JRot& Rq = Rc[pair_index(q, r, m)];
+          const int lp = (p == Rp.p) ? 0 : 1, lq = (q == Rq.p) ? 0 : 1;
+          const double app = Rp.id ? cur[(long long)p * m + p].x : (lp ? Rp.dq : Rp.dp);
+          const double aqq = Rq.id ? cur[(long long)q * m + q].x : (lq ? Rq.dq : Rq.dp);
+          double2 z;
+          if (Rp.id && Rq.id) {
+            z = cur[(long long)p * m + q];
+          } else {
+            const double2 b00 = cur[(long long)Rp.p * m + Rq.p], b01 = cur[(long long)Rp.p * m + Rq.q];
+            const double2 b10 = cur[(long long)Rp.q * m + Rq.p], b11 = cur[(long long)Rp.q * m + Rq.q];
+            double2 t0, t1;
+            right_col(Rq, lq, b00, b01, b10, b11, t0, t1);
+            z = left_row(Rp, lp, t0, t1);
           }
+          Rn[k] = make_rot(app, aqq, z, p, q, n, thr);
         }
       }
+      if (last) block_norms(off, tot, a.part);
       if (!grid_barrier(a.bar, a.status)) return;
-      double2* tmp = cur; cur = nxt; nxt = tmp;
+      double2* tA = cur; cur = nxt; nxt = tA;
+      JRot* tR = Rc; Rc = Rn; Rn = tR;
       which ^= 1;
+    }
+    stop = decide_stop(a, sweep, &thr);
+    if (!stop) {
+      // round-0 rotations were computed with the previous threshold; refresh
+      // them with the new one (cheap; needs one barrier)
+      for (int k = gtid; k < h; k += gsz) {
+        int p, q;
+        pair_of(k, 0, m, p, q);
+        Rc[k] = make_rot(cur[(long long)p * m + p].x, cur[(long long)q * m + q].x,
+                         cur[(long long)p * m + q], p, q, n, thr);
+      }
+      if (!grid_barrier(a.bar, a.status)) return;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.result = which;
@@ -233,7 +301,8 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacArgs a) {
 
 // Copy A (n x n) into the padded m x m buffer, V = identity, reset the barrier.
 __global__ void k_jacobi_init(const double2* A, int n, int m, double2* A0, double2* V,
-                              unsigned* bar, int* result) {
+                              unsigned* bar, int* result, const int* run) {
+  if (run && *run == 0) return;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e == 0) { bar[0] = 0u; *result = 0; }
   if (e >= (long long)m * m) return;
@@ -244,7 +313,9 @@ __global__ void k_jacobi_init(const double2* A, int n, int m, double2* A0, doubl
 
 // Eigenvalues ascending (ties by index) and the matching columns of V.
 __global__ void k_jacobi_finish(const double2* A0, const double2* A1, const double2* V,
-                                const int* result, int n, int m, double* w, double2* Z) {
+                                const int* result, int n, int m, double* w, double2* Z,
+                                const int* run) {
+  if (run && *run == 0) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const double2* A = (*result) ? A1 : A0;
@@ -262,28 +333,36 @@ int jacobi_max_grid(Ctx* c) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, kJacThreads, 0);
   if (per_sm < 1) per_sm = 1;
+  if (per_sm > 1) per_sm = 1;   // one block per SM keeps the barrier short
   return per_sm * c->num_sms;
 }
 
-sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z) {
+size_t jacobi_rot_bytes(int m) { return (size_t)2 * (m / 2 + 1) * sizeof(JRot); }
+
+sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z, const int* run) {
   if (I == 0) return SKY_OK;
   const int m = I + (I & 1);
   k_jacobi_init<<<div_up((long long)m * m, 256), 256, 0, c->stream>>>(A, I, m, c->d_eigA[0],
                                                                       c->d_eigV, c->d_bar,
-                                                                      c->d_eigres); note_launch();
+                                                                      c->d_eigres, run);
+  note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(c, e, "jacobi init");
   if (m >= 2) {
     const int h = m / 2;
-    const int ntA = (h + kJacTile - 1) / kJacTile, ntV = (m + kJacTile - 1) / kJacTile;
-    int grid = ntA * ntA + ntV * ntA;
+    const long long items = (long long)h * h + (long long)m * h + h;
+    int grid = (int)((items + kJacThreads - 1) / kJacThreads);
     if (grid > c->eig_grid) grid = c->eig_grid;
+    if (grid < 1) grid = 1;
     JacArgs a;
     a.A0 = c->d_eigA[0]; a.A1 = c->d_eigA[1]; a.V = c->d_eigV;
+    a.R0 = reinterpret_cast<JRot*>(c->d_eigrot);
+    a.R1 = a.R0 + h;
     a.n = I; a.m = m;
     a.tol = 1e-15;
     a.max_sweeps = 60;
     a.part = c->d_eigpart; a.bar = c->d_bar; a.status = c->d_status; a.result = c->d_eigres;
+    a.run = run;
     void* args[] = {&a};
     note_launch();
     e = cudaLaunchCooperativeKernel((const void*)k_jacobi, dim3(grid), dim3(kJacThreads), args, 0,
@@ -291,12 +370,15 @@ sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z) {
     if (e != cudaSuccess) return cuda_check(c, e, "jacobi");
   }
   k_jacobi_finish<<<div_up(I, 128), 128, 0, c->stream>>>(c->d_eigA[0], c->d_eigA[1], c->d_eigV,
-                                                        c->d_eigres, I, m, w, Z); note_launch();
+                                                        c->d_eigres, I, m, w, Z, run);
+  note_launch();
   return cuda_check(c, cudaGetLastError(), "jacobi finish");
 }
 
 // Y = X diag(lambda^{-1/2}); flags SKY_ENOTPD for a non-positive eigenvalue.
-__global__ void k_inv_sqrt_cols(const double2* X, const double* lam, int n, double2* Y, int* status) {
+__global__ void k_inv_sqrt_cols(const double2* X, const double* lam, int n, double2* Y, int* status,
+                                const int* run) {
+  if (run && *run == 0) return;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)n * n) return;
   const int j = (int)(e % n);
@@ -320,17 +402,126 @@ __global__ void k_hermitize(double2* A, int n) {
   A[(long long)j * n + i] = conjx(s);
 }
 
+// ---- Loewdin factor C = S^{-1/2} (Eq. Loewedin) ----------------------------
+// When ||S - I||_F < 1/2 (every iteration after the first few: S is the
+// overlap of slightly damped orthonormal states) C comes from the coupled
+// Newton-Schulz iteration for the inverse square root (Higham, Functions of
+// Matrices, 2008):  Y0 = S, Z0 = I;  T = (3I - Z Y)/2;  Y <- Y T;  Z <- T Z;
+// Z -> S^{-1/2} quadratically.  Otherwise C = X Lambda^{-1/2} X^H from the
+// Jacobi eigendecomposition of S, as the paper describes.  The choice is made
+// on the device: gate[0] = Newton-Schulz running, gate[1] = eigendecomposition
+// path, gate[2] = Newton-Schulz converged (one final update pending).
+constexpr int kNsMaxIter = 10;
+constexpr double kNsSwitch = 0.5;      // ||S - I||_F bound for Newton-Schulz
+constexpr double kNsConv = 1e-10;      // ||I - Z Y||_F after which one more update suffices
+
+__global__ void __launch_bounds__(1024) k_ns_init(const double2* S, int n, double2* Y, double2* Z,
+                                                  int* gate) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    double2 v = S[e];
+    if (i == j) v.x -= 1.0;
+    acc += v.x * v.x + v.y * v.y;
+    Y[e] = S[e];
+    Z[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    const int ns = sqrt(t) < kNsSwitch;
+    gate[0] = ns;
+    gate[1] = !ns;
+    gate[2] = 0;
+  }
+}
+
+// T = (3I - W)/2 in place of W = Z Y; records convergence; ends the
+// iteration one step after convergence was seen.
+__global__ void __launch_bounds__(1024) k_ns_step(double2* W, int n, int* gate) {
+  __shared__ double red[32];
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) {
+    if (gate[0] && gate[2]) gate[0] = 0;   // the final update has been applied
+    s_skip = !gate[0];
+  }
+  __syncthreads();
+  if (s_skip) return;
+  double acc = 0.0;
+  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    double2 d = W[e];
+    if (i == j) d.x -= 1.0;                 // W - I
+    acc += d.x * d.x + d.y * d.y;
+    W[e] = make_double2((i == j ? 1.0 : 0.0) - 0.5 * d.x, -0.5 * d.y);   // I - (W - I)/2
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    if (sqrt(t) < kNsConv) gate[2] = 1;
+  }
+}
+
+__global__ void k_ns_copy(double2* Y, double2* Z, const double2* Yn, const double2* Zn, int n,
+                          const int* gate) {
+  if (!gate[0]) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  Y[e] = Yn[e];
+  Z[e] = Zn[e];
+}
+
+// C = (Z + Z^H)/2 when Newton-Schulz was used; flags non-convergence.
+__global__ void k_ns_final(const double2* Z, int n, double2* C, const int* gate, int* status) {
+  if (gate[1]) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e == 0 && gate[0] && !gate[2]) flag_status(status, SKY_ENOCONV);
+  if (e >= (long long)n * n) return;
+  const int i = (int)(e / n), j = (int)(e % n);
+  C[e] = 0.5 * (Z[e] + conjx(Z[(long long)j * n + i]));
+}
+
 sky_status lowdin_impl(Ctx* c, const double2* S, int I, double2* C) {
   if (I == 0) return SKY_OK;
-  double2* X = c->d_small[0];
-  double2* Y = c->d_small[1];
-  sky_status st = eigh_impl(c, S, I, c->d_eigw, X);
+  double2 *Y = c->d_small[0], *Z = c->d_small[1], *W = c->d_small[2];
+  double2 *Yn = c->d_small[3], *Zn = c->d_small[4];
+  int* gate = c->d_gate;
+  const long long nn = (long long)I * I;
+  cudaError_t e;
+  k_ns_init<<<1, 1024, 0, c->stream>>>(S, I, Y, Z, gate);
+  note_launch();
+  for (int it = 0; it < kNsMaxIter; ++it) {
+    sky_status st = zgemm_small(c, false, false, Z, Y, W, I, gate, gate + 2);   // W = Z Y
+    if (st != SKY_OK) return st;
+    k_ns_step<<<1, 1024, 0, c->stream>>>(W, I, gate);
+    note_launch();
+    st = zgemm_small(c, false, false, Y, W, Yn, I, gate);                       // Y T
+    if (st == SKY_OK) st = zgemm_small(c, false, false, W, Z, Zn, I, gate);     // T Z
+    if (st != SKY_OK) return st;
+    k_ns_copy<<<div_up(nn, 256), 256, 0, c->stream>>>(Y, Z, Yn, Zn, I, gate);
+    note_launch();
+  }
+  k_ns_final<<<div_up(nn, 256), 256, 0, c->stream>>>(Z, I, C, gate, c->d_status);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "newton-schulz");
+  // eigendecomposition path (runs only when gate[1] is set)
+  double2 *X = c->d_small[3], *Xs = c->d_small[4];
+  sky_status st = eigh_impl(c, S, I, c->d_eigw, X, gate + 1);
   if (st != SKY_OK) return st;
-  k_inv_sqrt_cols<<<div_up((long long)I * I, 256), 256, 0, c->stream>>>(X, c->d_eigw, I, Y,
-                                                                       c->d_status); note_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_check(c, e, "loewdin scale");
-  return zgemm_small(c, false, true, Y, X, C, I);   // C = Y X^H
+  k_inv_sqrt_cols<<<div_up(nn, 256), 256, 0, c->stream>>>(X, c->d_eigw, I, Xs, c->d_status,
+                                                          gate + 1);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "loewdin scale");
+  return zgemm_small(c, false, true, Xs, X, C, I, gate + 1);   // C = X Lambda^{-1/2} X^H
 }
 
 sky_status subspace_impl(Ctx* c, const double2* H, const double2* C, int I, double2* M,

@@ -7,25 +7,34 @@
 
 namespace sky {
 
-static int overlap_splits(int I, long long V, int num_sms, int* ntiles_out) {
+// K-splits so that tiles x splits fills whole waves of resident CTAs
+// (`slots` = CTAs resident on the GPU at once), capped by the K blocks.
+static int overlap_splits(int I, long long V, int slots, int* ntiles_out) {
   const int nt = (I + BM - 1) / BM;
   const int ntiles = nt * (nt + 1) / 2;
   const long long kblocks = (V + BK - 1) / BK;
-  long long want = (4LL * num_sms + ntiles - 1) / ntiles;
-  if (want > kblocks) want = kblocks;
+  long long want = slots / ntiles;
   if (want < 1) want = 1;
+  if (want > kblocks) want = kblocks;
   if (ntiles_out) *ntiles_out = ntiles;
   return (int)want;
 }
 
-size_t overlap_partial_elems(int I, long long V, int num_sms) {
-  return (size_t)overlap_splits(I, V, num_sms, nullptr) * (size_t)I * (size_t)I;
+int overlap_slots(int num_sms) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_overlap<double2>, 256, 0);
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * num_sms;
+}
+
+size_t overlap_partial_elems(int I, long long V, int slots) {
+  return (size_t)overlap_splits(I, V, slots, nullptr) * (size_t)I * (size_t)I;
 }
 
 sky_status overlap_impl(Ctx* c, const void* a, const void* b, int I, double2* X) {
   const long long V = 2LL * c->G;
   int ntiles;
-  const int nsplit = overlap_splits(I, V, c->num_sms, &ntiles);
+  const int nsplit = overlap_splits(I, V, c->ov_slots, &ntiles);
   const long long kblocks = (V + BK - 1) / BK;
   const long long kchunk = ((kblocks + nsplit - 1) / nsplit) * BK;
   const int nsplit_eff = (int)((V + kchunk - 1) / kchunk);
@@ -78,10 +87,10 @@ __global__ void __launch_bounds__(256) k_rotate(const S* __restrict__ phi, const
     for (int kk = 0; kk < BK; ++kk) {
       const double2 a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
       const double2 b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-      acc[0][0] = acc[0][0] + cmul(a0, b0);
-      acc[0][1] = acc[0][1] + cmul(a0, b1);
-      acc[1][0] = acc[1][0] + cmul(a1, b0);
-      acc[1][1] = acc[1][1] + cmul(a1, b1);
+      cfma(acc[0][0], a0, b0);
+      cfma(acc[0][1], a0, b1);
+      cfma(acc[1][0], a1, b0);
+      cfma(acc[1][1], a1, b1);
     }
     __syncthreads();
   }
@@ -113,24 +122,28 @@ sky_status rotate_impl(Ctx* c, const void* phi, const double2* M, int I, void* o
 
 // ---------------------------------------------------------------- small GEMM
 // C = opA(A) opB(B), n x n row-major; op = identity or conjugate transpose.
-template <bool AH, bool BH>
-__global__ void __launch_bounds__(256) k_zgemm(const double2* __restrict__ A,
-                                               const double2* __restrict__ B,
-                                               double2* __restrict__ C, int n) {
-  __shared__ double2 As[BK][BM + 1];
-  __shared__ double2 Bs[BK][BN + 1];
-  const int r0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+// TS x TS output tile per block, 2 x 2 per thread.  Runs only if `run` is null
+// or *run != 0, and `stop` is null or *stop == 0 (device-side gating, so a
+// fixed launch sequence can skip work the device decided is not needed).
+template <bool AH, bool BH, int TS>
+__global__ void __launch_bounds__(TS * TS / 4) k_zgemm(const double2* __restrict__ A,
+                                                       const double2* __restrict__ B,
+                                                       double2* __restrict__ C, int n,
+                                                       const int* run, const int* stop) {
+  if ((run && *run == 0) || (stop && *stop != 0)) return;
+  constexpr int NT = TS * TS / 4, TH = TS / 2;
+  __shared__ double2 As[BK][TS + 1];
+  __shared__ double2 Bs[BK][TS + 1];
+  const int r0 = blockIdx.y * TS, c0 = blockIdx.x * TS;
+  const int tid = threadIdx.x, ty = tid / TH, tx = tid % TH;
   double2 acc[2][2];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
   for (int k0 = 0; k0 < n; k0 += BK) {
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int e = tid * 2 + u;
-      const int kk = e >> 5, col = e & 31;
+    for (int e = tid; e < BK * TS; e += NT) {
+      const int kk = e / TS, col = e % TS;
       const int k = k0 + kk, r = r0 + col, cc = c0 + col;
       double2 av = make_double2(0.0, 0.0), bv = make_double2(0.0, 0.0);
       if (k < n && r < n) av = AH ? conjx(A[(long long)k * n + r]) : A[(long long)r * n + k];
@@ -143,10 +156,10 @@ __global__ void __launch_bounds__(256) k_zgemm(const double2* __restrict__ A,
     for (int kk = 0; kk < BK; ++kk) {
       const double2 a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
       const double2 b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-      acc[0][0] = acc[0][0] + cmul(a0, b0);
-      acc[0][1] = acc[0][1] + cmul(a0, b1);
-      acc[1][0] = acc[1][0] + cmul(a1, b0);
-      acc[1][1] = acc[1][1] + cmul(a1, b1);
+      cfma(acc[0][0], a0, b0);
+      cfma(acc[0][1], a0, b1);
+      cfma(acc[1][0], a1, b0);
+      cfma(acc[1][1], a1, b1);
     }
     __syncthreads();
   }
@@ -159,13 +172,23 @@ __global__ void __launch_bounds__(256) k_zgemm(const double2* __restrict__ A,
     }
 }
 
+template <int TS>
+static void launch_zgemm(Ctx* c, bool ah, bool bh, const double2* A, const double2* B,
+                         double2* C, int n, const int* run, const int* stop) {
+  dim3 grid(div_up(n, TS), div_up(n, TS));
+  constexpr int NT = TS * TS / 4;
+  if (!ah && !bh) k_zgemm<false, false, TS><<<grid, NT, 0, c->stream>>>(A, B, C, n, run, stop);
+  else if (ah && !bh) k_zgemm<true, false, TS><<<grid, NT, 0, c->stream>>>(A, B, C, n, run, stop);
+  else if (!ah && bh) k_zgemm<false, true, TS><<<grid, NT, 0, c->stream>>>(A, B, C, n, run, stop);
+  else k_zgemm<true, true, TS><<<grid, NT, 0, c->stream>>>(A, B, C, n, run, stop);
+}
+
 sky_status zgemm_small(Ctx* c, bool ah, bool bh, const double2* A, const double2* B, double2* C,
-                       int n) {
-  dim3 grid(div_up(n, BN), div_up(n, BM));
-  if (!ah && !bh) k_zgemm<false, false><<<grid, 256, 0, c->stream>>>(A, B, C, n);
-  else if (ah && !bh) k_zgemm<true, false><<<grid, 256, 0, c->stream>>>(A, B, C, n);
-  else if (!ah && bh) k_zgemm<false, true><<<grid, 256, 0, c->stream>>>(A, B, C, n);
-  else k_zgemm<true, true><<<grid, 256, 0, c->stream>>>(A, B, C, n);
+                       int n, const int* run, const int* stop) {
+  // 32 x 32 tiles once they give at least two blocks per SM, else 16 x 16
+  const long long t32 = (long long)div_up(n, 32) * div_up(n, 32);
+  if (t32 >= 2LL * c->num_sms) launch_zgemm<32>(c, ah, bh, A, B, C, n, run, stop);
+  else launch_zgemm<16>(c, ah, bh, A, B, C, n, run, stop);
   note_launch();
   return cuda_check(c, cudaGetLastError(), "zgemm");
 }

@@ -12,6 +12,20 @@ constexpr int BM = 32, BN = 32, BK = 16;   // tile of 32 x 32 complex outputs
 __device__ __forceinline__ double2 ld2(const double2* p) { return *p; }
 __device__ __forceinline__ double2 ld2(const float2* p) { const float2 v = *p; return make_double2(v.x, v.y); }
 
+// acc += conj(a) b and acc += a b as four FMAs each.
+__device__ __forceinline__ void cfma_conj(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfma(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
 // ---------------------------------------------------------------- overlap
 // Lower-triangle tile t -> (ti, tj), ti >= tj.
 __device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
@@ -54,10 +68,10 @@ __global__ void __launch_bounds__(256) k_overlap(const S* __restrict__ A, const 
     for (int kk = 0; kk < BK; ++kk) {
       const double2 a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
       const double2 b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-      acc[0][0] = acc[0][0] + cmulc(a0, b0);
-      acc[0][1] = acc[0][1] + cmulc(a0, b1);
-      acc[1][0] = acc[1][0] + cmulc(a1, b0);
-      acc[1][1] = acc[1][1] + cmulc(a1, b1);
+      cfma_conj(acc[0][0], a0, b0);
+      cfma_conj(acc[0][1], a0, b1);
+      cfma_conj(acc[1][0], a1, b0);
+      cfma_conj(acc[1][1], a1, b1);
     }
     __syncthreads();
   }

@@ -74,7 +74,8 @@ static void free_all(Ctx* c) {
                   c->d_ktf[2], c->d_kp[0], c->d_kp[1], c->d_kp[2], c->d_damp[0], c->d_damp[1],
                   c->d_coul, c->d_gscr, c->d_red, c->d_dpart, c->d_ftmp, c->d_fcx, c->d_gpart,
                   c->d_eigA[0], c->d_eigA[1], c->d_eigV, c->d_eigw, c->d_eigpart, c->d_bar,
-                  c->d_eigres, c->d_small[0], c->d_small[1], c->d_small[2]};
+                  c->d_eigres, c->d_eigrot, c->d_small[0], c->d_small[1], c->d_small[2],
+                  c->d_small[3], c->d_small[4], c->d_small[5], c->d_gate};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -144,9 +145,10 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   c->red_nblk = (int)((2 * G + 4095) / 4096);
   if (c->red_nblk < 1) c->red_nblk = 1;
   if (c->red_nblk > 64) c->red_nblk = 64;
+  c->ov_slots = overlap_slots(c->num_sms);
   size_t gpart = 0;
   for (int I = 1; I <= Imax; ++I) {
-    const size_t need = overlap_partial_elems(I, V, c->num_sms);
+    const size_t need = overlap_partial_elems(I, V, c->ov_slots);
     if (need > gpart) gpart = need;
   }
   c->gpart_elems = gpart;
@@ -179,7 +181,13 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   ALLOC(c->d_eigw, m);
   ALLOC(c->d_bar, 2);
   ALLOC(c->d_eigres, 1);
-  for (int k = 0; k < 3; ++k) ALLOC(c->d_small[k], (size_t)Imax * Imax);
+  if (s == SKY_OK) {
+    char* p = nullptr;
+    s = dalloc(c, &p, jacobi_rot_bytes(m));
+    c->d_eigrot = p;
+  }
+  for (int k = 0; k < 6; ++k) ALLOC(c->d_small[k], (size_t)Imax * Imax);
+  ALLOC(c->d_gate, 4);
   if (s == SKY_OK) {
     c->eig_grid = jacobi_max_grid(c);
     ALLOC(c->d_eigpart, (size_t)2 * c->eig_grid);

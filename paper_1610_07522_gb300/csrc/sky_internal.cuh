@@ -85,14 +85,17 @@ struct Ctx {
   double2* d_fcx;                   // complex field scratch [G]
   double2* d_gpart;                 // split-K partials of sky_overlap
   size_t gpart_elems;
+  int ov_slots;                     // resident CTAs of the overlap kernel
   double2* d_eigA[2];               // Jacobi ping-pong matrices [m*m]
   double2* d_eigV;                  // Jacobi rotations accumulated [m*m]
   double* d_eigw;                   // eigenvalues [m]
   double* d_eigpart;                // per-block partial norms
   unsigned* d_bar;                  // grid barrier {count, generation}
   int* d_eigres;                    // which ping-pong buffer holds the result
+  void* d_eigrot;                   // Jacobi rotations of two consecutive rounds
   int eig_grid;                     // co-resident blocks of the Jacobi kernel
-  double2* d_small[3];              // I x I temporaries
+  double2* d_small[6];              // I x I temporaries
+  int* d_gate;                      // device-side gates of the Loewdin paths [4]
   char err[256];
 };
 
@@ -128,13 +131,16 @@ sky_status sp_spread_impl(Ctx* c, const double* eps, const double* hn2, int A, d
 sky_status overlap_impl(Ctx* c, const void* a, const void* b, int I, double2* X);
 sky_status rotate_impl(Ctx* c, const void* phi, const double2* M, int I, void* out);
 sky_status zgemm_small(Ctx* c, bool ah, bool bh, const double2* A, const double2* B,
-                       double2* C, int n);
-sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z);
+                       double2* C, int n, const int* run = nullptr, const int* stop = nullptr);
+sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z,
+                     const int* run = nullptr);
 sky_status lowdin_impl(Ctx* c, const double2* S, int I, double2* C);
 sky_status subspace_impl(Ctx* c, const double2* H, const double2* C, int I, double2* M,
                          double* eps);
 int jacobi_max_grid(Ctx* c);
-size_t overlap_partial_elems(int I, long long V, int num_sms);
+size_t jacobi_rot_bytes(int m);
+size_t overlap_partial_elems(int I, long long V, int slots);
+int overlap_slots(int num_sms);
 
 }  // namespace sky
 

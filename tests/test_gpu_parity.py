@@ -321,3 +321,23 @@ def test_iterations_24cubed_280n120p_coulomb():
     w = IN.WORKLOADS["sly4_24cubed_280n120p_coulomb_fp64"]
     inp = IN.make_inputs(w)
     _compare_runs(_gpu_run(w, inp, 2), _oracle_run(w, inp, 2))
+
+
+@pytest.mark.parametrize("eta", [1e-3, 0.02, 0.5, 15.0])
+def test_loewdin_both_routes(eta):
+    """Near-orthonormal states (||S - I||_F < 1/2: Newton-Schulz route) and
+    strongly non-orthonormal ones (eigendecomposition route) give the oracle's
+    S^{-1/2}."""
+    rng = np.random.default_rng(int(eta * 1e4))
+    with Ctx((16, 16, 16)) as c:
+        g = c.grid
+        I = 40
+        psi = O.orthonormalize(IN.random_superpositions(g.n, g.dx, I, rng), g)
+        phi = psi + eta * IN.random_superpositions(g.n, g.dx, I, rng) / np.sqrt(g.L[0] ** 3) / 10
+        S = O.overlap(phi, phi, g)
+        C = torch.zeros((I, I), dtype=torch.complex128, device="cuda:0")
+        B.sky_orthonormalize(c.ctx, dev(S), I, C)
+        B.sky_sync(c.ctx)
+        Cg = host(C)
+        assert relerr(Cg, O.loewdin(S)) < 1e-11
+        assert np.max(np.abs(Cg.conj().T @ S @ Cg - np.eye(I))) < 1e-11
