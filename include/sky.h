@@ -87,6 +87,13 @@ sky_status sky_set_stream(sky_ctx* ctx, void* stream);
 /* Wait for the context's stream; return and clear the device status word. */
 sky_status sky_sync(sky_ctx* ctx);
 
+/* Solver counters of the context (waits for its stream): out[0] Jacobi
+ * eigensolves run, out[1] Jacobi sweeps in total, out[2] sweeps of the last
+ * eigensolve, out[3] Loewdin factors computed, out[4] of them by the
+ * Newton-Schulz route, out[5] Newton-Schulz iterations in total, out[6..7]
+ * reserved (0).  reset != 0 clears them afterwards. */
+sky_status sky_stats(sky_ctx* ctx, long long out[8], int reset);
+
 /* Human-readable text of the last error the context saw (never NULL). */
 const char* sky_last_error(const sky_ctx* ctx);
 

@@ -45,6 +45,7 @@ _SIGNATURES = {
     "sky_last_error": (ctypes.c_char_p, [_P]),
     "sky_supported_size": (_I, [_I, _I]),
     "sky_kernel_launches": (ctypes.c_ulonglong, []),
+    "sky_stats": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), _I]),
     "sky_apply_h": (_I, [_P, _P, _P, _P, _P, _P, _I, _P, _P]),
     "sky_damped_step": (_I, [_P, _I, _P, _P, _P, _P, _I, _D, _D, _P]),
     "sky_overlap": (_I, [_P, _P, _P, _I, _P]),
@@ -130,6 +131,15 @@ def sky_sync(ctx):
 
 def sky_supported_size(n, prec):
     return bool(lib().sky_supported_size(int(n), int(prec)))
+
+
+def sky_stats(ctx, reset=False):
+    """Solver counters: dict of Jacobi solves / sweeps and Loewdin routes."""
+    buf = (ctypes.c_longlong * 8)()
+    _check(ctx, lib().sky_stats(ctx, buf, 1 if reset else 0))
+    keys = ("jacobi_solves", "jacobi_sweeps", "jacobi_last_sweeps", "loewdin_calls",
+            "loewdin_newton_schulz", "newton_schulz_iters")
+    return {k: int(buf[i]) for i, k in enumerate(keys)}
 
 
 def sky_kernel_launches():

@@ -57,19 +57,24 @@ sky_status overlap_impl(Ctx* c, const void* a, const void* b, int I, double2* X)
 
 // ---------------------------------------------------------------- rotate
 // out[a][v] = sum_b M[b][a] phi[b][v]; tile rows a (32) x columns v (32).
+// Three real products per complex multiply-add (Gauss):
+//   P1 = sum m.x f.x,  P2 = sum m.y f.y,  P3 = sum (m.x + m.y)(f.x + f.y),
+//   Re = P1 - P2,  Im = P3 - P1 - P2.
 template <typename S>
 __global__ void __launch_bounds__(256) k_rotate(const S* __restrict__ phi, const double2* __restrict__ M,
                                                 int I, long long V, S* __restrict__ out) {
   __shared__ double2 As[BK][BM + 1];
   __shared__ double2 Bs[BK][BN + 1];
+  __shared__ double Ad[BK][BM + 1];
+  __shared__ double Bd[BK][BN + 1];
   const int r0 = blockIdx.y * BM;
   const long long v0 = (long long)blockIdx.x * BN;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  double2 acc[2][2];
+  double p1[2][2], p2[2][2], p3[2][2];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
+    for (int j = 0; j < 2; ++j) p1[i][j] = p2[i][j] = p3[i][j] = 0.0;
   for (int k0 = 0; k0 < I; k0 += BK) {
     // 16 k x 32 entries per operand, 2 per thread, contiguous along the tile row
 #pragma unroll
@@ -79,18 +84,33 @@ __global__ void __launch_bounds__(256) k_rotate(const S* __restrict__ phi, const
       const int k = k0 + kk;
       const int a = r0 + col;
       const long long v = v0 + col;
-      As[kk][col] = (k < I && a < I) ? M[(long long)k * I + a] : make_double2(0.0, 0.0);
-      Bs[kk][col] = (k < I && v < V) ? ld2(phi + (long long)k * V + v) : make_double2(0.0, 0.0);
+      const double2 mv = (k < I && a < I) ? M[(long long)k * I + a] : make_double2(0.0, 0.0);
+      const double2 fv = (k < I && v < V) ? ld2(phi + (long long)k * V + v) : make_double2(0.0, 0.0);
+      As[kk][col] = mv;
+      Ad[kk][col] = mv.x + mv.y;
+      Bs[kk][col] = fv;
+      Bd[kk][col] = fv.x + fv.y;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      const double2 a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
-      const double2 b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-      cfma(acc[0][0], a0, b0);
-      cfma(acc[0][1], a0, b1);
-      cfma(acc[1][0], a1, b0);
-      cfma(acc[1][1], a1, b1);
+      double2 a[2], b[2];
+      double ad[2], bd[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        a[i] = As[kk][ty * 2 + i];
+        ad[i] = Ad[kk][ty * 2 + i];
+        b[i] = Bs[kk][tx * 2 + i];
+        bd[i] = Bd[kk][tx * 2 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          p1[i][j] = fma(a[i].x, b[j].x, p1[i][j]);
+          p2[i][j] = fma(a[i].y, b[j].y, p2[i][j]);
+          p3[i][j] = fma(ad[i], bd[j], p3[i][j]);
+        }
     }
     __syncthreads();
   }
@@ -101,10 +121,11 @@ __global__ void __launch_bounds__(256) k_rotate(const S* __restrict__ phi, const
       const int r = r0 + ty * 2 + i;
       const long long v = v0 + tx * 2 + j;
       if (r < I && v < V) {
+        const double re = p1[i][j] - p2[i][j], im = p3[i][j] - p1[i][j] - p2[i][j];
         if constexpr (std::is_same<S, double2>::value)
-          out[(long long)r * V + v] = acc[i][j];
+          out[(long long)r * V + v] = make_double2(re, im);
         else
-          out[(long long)r * V + v] = make_float2((float)acc[i][j].x, (float)acc[i][j].y);
+          out[(long long)r * V + v] = make_float2((float)re, (float)im);
       }
     }
 }

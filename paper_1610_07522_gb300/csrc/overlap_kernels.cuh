@@ -37,12 +37,18 @@ __device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
 }
 
 // part[split][a][b] = sum_{v in split} conj(A[a][v]) Bm[b][v] for the lower tiles.
+// Three real products per complex multiply-add (Gauss):
+//   P1 = sum a.x b.x,  P2 = sum a.y b.y,  P3 = sum (a.x - a.y)(b.x + b.y),
+//   Re = P1 + P2,  Im = P3 - P1 + P2;
+// the sums a.x - a.y and b.x + b.y are formed once when staging the tile.
 template <typename S>
 __global__ void __launch_bounds__(256) k_overlap(const S* __restrict__ A, const S* __restrict__ Bm,
                                                  int I, long long V, long long kchunk,
                                                  double2* __restrict__ part) {
   __shared__ double2 As[BK][BM + 1];
   __shared__ double2 Bs[BK][BN + 1];
+  __shared__ double Ad[BK][BM + 1];
+  __shared__ double Bd[BK][BN + 1];
   int ti, tj;
   tri_tile(blockIdx.x, ti, tj);
   const int r0 = ti * BM, c0 = tj * BN;
@@ -50,28 +56,43 @@ __global__ void __launch_bounds__(256) k_overlap(const S* __restrict__ A, const 
   const long long ke = (kb + kchunk) < V ? (kb + kchunk) : V;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int lrow = tid >> 3, lk = (tid & 7) * 2;   // loader: 32 rows x 16 k
-  double2 acc[2][2];
+  double p1[2][2], p2[2][2], p3[2][2];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
+    for (int j = 0; j < 2; ++j) p1[i][j] = p2[i][j] = p3[i][j] = 0.0;
   for (long long k0 = kb; k0 < ke; k0 += BK) {
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const long long k = k0 + lk + u;
       const int ra = r0 + lrow, rb = c0 + lrow;
-      As[lk + u][lrow] = (ra < I && k < ke) ? ld2(A + (long long)ra * V + k) : make_double2(0.0, 0.0);
-      Bs[lk + u][lrow] = (rb < I && k < ke) ? ld2(Bm + (long long)rb * V + k) : make_double2(0.0, 0.0);
+      const double2 av = (ra < I && k < ke) ? ld2(A + (long long)ra * V + k) : make_double2(0.0, 0.0);
+      const double2 bv = (rb < I && k < ke) ? ld2(Bm + (long long)rb * V + k) : make_double2(0.0, 0.0);
+      As[lk + u][lrow] = av;
+      Ad[lk + u][lrow] = av.x - av.y;
+      Bs[lk + u][lrow] = bv;
+      Bd[lk + u][lrow] = bv.x + bv.y;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      const double2 a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
-      const double2 b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-      cfma_conj(acc[0][0], a0, b0);
-      cfma_conj(acc[0][1], a0, b1);
-      cfma_conj(acc[1][0], a1, b0);
-      cfma_conj(acc[1][1], a1, b1);
+      double2 a[2], b[2];
+      double ad[2], bd[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        a[i] = As[kk][ty * 2 + i];
+        ad[i] = Ad[kk][ty * 2 + i];
+        b[i] = Bs[kk][tx * 2 + i];
+        bd[i] = Bd[kk][tx * 2 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          p1[i][j] = fma(a[i].x, b[j].x, p1[i][j]);
+          p2[i][j] = fma(a[i].y, b[j].y, p2[i][j]);
+          p3[i][j] = fma(ad[i], bd[j], p3[i][j]);
+        }
     }
     __syncthreads();
   }
@@ -81,7 +102,8 @@ __global__ void __launch_bounds__(256) k_overlap(const S* __restrict__ A, const 
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int r = r0 + ty * 2 + i, cc = c0 + tx * 2 + j;
-      if (r < I && cc < I && r >= cc) dst[(long long)r * I + cc] = acc[i][j];
+      if (r < I && cc < I && r >= cc)
+        dst[(long long)r * I + cc] = make_double2(p1[i][j] + p2[i][j], p3[i][j] - p1[i][j] + p2[i][j]);
     }
 }
 

@@ -75,7 +75,8 @@ static void free_all(Ctx* c) {
                   c->d_coul, c->d_gscr, c->d_red, c->d_dpart, c->d_ftmp, c->d_fcx, c->d_gpart,
                   c->d_eigA[0], c->d_eigA[1], c->d_eigV, c->d_eigw, c->d_eigpart, c->d_bar,
                   c->d_eigres, c->d_eigrot, c->d_small[0], c->d_small[1], c->d_small[2],
-                  c->d_small[3], c->d_small[4], c->d_small[5], c->d_gate};
+                  c->d_small[3], c->d_small[4], c->d_small[5], c->d_gate,
+                  c->d_stats};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -187,7 +188,8 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
     c->d_eigrot = p;
   }
   for (int k = 0; k < 6; ++k) ALLOC(c->d_small[k], (size_t)Imax * Imax);
-  ALLOC(c->d_gate, 4);
+  ALLOC(c->d_gate, 8);
+  ALLOC(c->d_stats, 8);
   if (s == SKY_OK) {
     c->eig_grid = jacobi_max_grid(c);
     ALLOC(c->d_eigpart, (size_t)2 * c->eig_grid);
@@ -214,6 +216,7 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
     }
   }
   if (s == SKY_OK) s = cuda_check(c, cudaMemset(c->d_status, 0, sizeof(int)), "status reset");
+  if (s == SKY_OK) s = cuda_check(c, cudaMemset(c->d_stats, 0, 8 * sizeof(long long)), "stats reset");
   if (s == SKY_OK) s = cuda_check(c, cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned)), "barrier reset");
   if (s == SKY_OK) s = upload_twiddles_hamiltonian(c);
   if (s == SKY_OK) s = upload_twiddles_fields(c);
@@ -260,6 +263,15 @@ sky_status sky_sync(sky_ctx* c) {
 }
 
 const char* sky_last_error(const sky_ctx* c) { return c ? c->err : "null context"; }
+
+sky_status sky_stats(sky_ctx* c, long long out[8], int reset) {
+  if (!c || !out) return SKY_EINVAL;
+  cudaError_t e = cudaMemcpyAsync(out, c->d_stats, 8 * sizeof(long long), cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e == cudaSuccess && reset) e = cudaMemsetAsync(c->d_stats, 0, 8 * sizeof(long long), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return cuda_check(c, e, "stats");
+}
 
 #define CHECK_CTX()                                     \
   if (!c) return SKY_EINVAL;                            \

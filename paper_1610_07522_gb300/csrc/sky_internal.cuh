@@ -95,7 +95,8 @@ struct Ctx {
   void* d_eigrot;                   // Jacobi rotations of two consecutive rounds
   int eig_grid;                     // co-resident blocks of the Jacobi kernel
   double2* d_small[6];              // I x I temporaries
-  int* d_gate;                      // device-side gates of the Loewdin paths [4]
+  int* d_gate;                      // device-side gates of the Loewdin paths [8]
+  long long* d_stats;               // solver counters reported by sky_stats [8]
   char err[256];
 };
 

@@ -341,3 +341,65 @@ def test_loewdin_both_routes(eta):
         Cg = host(C)
         assert relerr(Cg, O.loewdin(S)) < 1e-11
         assert np.max(np.abs(Cg.conj().T @ S @ Cg - np.eye(I))) < 1e-11
+
+
+# ------------------------------------------------------------------ FP32 form
+# Spinors stored as complex64 with FP32 FFTs; matrices, reductions and fields
+# FP64.  The oracle runs in FP64 on the same FP32-rounded inputs, so the
+# differences are the kernels' FP32 arithmetic only.  FFT-based results:
+# within 4e-6 of the largest magnitude (single-precision rounding times the
+# log2 n passes of each transform); FP64-accumulated contractions of FP32
+# inputs: 1e-12 (no FP32 arithmetic involved).
+REL32 = 4e-6
+
+
+def _r32(a):
+    return a.astype(np.complex64).astype(np.complex128)
+
+
+def dev32(a):
+    return torch.from_numpy(np.ascontiguousarray(a.astype(np.complex64))).to("cuda:0")
+
+
+@pytest.mark.parametrize("case", [CASES[2], CASES[3], ((32, 32, 32), (1.0, 1.0, 1.0), (0.5, 0.0, -0.5)),
+                                  ((64, 48, 16), (1.0, 1.0, 1.0), (0.0, 0.0, 0.0))])
+def test_fp32_apply_h_damped_densities(case):
+    rng = np.random.default_rng(21)
+    with Ctx(*case, prec=B.SKY_F32) as c:
+        g = c.grid
+        I = 3
+        psi = _r32(IN.random_spinors(g.n, I, rng))
+        U, Bf, W = _fields(g, rng)
+        want = O.apply_h(psi, U, Bf, W, g)
+        d_h = torch.zeros(psi.shape, dtype=torch.complex64, device="cuda:0")
+        eps = torch.zeros(I, dtype=torch.float64, device="cuda:0")
+        B.sky_apply_h(c.ctx, dev(U), dev(Bf), dev(W), dev32(psi), d_h, I, eps, None)
+        assert relerr(host(d_h), want) < REL32
+        assert relerr(host(eps), O.sp_energies(psi, want, g)[0]) < REL32
+        hpsi = _r32(want)
+        e = rng.uniform(-40, 10, I)
+        phi = torch.zeros(psi.shape, dtype=torch.complex64, device="cuda:0")
+        B.sky_damped_step(c.ctx, 1, dev32(psi), dev32(hpsi), dev(e), phi, I, 0.45, 100.0)
+        assert relerr(host(phi), O.damped_step(psi, hpsi, e, g, P["hb2m_p"], 0.45, 100.0)) < REL32
+        z = lambda n: torch.zeros(n, dtype=torch.float64, device="cuda:0")
+        rho, tau, J, dJ = z(g.G), z(g.G), z(3 * g.G), z(g.G)
+        B.sky_densities(c.ctx, dev32(psi), I, rho, tau, J, dJ)
+        rw, tw, Jw, dJw = O.densities(psi, g)
+        assert relerr(host(rho), rw.ravel()) < REL32
+        assert relerr(host(tau), tw.ravel()) < REL32
+        assert relerr(host(J), Jw.ravel()) < REL32
+
+
+def test_fp32_overlap_and_rotate():
+    rng = np.random.default_rng(22)
+    with Ctx((32, 32, 32), prec=B.SKY_F32, max_states=70) as c:
+        g = c.grid
+        I = 67
+        a, b = _r32(IN.random_spinors(g.n, I, rng)), _r32(IN.random_spinors(g.n, I, rng))
+        X = torch.zeros((I, I), dtype=torch.complex128, device="cuda:0")
+        B.sky_overlap(c.ctx, dev32(a), dev32(b), I, X)
+        assert relerr(host(X), O.overlap(a, b, g)) < 1e-12
+        M = rng.standard_normal((I, I)) + 1j * rng.standard_normal((I, I))
+        out = torch.zeros(a.shape, dtype=torch.complex64, device="cuda:0")
+        B.sky_rotate(c.ctx, dev32(a), dev(M), I, out)
+        assert relerr(host(out), O.rotate(a, M)) < 1e-6
