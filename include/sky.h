@@ -50,7 +50,10 @@ typedef enum {
 
 typedef enum {
   SKY_F64 = 0,          /* complex double spinors, FP64 everywhere               */
-  SKY_F32 = 1           /* complex float spinors; matrices and sums FP64         */
+  SKY_F32 = 1,          /* complex float spinors; matrices and sums FP64         */
+  SKY_F32_BF16X3 = 2,   /* as SKY_F32, with the overlap and recombination on the
+                           tensor cores: 2-way bf16 split, 3 products, FP32 sums */
+  SKY_F32_BF16X6 = 3    /* as SKY_F32_BF16X3 with a 3-way split and 6 products   */
 } sky_prec;
 
 /* Skyrme parameters (Eq. Skyrme; the paper fits them without printing them).

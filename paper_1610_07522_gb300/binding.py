@@ -16,7 +16,7 @@ from . import build as _build
 SKY_OK, SKY_EINVAL, SKY_ENOMEM, SKY_ECUDA, SKY_ENOTPD, SKY_ENOCONV, SKY_ETIMEOUT, SKY_ENAN, SKY_EUNSUPPORTED = range(9)
 STATUS_NAMES = ["SKY_OK", "SKY_EINVAL", "SKY_ENOMEM", "SKY_ECUDA", "SKY_ENOTPD",
                 "SKY_ENOCONV", "SKY_ETIMEOUT", "SKY_ENAN", "SKY_EUNSUPPORTED"]
-SKY_F64, SKY_F32 = 0, 1
+SKY_F64, SKY_F32, SKY_F32_BF16X3, SKY_F32_BF16X6 = 0, 1, 2, 3
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int

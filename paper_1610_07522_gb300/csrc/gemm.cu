@@ -32,6 +32,7 @@ size_t overlap_partial_elems(int I, long long V, int slots) {
 }
 
 sky_status overlap_impl(Ctx* c, const void* a, const void* b, int I, double2* X) {
+  if (is_tc(c->prec)) return tc_overlap(c, a, b, I, X);
   const long long V = 2LL * c->G;
   int ntiles;
   const int nsplit = overlap_splits(I, V, c->ov_slots, &ntiles);
@@ -131,6 +132,7 @@ __global__ void __launch_bounds__(256) k_rotate(const S* __restrict__ phi, const
 }
 
 sky_status rotate_impl(Ctx* c, const void* phi, const double2* M, int I, void* out) {
+  if (is_tc(c->prec)) return tc_rotate(c, phi, M, I, out);
   const long long V = 2LL * c->G;
   dim3 grid(div_up(V, BN), div_up(I, BM));
   if (c->prec == SKY_F64)

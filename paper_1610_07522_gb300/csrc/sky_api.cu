@@ -31,7 +31,7 @@ sky_status build_coulomb_table(Ctx* c);   // fields.cu
 static bool size_ok(int n, sky_prec p) {
   switch (n) {
     case 8: case 12: case 16: case 20: case 24: case 32: return true;
-    case 48: case 64: return p == SKY_F32;
+    case 48: case 64: return p != SKY_F64;
     default: return false;
   }
 }
@@ -76,7 +76,9 @@ static void free_all(Ctx* c) {
                   c->d_eigA[0], c->d_eigA[1], c->d_eigV, c->d_eigw, c->d_eigpart, c->d_bar,
                   c->d_eigres, c->d_eigrot, c->d_small[0], c->d_small[1], c->d_small[2],
                   c->d_small[3], c->d_small[4], c->d_small[5], c->d_gate,
-                  c->d_stats};
+                  c->d_stats, c->d_tcA[0], c->d_tcA[1], c->d_tcA[2], c->d_tcB[0],
+                  c->d_tcB[1], c->d_tcB[2], c->d_tcRotA[0], c->d_tcRotA[1], c->d_tcRotA[2],
+                  c->d_tcPart};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -105,7 +107,8 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   if (!out) return SKY_EINVAL;
   *out = nullptr;
   if (!grid || !dx || !params || max_states < 0) return SKY_EINVAL;
-  if (prec != SKY_F64 && prec != SKY_F32) return SKY_EUNSUPPORTED;
+  if (prec != SKY_F64 && prec != SKY_F32 && prec != SKY_F32_BF16X3 && prec != SKY_F32_BF16X6)
+    return SKY_EUNSUPPORTED;
   for (int j = 0; j < 3; ++j) {
     if (!size_ok(grid[j], prec)) return SKY_EUNSUPPORTED;
     if (!(dx[j] > 0.0)) return SKY_EINVAL;
@@ -189,6 +192,20 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   }
   for (int k = 0; k < 6; ++k) ALLOC(c->d_small[k], (size_t)Imax * Imax);
   ALLOC(c->d_gate, 8);
+  if (s == SKY_OK && is_tc(prec)) {
+    size_t pa, pb, pra, part;
+    tc_scratch_sizes(Imax, V, c->num_sms, &pa, &pb, &pra, &part);
+    const int n = tc_nsplit(prec);
+    for (int k = 0; k < n && s == SKY_OK; ++k) {
+      unsigned short *x = nullptr, *y = nullptr, *z = nullptr;
+      s = dalloc(c, &x, pa);
+      if (s == SKY_OK) s = dalloc(c, &y, pb);
+      if (s == SKY_OK) s = dalloc(c, &z, pra);
+      c->d_tcA[k] = x; c->d_tcB[k] = y; c->d_tcRotA[k] = z;
+    }
+    ALLOC(c->d_tcPart, part);
+    c->tc_partial_elems = part;
+  }
   ALLOC(c->d_stats, 8);
   if (s == SKY_OK) {
     c->eig_grid = jacobi_max_grid(c);

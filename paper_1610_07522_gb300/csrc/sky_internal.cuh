@@ -95,6 +95,11 @@ struct Ctx {
   void* d_eigrot;                   // Jacobi rotations of two consecutive rounds
   int eig_grid;                     // co-resident blocks of the Jacobi kernel
   double2* d_small[6];              // I x I temporaries
+  void* d_tcA[3];                   // split-BF16 operand pieces (tensor-core forms)
+  void* d_tcB[3];
+  void* d_tcRotA[3];
+  float* d_tcPart;                  // split-K partial tiles of the tensor-core overlap
+  size_t tc_partial_elems;
   int* d_gate;                      // device-side gates of the Loewdin paths [8]
   long long* d_stats;               // solver counters reported by sky_stats [8]
   char err[256];
@@ -139,6 +144,12 @@ sky_status lowdin_impl(Ctx* c, const double2* S, int I, double2* C);
 sky_status subspace_impl(Ctx* c, const double2* H, const double2* C, int I, double2* M,
                          double* eps);
 int jacobi_max_grid(Ctx* c);
+int tc_nsplit(sky_prec p);
+void tc_scratch_sizes(int I, long long V, int num_sms, size_t* piece_a, size_t* piece_b,
+                      size_t* piece_rot_a, size_t* partial);
+sky_status tc_overlap(Ctx* c, const void* a, const void* b, int I, double2* X);
+sky_status tc_rotate(Ctx* c, const void* phi, const double2* M, int I, void* out);
+inline bool is_tc(sky_prec p) { return p == SKY_F32_BF16X3 || p == SKY_F32_BF16X6; }
 size_t jacobi_rot_bytes(int m);
 size_t overlap_partial_elems(int I, long long V, int slots);
 int overlap_slots(int num_sms);

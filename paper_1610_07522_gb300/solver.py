@@ -25,7 +25,7 @@ class Solver:
         self.w = workload
         self.device = torch.device(device)
         self.prec = prec
-        self.cdtype = torch.complex128 if prec == B.SKY_F64 else torch.complex64
+        self.cdtype = torch.complex128 if prec == B.SKY_F64 else torch.complex64   # FP32 forms
         nx, ny, nz = workload.grid
         self.shape = (nz, ny, nx)
         self.G = nx * ny * nz

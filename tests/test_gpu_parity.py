@@ -403,3 +403,75 @@ def test_fp32_overlap_and_rotate():
         out = torch.zeros(a.shape, dtype=torch.complex64, device="cuda:0")
         B.sky_rotate(c.ctx, dev32(a), dev(M), I, out)
         assert relerr(host(out), O.rotate(a, M)) < 1e-6
+
+
+# ------------------------------------------------------------ split-BF16 forms
+# Tensor-core contractions of FP32 spinors.  A 2-way bf16 split with 3 products
+# keeps ~16 significant bits per product (error ~2^-17 of the summed |terms|);
+# a 3-way split with 6 products keeps ~24 bits, which leaves the tensor cores'
+# FP32 accumulation as the limit: a systematic bias of up to ~1e-5 of the
+# largest entry over the ~1000-term runs of one K-split (measured 8.7e-6 at
+# 24^3, I = 150).  Tolerances relative to the largest entry.
+TC_TOL = {B.SKY_F32_BF16X3: 4e-5, B.SKY_F32_BF16X6: 2e-5}
+
+
+@pytest.mark.parametrize("prec", [B.SKY_F32_BF16X3, B.SKY_F32_BF16X6])
+@pytest.mark.parametrize("grid,I", [((16, 16, 16), 37), ((24, 24, 24), 150), ((12, 16, 20), 5)])
+def test_tc_overlap_and_rotate(prec, grid, I):
+    rng = np.random.default_rng(31 + I)
+    with Ctx(grid, prec=prec, max_states=I) as c:
+        g = c.grid
+        a = _r32(O.orthonormalize(IN.random_superpositions(g.n, g.dx, I, rng), g))
+        b = _r32(a + 0.05 * IN.random_spinors(g.n, I, rng) / np.sqrt(g.G))
+        X = torch.zeros((I, I), dtype=torch.complex128, device="cuda:0")
+        B.sky_overlap(c.ctx, dev32(a), dev32(b), I, X)
+        B.sky_sync(c.ctx)
+        assert relerr(host(X), O.overlap(a, b, g)) < TC_TOL[prec]
+        B.sky_overlap(c.ctx, dev32(a), dev32(a), I, X)
+        Xg = host(X)
+        assert relerr(Xg, O.overlap(a, a, g)) < TC_TOL[prec]
+        off = ~np.eye(I, dtype=bool)
+        assert np.max(np.abs((Xg - Xg.conj().T)[off])) == 0.0   # mirrored lower triangle
+        M = (rng.standard_normal((I, I)) + 1j * rng.standard_normal((I, I))) / np.sqrt(I)
+        out = torch.zeros(a.shape, dtype=torch.complex64, device="cuda:0")
+        B.sky_rotate(c.ctx, dev32(a), dev(M), I, out)
+        assert relerr(host(out), O.rotate(a, M)) < TC_TOL[prec]
+
+
+# Per-nucleon energy and level bounds of the FP32 forms over eight iterations
+# of the 16^3 workload (E passes through zero there, so bounds are absolute).
+FORM_TOL = {B.SKY_F32: (5e-6, 5e-4), B.SKY_F32_BF16X3: (5e-5, 5e-3), B.SKY_F32_BF16X6: (5e-6, 5e-4)}
+
+
+@pytest.mark.parametrize("prec", [B.SKY_F32, B.SKY_F32_BF16X3, B.SKY_F32_BF16X6])
+def test_fp32_forms_follow_the_fp64_iteration(prec):
+    """Eight iterations of the 16^3, 16 n + 16 p workload in the FP32 forms stay
+    within the stated distance of the FP64 oracle: |dE|/A (MeV) and the
+    single-particle levels (MeV); also reports rho and orthonormality errors."""
+    from paper_1610_07522_gb300.solver import Solver
+    e_tol, lam_tol = FORM_TOL[prec]
+    w = IN.WORKLOADS["sly4_16cubed_16n16p_fp64"]
+    inp = IN.make_inputs(w)
+    s = Solver(w, prec=prec)
+    s.load(inp["psi0"])
+    ora = _oracle_run(w, inp, 8)
+    A = w.N + w.Z
+    worst = {"dE/A": 0.0, "dlam": 0.0, "drho": 0.0}
+    for k in range(8):
+        s.step()
+        E, de, _ = s.energy()
+        lam = host(s.lam)
+        dE = abs(E - ora[k]["E"]) / A
+        dl = max(np.max(np.abs(np.sort(lam[:w.N]) - np.sort(ora[k]["lam"][0]))),
+                 np.max(np.abs(np.sort(lam[w.N:]) - np.sort(ora[k]["lam"][1]))))
+        dr = relerr(host(s.rho), ora[k]["rho"].reshape(2, -1))
+        worst = {"dE/A": max(worst["dE/A"], dE), "dlam": max(worst["dlam"], dl),
+                 "drho": max(worst["drho"], dr)}
+        assert dE <= e_tol, (k, E, ora[k]["E"])
+        assert dl <= lam_tol, k
+    g = O.Grid(w.grid, w.dx)
+    psi = [host(s.psi[q]).astype(np.complex128) for q in range(2)]
+    ortho = max(np.max(np.abs(O.overlap(p, p, g) - np.eye(p.shape[0]))) for p in psi)
+    print(f"form {prec}: max |dE|/A {worst['dE/A']:.2e} MeV, max |d eps| {worst['dlam']:.2e} MeV, "
+          f"rho rel {worst['drho']:.2e}, ||Psi^H Psi - I||_max {ortho:.2e}")
+    s.close()
