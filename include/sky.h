@@ -147,6 +147,18 @@ sky_status sky_orthonormalize(sky_ctx* ctx, const double* S, int I, double* C);
 sky_status sky_subspace_diag(sky_ctx* ctx, const double* H, const double* C, int I,
                              double* M, double* eps);
 
+/* ---- Steps 3b-3d for several independent species at once --------------------
+ * The same operations as sky_orthonormalize and sky_subspace_diag for nb
+ * problems (1 <= nb <= 2, e.g. neutrons and protons, which interact only
+ * through the mean field, Sec. 3.2), solved together in one batched launch
+ * sequence.  S, H, C, M, eps, I are HOST arrays of nb entries; the matrices
+ * they point to are device memory as above. */
+sky_status sky_orthonormalize_batched(sky_ctx* ctx, int nb, const double* const* S, const int* I,
+                                      double* const* C);
+sky_status sky_subspace_diag_batched(sky_ctx* ctx, int nb, const double* const* H,
+                                     const double* const* C, const int* I, double* const* M,
+                                     double* const* eps);
+
 /* ---- Step 3e: recombination (Sec. 3.3.3, Fig. 3) ---------------------------
  * psi_out[a] = sum_b M[b*I + a] phi[b] for all V entries.  phi, psi_out:
  * [I][2][G] and must not overlap.  Also the Loewdin application of

@@ -57,6 +57,9 @@ _SIGNATURES = {
     "sky_energy": (_I, [_P, _P, _P, _P, _P]),
     "sky_sp_spread": (_I, [_P, _P, _P, _I, _P]),
     "sky_overlap_noalloc": (_I, [_P, _P, _I, ctypes.c_longlong, _D, _I, _P, _P]),
+    "sky_orthonormalize_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_P)]),
+    "sky_subspace_diag_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I),
+                                       ctypes.POINTER(_P), ctypes.POINTER(_P)]),
 }
 
 _LIB = None
@@ -166,6 +169,21 @@ def sky_orthonormalize(ctx, S, I, C):
 
 def sky_subspace_diag(ctx, H, C, I, M, eps):
     _check(ctx, lib().sky_subspace_diag(ctx, _ptr(H), _ptr(C), int(I), _ptr(M), _ptr(eps)))
+
+
+def _ptrs(xs):
+    return (_P * len(xs))(*[_ptr(x) for x in xs])
+
+
+def sky_orthonormalize_batched(ctx, S, I, C):
+    n = len(I)
+    _check(ctx, lib().sky_orthonormalize_batched(ctx, n, _ptrs(S), (_I * n)(*I), _ptrs(C)))
+
+
+def sky_subspace_diag_batched(ctx, H, C, I, M, eps):
+    n = len(I)
+    _check(ctx, lib().sky_subspace_diag_batched(ctx, n, _ptrs(H), _ptrs(C), (_I * n)(*I), _ptrs(M),
+                                                _ptrs(eps)))
 
 
 def sky_rotate(ctx, phi, M, I, psi_out):

@@ -173,20 +173,33 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, int
   return s_ok != 0;
 }
 
-struct JacArgs {
+// ---- batched solve -----------------------------------------------------------
+// Up to kMaxBatch independent Hermitian problems share one cooperative launch:
+// every round serves all unfinished problems, so the fixed cost of a round
+// (grid barrier, memory latency) is paid once for the batch.  Problem b works in
+// its own slices of the workspace; its rounds follow its own size m_b.
+struct JacProb {
   double2* A0; double2* A1; double2* V;
   JRot* R0; JRot* R1;   // rotations of the current / next round, [m/2] each
   int n, m;
+};
+
+struct JacBatch {
+  JacProb p[kMaxBatch];
+  long long off[kMaxBatch + 1];   // work items per round, prefix over problems
+  int np;
   double tol;
   int max_sweeps;
-  double* part;         // [gridDim.x][2]
+  double* part;         // [np][gridDim.x][2] partial norms
   unsigned* bar;
   int* status;
-  int* result;          // 0: A0 holds the result, 1: A1
-  const int* run;       // device gate: skip the whole solve when *run == 0
+  int* result;          // [np] 0: A0 holds the result, 1: A1
+  const int* run;       // problem b runs iff run == null or run[b * run_stride] != 0
+  int run_stride;
   long long* stats;     // [0] solves, [1] sweeps in total, [2] sweeps of the last solve
 };
 
+// Per-block reduction of (off, tot) into part[2 * blockIdx.x] (blockDim == kJacThreads).
 __device__ __forceinline__ void block_norms(double off, double tot, double* part) {
   __shared__ double s_red[2][kJacThreads / 32];
 #pragma unroll
@@ -205,199 +218,255 @@ __device__ __forceinline__ void block_norms(double off, double tot, double* part
     part[2 * blockIdx.x] = x;
     part[2 * blockIdx.x + 1] = y;
   }
-}
-
-// Every block sums the partial norms in the same order: same decision everywhere.
-__device__ __forceinline__ bool decide_stop(const JacArgs& a, int sweep, double* thr) {
-  __shared__ int s_stop;
-  __shared__ double s_thr;
-  if (threadIdx.x == 0) {
-    double x = 0.0, y = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) { x += a.part[2 * b]; y += a.part[2 * b + 1]; }
-    int stop = (x <= a.tol * a.tol * y) || (y == 0.0);
-    if (!stop && sweep >= a.max_sweeps) {
-      flag_status(a.status, SKY_ENOCONV);
-      stop = 1;
-    }
-    s_stop = stop;
-    s_thr = 1e-19 * sqrt(y);     // rotations below this change nothing measurable
-  }
   __syncthreads();
-  *thr = s_thr;
-  return s_stop != 0;
 }
 
-__global__ void __launch_bounds__(kJacThreads) k_jacobi(JacArgs a) {
-  if (a.run && *a.run == 0) return;   // uniform across the grid: no barrier is entered
-  const int m = a.m, n = a.n, h = m / 2;
+// The same sums in every block, in the same order: the same decision everywhere.
+__device__ __forceinline__ void sum_parts(const double* part, double& off, double& tot) {
+  off = 0.0;
+  tot = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) { off += part[2 * b]; tot += part[2 * b + 1]; }
+}
+
+__global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
+  __shared__ int s_done[kMaxBatch], s_which[kMaxBatch], s_sweep[kMaxBatch];
+  __shared__ double s_thr[kMaxBatch];
+  __shared__ int s_active;
   const int gtid = blockIdx.x * kJacThreads + threadIdx.x;
   const int gsz = gridDim.x * kJacThreads;
-  double2* cur = a.A0;
-  double2* nxt = a.A1;
-  JRot* Rc = a.R0;
-  JRot* Rn = a.R1;
-  int which = 0;
+  const int np = a.np;
   unsigned epoch = 0;
-  // prologue: norms of the input
-  {
+  // ---- prologue: norms of every problem (||A||_F is invariant under the rotations)
+  for (int b = 0; b < np; ++b) {
+    const JacProb& P = a.p[b];
     double off = 0.0, tot = 0.0;
-    for (int e = gtid; e < n * n; e += gsz) {
-      const int i = e / n, j = e % n;
-      const double2 v = cur[(long long)i * m + j];
+    for (long long e = gtid; e < (long long)P.n * P.n; e += gsz) {
+      const int i = (int)(e / P.n), j = (int)(e % P.n);
+      const double2 v = P.A0[(long long)i * P.m + j];
       const double w2 = v.x * v.x + v.y * v.y;
       tot += w2;
       if (i != j) off += w2;
     }
-    block_norms(off, tot, a.part);
+    block_norms(off, tot, a.part + (long long)b * 2 * gridDim.x);
   }
   if (!grid_barrier(a.bar, epoch, a.status)) return;
-  double thr;
-  bool stop = decide_stop(a, 0, &thr);
+  if (threadIdx.x == 0) {
+    int active = 0;
+    for (int b = 0; b < np; ++b) {
+      double off, tot;
+      sum_parts(a.part + (long long)b * 2 * gridDim.x, off, tot);
+      const bool run = !a.run || a.run[b * a.run_stride] != 0;
+      s_done[b] = !run || (off <= a.tol * a.tol * tot) || (tot == 0.0) || a.p[b].m < 2;
+      s_thr[b] = 1e-19 * sqrt(tot);   // rotations below this change nothing measurable
+      s_which[b] = 0;
+      s_sweep[b] = 0;
+      active |= !s_done[b];
+    }
+    s_active = active;
+  }
+  __syncthreads();
   // rotations of round 0
-  for (int k = gtid; k < h; k += gsz) {
-    int p, q;
-    pair_of(k, 0, m, p, q);
-    Rc[k] = make_rot(cur[(long long)p * m + p].x, cur[(long long)q * m + q].x,
-                     cur[(long long)p * m + q], p, q, n, thr);
+  for (int b = 0; b < np; ++b) {
+    if (s_done[b]) continue;
+    const JacProb& P = a.p[b];
+    const int h = P.m / 2;
+    for (int k = gtid; k < h; k += gsz) {
+      int p, q;
+      pair_of(k, 0, P.m, p, q);
+      P.R0[k] = make_rot(P.A0[(long long)p * P.m + p].x, P.A0[(long long)q * P.m + q].x,
+                         P.A0[(long long)p * P.m + q], p, q, P.n, s_thr[b]);
+    }
   }
   if (!grid_barrier(a.bar, epoch, a.status)) return;
-  const int nblk = h * h, nV = m * h;
-  int sweeps_done = 0;
-  for (int sweep = 1; !stop; ++sweep) {
-    sweeps_done = sweep;
-    for (int r = 0; r < m - 1; ++r) {
+  double acc_off[kMaxBatch], acc_tot[kMaxBatch];
+  for (int t = 0; s_active; ++t) {
+#pragma unroll
+    for (int b = 0; b < kMaxBatch; ++b) acc_off[b] = acc_tot[b] = 0.0;
+    // Pair indices follow from (k, r) alone, so every item issues its matrix
+    // loads together with the rotation loads (one L2 round trip, not two).
+    for (long long w = gtid; w < a.off[np]; w += gsz) {
+      int b = 0;
+      while (w >= a.off[b + 1]) ++b;
+      if (s_done[b]) continue;
+      const JacProb& P = a.p[b];
+      const int m = P.m, n = P.n, h = m / 2;
+      const int r = t % (m - 1);
       const bool last = (r == m - 2);
       const int rn = last ? 0 : r + 1;
-      double off = 0.0, tot = 0.0;
-      // Pair indices follow from (k, r) alone, so every item issues its matrix
-      // loads together with the rotation loads (one L2 round trip, not two).
-      for (int w = gtid; w < nblk + nV + h; w += gsz) {
-        if (w < nblk) {
-          // 2x2 block (P1 rows, P2 columns): B' = J1^H B J2 into the other buffer
-          const int k1 = w / h, k2 = w % h;
-          int p1, q1, p2, q2;
-          pair_of(k1, r, m, p1, q1);
-          pair_of(k2, r, m, p2, q2);
-          const long long i00 = (long long)p1 * m + p2, i01 = (long long)p1 * m + q2;
-          const long long i10 = (long long)q1 * m + p2, i11 = (long long)q1 * m + q2;
-          const double2 b00 = cur[i00], b01 = cur[i01], b10 = cur[i10], b11 = cur[i11];
-          const JRot R1 = Rc[k1];
-          const JRot R2 = Rc[k2];
-          double2 o00, o01, o10, o11;
-          if (R1.id && R2.id) {
-            o00 = b00; o01 = b01; o10 = b10; o11 = b11;
-          } else if (k1 == k2) {
-            // pivot block: the exact result of the 2x2 diagonalisation
-            o00 = make_double2(R1.dp, 0.0); o11 = make_double2(R1.dq, 0.0);
-            o01 = make_double2(0.0, 0.0); o10 = o01;
-          } else {
-            double2 t0, t1;
-            right_col(R2, 0, b00, b01, b10, b11, t0, t1);
-            o00 = left_row(R1, 0, t0, t1);
-            o10 = left_row(R1, 1, t0, t1);
-            right_col(R2, 1, b00, b01, b10, b11, t0, t1);
-            o01 = left_row(R1, 0, t0, t1);
-            o11 = left_row(R1, 1, t0, t1);
-          }
-          nxt[i00] = o00; nxt[i01] = o01; nxt[i10] = o10; nxt[i11] = o11;
-          if (last) {
-            const double w00 = o00.x * o00.x + o00.y * o00.y, w01 = o01.x * o01.x + o01.y * o01.y;
-            const double w10 = o10.x * o10.x + o10.y * o10.y, w11 = o11.x * o11.x + o11.y * o11.y;
-            tot += w00 + w01 + w10 + w11;
-            off += (p1 != p2 ? w00 : 0.0) + (p1 != q2 ? w01 : 0.0) +
-                   (q1 != p2 ? w10 : 0.0) + (q1 != q2 ? w11 : 0.0);
-          }
-        } else if (w < nblk + nV) {
-          // accumulate the rotation into row `row` of V (in place)
-          const int u = w - nblk, row = u / h, k = u % h;
-          int p, q;
-          pair_of(k, r, m, p, q);
-          double2* vr = a.V + (long long)row * m;
-          const double2 vp = vr[p], vq = vr[q];
-          const JRot R = Rc[k];
-          if (!R.id) {
-            vr[p] = rx_plus_cy(R.c, vp, R.j10, vq);
-            vr[q] = rx_plus_cy(R.s, vp, R.j11, vq);
-          }
+      const double2* cur = s_which[b] ? P.A1 : P.A0;
+      double2* nxt = s_which[b] ? P.A0 : P.A1;
+      const JRot* Rc = (t & 1) ? P.R1 : P.R0;
+      JRot* Rn = (t & 1) ? P.R0 : P.R1;
+      const int nblk = h * (h + 1) / 2, nV = m * h;
+      const int u = (int)(w - a.off[b]);
+      if (u < nblk) {
+        // 2x2 block (P1 rows, P2 columns), k1 >= k2: B' = J1^H B J2 into the
+        // other buffer, and its conjugate transpose into the mirrored block
+        int k1 = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
+        while ((k1 + 1) * (k1 + 2) / 2 <= u) ++k1;
+        while (k1 * (k1 + 1) / 2 > u) --k1;
+        const int k2 = u - k1 * (k1 + 1) / 2;
+        int p1, q1, p2, q2;
+        pair_of(k1, r, m, p1, q1);
+        pair_of(k2, r, m, p2, q2);
+        const long long i00 = (long long)p1 * m + p2, i01 = (long long)p1 * m + q2;
+        const long long i10 = (long long)q1 * m + p2, i11 = (long long)q1 * m + q2;
+        const double2 b00 = cur[i00], b01 = cur[i01], b10 = cur[i10], b11 = cur[i11];
+        const JRot R1 = Rc[k1];
+        const JRot R2 = Rc[k2];
+        double2 o00, o01, o10, o11;
+        if (R1.id && R2.id) {
+          o00 = b00; o01 = b01; o10 = b10; o11 = b11;
+        } else if (k1 == k2) {
+          // pivot block: the exact result of the 2x2 diagonalisation
+          o00 = make_double2(R1.dp, 0.0); o11 = make_double2(R1.dq, 0.0);
+          o01 = make_double2(0.0, 0.0); o10 = o01;
         } else {
-          // rotation of pair k of the next round from this round's result,
-          // recomputed here from the old blocks (no extra barrier)
-          const int k = w - nblk - nV;
-          int p, q;
-          pair_of(k, rn, m, p, q);
-          const int kp = pair_index(p, r, m), kq = pair_index(q, r, m);
-          int pp, pq, qp, qq;
-          pair_of(kp, r, m, pp, pq);
-          pair_of(kq, r, m, qp, qq);
-          const double2 b00 = cur[(long long)pp * m + qp], b01 = cur[(long long)pp * m + qq];
-          const double2 b10 = cur[(long long)pq * m + qp], b11 = cur[(long long)pq * m + qq];
-          const double dpp = cur[(long long)p * m + p].x, dqq = cur[(long long)q * m + q].x;
-          const JRot Rp = Rc[kp];
-          const JRot Rq = Rc[kq];
-          const int lp = (p == pp) ? 0 : 1, lq = (q == qp) ? 0 : 1;
-          const double app = Rp.id ? dpp : (lp ? Rp.dq : Rp.dp);
-          const double aqq = Rq.id ? dqq : (lq ? Rq.dq : Rq.dp);
           double2 t0, t1;
-          right_col(Rq, lq, b00, b01, b10, b11, t0, t1);
-          const double2 z = left_row(Rp, lp, t0, t1);
-          Rn[k] = make_rot(app, aqq, z, p, q, n, thr);
+          right_col(R2, 0, b00, b01, b10, b11, t0, t1);
+          o00 = left_row(R1, 0, t0, t1);
+          o10 = left_row(R1, 1, t0, t1);
+          right_col(R2, 1, b00, b01, b10, b11, t0, t1);
+          o01 = left_row(R1, 0, t0, t1);
+          o11 = left_row(R1, 1, t0, t1);
         }
-      }
-      if (last) block_norms(off, tot, a.part);
-      if (!grid_barrier(a.bar, epoch, a.status)) return;
-      double2* tA = cur; cur = nxt; nxt = tA;
-      JRot* tR = Rc; Rc = Rn; Rn = tR;
-      which ^= 1;
-    }
-    stop = decide_stop(a, sweep, &thr);
-    if (!stop) {
-      // round-0 rotations were computed with the previous threshold; refresh
-      // them with the new one (cheap; needs one barrier)
-      for (int k = gtid; k < h; k += gsz) {
+        nxt[i00] = o00; nxt[i01] = o01; nxt[i10] = o10; nxt[i11] = o11;
+        if (k1 != k2) {
+          nxt[(long long)p2 * m + p1] = conjx(o00);
+          nxt[(long long)q2 * m + p1] = conjx(o01);
+          nxt[(long long)p2 * m + q1] = conjx(o10);
+          nxt[(long long)q2 * m + q1] = conjx(o11);
+        }
+        if (last) {
+          const double w00 = o00.x * o00.x + o00.y * o00.y, w01 = o01.x * o01.x + o01.y * o01.y;
+          const double w10 = o10.x * o10.x + o10.y * o10.y, w11 = o11.x * o11.x + o11.y * o11.y;
+          const double mult = (k1 != k2) ? 2.0 : 1.0;   // the mirrored block counts too
+          acc_tot[b] += mult * (w00 + w01 + w10 + w11);
+          acc_off[b] += mult * ((p1 != p2 ? w00 : 0.0) + (p1 != q2 ? w01 : 0.0) +
+                                (q1 != p2 ? w10 : 0.0) + (q1 != q2 ? w11 : 0.0));
+        }
+      } else if (u < nblk + nV) {
+        // accumulate the rotation into row `row` of V (in place)
+        const int v = u - nblk, row = v / h, k = v % h;
         int p, q;
-        pair_of(k, 0, m, p, q);
-        Rc[k] = make_rot(cur[(long long)p * m + p].x, cur[(long long)q * m + q].x,
-                         cur[(long long)p * m + q], p, q, n, thr);
+        pair_of(k, r, m, p, q);
+        double2* vr = P.V + (long long)row * m;
+        const double2 vp = vr[p], vq = vr[q];
+        const JRot R = Rc[k];
+        if (!R.id) {
+          vr[p] = rx_plus_cy(R.c, vp, R.j10, vq);
+          vr[q] = rx_plus_cy(R.s, vp, R.j11, vq);
+        }
+      } else {
+        // rotation of pair k of the next round from this round's result,
+        // recomputed here from the old blocks (no extra barrier)
+        const int k = u - nblk - nV;
+        int p, q;
+        pair_of(k, rn, m, p, q);
+        const int kp = pair_index(p, r, m), kq = pair_index(q, r, m);
+        int pp, pq, qp, qq;
+        pair_of(kp, r, m, pp, pq);
+        pair_of(kq, r, m, qp, qq);
+        const double2 b00 = cur[(long long)pp * m + qp], b01 = cur[(long long)pp * m + qq];
+        const double2 b10 = cur[(long long)pq * m + qp], b11 = cur[(long long)pq * m + qq];
+        const double dpp = cur[(long long)p * m + p].x, dqq = cur[(long long)q * m + q].x;
+        const JRot Rp = Rc[kp];
+        const JRot Rq = Rc[kq];
+        const int lp = (p == pp) ? 0 : 1, lq = (q == qp) ? 0 : 1;
+        const double app = Rp.id ? dpp : (lp ? Rp.dq : Rp.dp);
+        const double aqq = Rq.id ? dqq : (lq ? Rq.dq : Rq.dp);
+        double2 t0, t1;
+        right_col(Rq, lq, b00, b01, b10, b11, t0, t1);
+        const double2 z = left_row(Rp, lp, t0, t1);
+        Rn[k] = make_rot(app, aqq, z, p, q, n, s_thr[b]);
       }
-      if (!grid_barrier(a.bar, epoch, a.status)) return;
     }
+    // partial norms of the problems that end a sweep this round
+    for (int b = 0; b < np; ++b) {
+      if (s_done[b] || (t % (a.p[b].m - 1)) != a.p[b].m - 2) continue;
+      block_norms(acc_off[b], acc_tot[b], a.part + (long long)b * 2 * gridDim.x);
+    }
+    if (!grid_barrier(a.bar, epoch, a.status)) return;
+    if (threadIdx.x == 0) {
+      int active = 0;
+      for (int b = 0; b < np; ++b) {
+        if (s_done[b]) continue;
+        s_which[b] ^= 1;
+        if ((t % (a.p[b].m - 1)) == a.p[b].m - 2) {
+          s_sweep[b] += 1;
+          double off, tot;
+          sum_parts(a.part + (long long)b * 2 * gridDim.x, off, tot);
+          if (off <= a.tol * a.tol * tot || tot == 0.0) {
+            s_done[b] = 1;
+          } else if (s_sweep[b] >= a.max_sweeps) {
+            flag_status(a.status, SKY_ENOCONV);
+            s_done[b] = 1;
+          }
+        }
+        active |= !s_done[b];
+      }
+      s_active = active;
+    }
+    __syncthreads();
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *a.result = which;
-    a.stats[0] += 1;
-    a.stats[1] += sweeps_done;
-    a.stats[2] = sweeps_done;
+    for (int b = 0; b < np; ++b) {
+      a.result[b] = s_which[b];
+      const bool run = !a.run || a.run[b * a.run_stride] != 0;
+      if (run) {
+        a.stats[0] += 1;
+        a.stats[1] += s_sweep[b];
+        a.stats[2] = s_sweep[b];
+      }
+    }
   }
 }
 
-// Copy A (n x n) into the padded m x m buffer, V = identity, reset the barrier.
-__global__ void k_jacobi_init(const double2* A, int n, int m, double2* A0, double2* V,
-                              unsigned* bar, int* result, const int* run) {
-  if (run && *run == 0) return;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e == 0) { bar[0] = 0u; *result = 0; }
-  if (e >= (long long)m * m) return;
-  const int i = (int)(e / m), j = (int)(e % m);
-  A0[e] = (i < n && j < n) ? A[(long long)i * n + j] : make_double2(0.0, 0.0);
-  V[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+struct EigJobs {
+  const double2* A[kMaxBatch];
+  double* w[kMaxBatch];
+  double2* Z[kMaxBatch];
+  double2* A0[kMaxBatch];
+  double2* V[kMaxBatch];
+  int n[kMaxBatch], m[kMaxBatch];
+  int np;
+  const int* run;
+  int run_stride;
+};
+
+// Copy each A (n x n) into its padded m x m buffer, V = identity, reset the barrier.
+__global__ void k_jacobi_init(EigJobs j, unsigned* bar, int* result) {
+  const int b = blockIdx.y;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    result[b] = 0;
+    if (b == 0) bar[0] = 0u;
+  }
+  if (j.run && j.run[b * j.run_stride] == 0) return;
+  const int n = j.n[b], m = j.m[b];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)m * m;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / m), k = (int)(e % m);
+    j.A0[b][e] = (i < n && k < n) ? j.A[b][(long long)i * n + k] : make_double2(0.0, 0.0);
+    j.V[b][e] = make_double2(i == k ? 1.0 : 0.0, 0.0);
+  }
 }
 
 // Eigenvalues ascending (ties by index) and the matching columns of V.
-__global__ void k_jacobi_finish(const double2* A0, const double2* A1, const double2* V,
-                                const int* result, int n, int m, double* w, double2* Z,
-                                const int* run) {
-  if (run && *run == 0) return;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const double2* A = (*result) ? A1 : A0;
-  const double dj = A[(long long)j * m + j].x;
+__global__ void k_jacobi_finish(EigJobs j, double2* const* A1, const int* result) {
+  const int b = blockIdx.y;
+  if (j.run && j.run[b * j.run_stride] == 0) return;
+  const int n = j.n[b], m = j.m[b];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const double2* A = result[b] ? A1[b] : j.A0[b];
+  const double dc = A[(long long)c * m + c].x;
   int rank = 0;
   for (int i = 0; i < n; ++i) {
     const double di = A[(long long)i * m + i].x;
-    rank += (di < dj) || (di == dj && i < j);
+    rank += (di < dc) || (di == dc && i < c);
   }
-  w[rank] = dj;
-  for (int i = 0; i < n; ++i) Z[(long long)i * n + rank] = V[(long long)i * m + j];
+  j.w[b][rank] = dc;
+  for (int i = 0; i < n; ++i) j.Z[b][(long long)i * n + rank] = j.V[b][(long long)i * m + c];
 }
 
 int jacobi_max_grid(Ctx* c) {
@@ -410,69 +479,103 @@ int jacobi_max_grid(Ctx* c) {
 
 size_t jacobi_rot_bytes(int m) { return (size_t)2 * (m / 2 + 1) * sizeof(JRot); }
 
-sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z, const int* run) {
-  if (I == 0) return SKY_OK;
-  const int m = I + (I & 1);
-  k_jacobi_init<<<div_up((long long)m * m, 256), 256, 0, c->stream>>>(A, I, m, c->d_eigA[0],
-                                                                      c->d_eigV, c->d_bar,
-                                                                      c->d_eigres, run);
-  note_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_check(c, e, "jacobi init");
-  if (m >= 2) {
+// Eigendecomposition of np Hermitian matrices A[b] (n[b] x n[b]) into ascending
+// w[b] and eigenvector columns Z[b]; problem b is skipped when run[b*stride] == 0.
+sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, double* const* w,
+                      double2* const* Z, const int* run, int run_stride) {
+  if (np < 1) return SKY_OK;
+  if (np > c->eig_batch) return set_err(c, SKY_EINVAL, "eigensolver batch %d > %d", np, c->eig_batch);
+  EigJobs j;
+  JacBatch a;
+  double2* A1p[kMaxBatch];
+  long long items = 0;
+  int nmax = 1, mmax = 2;
+  j.np = np; j.run = run; j.run_stride = run_stride;
+  a.np = np; a.off[0] = 0;
+  for (int b = 0; b < np; ++b) {
+    const int m = n[b] + (n[b] & 1);
     const int h = m / 2;
-    const long long items = (long long)h * h + (long long)m * h + h;
-    int grid = (int)((items + kJacThreads - 1) / kJacThreads);
-    if (grid < c->eig_grid / 2) grid = c->eig_grid / 2;   // spread the FP64 work over the SMs
-    if (grid > c->eig_grid) grid = c->eig_grid;
-    if (grid < 1) grid = 1;
-    JacArgs a;
-    a.A0 = c->d_eigA[0]; a.A1 = c->d_eigA[1]; a.V = c->d_eigV;
-    a.R0 = reinterpret_cast<JRot*>(c->d_eigrot);
-    a.R1 = a.R0 + h;
-    a.n = I; a.m = m;
-    a.tol = 1e-14;
-    a.max_sweeps = 60;
-    a.part = c->d_eigpart; a.bar = c->d_bar; a.status = c->d_status; a.result = c->d_eigres;
-    a.run = run;
-    a.stats = c->d_stats;
-    void* args[] = {&a};
-    note_launch();
-    e = cudaLaunchCooperativeKernel((const void*)k_jacobi, dim3(grid), dim3(kJacThreads), args, 0,
-                                    c->stream);
-    if (e != cudaSuccess) return cuda_check(c, e, "jacobi");
+    double2* base = c->d_eigA[0] + (size_t)b * c->eig_slot;
+    j.A[b] = A[b]; j.w[b] = w[b]; j.Z[b] = Z[b]; j.n[b] = n[b]; j.m[b] = m;
+    j.A0[b] = base;
+    A1p[b] = c->d_eigA[1] + (size_t)b * c->eig_slot;
+    j.V[b] = c->d_eigV + (size_t)b * c->eig_slot;
+    JacProb& P = a.p[b];
+    P.A0 = j.A0[b]; P.A1 = A1p[b]; P.V = j.V[b];
+    P.R0 = reinterpret_cast<JRot*>(c->d_eigrot) + (size_t)b * 2 * (c->eig_slot_rot);
+    P.R1 = P.R0 + c->eig_slot_rot;
+    P.n = n[b]; P.m = m;
+    items += (long long)h * (h + 1) / 2 + (long long)m * h + h;
+    a.off[b + 1] = items;
+    if (n[b] > nmax) nmax = n[b];
+    if (m > mmax) mmax = m;
   }
-  k_jacobi_finish<<<div_up(I, 128), 128, 0, c->stream>>>(c->d_eigA[0], c->d_eigA[1], c->d_eigV,
-                                                        c->d_eigres, I, m, w, Z, run);
+  double2** dA1 = reinterpret_cast<double2**>(c->d_eigptr);
+  cudaError_t e = cudaMemcpyAsync(dA1, A1p, np * sizeof(double2*), cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "jacobi pointers");
+  dim3 gi(div_up((long long)mmax * mmax, 256) < 1024 ? div_up((long long)mmax * mmax, 256) : 1024, np);
+  k_jacobi_init<<<gi, 256, 0, c->stream>>>(j, c->d_bar, c->d_eigres);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "jacobi init");
+  int grid = (int)((items + kJacThreads - 1) / kJacThreads);
+  if (grid < c->eig_grid / 2) grid = c->eig_grid / 2;   // spread the FP64 work over the SMs
+  if (grid > c->eig_grid) grid = c->eig_grid;
+  if (grid < 1) grid = 1;
+  a.tol = 1e-14;
+  a.max_sweeps = 60;
+  a.part = c->d_eigpart; a.bar = c->d_bar; a.status = c->d_status; a.result = c->d_eigres;
+  a.run = run; a.run_stride = run_stride;
+  a.stats = c->d_stats;
+  void* args[] = {&a};
+  note_launch();
+  e = cudaLaunchCooperativeKernel((const void*)k_jacobi, dim3(grid), dim3(kJacThreads), args, 0,
+                                  c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "jacobi");
+  k_jacobi_finish<<<dim3(div_up(nmax, 128), np), 128, 0, c->stream>>>(j, dA1, c->d_eigres);
   note_launch();
   return cuda_check(c, cudaGetLastError(), "jacobi finish");
 }
 
+sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z, const int* run) {
+  if (I == 0) return SKY_OK;
+  return eigh_batch(c, 1, &A, &I, &w, &Z, run, 0);
+}
+
 // Y = X diag(lambda^{-1/2}); flags SKY_ENOTPD for a non-positive eigenvalue.
-__global__ void k_inv_sqrt_cols(const double2* X, const double* lam, int n, double2* Y, int* status,
-                                const int* run) {
-  if (run && *run == 0) return;
+struct ScaleJobs {
+  const double2* X[kMaxBatch];
+  const double* lam[kMaxBatch];
+  double2* Y[kMaxBatch];
+  int n[kMaxBatch];
+};
+__global__ void k_inv_sqrt_cols(ScaleJobs j, int* status, const int* run, int run_stride) {
+  const int b = blockIdx.y;
+  if (run && run[b * run_stride] == 0) return;
+  const int n = j.n[b];
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)n * n) return;
-  const int j = (int)(e % n);
-  double l = lam[j];
+  const int c = (int)(e % n);
+  double l = j.lam[b][c];
   if (!(l > 0.0)) {
-    if (e == j) flag_status(status, SKY_ENOTPD);
+    if (e == c) flag_status(status, SKY_ENOTPD);
     l = 1e-300;
   }
-  Y[e] = (1.0 / sqrt(l)) * X[e];
+  j.Y[b][e] = (1.0 / sqrt(l)) * j.X[b][e];
 }
 
 // H' = (H' + H'^H) / 2 in place.
-__global__ void k_hermitize(double2* A, int n) {
+__global__ void k_hermitize(double2* const* Ap, const int* nn) {
+  const int b = blockIdx.y;
+  double2* A = Ap[b];
+  const int n = nn[b];
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)n * n) return;
-  const int i = (int)(e / n), j = (int)(e % n);
-  if (i > j) return;
-  const double2 a = A[(long long)i * n + j], b = A[(long long)j * n + i];
-  const double2 s = 0.5 * (a + conjx(b));
-  A[(long long)i * n + j] = s;
-  A[(long long)j * n + i] = conjx(s);
+  const int i = (int)(e / n), k = (int)(e % n);
+  if (i > k) return;
+  const double2 x = A[(long long)i * n + k], y = A[(long long)k * n + i];
+  const double2 s = 0.5 * (x + conjx(y));
+  A[(long long)i * n + k] = s;
+  A[(long long)k * n + i] = conjx(s);
 }
 
 // ---- Loewdin factor C = S^{-1/2} (Eq. Loewedin) ----------------------------
@@ -485,25 +588,43 @@ __global__ void k_hermitize(double2* A, int n) {
 // by |Re| + |Im|), which holds for the overlaps of damped orthonormal states.
 // Otherwise, or if it has not converged after kNsMaxIter steps, C is
 // X Lambda^{-1/2} X^H from the Jacobi eigendecomposition of S, as the paper
-// describes.  Device gates: [0] Newton-Schulz running, [1] eigendecomposition
-// needed, [2] Newton-Schulz converged (one final update pending or done),
-// [3] Newton-Schulz chosen; [4..5] the row-sum bound as integer bits.
+// describes.  Device gates per problem b at gate[8 b + k]: [0] Newton-Schulz
+// running, [1] eigendecomposition needed, [2] Newton-Schulz converged (one
+// final update pending or done), [3] Newton-Schulz chosen; [4..5] the row-sum
+// bound as integer bits.
 constexpr int kNsMaxIter = 14;
 constexpr double kNsSwitch = 2.5;      // spectral bound for the Newton-Schulz route
 constexpr double kNsConv = 1e-10;      // ||I - Z Y||_F after which one more update suffices
 
+struct NsJobs {
+  const double2* S[kMaxBatch];
+  double2* Y[kMaxBatch];
+  double2* Z[kMaxBatch];
+  double2* W[kMaxBatch];
+  double2* Yn[kMaxBatch];
+  double2* Zn[kMaxBatch];
+  double2* C[kMaxBatch];
+  int n[kMaxBatch];
+};
+
+__global__ void k_ns_reset(int* gate) {
+  int* g = gate + 8 * threadIdx.x;
+  g[0] = g[1] = g[2] = g[3] = 0;
+  *reinterpret_cast<unsigned long long*>(g + 4) = 0ull;
+}
+
 // Row sums of |S| (bounded by |Re| + |Im|) -> max into gate[4..5]; Y = S, Z = I.
-__global__ void __launch_bounds__(256) k_ns_rows(const double2* S, int n, double2* Y, double2* Z,
-                                                 int* gate) {
+__global__ void __launch_bounds__(256) k_ns_rows(NsJobs j, int* gate) {
   __shared__ double red[8];
-  const int i = blockIdx.x;
+  const int b = blockIdx.y, n = j.n[b], i = blockIdx.x;
+  if (i >= n) return;
   double acc = 0.0;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const long long e = (long long)i * n + j;
-    const double2 v = S[e];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const long long e = (long long)i * n + k;
+    const double2 v = j.S[b][e];
     acc += fabs(v.x) + fabs(v.y);
-    Y[e] = v;
-    Z[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    j.Y[b][e] = v;
+    j.Z[b][e] = make_double2(i == k ? 1.0 : 0.0, 0.0);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -513,44 +634,43 @@ __global__ void __launch_bounds__(256) k_ns_rows(const double2* S, int n, double
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
     // non-negative doubles order like their bit patterns
-    atomicMax(reinterpret_cast<unsigned long long*>(gate + 4),
+    atomicMax(reinterpret_cast<unsigned long long*>(gate + 8 * b + 4),
               (unsigned long long)__double_as_longlong(t));
   }
 }
 
-__global__ void k_ns_reset(int* gate) {
-  gate[0] = gate[1] = gate[2] = gate[3] = 0;
-  *reinterpret_cast<unsigned long long*>(gate + 4) = 0ull;
-}
-
 __global__ void k_ns_choose(int* gate) {
-  const double R = __longlong_as_double(*reinterpret_cast<long long*>(gate + 4));
+  int* g = gate + 8 * threadIdx.x;
+  const double R = __longlong_as_double(*reinterpret_cast<long long*>(g + 4));
   const int ns = R < kNsSwitch;
-  gate[3] = ns;
-  gate[0] = ns;
-  gate[1] = !ns;
-  gate[2] = 0;
+  g[3] = ns;
+  g[0] = ns;
+  g[1] = !ns;
+  g[2] = 0;
 }
 
 // T = (3I - W)/2 in place of W = Z Y; records convergence; ends the
-// iteration one step after convergence was seen.
-__global__ void __launch_bounds__(1024) k_ns_step(double2* W, int n, int* gate, long long* stats) {
+// iteration one step after convergence was seen.  Block b serves problem b.
+__global__ void __launch_bounds__(1024) k_ns_step(NsJobs j, int* gate, long long* stats) {
   __shared__ double red[32];
   __shared__ int s_skip;
+  const int b = blockIdx.x, n = j.n[b];
+  int* g = gate + 8 * b;
   if (threadIdx.x == 0) {
-    if (gate[0] && gate[2]) gate[0] = 0;   // the final update has been applied
-    s_skip = !gate[0];
+    if (g[0] && g[2]) g[0] = 0;   // the final update has been applied
+    s_skip = !g[0];
   }
   __syncthreads();
   if (s_skip) return;
-  if (threadIdx.x == 0) stats[5] += 1;
+  if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(stats + 5), 1ull);
+  double2* W = j.W[b];
   double acc = 0.0;
   for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
-    const int i = (int)(e / n), j = (int)(e % n);
+    const int i = (int)(e / n), k = (int)(e % n);
     double2 d = W[e];
-    if (i == j) d.x -= 1.0;                 // W - I
+    if (i == k) d.x -= 1.0;                 // W - I
     acc += d.x * d.x + d.y * d.y;
-    W[e] = make_double2((i == j ? 1.0 : 0.0) - 0.5 * d.x, -0.5 * d.y);   // I - (W - I)/2
+    W[e] = make_double2((i == k ? 1.0 : 0.0) - 0.5 * d.x, -0.5 * d.y);   // I - (W - I)/2
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -559,88 +679,139 @@ __global__ void __launch_bounds__(1024) k_ns_step(double2* W, int n, int* gate, 
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    if (sqrt(t) < kNsConv) gate[2] = 1;
+    if (sqrt(t) < kNsConv) g[2] = 1;
   }
 }
 
-__global__ void k_ns_copy(double2* Y, double2* Z, const double2* Yn, const double2* Zn, int n,
-                          const int* gate) {
-  if (!gate[0]) return;
+__global__ void k_ns_copy(NsJobs j, const int* gate) {
+  const int b = blockIdx.y, n = j.n[b];
+  if (!gate[8 * b]) return;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)n * n) return;
-  Y[e] = Yn[e];
-  Z[e] = Zn[e];
+  j.Y[b][e] = j.Yn[b][e];
+  j.Z[b][e] = j.Zn[b][e];
 }
 
 // C = (Z + Z^H)/2 when Newton-Schulz converged; otherwise request the
 // eigendecomposition route.
-__global__ void k_ns_final(const double2* Z, int n, double2* C, int* gate, long long* stats) {
+__global__ void k_ns_final(NsJobs j, int* gate, long long* stats) {
+  const int b = blockIdx.y, n = j.n[b];
+  int* g = gate + 8 * b;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int ok = gate[3] && gate[2];
+  const int ok = g[3] && g[2];
   if (e == 0) {
-    stats[3] += 1;
-    stats[4] += ok;
+    atomicAdd(reinterpret_cast<unsigned long long*>(stats + 3), 1ull);
+    atomicAdd(reinterpret_cast<unsigned long long*>(stats + 4), (unsigned long long)ok);
   }
   if (!ok) {
-    if (e == 0) gate[1] = 1;
+    if (e == 0) g[1] = 1;
     return;
   }
   if (e >= (long long)n * n) return;
-  const int i = (int)(e / n), j = (int)(e % n);
-  C[e] = 0.5 * (Z[e] + conjx(Z[(long long)j * n + i]));
+  const int i = (int)(e / n), k = (int)(e % n);
+  j.C[b][e] = 0.5 * (j.Z[b][e] + conjx(j.Z[b][(long long)k * n + i]));
+}
+
+sky_status lowdin_batch(Ctx* c, int np, const double2* const* S, const int* I, double2* const* C) {
+  if (np < 1) return SKY_OK;
+  if (np > c->eig_batch) return set_err(c, SKY_EINVAL, "Loewdin batch %d > %d", np, c->eig_batch);
+  NsJobs j;
+  int nmax = 1;
+  for (int b = 0; b < np; ++b) {
+    const size_t off = (size_t)b * c->small_slot;
+    j.S[b] = S[b]; j.n[b] = I[b]; j.C[b] = C[b];
+    j.Y[b] = c->d_small[0] + off; j.Z[b] = c->d_small[1] + off; j.W[b] = c->d_small[2] + off;
+    j.Yn[b] = c->d_small[3] + off; j.Zn[b] = c->d_small[4] + off;
+    if (I[b] > nmax) nmax = I[b];
+  }
+  int* gate = c->d_gate;
+  const long long nn = (long long)nmax * nmax;
+  cudaError_t e;
+  k_ns_reset<<<1, np, 0, c->stream>>>(gate);
+  k_ns_rows<<<dim3(nmax, np), 256, 0, c->stream>>>(j, gate);
+  k_ns_choose<<<1, np, 0, c->stream>>>(gate);
+  note_launch(3);
+  const int *run[kMaxBatch], *stop[kMaxBatch], *fb[kMaxBatch];
+  for (int b = 0; b < np; ++b) {
+    run[b] = gate + 8 * b;
+    stop[b] = gate + 8 * b + 2;
+    fb[b] = gate + 8 * b + 1;
+  }
+  const int* none[kMaxBatch] = {nullptr};
+  for (int it = 0; it < kNsMaxIter; ++it) {
+    ZJobs w_ = zjobs(np, false, false, (const double2* const*)j.Z, (const double2* const*)j.Y, j.W, I, run, stop);
+    sky_status st = zgemm_batch(c, w_);   // W = Z Y
+    if (st != SKY_OK) return st;
+    k_ns_step<<<np, 1024, 0, c->stream>>>(j, gate, c->d_stats);
+    note_launch();
+    ZJobs y_ = zjobs(np, false, false, (const double2* const*)j.Y, (const double2* const*)j.W, j.Yn, I, run, none);
+    ZJobs z_ = zjobs(np, false, false, (const double2* const*)j.W, (const double2* const*)j.Z, j.Zn, I, run, none);
+    if ((st = zgemm_batch(c, y_)) != SKY_OK) return st;                      // Y T
+    if ((st = zgemm_batch(c, z_)) != SKY_OK) return st;                      // T Z
+    k_ns_copy<<<dim3(div_up(nn, 256), np), 256, 0, c->stream>>>(j, gate);
+    note_launch();
+  }
+  k_ns_final<<<dim3(div_up(nn, 256), np), 256, 0, c->stream>>>(j, gate, c->d_stats);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "newton-schulz");
+  // eigendecomposition route (problem b runs only when gate[8 b + 1] is set)
+  double2* X[kMaxBatch];
+  double* lam[kMaxBatch];
+  ScaleJobs sj;
+  for (int b = 0; b < np; ++b) {
+    const size_t off = (size_t)b * c->small_slot;
+    X[b] = c->d_small[3] + off;
+    lam[b] = c->d_eigw + (size_t)b * (c->eig_slot_rot * 2 + 2);
+    sj.X[b] = X[b]; sj.lam[b] = lam[b]; sj.Y[b] = c->d_small[4] + off; sj.n[b] = I[b];
+  }
+  sky_status st = eigh_batch(c, np, S, I, lam, X, gate + 1, 8);
+  if (st != SKY_OK) return st;
+  k_inv_sqrt_cols<<<dim3(div_up(nn, 256), np), 256, 0, c->stream>>>(sj, c->d_status, gate + 1, 8);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "loewdin scale");
+  ZJobs c_ = zjobs(np, false, true, (const double2* const*)sj.Y, (const double2* const*)X, C, I, fb, none);
+  return zgemm_batch(c, c_);   // C = X Lambda^{-1/2} X^H
 }
 
 sky_status lowdin_impl(Ctx* c, const double2* S, int I, double2* C) {
   if (I == 0) return SKY_OK;
-  double2 *Y = c->d_small[0], *Z = c->d_small[1], *W = c->d_small[2];
-  double2 *Yn = c->d_small[3], *Zn = c->d_small[4];
-  int* gate = c->d_gate;
-  const long long nn = (long long)I * I;
-  cudaError_t e;
-  k_ns_reset<<<1, 1, 0, c->stream>>>(gate);
-  k_ns_rows<<<I, 256, 0, c->stream>>>(S, I, Y, Z, gate);
-  k_ns_choose<<<1, 1, 0, c->stream>>>(gate);
-  note_launch(3);
-  for (int it = 0; it < kNsMaxIter; ++it) {
-    sky_status st = zgemm_small(c, false, false, Z, Y, W, I, gate, gate + 2);   // W = Z Y
-    if (st != SKY_OK) return st;
-    k_ns_step<<<1, 1024, 0, c->stream>>>(W, I, gate, c->d_stats);
-    note_launch();
-    st = zgemm_small(c, false, false, Y, W, Yn, I, gate);                       // Y T
-    if (st == SKY_OK) st = zgemm_small(c, false, false, W, Z, Zn, I, gate);     // T Z
-    if (st != SKY_OK) return st;
-    k_ns_copy<<<div_up(nn, 256), 256, 0, c->stream>>>(Y, Z, Yn, Zn, I, gate);
-    note_launch();
+  return lowdin_batch(c, 1, &S, &I, &C);
+}
+
+// Rayleigh-Ritz for np problems: H' = C^H H C, H' = Z Lambda Z^H, M = C Z.
+sky_status subspace_batch(Ctx* c, int np, const double2* const* H, const double2* const* C,
+                          const int* I, double2* const* M, double* const* eps) {
+  if (np < 1) return SKY_OK;
+  if (np > c->eig_batch) return set_err(c, SKY_EINVAL, "subspace batch %d > %d", np, c->eig_batch);
+  double2 *T1[kMaxBatch], *Hp[kMaxBatch], *Z[kMaxBatch];
+  int nmax = 1;
+  for (int b = 0; b < np; ++b) {
+    const size_t off = (size_t)b * c->small_slot;
+    T1[b] = c->d_small[0] + off; Hp[b] = c->d_small[1] + off; Z[b] = c->d_small[2] + off;
+    if (I[b] > nmax) nmax = I[b];
   }
-  k_ns_final<<<div_up(nn, 256), 256, 0, c->stream>>>(Z, I, C, gate, c->d_stats);
-  note_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "newton-schulz");
-  // eigendecomposition route (runs only when gate[1] is set)
-  double2 *X = c->d_small[3], *Xs = c->d_small[4];
-  sky_status st = eigh_impl(c, S, I, c->d_eigw, X, gate + 1);
+  const int* none[kMaxBatch] = {nullptr};
+  sky_status st = zgemm_batch(c, zjobs(np, true, false, C, H, T1, I, none, none));   // C^H H
+  if (st == SKY_OK)
+    st = zgemm_batch(c, zjobs(np, false, false, (const double2* const*)T1, C, Hp, I, none, none));
   if (st != SKY_OK) return st;
-  k_inv_sqrt_cols<<<div_up(nn, 256), 256, 0, c->stream>>>(X, c->d_eigw, I, Xs, c->d_status,
-                                                          gate + 1);
+  double2** dHp = reinterpret_cast<double2**>(c->d_eigptr) + kMaxBatch;
+  int* dI = reinterpret_cast<int*>(reinterpret_cast<double2**>(c->d_eigptr) + 2 * kMaxBatch);
+  cudaError_t e = cudaMemcpyAsync(dHp, Hp, np * sizeof(double2*), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dI, I, np * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "subspace pointers");
+  k_hermitize<<<dim3(div_up((long long)nmax * nmax, 256), np), 256, 0, c->stream>>>(dHp, dI);
   note_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "loewdin scale");
-  return zgemm_small(c, false, true, Xs, X, C, I, gate + 1);   // C = X Lambda^{-1/2} X^H
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "hermitize");
+  st = eigh_batch(c, np, (const double2* const*)Hp, I, eps, Z, nullptr, 0);
+  if (st != SKY_OK) return st;
+  return zgemm_batch(c, zjobs(np, false, false, C, (const double2* const*)Z, M, I, none, none));   // M = C Z
 }
 
 sky_status subspace_impl(Ctx* c, const double2* H, const double2* C, int I, double2* M,
                          double* eps) {
   if (I == 0) return SKY_OK;
-  double2* T1 = c->d_small[0];
-  double2* Hp = c->d_small[1];
-  double2* Z = c->d_small[2];
-  sky_status st = zgemm_small(c, true, false, C, H, T1, I);   // C^H H
-  if (st == SKY_OK) st = zgemm_small(c, false, false, T1, C, Hp, I);   // (C^H H) C
-  if (st != SKY_OK) return st;
-  k_hermitize<<<div_up((long long)I * I, 256), 256, 0, c->stream>>>(Hp, I); note_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_check(c, e, "hermitize");
-  st = eigh_impl(c, Hp, I, eps, Z);
-  if (st != SKY_OK) return st;
-  return zgemm_small(c, false, false, C, Z, M, I);   // M = C Z
+  return subspace_batch(c, 1, &H, &C, &I, &M, &eps);
 }
 
 }  // namespace sky

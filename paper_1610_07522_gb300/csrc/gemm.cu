@@ -143,27 +143,45 @@ sky_status rotate_impl(Ctx* c, const void* phi, const double2* M, int I, void* o
   return cuda_check(c, cudaGetLastError(), "rotate");
 }
 
-// ---------------------------------------------------------------- small GEMM
-// C = opA(A) opB(B), n x n row-major; op = identity or conjugate transpose.
-// TS x TS output tile per block, 2 x 2 per thread.  Runs only if `run` is null
-// or *run != 0, and `stop` is null or *stop == 0 (device-side gating, so a
+// ---------------------------------------------------------------- small GEMMs
+// C[b] = opA(A[b]) opB(B[b]) for a batch of n[b] x n[b] row-major products
+// (op = identity or conjugate transpose), blockIdx.z = problem.  TS x TS output
+// tile per block, 2 x 2 per thread.  Problem b runs only if run[b] is null or
+// *run[b] != 0, and stop[b] is null or *stop[b] == 0 (device-side gating, so a
 // fixed launch sequence can skip work the device decided is not needed).
+ZJobs zjobs(int np, bool ah, bool bh, const double2* const* A, const double2* const* B,
+            double2* const* C, const int* n, const int* const* run, const int* const* stop) {
+  ZJobs j;
+  j.np = np; j.ah = ah; j.bh = bh;
+  for (int b = 0; b < kMaxBatch; ++b) {
+    const bool in = b < np;
+    j.A[b] = in ? A[b] : nullptr;
+    j.B[b] = in ? B[b] : nullptr;
+    j.C[b] = in ? C[b] : nullptr;
+    j.n[b] = in ? n[b] : 0;
+    j.run[b] = in ? run[b] : nullptr;
+    j.stop[b] = in ? stop[b] : nullptr;
+  }
+  return j;
+}
+
 template <bool AH, bool BH, int TS>
-__global__ void __launch_bounds__(TS * TS / 4) k_zgemm(const double2* __restrict__ A,
-                                                       const double2* __restrict__ B,
-                                                       double2* __restrict__ C, int n,
-                                                       const int* run, const int* stop) {
-  if ((run && *run == 0) || (stop && *stop != 0)) return;
+__global__ void __launch_bounds__(TS * TS / 4) k_zgemm(ZJobs j) {
+  const int b = blockIdx.z, n = j.n[b];
+  const int r0 = blockIdx.y * TS, c0 = blockIdx.x * TS;
+  if (r0 >= n || c0 >= n) return;
+  if ((j.run[b] && *j.run[b] == 0) || (j.stop[b] && *j.stop[b] != 0)) return;
+  const double2* __restrict__ A = j.A[b];
+  const double2* __restrict__ B = j.B[b];
   constexpr int NT = TS * TS / 4, TH = TS / 2;
   __shared__ double2 As[BK][TS + 1];
   __shared__ double2 Bs[BK][TS + 1];
-  const int r0 = blockIdx.y * TS, c0 = blockIdx.x * TS;
   const int tid = threadIdx.x, ty = tid / TH, tx = tid % TH;
   double2 acc[2][2];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
+    for (int k = 0; k < 2; ++k) acc[i][k] = make_double2(0.0, 0.0);
   for (int k0 = 0; k0 < n; k0 += BK) {
     for (int e = tid; e < BK * TS; e += NT) {
       const int kk = e / TS, col = e % TS;
@@ -186,34 +204,44 @@ __global__ void __launch_bounds__(TS * TS / 4) k_zgemm(const double2* __restrict
     }
     __syncthreads();
   }
+  double2* C = j.C[b];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int r = r0 + ty * 2 + i, cc = c0 + tx * 2 + j;
-      if (r < n && cc < n) C[(long long)r * n + cc] = acc[i][j];
+    for (int k = 0; k < 2; ++k) {
+      const int r = r0 + ty * 2 + i, cc = c0 + tx * 2 + k;
+      if (r < n && cc < n) C[(long long)r * n + cc] = acc[i][k];
     }
 }
 
 template <int TS>
-static void launch_zgemm(Ctx* c, bool ah, bool bh, const double2* A, const double2* B,
-                         double2* C, int n, const int* run, const int* stop) {
-  dim3 grid(div_up(n, TS), div_up(n, TS));
+static void launch_zgemm(Ctx* c, const ZJobs& j, int nmax) {
+  dim3 grid(div_up(nmax, TS), div_up(nmax, TS), j.np);
   constexpr int NT = TS * TS / 4;
-  if (!ah && !bh) k_zgemm<false, false, TS><<<grid, NT, 0, c->stream>>>(A, B, C, n, run, stop);
-  else if (ah && !bh) k_zgemm<true, false, TS><<<grid, NT, 0, c->stream>>>(A, B, C, n, run, stop);
-  else if (!ah && bh) k_zgemm<false, true, TS><<<grid, NT, 0, c->stream>>>(A, B, C, n, run, stop);
-  else k_zgemm<true, true, TS><<<grid, NT, 0, c->stream>>>(A, B, C, n, run, stop);
+  if (!j.ah && !j.bh) k_zgemm<false, false, TS><<<grid, NT, 0, c->stream>>>(j);
+  else if (j.ah && !j.bh) k_zgemm<true, false, TS><<<grid, NT, 0, c->stream>>>(j);
+  else if (!j.ah && j.bh) k_zgemm<false, true, TS><<<grid, NT, 0, c->stream>>>(j);
+  else k_zgemm<true, true, TS><<<grid, NT, 0, c->stream>>>(j);
+}
+
+sky_status zgemm_batch(Ctx* c, const ZJobs& j) {
+  int nmax = 0;
+  long long tiles32 = 0;
+  for (int b = 0; b < j.np; ++b) {
+    if (j.n[b] > nmax) nmax = j.n[b];
+    tiles32 += (long long)div_up(j.n[b], 32) * div_up(j.n[b], 32);
+  }
+  if (nmax == 0) return SKY_OK;
+  // 32 x 32 tiles once they give at least two blocks per SM, else 16 x 16
+  if (tiles32 >= 2LL * c->num_sms) launch_zgemm<32>(c, j, nmax);
+  else launch_zgemm<16>(c, j, nmax);
+  note_launch();
+  return cuda_check(c, cudaGetLastError(), "zgemm");
 }
 
 sky_status zgemm_small(Ctx* c, bool ah, bool bh, const double2* A, const double2* B, double2* C,
                        int n, const int* run, const int* stop) {
-  // 32 x 32 tiles once they give at least two blocks per SM, else 16 x 16
-  const long long t32 = (long long)div_up(n, 32) * div_up(n, 32);
-  if (t32 >= 2LL * c->num_sms) launch_zgemm<32>(c, ah, bh, A, B, C, n, run, stop);
-  else launch_zgemm<16>(c, ah, bh, A, B, C, n, run, stop);
-  note_launch();
-  return cuda_check(c, cudaGetLastError(), "zgemm");
+  return zgemm_batch(c, zjobs(1, ah, bh, &A, &B, &C, &n, &run, &stop));
 }
 
 }  // namespace sky

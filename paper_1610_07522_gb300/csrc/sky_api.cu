@@ -74,7 +74,7 @@ static void free_all(Ctx* c) {
                   c->d_ktf[2], c->d_kp[0], c->d_kp[1], c->d_kp[2], c->d_damp[0], c->d_damp[1],
                   c->d_coul, c->d_gscr, c->d_red, c->d_dpart, c->d_ftmp, c->d_fcx, c->d_gpart,
                   c->d_eigA[0], c->d_eigA[1], c->d_eigV, c->d_eigw, c->d_eigpart, c->d_bar,
-                  c->d_eigres, c->d_eigrot, c->d_small[0], c->d_small[1], c->d_small[2],
+                  c->d_eigres, c->d_eigrot, c->d_eigptr, c->d_small[0], c->d_small[1], c->d_small[2],
                   c->d_small[3], c->d_small[4], c->d_small[5], c->d_gate,
                   c->d_stats, c->d_tcA[0], c->d_tcA[1], c->d_tcA[2], c->d_tcB[0],
                   c->d_tcB[1], c->d_tcB[2], c->d_tcRotA[0], c->d_tcRotA[1], c->d_tcRotA[2],
@@ -179,19 +179,29 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   ALLOC(c->d_ftmp, (size_t)16 * G);
   ALLOC(c->d_fcx, G);
   ALLOC(c->d_gpart, gpart);
-  ALLOC(c->d_eigA[0], (size_t)m * m);
-  ALLOC(c->d_eigA[1], (size_t)m * m);
-  ALLOC(c->d_eigV, (size_t)m * m);
-  ALLOC(c->d_eigw, m);
+  // eigensolver and small-matrix workspace: eig_batch problems of size Imax
+  c->eig_batch = 2;
+  c->eig_slot = (size_t)m * m;
+  c->eig_slot_rot = (size_t)(m / 2 + 1);
+  c->small_slot = (size_t)Imax * Imax;
+  ALLOC(c->d_eigA[0], c->eig_slot * c->eig_batch);
+  ALLOC(c->d_eigA[1], c->eig_slot * c->eig_batch);
+  ALLOC(c->d_eigV, c->eig_slot * c->eig_batch);
+  ALLOC(c->d_eigw, (2 * c->eig_slot_rot + 2) * c->eig_batch);
   ALLOC(c->d_bar, 2);
-  ALLOC(c->d_eigres, 1);
+  ALLOC(c->d_eigres, kMaxBatch);
   if (s == SKY_OK) {
     char* p = nullptr;
-    s = dalloc(c, &p, jacobi_rot_bytes(m));
+    s = dalloc(c, &p, jacobi_rot_bytes(m) * c->eig_batch);
     c->d_eigrot = p;
   }
-  for (int k = 0; k < 6; ++k) ALLOC(c->d_small[k], (size_t)Imax * Imax);
-  ALLOC(c->d_gate, 8);
+  if (s == SKY_OK) {
+    char* p = nullptr;
+    s = dalloc(c, &p, (size_t)3 * kMaxBatch * sizeof(void*));
+    c->d_eigptr = p;
+  }
+  for (int k = 0; k < 6; ++k) ALLOC(c->d_small[k], c->small_slot * c->eig_batch);
+  ALLOC(c->d_gate, 8 * kMaxBatch);
   if (s == SKY_OK && is_tc(prec)) {
     size_t pa, pb, pra, part;
     tc_scratch_sizes(Imax, V, c->num_sms, &pa, &pb, &pra, &part);
@@ -209,7 +219,7 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   ALLOC(c->d_stats, 8);
   if (s == SKY_OK) {
     c->eig_grid = jacobi_max_grid(c);
-    ALLOC(c->d_eigpart, (size_t)2 * c->eig_grid);
+    ALLOC(c->d_eigpart, (size_t)2 * c->eig_grid * kMaxBatch);
   }
 #undef ALLOC
   if (s == SKY_OK) {
@@ -335,6 +345,41 @@ sky_status sky_subspace_diag(sky_ctx* c, const double* H, const double* C, int I
   if (I == 0) return SKY_OK;
   if (!H || !C || !M || !eps) return set_err(c, SKY_EINVAL, "subspace_diag: null pointer");
   return subspace_impl(c, (const double2*)H, (const double2*)C, I, (double2*)M, eps);
+}
+
+static sky_status check_batch(sky_ctx* c, int nb, const int* I) {
+  if (nb < 1 || nb > c->eig_batch || !I)
+    return set_err(c, SKY_EINVAL, "batch of %d outside [1, %d]", nb, c->eig_batch);
+  for (int b = 0; b < nb; ++b)
+    if (I[b] < 1 || I[b] > c->max_states)
+      return set_err(c, SKY_EINVAL, "I=%d outside [1, %d]", I[b], c->max_states);
+  return SKY_OK;
+}
+
+sky_status sky_orthonormalize_batched(sky_ctx* c, int nb, const double* const* S, const int* I,
+                                      double* const* C) {
+  if (!c) return SKY_EINVAL;
+  sky_status st = check_batch(c, nb, I);
+  if (st != SKY_OK) return st;
+  if (!S || !C) return set_err(c, SKY_EINVAL, "orthonormalize_batched: null pointer");
+  for (int b = 0; b < nb; ++b)
+    if (!S[b] || !C[b] || S[b] == C[b]) return set_err(c, SKY_EINVAL, "orthonormalize_batched: bad pointers");
+  return lowdin_batch(c, nb, reinterpret_cast<const double2* const*>(S), I,
+                      reinterpret_cast<double2* const*>(C));
+}
+
+sky_status sky_subspace_diag_batched(sky_ctx* c, int nb, const double* const* H,
+                                     const double* const* C, const int* I, double* const* M,
+                                     double* const* eps) {
+  if (!c) return SKY_EINVAL;
+  sky_status st = check_batch(c, nb, I);
+  if (st != SKY_OK) return st;
+  if (!H || !C || !M || !eps) return set_err(c, SKY_EINVAL, "subspace_diag_batched: null pointer");
+  for (int b = 0; b < nb; ++b)
+    if (!H[b] || !C[b] || !M[b] || !eps[b]) return set_err(c, SKY_EINVAL, "subspace_diag_batched: null pointer");
+  return subspace_batch(c, nb, reinterpret_cast<const double2* const*>(H),
+                        reinterpret_cast<const double2* const*>(C), I,
+                        reinterpret_cast<double2* const*>(M), eps);
 }
 
 sky_status sky_rotate(sky_ctx* c, const void* phi, const double* M, int I, void* psi_out) {

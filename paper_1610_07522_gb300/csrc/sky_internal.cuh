@@ -54,6 +54,7 @@ struct Couplings {
 struct Ctx;  // defined below; sky_ctx is an alias at the C boundary
 
 constexpr int kDensSplits = 8;     // state splits of the density accumulation
+constexpr int kMaxBatch = 8;       // problems per batched eigensolve / small GEMM
 constexpr int kRedBlock = 256;     // threads of the per-state reduction blocks
 
 struct Ctx {
@@ -91,7 +92,12 @@ struct Ctx {
   double* d_eigw;                   // eigenvalues [m]
   double* d_eigpart;                // per-block partial norms
   unsigned* d_bar;                  // grid barrier {count, generation}
-  int* d_eigres;                    // which ping-pong buffer holds the result
+  int* d_eigres;                    // which ping-pong buffer holds each result [kMaxBatch]
+  void* d_eigptr;                   // device pointer tables of the batched calls
+  int eig_batch;                    // problems a batched eigensolve may hold
+  size_t eig_slot;                  // elements per problem in d_eigA / d_eigV
+  size_t eig_slot_rot;              // rotations per problem and round buffer
+  size_t small_slot;                // elements per problem in each d_small buffer
   void* d_eigrot;                   // Jacobi rotations of two consecutive rounds
   int eig_grid;                     // co-resident blocks of the Jacobi kernel
   double2* d_small[6];              // I x I temporaries
@@ -136,8 +142,26 @@ sky_status energy_impl(Ctx* c, const double* rho, const double* tau, const doubl
 sky_status sp_spread_impl(Ctx* c, const double* eps, const double* hn2, int A, double* out);
 sky_status overlap_impl(Ctx* c, const void* a, const void* b, int I, double2* X);
 sky_status rotate_impl(Ctx* c, const void* phi, const double2* M, int I, void* out);
+struct ZJobs {
+  const double2* A[kMaxBatch];
+  const double2* B[kMaxBatch];
+  double2* C[kMaxBatch];
+  int n[kMaxBatch];
+  const int* run[kMaxBatch];
+  const int* stop[kMaxBatch];
+  int np;
+  bool ah, bh;
+};
+ZJobs zjobs(int np, bool ah, bool bh, const double2* const* A, const double2* const* B,
+            double2* const* C, const int* n, const int* const* run, const int* const* stop);
+sky_status zgemm_batch(Ctx* c, const ZJobs& j);
 sky_status zgemm_small(Ctx* c, bool ah, bool bh, const double2* A, const double2* B,
                        double2* C, int n, const int* run = nullptr, const int* stop = nullptr);
+sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, double* const* w,
+                      double2* const* Z, const int* run, int run_stride);
+sky_status lowdin_batch(Ctx* c, int np, const double2* const* S, const int* I, double2* const* C);
+sky_status subspace_batch(Ctx* c, int np, const double2* const* H, const double2* const* C,
+                          const int* I, double2* const* M, double* const* eps);
 sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z,
                      const int* run = nullptr);
 sky_status lowdin_impl(Ctx* c, const double2* S, int I, double2* C);

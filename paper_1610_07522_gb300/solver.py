@@ -62,19 +62,21 @@ class Solver:
         self.overlap_events = None   # list to collect (I, start, end) CUDA events, or None
 
     # ------------------------------------------------------------ set-up
-    def _orthonormalize_into_psi(self, q):
-        """psi = Loewdin(phi) (Eqs. Loewedin, orthmatvec), phi holding raw states."""
-        I = self.I[q]
-        B.sky_overlap(self.ctx, self.phi[q], self.phi[q], I, self.S[q])
-        B.sky_orthonormalize(self.ctx, self.S[q], I, self.C[q])
-        B.sky_rotate(self.ctx, self.phi[q], self.C[q], I, self.psi[q])
+    def _species(self):
+        return [q for q in range(2) if self.I[q] > 0]
 
     def load(self, psi0, rho0=None, tau0=None):
-        """Fig. 1 step 1 from host arrays: orthonormalise the trial states; the
-        mean field from their densities or from given initial densities."""
-        for q in range(2):
+        """Fig. 1 step 1 from host arrays: orthonormalise the trial states
+        (psi = Loewdin(phi), Eqs. Loewedin, orthmatvec); the mean field from
+        their densities or from given initial densities."""
+        qs = self._species()
+        for q in qs:
             self.phi[q].copy_(torch.from_numpy(np.ascontiguousarray(psi0[q])).to(self.cdtype))
-            self._orthonormalize_into_psi(q)
+            B.sky_overlap(self.ctx, self.phi[q], self.phi[q], self.I[q], self.S[q])
+        B.sky_orthonormalize_batched(self.ctx, [self.S[q] for q in qs], [self.I[q] for q in qs],
+                                     [self.C[q] for q in qs])
+        for q in qs:
+            B.sky_rotate(self.ctx, self.phi[q], self.C[q], self.I[q], self.psi[q])
         if rho0 is None:
             self.densities()
         else:
@@ -86,12 +88,12 @@ class Solver:
 
     # ------------------------------------------------------------ iteration
     def densities(self):
-        for q in range(2):
+        for q in range(2):   # I = 0 gives zero densities
             B.sky_densities(self.ctx, self.psi[q], self.I[q], self.rho[q], self.tau[q], self.J[q],
                             self.divJ[q])
 
     def species_step(self, q):
-        """Steps 2-3 for species q."""
+        """Step 2 and 3a for species q: h psi, damped step, h phi, S and H."""
         I, o = self.I[q], self.off[q]
         ctx = self.ctx
         B.sky_apply_h(ctx, self.U[q], self.Bf[q], self.W[q], self.psi[q], self.h[q], I,
@@ -109,14 +111,25 @@ class Solver:
                 B.sky_overlap(ctx, self.phi[q], rhs, I, X)
                 e1.record(self.stream)
                 self.overlap_events.append((I, e0, e1))
-        B.sky_orthonormalize(ctx, self.S[q], I, self.C[q])
-        B.sky_subspace_diag(ctx, self.H[q], self.C[q], I, self.M[q], self.lam[o:o + I])
-        B.sky_rotate(ctx, self.phi[q], self.M[q], I, self.psi[q])
+
+    def ritz_step(self):
+        """Steps 3b-3e for both species: Loewdin factors and Rayleigh-Ritz in one
+        batched solve (the species couple only through the mean field), then
+        the recombination psi = phi M."""
+        qs = self._species()
+        I = [self.I[q] for q in qs]
+        B.sky_orthonormalize_batched(self.ctx, [self.S[q] for q in qs], I, [self.C[q] for q in qs])
+        B.sky_subspace_diag_batched(self.ctx, [self.H[q] for q in qs], [self.C[q] for q in qs], I,
+                                    [self.M[q] for q in qs],
+                                    [self.lam[self.off[q]:self.off[q] + self.I[q]] for q in qs])
+        for q in qs:
+            B.sky_rotate(self.ctx, self.phi[q], self.M[q], self.I[q], self.psi[q])
 
     def step(self, frozen=False):
         """One full iteration (Fig. 1 steps 2-5); enqueued, not synchronised."""
-        for q in range(2):
+        for q in self._species():
             self.species_step(q)
+        self.ritz_step()
         B.sky_sp_spread(self.ctx, self.eps, self.hn2, self.A, self.spread)
         self.densities()
         if not frozen:

@@ -475,3 +475,38 @@ def test_fp32_forms_follow_the_fp64_iteration(prec):
     print(f"form {prec}: max |dE|/A {worst['dE/A']:.2e} MeV, max |d eps| {worst['dlam']:.2e} MeV, "
           f"rho rel {worst['drho']:.2e}, ||Psi^H Psi - I||_max {ortho:.2e}")
     s.close()
+
+
+def test_batched_loewdin_and_rayleigh_ritz():
+    """Two species of different sizes in one batched solve: one overlap close to
+    the identity (Newton-Schulz route), one far from it (eigendecomposition
+    route); each matches the oracle's Loewdin factor and Ritz values."""
+    rng = np.random.default_rng(41)
+    with Ctx((16, 16, 16), max_states=40) as c:
+        g = c.grid
+        psi = O.orthonormalize(IN.random_superpositions(g.n, g.dx, 37, rng), g)
+        near = psi + 1e-3 * IN.random_superpositions(g.n, g.dx, 37, rng) / np.sqrt(g.G)
+        # S close to 4 I: outside the region (0, 3) where Newton-Schulz converges
+        far = 2.0 * O.orthonormalize(IN.random_superpositions(g.n, g.dx, 16, rng), g)
+        far = far + 0.05 * IN.random_superpositions(g.n, g.dx, 16, rng) / np.sqrt(g.G)
+        Ss, Hs, Cw, Lw = [], [], [], []
+        for phi in (near, far):
+            U, Bf, W = _fields(g, rng)
+            hphi = O.apply_h(phi, U, Bf, W, g)
+            S, H = O.overlap(phi, phi, g), O.overlap(phi, hphi, g)
+            Ss.append(S); Hs.append(H); Cw.append(O.loewdin(S)); Lw.append(O.rayleigh_ritz(S, H)[1])
+        I = [37, 16]
+        dS = [dev(x) for x in Ss]; dH = [dev(x) for x in Hs]
+        C = [torch.zeros_like(x) for x in dS]; M = [torch.zeros_like(x) for x in dS]
+        lam = [torch.zeros(n, dtype=torch.float64, device="cuda:0") for n in I]
+        B.sky_stats(c.ctx, reset=True)
+        B.sky_orthonormalize_batched(c.ctx, dS, I, C)
+        B.sky_subspace_diag_batched(c.ctx, dH, C, I, M, lam)
+        B.sky_sync(c.ctx)
+        st = B.sky_stats(c.ctx)
+        assert st["loewdin_calls"] == 2 and st["loewdin_newton_schulz"] == 1
+        for b in range(2):
+            assert relerr(host(C[b]), Cw[b]) < 1e-11
+            assert np.max(np.abs(host(lam[b]) - Lw[b])) < 1e-9
+            Mg = host(M[b])
+            assert np.max(np.abs(Mg.conj().T @ Ss[b] @ Mg - np.eye(I[b]))) < 1e-11
