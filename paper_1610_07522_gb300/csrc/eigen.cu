@@ -186,7 +186,9 @@ struct JacProb {
 
 struct JacBatch {
   JacProb p[kMaxBatch];
-  long long off[kMaxBatch + 1];   // work items per round, prefix over problems
+  // prefix offsets over problems of the three kinds of work items of a round:
+  // next-round rotations (m/2), 2x2 block updates (h(h+1)/2), V row updates (m h)
+  int offR[kMaxBatch + 1], offB[kMaxBatch + 1], offV[kMaxBatch + 1];
   int np;
   double tol;
   int max_sweeps;
@@ -231,6 +233,7 @@ __device__ __forceinline__ void sum_parts(const double* part, double& off, doubl
 __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
   __shared__ int s_done[kMaxBatch], s_which[kMaxBatch], s_sweep[kMaxBatch];
   __shared__ double s_thr[kMaxBatch];
+  __shared__ double s_acc[kMaxBatch][2];   // (off, tot) of problems ending a sweep
   __shared__ int s_active;
   const int gtid = blockIdx.x * kJacThreads + threadIdx.x;
   const int gsz = gridDim.x * kJacThreads;
@@ -260,6 +263,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
       s_thr[b] = 1e-19 * sqrt(tot);   // rotations below this change nothing measurable
       s_which[b] = 0;
       s_sweep[b] = 0;
+      s_acc[b][0] = s_acc[b][1] = 0.0;
       active |= !s_done[b];
     }
     s_active = active;
@@ -278,30 +282,65 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
     }
   }
   if (!grid_barrier(a.bar, epoch, a.status)) return;
-  double acc_off[kMaxBatch], acc_tot[kMaxBatch];
   for (int t = 0; s_active; ++t) {
-#pragma unroll
-    for (int b = 0; b < kMaxBatch; ++b) acc_off[b] = acc_tot[b] = 0.0;
+    // One item per thread.  Work is dealt out in 32-item warp chunks round-robin
+    // over the blocks, so every SM gets an even share of each kind of item (the
+    // FP64 units of one SM are narrow) while warps keep contiguous items.
+    // Items: next-round rotations, then 2x2 block updates, then V row updates.
     // Pair indices follow from (k, r) alone, so every item issues its matrix
-    // loads together with the rotation loads (one L2 round trip, not two).
-    for (long long w = gtid; w < a.off[np]; w += gsz) {
-      int b = 0;
-      while (w >= a.off[b + 1]) ++b;
-      if (s_done[b]) continue;
-      const JacProb& P = a.p[b];
-      const int m = P.m, n = P.n, h = m / 2;
-      const int r = t % (m - 1);
-      const bool last = (r == m - 2);
-      const int rn = last ? 0 : r + 1;
-      const double2* cur = s_which[b] ? P.A1 : P.A0;
-      double2* nxt = s_which[b] ? P.A0 : P.A1;
-      const JRot* Rc = (t & 1) ? P.R1 : P.R0;
-      JRot* Rn = (t & 1) ? P.R0 : P.R1;
-      const int nblk = h * (h + 1) / 2, nV = m * h;
-      const int u = (int)(w - a.off[b]);
-      if (u < nblk) {
+    // loads together with the rotation loads (one L2 round trip).
+    const int nR = a.offR[np], nB = a.offB[np], total = nR + nB + a.offV[np];
+    const int lane = threadIdx.x & 31, wslot = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * (kJacThreads / 32);
+    for (int ch = wslot * (int)gridDim.x + blockIdx.x; ch * 32 < total; ch += nwarps) {
+      int w = ch * 32 + lane;
+      if (w >= total) continue;
+      if (w < nR) {
+        // rotation of pair k of the next round from this round's result,
+        // recomputed from the old blocks (no extra barrier)
+        int b = 0;
+        while (w >= a.offR[b + 1]) ++b;
+        if (s_done[b]) continue;
+        const JacProb& P = a.p[b];
+        const int m = P.m, n = P.n;
+        const int r = t % (m - 1);
+        const int rn = (r == m - 2) ? 0 : r + 1;
+        const double2* cur = s_which[b] ? P.A1 : P.A0;
+        const JRot* Rc = (t & 1) ? P.R1 : P.R0;
+        JRot* Rn = (t & 1) ? P.R0 : P.R1;
+        const int k = w - a.offR[b];
+        int p, q;
+        pair_of(k, rn, m, p, q);
+        const int kp = pair_index(p, r, m), kq = pair_index(q, r, m);
+        int pp, pq, qp, qq;
+        pair_of(kp, r, m, pp, pq);
+        pair_of(kq, r, m, qp, qq);
+        const double2 b00 = cur[(long long)pp * m + qp], b01 = cur[(long long)pp * m + qq];
+        const double2 b10 = cur[(long long)pq * m + qp], b11 = cur[(long long)pq * m + qq];
+        const double dpp = cur[(long long)p * m + p].x, dqq = cur[(long long)q * m + q].x;
+        const JRot Rp = Rc[kp];
+        const JRot Rq = Rc[kq];
+        const int lp = (p == pp) ? 0 : 1, lq = (q == qp) ? 0 : 1;
+        const double app = Rp.id ? dpp : (lp ? Rp.dq : Rp.dp);
+        const double aqq = Rq.id ? dqq : (lq ? Rq.dq : Rq.dp);
+        double2 t0, t1;
+        right_col(Rq, lq, b00, b01, b10, b11, t0, t1);
+        const double2 z = left_row(Rp, lp, t0, t1);
+        Rn[k] = make_rot(app, aqq, z, p, q, n, s_thr[b]);
+      } else if ((w -= nR) < nB) {
         // 2x2 block (P1 rows, P2 columns), k1 >= k2: B' = J1^H B J2 into the
         // other buffer, and its conjugate transpose into the mirrored block
+        int b = 0;
+        while (w >= a.offB[b + 1]) ++b;
+        if (s_done[b]) continue;
+        const JacProb& P = a.p[b];
+        const int m = P.m;
+        const int r = t % (m - 1);
+        const bool last = (r == m - 2);
+        const double2* cur = s_which[b] ? P.A1 : P.A0;
+        double2* nxt = s_which[b] ? P.A0 : P.A1;
+        const JRot* Rc = (t & 1) ? P.R1 : P.R0;
+        const int u = w - a.offB[b];
         int k1 = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
         while ((k1 + 1) * (k1 + 2) / 2 <= u) ++k1;
         while (k1 * (k1 + 1) / 2 > u) --k1;
@@ -341,13 +380,21 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
           const double w00 = o00.x * o00.x + o00.y * o00.y, w01 = o01.x * o01.x + o01.y * o01.y;
           const double w10 = o10.x * o10.x + o10.y * o10.y, w11 = o11.x * o11.x + o11.y * o11.y;
           const double mult = (k1 != k2) ? 2.0 : 1.0;   // the mirrored block counts too
-          acc_tot[b] += mult * (w00 + w01 + w10 + w11);
-          acc_off[b] += mult * ((p1 != p2 ? w00 : 0.0) + (p1 != q2 ? w01 : 0.0) +
-                                (q1 != p2 ? w10 : 0.0) + (q1 != q2 ? w11 : 0.0));
+          atomicAdd(&s_acc[b][1], mult * (w00 + w01 + w10 + w11));
+          atomicAdd(&s_acc[b][0], mult * ((p1 != p2 ? w00 : 0.0) + (p1 != q2 ? w01 : 0.0) +
+                                          (q1 != p2 ? w10 : 0.0) + (q1 != q2 ? w11 : 0.0)));
         }
-      } else if (u < nblk + nV) {
+      } else {
+        w -= nB;
         // accumulate the rotation into row `row` of V (in place)
-        const int v = u - nblk, row = v / h, k = v % h;
+        int b = 0;
+        while (w >= a.offV[b + 1]) ++b;
+        if (s_done[b]) continue;
+        const JacProb& P = a.p[b];
+        const int m = P.m, h = m / 2;
+        const int r = t % (m - 1);
+        const JRot* Rc = (t & 1) ? P.R1 : P.R0;
+        const int v = w - a.offV[b], row = v / h, k = v % h;
         int p, q;
         pair_of(k, r, m, p, q);
         double2* vr = P.V + (long long)row * m;
@@ -357,34 +404,18 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
           vr[p] = rx_plus_cy(R.c, vp, R.j10, vq);
           vr[q] = rx_plus_cy(R.s, vp, R.j11, vq);
         }
-      } else {
-        // rotation of pair k of the next round from this round's result,
-        // recomputed here from the old blocks (no extra barrier)
-        const int k = u - nblk - nV;
-        int p, q;
-        pair_of(k, rn, m, p, q);
-        const int kp = pair_index(p, r, m), kq = pair_index(q, r, m);
-        int pp, pq, qp, qq;
-        pair_of(kp, r, m, pp, pq);
-        pair_of(kq, r, m, qp, qq);
-        const double2 b00 = cur[(long long)pp * m + qp], b01 = cur[(long long)pp * m + qq];
-        const double2 b10 = cur[(long long)pq * m + qp], b11 = cur[(long long)pq * m + qq];
-        const double dpp = cur[(long long)p * m + p].x, dqq = cur[(long long)q * m + q].x;
-        const JRot Rp = Rc[kp];
-        const JRot Rq = Rc[kq];
-        const int lp = (p == pp) ? 0 : 1, lq = (q == qp) ? 0 : 1;
-        const double app = Rp.id ? dpp : (lp ? Rp.dq : Rp.dp);
-        const double aqq = Rq.id ? dqq : (lq ? Rq.dq : Rq.dp);
-        double2 t0, t1;
-        right_col(Rq, lq, b00, b01, b10, b11, t0, t1);
-        const double2 z = left_row(Rp, lp, t0, t1);
-        Rn[k] = make_rot(app, aqq, z, p, q, n, s_thr[b]);
       }
     }
     // partial norms of the problems that end a sweep this round
-    for (int b = 0; b < np; ++b) {
-      if (s_done[b] || (t % (a.p[b].m - 1)) != a.p[b].m - 2) continue;
-      block_norms(acc_off[b], acc_tot[b], a.part + (long long)b * 2 * gridDim.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int b = 0; b < np; ++b) {
+        if (s_done[b] || (t % (a.p[b].m - 1)) != a.p[b].m - 2) continue;
+        double* part = a.part + (long long)b * 2 * gridDim.x;
+        part[2 * blockIdx.x] = s_acc[b][0];
+        part[2 * blockIdx.x + 1] = s_acc[b][1];
+        s_acc[b][0] = s_acc[b][1] = 0.0;
+      }
     }
     if (!grid_barrier(a.bar, epoch, a.status)) return;
     if (threadIdx.x == 0) {
@@ -491,7 +522,7 @@ sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, dou
   long long items = 0;
   int nmax = 1, mmax = 2;
   j.np = np; j.run = run; j.run_stride = run_stride;
-  a.np = np; a.off[0] = 0;
+  a.np = np; a.offR[0] = a.offB[0] = a.offV[0] = 0;
   for (int b = 0; b < np; ++b) {
     const int m = n[b] + (n[b] & 1);
     const int h = m / 2;
@@ -506,7 +537,9 @@ sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, dou
     P.R1 = P.R0 + c->eig_slot_rot;
     P.n = n[b]; P.m = m;
     items += (long long)h * (h + 1) / 2 + (long long)m * h + h;
-    a.off[b + 1] = items;
+    a.offR[b + 1] = a.offR[b] + h;
+    a.offB[b + 1] = a.offB[b] + h * (h + 1) / 2;
+    a.offV[b + 1] = a.offV[b] + m * h;
     if (n[b] > nmax) nmax = n[b];
     if (m > mmax) mmax = m;
   }
@@ -517,10 +550,8 @@ sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, dou
   k_jacobi_init<<<gi, 256, 0, c->stream>>>(j, c->d_bar, c->d_eigres);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "jacobi init");
-  int grid = (int)((items + kJacThreads - 1) / kJacThreads);
-  if (grid < c->eig_grid / 2) grid = c->eig_grid / 2;   // spread the FP64 work over the SMs
-  if (grid > c->eig_grid) grid = c->eig_grid;
-  if (grid < 1) grid = 1;
+  (void)items;
+  const int grid = c->eig_grid;   // every SM's FP64 units share each round
   a.tol = 1e-14;
   a.max_sweeps = 60;
   a.part = c->d_eigpart; a.bar = c->d_bar; a.status = c->d_status; a.result = c->d_eigres;
