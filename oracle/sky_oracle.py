@@ -370,9 +370,11 @@ def initial_state(psi0, grid, p, coulomb, rho0=None, tau0=None):
     return State(psi, U, B, W)
 
 
-def iterate(st, grid, p, coulomb, x0, E0, frozen=False):
+def iterate(st, grid, p, coulomb, x0, E0, frozen=False, damping=None):
     """One damped-gradient iteration.  Mutates ``st`` and returns a record
-    with the Ritz values, convergence measure and energy.
+    with the Ritz values, convergence measure and energy.  ``damping``, if
+    given, is a callable (q, U_q, B_q, W_q) -> w [nz,ny,nx] that scales the
+    update of the damped step voxel by voxel (phi = psi - w (psi - phi)).
 
     Step 2: h psi with h^(n); eps = <psi|h|psi>; phi = psi - x0/(T+E0)(h-eps)psi;
             h phi with the same h^(n).
@@ -387,6 +389,9 @@ def iterate(st, grid, p, coulomb, x0, E0, frozen=False):
         eps, hn2 = sp_energies(psi, hpsi, grid)
         eps_l.append(eps); hn2_l.append(hn2)
         phi = damped_step(psi, hpsi, eps, grid, hb2m[q], x0, E0)
+        if damping is not None:
+            w = damping(q, st.U[q], st.B[q], st.W[q])
+            phi = psi - w[None, None] * (psi - phi)
         hphi = apply_h(phi, st.U[q], st.B[q], st.W[q], grid)
         S = overlap(phi, phi, grid)
         H = overlap(phi, hphi, grid)
@@ -405,14 +410,14 @@ def iterate(st, grid, p, coulomb, x0, E0, frozen=False):
 
 
 def solve(psi0, grid, p, coulomb, x0, E0, maxit, tol, rho0=None, tau0=None,
-          frozen=False, callback=None):
+          frozen=False, callback=None, damping=None):
     """Iterate until |E_n/A - E_{n-1}/A| < tol (MeV) or maxit iterations."""
     st = initial_state(psi0, grid, p, coulomb, rho0, tau0)
     A = st.psi[0].shape[0] + st.psi[1].shape[0]
     hist = []
     E_prev = None
     for it in range(maxit):
-        rec = iterate(st, grid, p, coulomb, x0, E0, frozen=frozen)
+        rec = iterate(st, grid, p, coulomb, x0, E0, frozen=frozen, damping=damping)
         rec["it"] = it
         hist.append({k: rec[k] for k in ("it", "E", "delta_eps")})
         if callback is not None:
