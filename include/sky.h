@@ -123,7 +123,10 @@ sky_status sky_apply_h(sky_ctx* ctx, const double* U, const double* B, const dou
  * diagonal in momentum space (hb2m_q of species q = 0 neutrons, 1 protons).
  * psi, hpsi, phi: [I][2][G]; phi must not overlap psi or hpsi; eps: [I].
  * x0 dimensionless step (the paper's delta), E0 in MeV.
- * w must be NULL (a per-voxel damping weight is not built). */
+ * w: NULL for the paper's step, or a device float [G] weight that scales
+ * the update voxel by voxel, phi = psi - w(r) x0 P (hpsi - eps psi), the same
+ * w for both spin components (e.g. from sky_net_forward).  Any w keeps the
+ * fixed point, where (h - eps) psi = 0. */
 sky_status sky_damped_step(sky_ctx* ctx, int q, const void* psi, const void* hpsi,
                            const double* eps, void* phi, int I, double x0, double E0,
                            const float* w);
@@ -192,6 +195,66 @@ sky_status sky_energy(sky_ctx* ctx, const double* rho, const double* tau,
  * over A states (pass both species' arrays back to back). */
 sky_status sky_sp_spread(sky_ctx* ctx, const double* eps, const double* hnorm2, int A,
                          double* out);
+
+/* ---- Learned damping weight ----------------------------------------------
+ * The paper has no learned part; these calls build and train a per-voxel
+ * weight w_q(r) for the damped step of Eq. dampstep (sky_damped_step's w).
+ * Network: three periodic 3x3x3 cross-correlations,
+ *   x  = (U_q / SKY_NET_USCALE, B_q / hb2m_q - 1, |W_q| / SKY_NET_WSCALE)
+ *   h1 = tanh(conv(x; W1, b1)), h2 = tanh(conv(h1; W2, b2)),
+ *   w  = SKY_NET_WMAX * sigmoid(conv(h2; W3, b3)),
+ * conv(x; W, b)_o(r) = b_o + sum_i sum_d W[o][i][t] x_i(r + d) over
+ * d in {-1, 0, 1}^3 with t = 9 (dz+1) + 3 (dy+1) + (dx+1).
+ * theta: device float [SKY_NET_NPARAM] = W1 [16][3][27], b1 [16],
+ * W2 [16][16][27], b2 [16], W3 [1][16][27], b3 [1].
+ * ws: device float workspace [SKY_NET_WS_PER_POINT * G], owned by the caller;
+ * sky_net_backward reads the activations the previous sky_net_forward on the
+ * same ws left there.  Everything is FP32 except the loss, the statistics and
+ * the gradients (FP64); all sums are in a fixed order (deterministic). */
+#define SKY_NET_HIDDEN 16
+#define SKY_NET_NPARAM 8673
+#define SKY_NET_WS_PER_POINT 69
+#define SKY_NET_WMAX 4.0
+#define SKY_NET_USCALE 50.0
+#define SKY_NET_WSCALE 5.0
+
+/* The network's weight w_net [G] from the mean field of species q (U, B: [G];
+ * W: [3][G], the arrays sky_apply_h takes) is kept in ws; w receives the
+ * weight the step uses, w = 1 + scale (w_net - 1), scale in [0, 1] (1: the
+ * network's own weight, 0: the paper's step; a solver may lower it when the
+ * energy rises). */
+sky_status sky_net_forward(sky_ctx* ctx, int q, const float* theta, const double* U,
+                           const double* B, const double* W, double scale, float* ws, float* w);
+
+/* Loss L = sum_r (a w_net^2 - 2 b w_net + c) / norm of one training sample,
+ * where abc = [a; b; c] ([3][G] double) and norm (device double [1]) come
+ * from sky_precond_stats and w_net is the network weight the last
+ * sky_net_forward left in ws.  Adds L to loss[0] and dL/dtheta to grad
+ * [SKY_NET_NPARAM] (both device doubles, accumulated so that several
+ * samples sum). */
+sky_status sky_net_backward(sky_ctx* ctx, const float* theta, float* ws, const double* abc,
+                            const double* norm, double* grad, double* loss);
+
+/* One Adam step (Kingma and Ba, 2015) on theta with the moment estimates m, v
+ * (device doubles [SKY_NET_NPARAM], zero before step 1); step counts from 1.
+ * Sets grad to zero after using it. */
+sky_status sky_net_adam(sky_ctx* ctx, float* theta, double* grad, double* m, double* v, int step,
+                        double lr, double beta1, double beta2, double eps);
+
+/* Full cross overlap X[a*I + b] = <a_a | b_b> = dV sum_v conj(a_a[v]) b_b[v]
+ * of two different state sets (no Hermitian mirror), FP64 accumulation in
+ * every precision.  a, b: [I][2][G]; X: [I*I] double2.  With a = psi* and
+ * b = psi, sky_rotate(psi*, X) gives the projection of psi on span(psi*). */
+sky_status sky_cross_overlap(sky_ctx* ctx, const void* a, const void* b, int I, double* X);
+
+/* Per-voxel statistics of the one-step loss for one species:
+ *   a(r) = sum |psi - phi|^2,  b(r) = sum Re(conj(psi - phi)(psi - ppsi)),
+ *   c(r) = sum |psi - ppsi|^2  (sums over the I states and both spins),
+ * with phi the plain damped step of psi (w = NULL) and ppsi the projection
+ * of psi on the converged occupied space.  abc: [3][G] double; norm[0] =
+ * sum_r c(r).  psi, phi, ppsi: [I][2][G] in the context precision. */
+sky_status sky_precond_stats(sky_ctx* ctx, const void* psi, const void* phi, const void* ppsi,
+                             int I, double* abc, double* norm);
 
 /* ---- Overlap matrix without a context or any device allocation -----------
  * The paper has no counterpart to this entry point.  It computes the same

@@ -60,7 +60,20 @@ _SIGNATURES = {
     "sky_orthonormalize_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_P)]),
     "sky_subspace_diag_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I),
                                        ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "sky_net_forward": (_I, [_P, _I, _P, _P, _P, _P, _D, _P, _P]),
+    "sky_net_backward": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "sky_net_adam": (_I, [_P, _P, _P, _P, _P, _I, _D, _D, _D, _D]),
+    "sky_cross_overlap": (_I, [_P, _P, _P, _I, _P]),
+    "sky_precond_stats": (_I, [_P, _P, _P, _P, _I, _P, _P]),
 }
+
+# Constants of the damping network (the #defines of include/sky.h).
+SKY_NET_HIDDEN = 16
+SKY_NET_NPARAM = 8673
+SKY_NET_WS_PER_POINT = 69
+SKY_NET_WMAX = 4.0
+SKY_NET_USCALE = 50.0
+SKY_NET_WSCALE = 5.0
 
 _LIB = None
 
@@ -212,3 +225,27 @@ def sky_overlap_noalloc(a, b, I, V, dV, prec, X, stream=0):
                                    _P(stream) if stream else None)
     if st != SKY_OK:
         raise SkyError(st, "sky_overlap_noalloc failed")
+
+
+def sky_net_forward(ctx, q, theta, U, B, W, ws, w, scale=1.0):
+    _check(ctx, lib().sky_net_forward(ctx, int(q), _ptr(theta), _ptr(U), _ptr(B), _ptr(W),
+                                      float(scale), _ptr(ws), _ptr(w)))
+
+
+def sky_net_backward(ctx, theta, ws, abc, norm, grad, loss):
+    _check(ctx, lib().sky_net_backward(ctx, _ptr(theta), _ptr(ws), _ptr(abc), _ptr(norm),
+                                       _ptr(grad), _ptr(loss)))
+
+
+def sky_net_adam(ctx, theta, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(ctx, lib().sky_net_adam(ctx, _ptr(theta), _ptr(grad), _ptr(m), _ptr(v), int(step),
+                                   float(lr), float(beta1), float(beta2), float(eps)))
+
+
+def sky_cross_overlap(ctx, a, b, I, X):
+    _check(ctx, lib().sky_cross_overlap(ctx, _ptr(a), _ptr(b), int(I), _ptr(X)))
+
+
+def sky_precond_stats(ctx, psi, phi, ppsi, I, abc, norm):
+    _check(ctx, lib().sky_precond_stats(ctx, _ptr(psi), _ptr(phi), _ptr(ppsi), int(I), _ptr(abc),
+                                        _ptr(norm)))

@@ -56,6 +56,35 @@ sky_status overlap_impl(Ctx* c, const void* a, const void* b, int I, double2* X)
   return cuda_check(c, cudaGetLastError(), "overlap reduce");
 }
 
+// Full X = <a|b> for two different state sets (no Hermitian mirror), FP64
+// accumulation in every precision: split-K like overlap_impl.
+sky_status cross_overlap_impl(Ctx* c, const void* a, const void* b, int I, double2* X) {
+  const long long V = 2LL * c->G;
+  const int nt = (I + BM - 1) / BM;
+  const int ntiles = nt * nt;
+  const long long kblocks = (V + BK - 1) / BK;
+  long long want = c->ov_slots / ntiles;
+  if (want < 1) want = 1;
+  if (want > kblocks) want = kblocks;
+  const long long kchunk = ((kblocks + want - 1) / want) * BK;
+  const int nsplit = (int)((V + kchunk - 1) / kchunk);
+  if ((size_t)nsplit * I * I > c->gpart_elems)
+    return set_err(c, SKY_EINVAL, "cross overlap scratch too small for I=%d", I);
+  dim3 grid(ntiles, nsplit);
+  if (c->prec == SKY_F64)
+    k_overlap<double2, true><<<grid, 256, 0, c->stream>>>((const double2*)a, (const double2*)b, I, V,
+                                                          kchunk, c->d_gpart);
+  else
+    k_overlap<float2, true><<<grid, 256, 0, c->stream>>>((const float2*)a, (const float2*)b, I, V,
+                                                         kchunk, c->d_gpart);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(c, e, "cross overlap");
+  k_overlap_reduce_full<<<div_up((long long)I * I, 256), 256, 0, c->stream>>>(c->d_gpart, nsplit, I,
+                                                                            c->dV, X); note_launch();
+  return cuda_check(c, cudaGetLastError(), "cross overlap reduce");
+}
+
 // ---------------------------------------------------------------- rotate
 // out[a][v] = sum_b M[b][a] phi[b][v]; tile rows a (32) x columns v (32).
 // Three real products per complex multiply-add (Gauss):

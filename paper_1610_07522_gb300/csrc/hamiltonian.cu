@@ -61,13 +61,18 @@ template <typename T> struct OpDampX {
   }
   __device__ __forceinline__ void store(long long b, int i, cx<T> v) const { a[b * G + i] = v; }
 };
-// Damped step, z pass: inverse along z, phi = psi - result.
+// Damped step, z pass: inverse along z, phi = psi - w(r) result (w = 1 when
+// no per-voxel weight is given).
 template <typename T> struct OpDampZInv {
   static constexpr bool kFwd = false, kInv = true;
-  const cx<T>* psi; cx<T>* phi; long long G;
+  const cx<T>* psi; cx<T>* phi; const float* w; long long G;
   __device__ __forceinline__ cx<T> load(long long b, int i) const { return phi[b * G + i]; }
   __device__ __forceinline__ void mid(cx<T>&, long long, int, int) const {}
   __device__ __forceinline__ void store(long long b, int i, cx<T> v) const {
+    if (w) {
+      const T s = (T)w[i];
+      v = mkc<T>(s * v.x, s * v.y);
+    }
     phi[b * G + i] = psi[b * G + i] - v;
   }
 };
@@ -270,7 +275,8 @@ __global__ void k_damp_table(double* P, const double* kx, const double* ky, cons
 
 template <typename T>
 static sky_status damped_t(Ctx* c, int q, const cx<T>* psi, const cx<T>* hpsi,
-                           const double* eps, cx<T>* phi, int I, double x0, double E0) {
+                           const double* eps, cx<T>* phi, int I, double x0, double E0,
+                           const float* w) {
   const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
   const long long G = c->G;
   cudaError_t e;
@@ -285,7 +291,7 @@ static sky_status damped_t(Ctx* c, int q, const cx<T>* psi, const cx<T>* hpsi,
   OpPass<T, false> o2{phi, G};
   OpDampX<T> o3{phi, c->d_damp[q], (T)(x0 / (double)G), G};
   OpPass<T, true> o4{phi, G};
-  OpDampZInv<T> o5{psi, phi, G};
+  OpDampZInv<T> o5{psi, phi, w, G};
   constexpr bool L = std::is_same<T, float>::value;
   e = dispatch_n<L>(nz, [&](auto NC) { return launch_line<T, decltype(NC)::value, 2>(o1, nx, ny, nz, nb, c->stream); });
   if (e == cudaSuccess)
@@ -300,12 +306,13 @@ static sky_status damped_t(Ctx* c, int q, const cx<T>* psi, const cx<T>* hpsi,
 }
 
 sky_status damped_step_impl(Ctx* c, int q, const void* psi, const void* hpsi,
-                            const double* eps, void* phi, int I, double x0, double E0) {
+                            const double* eps, void* phi, int I, double x0, double E0,
+                            const float* w) {
   if (c->prec == SKY_F64)
     return damped_t<double>(c, q, (const double2*)psi, (const double2*)hpsi, eps,
-                            (double2*)phi, I, x0, E0);
+                            (double2*)phi, I, x0, E0, w);
   return damped_t<float>(c, q, (const float2*)psi, (const float2*)hpsi, eps, (float2*)phi, I,
-                         x0, E0);
+                         x0, E0, w);
 }
 
 // ------------------------------------------------------------ densities

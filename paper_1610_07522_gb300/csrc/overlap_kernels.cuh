@@ -36,12 +36,13 @@ __device__ __forceinline__ void tri_tile(int t, int& ti, int& tj) {
   tj = t - i * (i + 1) / 2;
 }
 
-// part[split][a][b] = sum_{v in split} conj(A[a][v]) Bm[b][v] for the lower tiles.
+// part[split][a][b] = sum_{v in split} conj(A[a][v]) Bm[b][v] for the lower
+// tiles (FULL: for every tile, blockIdx.x = ti * ntile + tj).
 // Three real products per complex multiply-add (Gauss):
 //   P1 = sum a.x b.x,  P2 = sum a.y b.y,  P3 = sum (a.x - a.y)(b.x + b.y),
 //   Re = P1 + P2,  Im = P3 - P1 + P2;
 // the sums a.x - a.y and b.x + b.y are formed once when staging the tile.
-template <typename S>
+template <typename S, bool FULL = false>
 __global__ void __launch_bounds__(256) k_overlap(const S* __restrict__ A, const S* __restrict__ Bm,
                                                  int I, long long V, long long kchunk,
                                                  double2* __restrict__ part) {
@@ -50,7 +51,13 @@ __global__ void __launch_bounds__(256) k_overlap(const S* __restrict__ A, const 
   __shared__ double Ad[BK][BM + 1];
   __shared__ double Bd[BK][BN + 1];
   int ti, tj;
-  tri_tile(blockIdx.x, ti, tj);
+  if (FULL) {
+    const int nt = (I + BM - 1) / BM;
+    ti = blockIdx.x / nt;
+    tj = blockIdx.x % nt;
+  } else {
+    tri_tile(blockIdx.x, ti, tj);
+  }
   const int r0 = ti * BM, c0 = tj * BN;
   const long long kb = (long long)blockIdx.y * kchunk;
   const long long ke = (kb + kchunk) < V ? (kb + kchunk) : V;
@@ -102,7 +109,7 @@ __global__ void __launch_bounds__(256) k_overlap(const S* __restrict__ A, const 
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int r = r0 + ty * 2 + i, cc = c0 + tx * 2 + j;
-      if (r < I && cc < I && r >= cc)
+      if (r < I && cc < I && (FULL || r >= cc))
         dst[(long long)r * I + cc] = make_double2(p1[i][j] + p2[i][j], p3[i][j] - p1[i][j] + p2[i][j]);
     }
 }
@@ -118,6 +125,16 @@ static __global__ void k_overlap_reduce(const double2* part, int nsplit, int I, 
   s = dV * s;
   X[(long long)a * I + b] = s;
   if (a != b) X[(long long)b * I + a] = conjx(s);
+}
+
+// X[a][b] = dV sum_split part for every (a, b).
+static __global__ void k_overlap_reduce_full(const double2* part, int nsplit, int I, double dV,
+                                             double2* X) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)I * I) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int k = 0; k < nsplit; ++k) s = s + part[(long long)k * I * I + e];
+  X[e] = dV * s;
 }
 
 }  // namespace sky

@@ -78,7 +78,7 @@ static void free_all(Ctx* c) {
                   c->d_small[3], c->d_small[4], c->d_small[5], c->d_gate,
                   c->d_stats, c->d_tcA[0], c->d_tcA[1], c->d_tcA[2], c->d_tcB[0],
                   c->d_tcB[1], c->d_tcB[2], c->d_tcRotA[0], c->d_tcRotA[1], c->d_tcRotA[2],
-                  c->d_tcPart};
+                  c->d_tcPart, c->d_netpart};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -217,6 +217,7 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
     c->tc_partial_elems = part;
   }
   ALLOC(c->d_stats, 8);
+  ALLOC(c->d_netpart, net_partial_elems(c->G));
   if (s == SKY_OK) {
     c->eig_grid = jacobi_max_grid(c);
     ALLOC(c->d_eigpart, (size_t)2 * c->eig_grid * kMaxBatch);
@@ -320,9 +321,8 @@ sky_status sky_damped_step(sky_ctx* c, int q, const void* psi, const void* hpsi,
   if (I == 0) return SKY_OK;
   if (q != 0 && q != 1) return set_err(c, SKY_EINVAL, "damped_step: q must be 0 or 1");
   if (!psi || !hpsi || !eps || !phi) return set_err(c, SKY_EINVAL, "damped_step: null pointer");
-  if (w) return set_err(c, SKY_EUNSUPPORTED, "damped_step: per-voxel weight not built");
   if (phi == psi || phi == hpsi) return set_err(c, SKY_EINVAL, "damped_step: phi must be a separate buffer");
-  return damped_step_impl(c, q, psi, hpsi, eps, phi, I, x0, E0);
+  return damped_step_impl(c, q, psi, hpsi, eps, phi, I, x0, E0, w);
 }
 
 sky_status sky_overlap(sky_ctx* c, const void* a, const void* b, int I, double* X) {
@@ -415,6 +415,48 @@ sky_status sky_sp_spread(sky_ctx* c, const double* eps, const double* hnorm2, in
   if (!c) return SKY_EINVAL;
   if (A < 0 || (A > 0 && (!eps || !hnorm2)) || !out) return set_err(c, SKY_EINVAL, "sp_spread: bad arguments");
   return sp_spread_impl(c, eps, hnorm2, A, out);
+}
+
+sky_status sky_net_forward(sky_ctx* c, int q, const float* theta, const double* U,
+                           const double* B, const double* W, double scale, float* ws, float* w) {
+  if (!c) return SKY_EINVAL;
+  if (q != 0 && q != 1) return set_err(c, SKY_EINVAL, "net_forward: q must be 0 or 1");
+  if (!theta || !U || !B || !W || !ws || !w) return set_err(c, SKY_EINVAL, "net_forward: null pointer");
+  if (!(scale >= 0.0 && scale <= 1.0)) return set_err(c, SKY_EINVAL, "net_forward: scale outside [0, 1]");
+  return net_forward_impl(c, q, theta, U, B, W, scale, ws, w);
+}
+
+sky_status sky_net_backward(sky_ctx* c, const float* theta, float* ws, const double* abc,
+                            const double* norm, double* grad, double* loss) {
+  if (!c) return SKY_EINVAL;
+  if (!theta || !ws || !abc || !norm || !grad || !loss)
+    return set_err(c, SKY_EINVAL, "net_backward: null pointer");
+  return net_backward_impl(c, theta, ws, abc, norm, grad, loss);
+}
+
+sky_status sky_net_adam(sky_ctx* c, float* theta, double* grad, double* m, double* v, int step,
+                        double lr, double beta1, double beta2, double eps) {
+  if (!c) return SKY_EINVAL;
+  if (!theta || !grad || !m || !v) return set_err(c, SKY_EINVAL, "net_adam: null pointer");
+  if (step < 1 || !(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) ||
+      !(eps >= 0.0))
+    return set_err(c, SKY_EINVAL, "net_adam: bad hyper-parameters");
+  return net_adam_impl(c, theta, grad, m, v, step, lr, beta1, beta2, eps);
+}
+
+sky_status sky_cross_overlap(sky_ctx* c, const void* a, const void* b, int I, double* X) {
+  CHECK_CTX();
+  if (I == 0) return SKY_OK;
+  if (!a || !b || !X) return set_err(c, SKY_EINVAL, "cross_overlap: null pointer");
+  return cross_overlap_impl(c, a, b, I, (double2*)X);
+}
+
+sky_status sky_precond_stats(sky_ctx* c, const void* psi, const void* phi, const void* ppsi, int I,
+                             double* abc, double* norm) {
+  CHECK_CTX();
+  if ((I > 0 && (!psi || !phi || !ppsi)) || !abc || !norm)
+    return set_err(c, SKY_EINVAL, "precond_stats: null pointer");
+  return precond_stats_impl(c, psi, phi, ppsi, I, abc, norm);
 }
 
 }  // extern "C"

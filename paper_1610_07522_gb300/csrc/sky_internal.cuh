@@ -108,6 +108,7 @@ struct Ctx {
   size_t tc_partial_elems;
   int* d_gate;                      // device-side gates of the Loewdin paths [8]
   long long* d_stats;               // solver counters reported by sky_stats [8]
+  double* d_netpart;                // partial sums of the damping-network kernels
   char err[256];
 };
 
@@ -132,7 +133,8 @@ sky_status upload_twiddles_fields(Ctx* c);
 sky_status apply_h_impl(Ctx* c, const double* U, const double* B, const double* W,
                         const void* psi, void* hpsi, int I, double* eps, double* hn2);
 sky_status damped_step_impl(Ctx* c, int q, const void* psi, const void* hpsi,
-                            const double* eps, void* phi, int I, double x0, double E0);
+                            const double* eps, void* phi, int I, double x0, double E0,
+                            const float* w);
 sky_status densities_impl(Ctx* c, const void* psi, int I, double* rho, double* tau,
                           double* J, double* divJ);
 sky_status mean_fields_impl(Ctx* c, const double* rho, const double* tau,
@@ -142,6 +144,16 @@ sky_status energy_impl(Ctx* c, const double* rho, const double* tau, const doubl
 sky_status sp_spread_impl(Ctx* c, const double* eps, const double* hn2, int A, double* out);
 sky_status overlap_impl(Ctx* c, const void* a, const void* b, int I, double2* X);
 sky_status rotate_impl(Ctx* c, const void* phi, const double2* M, int I, void* out);
+sky_status cross_overlap_impl(Ctx* c, const void* a, const void* b, int I, double2* X);
+size_t net_partial_elems(int G);
+sky_status net_forward_impl(Ctx* c, int q, const float* theta, const double* U, const double* B,
+                            const double* W, double scale, float* ws, float* w);
+sky_status net_backward_impl(Ctx* c, const float* theta, float* ws, const double* abc,
+                             const double* norm, double* grad, double* loss);
+sky_status net_adam_impl(Ctx* c, float* theta, double* grad, double* m, double* v, int step,
+                         double lr, double beta1, double beta2, double eps);
+sky_status precond_stats_impl(Ctx* c, const void* psi, const void* phi, const void* ppsi, int I,
+                              double* abc, double* norm);
 struct ZJobs {
   const double2* A[kMaxBatch];
   const double2* B[kMaxBatch];

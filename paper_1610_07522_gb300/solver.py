@@ -60,6 +60,25 @@ class Solver:
         self.spread = torch.zeros(2, **f64)
         self.off = (0, workload.N)
         self.overlap_events = None   # list to collect (I, start, end) CUDA events, or None
+        self.damping = None          # learned.DampingNet giving the per-voxel step weight, or None
+        self.damping_on = False
+        self.damping_fallbacks = 0
+        self.wq = None
+
+    def set_damping(self, net, rise_tol=1e-5, min_scale=1.0 / 16.0):
+        """Use the learned per-voxel weight in the damped step,
+        w_q(r) = 1 + s (net(U_q, B_q, |W_q|) - 1) with s = 1 at the start.
+        The plain step is the fallback: each time E/A rises by more than
+        ``rise_tol`` MeV in one iteration (the damped gradient step lowers the
+        energy) ``run`` halves s, and below ``min_scale`` it returns to the
+        plain step for good."""
+        self.damping = net
+        self.damping_on = net is not None
+        self.damping_scale = 1.0
+        self.rise_tol = rise_tol
+        self.min_scale = min_scale
+        if net is not None and self.wq is None:
+            self.wq = torch.zeros((2, self.G), dtype=torch.float32, device=self.device)
 
     # ------------------------------------------------------------ set-up
     def _species(self):
@@ -98,8 +117,13 @@ class Solver:
         ctx = self.ctx
         B.sky_apply_h(ctx, self.U[q], self.Bf[q], self.W[q], self.psi[q], self.h[q], I,
                       self.eps[o:o + I], self.hn2[o:o + I])
+        w = None
+        if self.damping_on:
+            self.damping.weights(ctx, self.G, q, self.U[q], self.Bf[q], self.W[q], self.wq[q],
+                                 self.damping_scale)
+            w = self.wq[q]
         B.sky_damped_step(ctx, q, self.psi[q], self.h[q], self.eps[o:o + I], self.phi[q], I,
-                          self.w.x0, self.w.E0)
+                          self.w.x0, self.w.E0, w)
         B.sky_apply_h(ctx, self.U[q], self.Bf[q], self.W[q], self.phi[q], self.h[q], I)
         for X, rhs in ((self.S[q], self.phi[q]), (self.H[q], self.h[q])):
             if self.overlap_events is None:
@@ -171,6 +195,12 @@ class Solver:
                 callback(it, hist[-1])
             if E_prev is not None and abs(E - E_prev) / self.A < tol:
                 return hist, True
+            if self.damping_on and E_prev is not None and (E - E_prev) / self.A > self.rise_tol:
+                self.damping_scale *= 0.5
+                self.damping_fallbacks += 1
+                hist[-1]["fallback"] = self.damping_scale
+                if self.damping_scale < self.min_scale:
+                    self.damping_on = False
             E_prev = E
         return hist, False
 

@@ -67,3 +67,16 @@ def test_product_path_has_no_cpu_fallback():
             if f.endswith(".py"):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def test_binding_net_constants_match_header():
+    from paper_1610_07522_gb300 import binding
+    from oracle import precond_oracle as P
+    src = open(os.path.join(ROOT, "include", "sky.h")).read()
+    defs = dict(re.findall(r"#define\s+(SKY_NET_[A-Z_]+)\s+([0-9.]+)", src))
+    assert len(defs) == 6
+    for k, v in defs.items():
+        assert float(getattr(binding, k)) == float(v), k
+    assert binding.SKY_NET_NPARAM == P.NPARAM
+    assert binding.SKY_NET_WMAX == P.WMAX and binding.SKY_NET_HIDDEN == P.HIDDEN
+    assert binding.SKY_NET_USCALE == P.U_SCALE and binding.SKY_NET_WSCALE == P.W_SCALE
