@@ -29,6 +29,16 @@ if ROOT not in sys.path:
 
 WORKLOAD = "sly4_24cubed_280n120p_coulomb_fp64"
 FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of GB300 (CUDA cores; FP64 tensor is no faster)
+FORMS = {"fp64": 0, "f32": 1, "bf16x3": 2, "bf16x6": 3}     # sky_prec values
+DTYPES = {"fp64": "f64", "f32": "f32", "bf16x3": "f32+bf16x3", "bf16x6": "f32+bf16x6"}
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
 def _dist():
@@ -184,6 +194,70 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- convergence
+CONV_WORKLOAD = "sly4_16cubed_16n16p_fp64"
+CONV_SNAPS = [0, 2, 5, 12, 25, 60, 120, 180, 240, 360, 480, 600, 720, 840, 960]
+
+
+CONV_WINDOW = 5
+
+
+def convergence_leg(dev, maxit=4000):
+    """Seconds and iterations to |E_n/A - E_{n-1}/A| < 1e-6 MeV (held for
+    CONV_WINDOW consecutive iterations, the same rule for every form) on the
+    16^3, 16n+16p workload for each form: plain FP64, FP32, split-BF16 (x3),
+    and the learned damping weight (trained here, on the GPU, by the
+    library's kernels from a plain FP64 trajectory; its training time is
+    reported apart).  The plain FP64 state is the judge: a form counts as
+    reaching the same fixed point when its E/A is within 1e-4 MeV of it."""
+    import torch
+    from paper_1610_07522_gb300 import binding as B
+    from paper_1610_07522_gb300 import inputs as IN
+    from paper_1610_07522_gb300 import learned
+    from paper_1610_07522_gb300.solver import Solver
+
+    w = IN.WORKLOADS[CONV_WORKLOAD]
+    inp = IN.make_inputs(w)
+
+    def solve(prec, net=None):
+        s = Solver(w, prec=prec, device=dev)
+        if net is not None:
+            s.set_damping(net)
+        s.load(inp["psi0"], inp.get("rho0"), inp.get("tau0"))
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        hist, conv = s.run(maxit=maxit, window=CONV_WINDOW)
+        dt = time.perf_counter() - t
+        r = {"converged": conv, "iterations": len(hist), "seconds": round(dt, 4),
+             "E_per_A": hist[-1]["E"] / s.A}
+        if net is not None:
+            r["fallbacks"] = s.damping_fallbacks
+        s.close()
+        return r
+
+    out = {"workload": CONV_WORKLOAD, "tol_MeV_per_A": w.tol, "window": CONV_WINDOW, "maxit": maxit}
+    for name, prec in (("fp64", B.SKY_F64), ("fp32", B.SKY_F32), ("bf16x3", B.SKY_F32_BF16X3)):
+        out[name] = solve(prec)
+    t = time.perf_counter()
+    s = Solver(w, prec=B.SKY_F64, device=dev)
+    s.load(inp["psi0"], inp.get("rho0"), inp.get("tau0"))
+    samples = learned.collect(s, CONV_SNAPS, ahead=4)
+    net = learned.DampingNet(dev, seed=0)
+    learned.train(net, samples, 300, lr=3e-3)
+    train_s = time.perf_counter() - t
+    s.close()
+    out["learned_train_seconds"] = round(train_s, 3)
+    out["learned_fp64"] = solve(B.SKY_F64, net)
+    out["learned_bf16x3"] = solve(B.SKY_F32_BF16X3, net)
+    base = out["fp64"]["seconds"]
+    forms = ("fp32", "bf16x3", "learned_fp64", "learned_bf16x3")
+    for k in forms:
+        out[k]["same_fixed_point"] = bool(out[k]["converged"] and
+                                          abs(out[k]["E_per_A"] - out["fp64"]["E_per_A"]) < 1e-4)
+    out["speedup_vs_fp64"] = {k: round(base / out[k]["seconds"], 3) for k in forms}
+    return out
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import numpy as np
@@ -198,7 +272,8 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     w = IN.WORKLOADS[args.workload]
     inp = IN.make_inputs(w)
-    s = Solver(w, prec=B.SKY_F64, device=dev)
+    prec = FORMS[args.form]
+    s = Solver(w, prec=prec, device=dev)
     s.load(inp["psi0"], inp.get("rho0"), inp.get("tau0"))
     units = 2 * (w.N + w.Z)
 
@@ -228,14 +303,37 @@ def run_gpu(args):
     ms_max = _max_over_ranks(ms, dist, dev)
     value = ws * units / (ms_max / 1e3)
 
-    # roofline: FP64 overlap (lower triangle, 8 flops per complex MAC)
+    # roofline of the overlap / Hamiltonian matrix call (the largest kernel of
+    # the FP64 step).  FP64 and FP32 forms: k_overlap, FP64 FMA on the lower
+    # triangle, 8 algorithmic flops per complex multiply-add (the 3M form
+    # executes 6).  Split-BF16 forms: the tcgen05 GEMM over the full complex
+    # product, counted as executed BF16 tensor flops (products x 8 I^2 V).
     V = 2 * s.G
-    ov_ms, ov_flops = 0.0, 0.0
-    for I, e0, e1 in ov_events:
+    ov_ms, ov_flops, ov_bytes = 0.0, 0.0, 0.0
+    nprod = {2: 3, 3: 6}.get(prec, 0)
+    csize = s.psi[0].element_size()
+    for I, e0, e1, same in ov_events:
         ov_ms += e0.elapsed_time(e1)
-        ov_flops += 8.0 * V * I * (I + 1) / 2
+        ov_flops += (8.0 * V * I * (I + 1) / 2) if nprod == 0 else nprod * 8.0 * V * I * I
+        ov_bytes += (1 if same else 2) * csize * V * I
     ov_launch_ms = ov_ms / max(1, len(ov_events))
     achieved = ov_flops / (ov_ms / 1e3) / 1e12 if ov_ms > 0 else None
+    peaks, peak_src = _measured_peaks()
+    if nprod == 0:
+        roof = {"kernel": "sky_overlap (k_overlap + split-K reduce), FP64 FMA", "bound": "alu",
+                "peak": FP64_PEAK_TFLOPS,
+                "peak_source": "nominal dense FP64 of GB300 (profiling recipe table)",
+                "traffic": ov_bytes / max(1, len(ov_events)),
+                "traffic_source": "ncu dram__bytes_read+write of one k_overlap launch (I = 120) equals "
+                                  "one read of each distinct operand; scaled to the mean launch of this run"}
+    else:
+        roof = {"kernel": "sky_overlap, split-BF16 (split + tcgen05 GEMM + reduce)", "bound": "tensor",
+                "peak": peaks["bf16_tflops"],
+                "peak_source": f"{peak_src} dense BF16 burst (MEASURED_PEAKS.json)"}
+    roof.setdefault("traffic", None)
+    roof.update({"achieved": achieved, "unit": "TFLOP/s",
+                 "frac": (achieved / roof["peak"]) if achieved else None,
+                 "avg_launch_ms": ov_launch_ms})
 
     # end to end through the public API with pinned host buffers
     host = {
@@ -257,6 +355,10 @@ def run_gpu(args):
     e2e_dt = _max_over_ranks(e2e_dt, dist, dev)
     e2e_value = ws * units / e2e_dt
 
+    conv = None
+    if rank == 0 and not args.no_convergence:
+        conv = convergence_leg(dev)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         r, dt, _ = cpu_baseline_sample(w, inp, 1.0)
@@ -267,21 +369,18 @@ def run_gpu(args):
         "metric": "h.psi spinor-applies/s (full iteration)", "value": value,
         "unit": "spinor-applies/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": DTYPES[args.form], "data": "synthetic",
         "config": {"workload": args.workload, "grid": list(w.grid), "dx_fm": list(w.dx),
-                   "N": w.N, "Z": w.Z, "coulomb": w.coulomb, "precision": "fp64",
+                   "N": w.N, "Z": w.Z, "coulomb": w.coulomb, "precision": args.form,
                    "parallelism": f"replicas x{ws}",
-                   "l2": "working set (psi, phi, h psi: ~0.53 GB) exceeds L2, no flush"},
-        "roofline": {"kernel": "sky_overlap (k_overlap + split-K reduce), FP64 FMA",
-                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                     "traffic": None, "avg_launch_ms": ov_launch_ms,
-                     "peak_source": "nominal dense FP64 of GB300 (profiling recipe table)"},
+                   "l2": f"working set (psi, phi, h psi: {3 * s.psi[0].element_size() * V * (w.N + w.Z) / 1e9:.2f} GB) exceeds L2 (129 MB), no flush"},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "spinor-applies/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": clocks,
+        "convergence": conv,
     }
     s.close()
     if rank == 0:
@@ -298,7 +397,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--form", default="fp64", choices=sorted(FORMS),
+                    help="spinor precision form (fp64: the paper's FP64 method)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-convergence", action="store_true",
+                    help="skip the time-to-convergence comparison of the forms")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -59,7 +59,7 @@ class Solver:
         self.eout = torch.zeros(8, **f64)
         self.spread = torch.zeros(2, **f64)
         self.off = (0, workload.N)
-        self.overlap_events = None   # list to collect (I, start, end) CUDA events, or None
+        self.overlap_events = None   # list to collect (I, start, end, a is b) per overlap call, or None
         self.damping = None          # learned.DampingNet giving the per-voxel step weight, or None
         self.damping_on = False
         self.damping_fallbacks = 0
@@ -134,7 +134,7 @@ class Solver:
                 e0.record(self.stream)
                 B.sky_overlap(ctx, self.phi[q], rhs, I, X)
                 e1.record(self.stream)
-                self.overlap_events.append((I, e0, e1))
+                self.overlap_events.append((I, e0, e1, rhs is self.phi[q]))
 
     def ritz_step(self):
         """Steps 3b-3e for both species: Loewdin factors and Rayleigh-Ritz in one
@@ -182,11 +182,14 @@ class Solver:
         e = self.eout.cpu().numpy()
         return float(e[0]), float(self.spread[0].item()), e
 
-    def run(self, maxit=None, tol=None, callback=None):
-        """Iterate until |E_n/A - E_{n-1}/A| < tol or maxit; returns history."""
+    def run(self, maxit=None, tol=None, callback=None, window=1):
+        """Iterate until |E_n/A - E_{n-1}/A| < tol for ``window`` consecutive
+        iterations (1: the plain rule) or maxit; returns (history, converged).
+        A window > 1 keeps a single small change, e.g. rounding noise of an
+        FP32 form on a flat stretch of the path, from ending the run."""
         maxit = self.w.maxit if maxit is None else maxit
         tol = self.w.tol if tol is None else tol
-        hist, E_prev = [], None
+        hist, E_prev, below = [], None, 0
         for it in range(maxit):
             self.step()
             E, de, _ = self.energy()
@@ -194,7 +197,11 @@ class Solver:
             if callback:
                 callback(it, hist[-1])
             if E_prev is not None and abs(E - E_prev) / self.A < tol:
-                return hist, True
+                below += 1
+                if below >= window:
+                    return hist, True
+            else:
+                below = 0
             if self.damping_on and E_prev is not None and (E - E_prev) / self.A > self.rise_tol:
                 self.damping_scale *= 0.5
                 self.damping_fallbacks += 1
