@@ -152,12 +152,24 @@ sky_status sky_subspace_diag(sky_ctx* ctx, const double* H, const double* C, int
 
 /* ---- Steps 3b-3d for several independent species at once --------------------
  * The same operations as sky_orthonormalize and sky_subspace_diag for nb
- * problems (1 <= nb <= 2, e.g. neutrons and protons, which interact only
- * through the mean field, Sec. 3.2), solved together in one batched launch
- * sequence.  S, H, C, M, eps, I are HOST arrays of nb entries; the matrices
- * they point to are device memory as above. */
+ * problems (e.g. neutrons and protons, which interact only through the mean
+ * field, Sec. 3.2, or the species of many independent boxes), solved together
+ * in one batched launch sequence: one cooperative eigensolver launch serves
+ * every problem.  1 <= nb <= the context's batch capacity (2 after sky_init,
+ * see sky_reserve_batch); each I[b] <= max_states.  The matrices may belong
+ * to other contexts' state sets: only their sizes matter here.  S, H, C, M,
+ * eps, I are HOST arrays of nb entries, read during the call (so a captured
+ * CUDA graph keeps the pointers it was captured with); the matrices they point
+ * to are device memory as above. */
 sky_status sky_orthonormalize_batched(sky_ctx* ctx, int nb, const double* const* S, const int* I,
                                       double* const* C);
+
+/* Raise the batch capacity of the batched calls to nb problems of up to
+ * max_states each (1 <= nb <= 128).  Allocates device memory (about
+ * 13 max_states^2 complex doubles per problem) and synchronises the context
+ * stream; call it outside stream capture.  SKY_ENOMEM leaves the context as
+ * it was. */
+sky_status sky_reserve_batch(sky_ctx* ctx, int nb);
 sky_status sky_subspace_diag_batched(sky_ctx* ctx, int nb, const double* const* H,
                                      const double* const* C, const int* I, double* const* M,
                                      double* const* eps);

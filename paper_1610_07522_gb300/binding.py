@@ -60,6 +60,7 @@ _SIGNATURES = {
     "sky_orthonormalize_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_P)]),
     "sky_subspace_diag_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I),
                                        ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "sky_reserve_batch": (_I, [_P, _I]),
     "sky_net_forward": (_I, [_P, _I, _P, _P, _P, _P, _D, _P, _P]),
     "sky_net_backward": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "sky_net_adam": (_I, [_P, _P, _P, _P, _P, _I, _D, _D, _D, _D]),
@@ -197,6 +198,10 @@ def sky_subspace_diag_batched(ctx, H, C, I, M, eps):
     n = len(I)
     _check(ctx, lib().sky_subspace_diag_batched(ctx, n, _ptrs(H), _ptrs(C), (_I * n)(*I), _ptrs(M),
                                                 _ptrs(eps)))
+
+
+def sky_reserve_batch(ctx, nb):
+    _check(ctx, lib().sky_reserve_batch(ctx, int(nb)))
 
 
 def sky_rotate(ctx, phi, M, I, psi_out):

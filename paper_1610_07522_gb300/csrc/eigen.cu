@@ -230,11 +230,20 @@ __device__ __forceinline__ void sum_parts(const double* part, double& off, doubl
   for (int b = 0; b < (int)gridDim.x; ++b) { off += part[2 * b]; tot += part[2 * b + 1]; }
 }
 
+// Problem of item w: the last b with off[b] <= w (off ascending, off[np] > w).
+__device__ __forceinline__ int find_prob(const int* off, int np, int w) {
+  int lo = 0, hi = np - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= w) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
   __shared__ int s_done[kMaxBatch], s_which[kMaxBatch], s_sweep[kMaxBatch];
   __shared__ double s_thr[kMaxBatch];
   __shared__ double s_acc[kMaxBatch][2];   // (off, tot) of problems ending a sweep
-  __shared__ int s_active;
   const int gtid = blockIdx.x * kJacThreads + threadIdx.x;
   const int gsz = gridDim.x * kJacThreads;
   const int np = a.np;
@@ -253,22 +262,21 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
     block_norms(off, tot, a.part + (long long)b * 2 * gridDim.x);
   }
   if (!grid_barrier(a.bar, epoch, a.status)) return;
-  if (threadIdx.x == 0) {
-    int active = 0;
-    for (int b = 0; b < np; ++b) {
-      double off, tot;
-      sum_parts(a.part + (long long)b * 2 * gridDim.x, off, tot);
-      const bool run = !a.run || a.run[b * a.run_stride] != 0;
-      s_done[b] = !run || (off <= a.tol * a.tol * tot) || (tot == 0.0) || a.p[b].m < 2;
-      s_thr[b] = 1e-19 * sqrt(tot);   // rotations below this change nothing measurable
-      s_which[b] = 0;
-      s_sweep[b] = 0;
-      s_acc[b][0] = s_acc[b][1] = 0.0;
-      active |= !s_done[b];
-    }
-    s_active = active;
+  // per-problem bookkeeping: thread b of every block serves problem b (the same
+  // sums in the same order in every block, so every block decides alike)
+  int act = 0;
+  for (int b = threadIdx.x; b < np; b += blockDim.x) {
+    double off, tot;
+    sum_parts(a.part + (long long)b * 2 * gridDim.x, off, tot);
+    const bool run = !a.run || a.run[b * a.run_stride] != 0;
+    s_done[b] = !run || (off <= a.tol * a.tol * tot) || (tot == 0.0) || a.p[b].m < 2;
+    s_thr[b] = 1e-19 * sqrt(tot);   // rotations below this change nothing measurable
+    s_which[b] = 0;
+    s_sweep[b] = 0;
+    s_acc[b][0] = s_acc[b][1] = 0.0;
+    act |= !s_done[b];
   }
-  __syncthreads();
+  int active = __syncthreads_or(act);
   // rotations of round 0
   for (int b = 0; b < np; ++b) {
     if (s_done[b]) continue;
@@ -282,7 +290,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
     }
   }
   if (!grid_barrier(a.bar, epoch, a.status)) return;
-  for (int t = 0; s_active; ++t) {
+  for (int t = 0; active; ++t) {
     // One item per thread.  Work is dealt out in 32-item warp chunks round-robin
     // over the blocks, so every SM gets an even share of each kind of item (the
     // FP64 units of one SM are narrow) while warps keep contiguous items.
@@ -298,8 +306,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
       if (w < nR) {
         // rotation of pair k of the next round from this round's result,
         // recomputed from the old blocks (no extra barrier)
-        int b = 0;
-        while (w >= a.offR[b + 1]) ++b;
+        const int b = find_prob(a.offR, np, w);
         if (s_done[b]) continue;
         const JacProb& P = a.p[b];
         const int m = P.m, n = P.n;
@@ -330,8 +337,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
       } else if ((w -= nR) < nB) {
         // 2x2 block (P1 rows, P2 columns), k1 >= k2: B' = J1^H B J2 into the
         // other buffer, and its conjugate transpose into the mirrored block
-        int b = 0;
-        while (w >= a.offB[b + 1]) ++b;
+        const int b = find_prob(a.offB, np, w);
         if (s_done[b]) continue;
         const JacProb& P = a.p[b];
         const int m = P.m;
@@ -387,8 +393,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
       } else {
         w -= nB;
         // accumulate the rotation into row `row` of V (in place)
-        int b = 0;
-        while (w >= a.offV[b + 1]) ++b;
+        const int b = find_prob(a.offV, np, w);
         if (s_done[b]) continue;
         const JacProb& P = a.p[b];
         const int m = P.m, h = m / 2;
@@ -408,37 +413,32 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
     }
     // partial norms of the problems that end a sweep this round
     __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int b = 0; b < np; ++b) {
-        if (s_done[b] || (t % (a.p[b].m - 1)) != a.p[b].m - 2) continue;
-        double* part = a.part + (long long)b * 2 * gridDim.x;
-        part[2 * blockIdx.x] = s_acc[b][0];
-        part[2 * blockIdx.x + 1] = s_acc[b][1];
-        s_acc[b][0] = s_acc[b][1] = 0.0;
-      }
+    for (int b = threadIdx.x; b < np; b += blockDim.x) {
+      if (s_done[b] || (t % (a.p[b].m - 1)) != a.p[b].m - 2) continue;
+      double* part = a.part + (long long)b * 2 * gridDim.x;
+      part[2 * blockIdx.x] = s_acc[b][0];
+      part[2 * blockIdx.x + 1] = s_acc[b][1];
+      s_acc[b][0] = s_acc[b][1] = 0.0;
     }
     if (!grid_barrier(a.bar, epoch, a.status)) return;
-    if (threadIdx.x == 0) {
-      int active = 0;
-      for (int b = 0; b < np; ++b) {
-        if (s_done[b]) continue;
-        s_which[b] ^= 1;
-        if ((t % (a.p[b].m - 1)) == a.p[b].m - 2) {
-          s_sweep[b] += 1;
-          double off, tot;
-          sum_parts(a.part + (long long)b * 2 * gridDim.x, off, tot);
-          if (off <= a.tol * a.tol * tot || tot == 0.0) {
-            s_done[b] = 1;
-          } else if (s_sweep[b] >= a.max_sweeps) {
-            flag_status(a.status, SKY_ENOCONV);
-            s_done[b] = 1;
-          }
+    act = 0;
+    for (int b = threadIdx.x; b < np; b += blockDim.x) {
+      if (s_done[b]) continue;
+      s_which[b] ^= 1;
+      if ((t % (a.p[b].m - 1)) == a.p[b].m - 2) {
+        s_sweep[b] += 1;
+        double off, tot;
+        sum_parts(a.part + (long long)b * 2 * gridDim.x, off, tot);
+        if (off <= a.tol * a.tol * tot || tot == 0.0) {
+          s_done[b] = 1;
+        } else if (s_sweep[b] >= a.max_sweeps) {
+          flag_status(a.status, SKY_ENOCONV);
+          s_done[b] = 1;
         }
-        active |= !s_done[b];
       }
-      s_active = active;
+      act |= !s_done[b];
     }
-    __syncthreads();
+    active = __syncthreads_or(act);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int b = 0; b < np; ++b) {
@@ -458,6 +458,7 @@ struct EigJobs {
   double* w[kMaxBatch];
   double2* Z[kMaxBatch];
   double2* A0[kMaxBatch];
+  double2* A1[kMaxBatch];
   double2* V[kMaxBatch];
   int n[kMaxBatch], m[kMaxBatch];
   int np;
@@ -483,13 +484,13 @@ __global__ void k_jacobi_init(EigJobs j, unsigned* bar, int* result) {
 }
 
 // Eigenvalues ascending (ties by index) and the matching columns of V.
-__global__ void k_jacobi_finish(EigJobs j, double2* const* A1, const int* result) {
+__global__ void k_jacobi_finish(EigJobs j, const int* result) {
   const int b = blockIdx.y;
   if (j.run && j.run[b * j.run_stride] == 0) return;
   const int n = j.n[b], m = j.m[b];
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n) return;
-  const double2* A = result[b] ? A1[b] : j.A0[b];
+  const double2* A = result[b] ? j.A1[b] : j.A0[b];
   const double dc = A[(long long)c * m + c].x;
   int rank = 0;
   for (int i = 0; i < n; ++i) {
@@ -518,7 +519,6 @@ sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, dou
   if (np > c->eig_batch) return set_err(c, SKY_EINVAL, "eigensolver batch %d > %d", np, c->eig_batch);
   EigJobs j;
   JacBatch a;
-  double2* A1p[kMaxBatch];
   long long items = 0;
   int nmax = 1, mmax = 2;
   j.np = np; j.run = run; j.run_stride = run_stride;
@@ -529,10 +529,10 @@ sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, dou
     double2* base = c->d_eigA[0] + (size_t)b * c->eig_slot;
     j.A[b] = A[b]; j.w[b] = w[b]; j.Z[b] = Z[b]; j.n[b] = n[b]; j.m[b] = m;
     j.A0[b] = base;
-    A1p[b] = c->d_eigA[1] + (size_t)b * c->eig_slot;
+    j.A1[b] = c->d_eigA[1] + (size_t)b * c->eig_slot;
     j.V[b] = c->d_eigV + (size_t)b * c->eig_slot;
     JacProb& P = a.p[b];
-    P.A0 = j.A0[b]; P.A1 = A1p[b]; P.V = j.V[b];
+    P.A0 = j.A0[b]; P.A1 = j.A1[b]; P.V = j.V[b];
     P.R0 = reinterpret_cast<JRot*>(c->d_eigrot) + (size_t)b * 2 * (c->eig_slot_rot);
     P.R1 = P.R0 + c->eig_slot_rot;
     P.n = n[b]; P.m = m;
@@ -543,9 +543,7 @@ sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, dou
     if (n[b] > nmax) nmax = n[b];
     if (m > mmax) mmax = m;
   }
-  double2** dA1 = reinterpret_cast<double2**>(c->d_eigptr);
-  cudaError_t e = cudaMemcpyAsync(dA1, A1p, np * sizeof(double2*), cudaMemcpyHostToDevice, c->stream);
-  if (e != cudaSuccess) return cuda_check(c, e, "jacobi pointers");
+  cudaError_t e;
   dim3 gi(div_up((long long)mmax * mmax, 256) < 1024 ? div_up((long long)mmax * mmax, 256) : 1024, np);
   k_jacobi_init<<<gi, 256, 0, c->stream>>>(j, c->d_bar, c->d_eigres);
   note_launch();
@@ -562,7 +560,7 @@ sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, dou
   e = cudaLaunchCooperativeKernel((const void*)k_jacobi, dim3(grid), dim3(kJacThreads), args, 0,
                                   c->stream);
   if (e != cudaSuccess) return cuda_check(c, e, "jacobi");
-  k_jacobi_finish<<<dim3(div_up(nmax, 128), np), 128, 0, c->stream>>>(j, dA1, c->d_eigres);
+  k_jacobi_finish<<<dim3(div_up(nmax, 128), np), 128, 0, c->stream>>>(j, c->d_eigres);
   note_launch();
   return cuda_check(c, cudaGetLastError(), "jacobi finish");
 }
@@ -595,10 +593,14 @@ __global__ void k_inv_sqrt_cols(ScaleJobs j, int* status, const int* run, int ru
 }
 
 // H' = (H' + H'^H) / 2 in place.
-__global__ void k_hermitize(double2* const* Ap, const int* nn) {
+struct HermJobs {
+  double2* A[kMaxBatch];
+  int n[kMaxBatch];
+};
+__global__ void k_hermitize(HermJobs h) {
   const int b = blockIdx.y;
-  double2* A = Ap[b];
-  const int n = nn[b];
+  double2* A = h.A[b];
+  const int n = h.n[b];
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)n * n) return;
   const int i = (int)(e / n), k = (int)(e % n);
@@ -826,13 +828,11 @@ sky_status subspace_batch(Ctx* c, int np, const double2* const* H, const double2
   if (st == SKY_OK)
     st = zgemm_batch(c, zjobs(np, false, false, (const double2* const*)T1, C, Hp, I, none, none));
   if (st != SKY_OK) return st;
-  double2** dHp = reinterpret_cast<double2**>(c->d_eigptr) + kMaxBatch;
-  int* dI = reinterpret_cast<int*>(reinterpret_cast<double2**>(c->d_eigptr) + 2 * kMaxBatch);
-  cudaError_t e = cudaMemcpyAsync(dHp, Hp, np * sizeof(double2*), cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dI, I, np * sizeof(int), cudaMemcpyHostToDevice, c->stream);
-  if (e != cudaSuccess) return cuda_check(c, e, "subspace pointers");
-  k_hermitize<<<dim3(div_up((long long)nmax * nmax, 256), np), 256, 0, c->stream>>>(dHp, dI);
+  HermJobs hj;
+  for (int b = 0; b < np; ++b) { hj.A[b] = Hp[b]; hj.n[b] = I[b]; }
+  k_hermitize<<<dim3(div_up((long long)nmax * nmax, 256), np), 256, 0, c->stream>>>(hj);
   note_launch();
+  cudaError_t e;
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "hermitize");
   st = eigh_batch(c, np, (const double2* const*)Hp, I, eps, Z, nullptr, 0);
   if (st != SKY_OK) return st;

@@ -74,7 +74,7 @@ static void free_all(Ctx* c) {
                   c->d_ktf[2], c->d_kp[0], c->d_kp[1], c->d_kp[2], c->d_damp[0], c->d_damp[1],
                   c->d_coul, c->d_gscr, c->d_red, c->d_dpart, c->d_ftmp, c->d_fcx, c->d_gpart,
                   c->d_eigA[0], c->d_eigA[1], c->d_eigV, c->d_eigw, c->d_eigpart, c->d_bar,
-                  c->d_eigres, c->d_eigrot, c->d_eigptr, c->d_small[0], c->d_small[1], c->d_small[2],
+                  c->d_eigres, c->d_eigrot, c->d_small[0], c->d_small[1], c->d_small[2],
                   c->d_small[3], c->d_small[4], c->d_small[5], c->d_gate,
                   c->d_stats, c->d_tcA[0], c->d_tcA[1], c->d_tcA[2], c->d_tcB[0],
                   c->d_tcB[1], c->d_tcB[2], c->d_tcRotA[0], c->d_tcRotA[1], c->d_tcRotA[2],
@@ -194,11 +194,6 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
     char* p = nullptr;
     s = dalloc(c, &p, jacobi_rot_bytes(m) * c->eig_batch);
     c->d_eigrot = p;
-  }
-  if (s == SKY_OK) {
-    char* p = nullptr;
-    s = dalloc(c, &p, (size_t)3 * kMaxBatch * sizeof(void*));
-    c->d_eigptr = p;
   }
   for (int k = 0; k < 6; ++k) ALLOC(c->d_small[k], c->small_slot * c->eig_batch);
   ALLOC(c->d_gate, 8 * kMaxBatch);
@@ -415,6 +410,38 @@ sky_status sky_sp_spread(sky_ctx* c, const double* eps, const double* hnorm2, in
   if (!c) return SKY_EINVAL;
   if (A < 0 || (A > 0 && (!eps || !hnorm2)) || !out) return set_err(c, SKY_EINVAL, "sp_spread: bad arguments");
   return sp_spread_impl(c, eps, hnorm2, A, out);
+}
+
+sky_status sky_reserve_batch(sky_ctx* c, int nb) {
+  if (!c) return SKY_EINVAL;
+  if (nb < 1 || nb > kMaxBatch) return set_err(c, SKY_EINVAL, "batch of %d outside [1, %d]", nb, kMaxBatch);
+  if (nb <= c->eig_batch) return SKY_OK;
+  const int Imax = c->max_states > 0 ? c->max_states : 1;
+  const int m = Imax + (Imax & 1);
+  double2 *a0 = nullptr, *a1 = nullptr, *v = nullptr, *sm[6] = {nullptr};
+  double* w = nullptr;
+  char* rot = nullptr;
+  sky_status s = dalloc(c, &a0, c->eig_slot * nb);
+  if (s == SKY_OK) s = dalloc(c, &a1, c->eig_slot * nb);
+  if (s == SKY_OK) s = dalloc(c, &v, c->eig_slot * nb);
+  if (s == SKY_OK) s = dalloc(c, &w, (2 * c->eig_slot_rot + 2) * nb);
+  if (s == SKY_OK) s = dalloc(c, &rot, jacobi_rot_bytes(m) * nb);
+  for (int k = 0; k < 6 && s == SKY_OK; ++k) s = dalloc(c, &sm[k], c->small_slot * nb);
+  if (s != SKY_OK) {
+    void* ptrs[] = {a0, a1, v, w, rot, sm[0], sm[1], sm[2], sm[3], sm[4], sm[5]};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    return s;
+  }
+  cudaStreamSynchronize(c->stream);   // no queued work may still use the old buffers
+  void* old[] = {c->d_eigA[0], c->d_eigA[1], c->d_eigV, c->d_eigw, c->d_eigrot, c->d_small[0],
+                 c->d_small[1], c->d_small[2], c->d_small[3], c->d_small[4], c->d_small[5]};
+  for (void* p : old)
+    if (p) cudaFree(p);
+  c->d_eigA[0] = a0; c->d_eigA[1] = a1; c->d_eigV = v; c->d_eigw = w; c->d_eigrot = rot;
+  for (int k = 0; k < 6; ++k) c->d_small[k] = sm[k];
+  c->eig_batch = nb;
+  return SKY_OK;
 }
 
 sky_status sky_net_forward(sky_ctx* c, int q, const float* theta, const double* U,

@@ -54,7 +54,7 @@ struct Couplings {
 struct Ctx;  // defined below; sky_ctx is an alias at the C boundary
 
 constexpr int kDensSplits = 8;     // state splits of the density accumulation
-constexpr int kMaxBatch = 8;       // problems per batched eigensolve / small GEMM
+constexpr int kMaxBatch = 128;     // problems per batched eigensolve / small GEMM
 constexpr int kRedBlock = 256;     // threads of the per-state reduction blocks
 
 struct Ctx {
@@ -93,7 +93,6 @@ struct Ctx {
   double* d_eigpart;                // per-block partial norms
   unsigned* d_bar;                  // grid barrier {count, generation}
   int* d_eigres;                    // which ping-pong buffer holds each result [kMaxBatch]
-  void* d_eigptr;                   // device pointer tables of the batched calls
   int eig_batch;                    // problems a batched eigensolve may hold
   size_t eig_slot;                  // elements per problem in d_eigA / d_eigV
   size_t eig_slot_rot;              // rotations per problem and round buffer

@@ -332,8 +332,16 @@ inline cudaError_t gemm_bf16(const void* const* A, long long lda, const void* co
     g.pb[i] = i < ph.n ? ph.pb[i] : 0;
   }
   g.D = D; g.ldd = ldd; g.sstride = sstride; g.status = status;
-  e = cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  if (e != cudaSuccess) return e;
+  // the shared-memory opt-in is set once per device (before any stream capture)
+  static bool smem_set[64] = {false};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!smem_set[dev]) {
+    e = cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    smem_set[dev] = true;
+  }
   dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, z);
   k_gemm_bf16<<<grid, THREADS, SMEM_BYTES, s>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], g);
   note_launch();

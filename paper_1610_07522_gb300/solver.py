@@ -19,7 +19,7 @@ from . import binding as B
 
 
 class Solver:
-    def __init__(self, workload, prec=B.SKY_F64, device="cuda:0", max_states=None):
+    def __init__(self, workload, prec=B.SKY_F64, device="cuda:0", max_states=None, stream=None):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (there is no CPU path)")
         self.w = workload
@@ -33,7 +33,7 @@ class Solver:
         self.A = workload.N + workload.Z
         Imax = max_states or max(self.I)
         with torch.cuda.device(self.device):
-            self.stream = torch.cuda.current_stream(self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             self.ctx = B.sky_init(workload.grid, workload.dx, workload.params, workload.coulomb,
                                   workload.twist, prec, Imax, self.stream.cuda_stream)
         dev, G = self.device, self.G

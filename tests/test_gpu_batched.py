@@ -1,0 +1,143 @@
+"""The batched form (GPU): many eigenproblems in one batched solve, and many
+independent boxes (uneven grids, particle numbers and twists) iterated
+together with the whole iteration captured in one CUDA graph.
+
+Parity: each problem of a 40-problem batched Loewdin + Rayleigh-Ritz solve
+against the oracle; every box of a 3-box batch against the same box iterated
+alone (itself parity-tested against the oracle) and, for one box, against
+the oracle directly; the graph replay against the eager launch sequence.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_1610_07522_gb300 import binding as B
+from paper_1610_07522_gb300 import inputs as IN
+from paper_1610_07522_gb300.batched import BatchSolver
+from paper_1610_07522_gb300.solver import Solver
+
+pytestmark = pytest.mark.gpu
+
+P = dict(IN.SLY4)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def relerr(got, want):
+    return float(np.max(np.abs(got - want)) / max(np.max(np.abs(want)), 1e-300))
+
+
+def test_forty_problems_in_one_batched_solve():
+    rng = np.random.default_rng(61)
+    sizes = [int(v) for v in rng.integers(1, 71, size=40)]
+    sizes[0], sizes[1] = 70, 1
+    g = O.Grid((8, 8, 8), (1.0, 1.0, 1.0))
+    ctx = B.sky_init((8, 8, 8), (1.0, 1.0, 1.0), P, False, (0.0, 0.0, 0.0), B.SKY_F64, 70,
+                     torch.cuda.current_stream().cuda_stream)
+    with pytest.raises(B.SkyError):
+        B.sky_reserve_batch(ctx, 129)
+    B.sky_reserve_batch(ctx, 40)
+    Ss, Hs = [], []
+    for b, n in enumerate(sizes):
+        A = rng.standard_normal((n, 2 * n)) + 1j * rng.standard_normal((n, 2 * n))
+        if b % 4 == 3:      # far from orthonormal: the eigendecomposition route
+            S = 4.0 * np.eye(n) + 0.1 * (A @ A.conj().T) / (2 * n)
+        else:               # near orthonormal: Newton-Schulz
+            S = np.eye(n) + 0.02 * (A @ A.conj().T) / (2 * n)
+        Hm = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        Ss.append(0.5 * (S + S.conj().T))
+        Hs.append(10.0 * (Hm + Hm.conj().T))
+    dS = [dev(x) for x in Ss]
+    dH = [dev(x) for x in Hs]
+    C = [torch.zeros_like(x) for x in dS]
+    M = [torch.zeros_like(x) for x in dS]
+    lam = [torch.zeros(n, dtype=torch.float64, device="cuda:0") for n in sizes]
+    B.sky_orthonormalize_batched(ctx, dS, sizes, C)
+    B.sky_subspace_diag_batched(ctx, dH, C, sizes, M, lam)
+    B.sky_sync(ctx)
+    for b, n in enumerate(sizes):
+        assert relerr(host(C[b]), O.loewdin(Ss[b])) < 1e-11, b
+        _, want = O.rayleigh_ritz(Ss[b], Hs[b])
+        assert np.max(np.abs(host(lam[b]) - want)) < 1e-9 * max(1.0, np.max(np.abs(want))), b
+        Mg = host(M[b])
+        assert np.max(np.abs(Mg.conj().T @ Ss[b] @ Mg - np.eye(n))) < 1e-11, b
+    B.sky_destroy(ctx)
+
+
+def _boxes():
+    return [
+        IN.Workload(name="box_a", grid=(8, 8, 8), dx=(1.0, 1.0, 1.0), N=6, Z=5, coulomb=True,
+                    twist=(0.7, -1.9, 2.5), init="blobs", seed=71),
+        IN.Workload(name="box_b", grid=(12, 12, 12), dx=(1.0, 1.0, 1.0), N=30, Z=13,
+                    twist=(-2.2, 0.4, 1.1), init="blobs", seed=72),
+        IN.Workload(name="box_c", grid=(16, 16, 16), dx=(1.0, 1.0, 1.0), N=16, Z=16,
+                    init="noisy_plane_waves", seed=73),
+    ]
+
+
+def test_batched_boxes_match_single_boxes_and_oracle():
+    ws = _boxes()
+    bs = BatchSolver(ws, prec=B.SKY_F64)
+    bs.load()
+    singles = []
+    for w in ws:
+        s = Solver(w, prec=B.SKY_F64)
+        inp = IN.make_inputs(w)
+        s.load(inp["psi0"], inp.get("rho0"), inp.get("tau0"))
+        singles.append(s)
+    # oracle for the twisted Coulomb box
+    w0 = ws[0]
+    inp0 = IN.make_inputs(w0)
+    g0 = O.Grid(w0.grid, w0.dx, w0.twist)
+    st = O.initial_state(inp0["psi0"], g0, w0.params, w0.coulomb, inp0["rho0"], inp0["tau0"])
+    for k in range(3):
+        bs.step_eager()
+        for s in singles:
+            s.step()
+        rec = O.iterate(st, g0, w0.params, w0.coulomb, w0.x0, w0.E0)
+        en = bs.energies()
+        for b, s in enumerate(singles):
+            E, _, _ = s.energy()
+            assert abs(en[b][0] - E) <= 1e-10 * abs(E), (k, b)
+            lam_b = host(bs.boxes[b].lam)
+            assert np.max(np.abs(lam_b - host(s.lam))) < 1e-9, (k, b)
+        assert abs(en[0][0] - rec["E"]) <= 1e-10 * abs(rec["E"]), k
+        want = np.concatenate(rec["lam"])
+        assert np.max(np.abs(np.sort(host(bs.boxes[0].lam)[:w0.N]) - np.sort(rec["lam"][0]))) < 1e-9
+        assert np.max(np.abs(np.sort(host(bs.boxes[0].lam)[w0.N:]) - np.sort(rec["lam"][1]))) < 1e-9
+        del want
+    for s in singles:
+        s.close()
+    bs.close()
+
+
+@pytest.mark.parametrize("prec", [B.SKY_F64, B.SKY_F32_BF16X3])
+def test_graph_replay_equals_eager_iteration(prec):
+    ws = _boxes()
+    a = BatchSolver(ws, prec=prec)
+    b = BatchSolver(ws, prec=prec)
+    a.load()
+    b.load()
+    a.step_eager()           # first iteration eager in both (builds the damping tables)
+    b.step_eager()
+    b.capture()
+    assert b.launches_per_step > 0
+    for _ in range(3):
+        a.step_eager()
+        b.step()
+    ea, eb = a.energies(), b.energies()
+    for x, y in zip(ea, eb):
+        assert x[0] == y[0] and x[1] == y[1]
+    for sa, sb in zip(a.boxes, b.boxes):
+        assert torch.equal(sa.psi[0], sb.psi[0]) and torch.equal(sa.rho, sb.rho)
+    a.close()
+    b.close()
