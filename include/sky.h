@@ -208,6 +208,31 @@ sky_status sky_energy(sky_ctx* ctx, const double* rho, const double* tau,
 sky_status sky_sp_spread(sky_ctx* ctx, const double* eps, const double* hnorm2, int A,
                          double* out);
 
+/* ---- Tunable launch shapes ---------------------------------------------------
+ * Launch-shape knobs of a context, for an autotuner that times the calls on
+ * its own workload and keeps the fastest values.  Every value gives the same
+ * result except for the order of floating-point sums (split counts, eigensolver
+ * blocks), so results may change in the last bits.  The paper has no
+ * counterpart (its tuning is the MPI/OpenMP layout, Sec. 5).
+ *   SKY_KNOB_LINE_YZ        threads per block of the y/z FFT line passes: 32, 64, 128
+ *   SKY_KNOB_LINE_X         lines per block of the x FFT line passes: 16, 32, 64
+ *   SKY_KNOB_OVERLAP_WAVES  FMA overlap: K splits filling 1 or 2 waves of blocks
+ *   SKY_KNOB_TC_WAVES       split-BF16 overlap: K splits filling 1, 2 or 4 waves of SMs
+ *   SKY_KNOB_JACOBI_BLOCKS  blocks of the cooperative eigensolver: 1..JACOBI_BLOCKS_MAX
+ *   SKY_KNOB_JACOBI_BLOCKS_MAX  (read only) co-resident blocks of that kernel
+ * sky_tune_set returns SKY_EINVAL for a value outside these sets; sky_tune_get
+ * returns the current value (-1 for an unknown knob or a NULL context). */
+typedef enum {
+  SKY_KNOB_LINE_YZ = 0,
+  SKY_KNOB_LINE_X = 1,
+  SKY_KNOB_OVERLAP_WAVES = 2,
+  SKY_KNOB_TC_WAVES = 3,
+  SKY_KNOB_JACOBI_BLOCKS = 4,
+  SKY_KNOB_JACOBI_BLOCKS_MAX = 5
+} sky_knob;
+sky_status sky_tune_set(sky_ctx* ctx, sky_knob knob, int value);
+int sky_tune_get(const sky_ctx* ctx, sky_knob knob);
+
 /* ---- Learned damping weight ----------------------------------------------
  * The paper has no learned part; these calls build and train a per-voxel
  * weight w_q(r) for the damped step of Eq. dampstep (sky_damped_step's w).

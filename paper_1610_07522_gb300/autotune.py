@@ -1,0 +1,126 @@
+"""Autotuner of the launch-shape knobs of libsky (include/sky.h, "Tunable
+launch shapes"): FFT line-pass block shapes, the K-split counts of the
+overlap contractions and the block count of the batched eigensolver.
+
+Each knob's candidate values are timed with CUDA events on the caller's own
+workload (the solver's buffers and matrices, the call the knob affects), and
+the fastest is kept.  Results can be cached in a JSON file keyed by GPU,
+grid, particle numbers and precision form.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+
+import torch
+
+from . import binding as B
+
+CANDIDATES = {
+    B.SKY_KNOB_LINE_YZ: (32, 64, 128),
+    B.SKY_KNOB_LINE_X: (16, 32, 64),
+    B.SKY_KNOB_OVERLAP_WAVES: (1, 2),
+    B.SKY_KNOB_TC_WAVES: (1, 2, 4),
+}
+NAMES = {B.SKY_KNOB_LINE_YZ: "line_yz", B.SKY_KNOB_LINE_X: "line_x",
+         B.SKY_KNOB_OVERLAP_WAVES: "overlap_waves", B.SKY_KNOB_TC_WAVES: "tc_waves",
+         B.SKY_KNOB_JACOBI_BLOCKS: "jacobi_blocks"}
+TC_FORMS = (B.SKY_F32_BF16X3, B.SKY_F32_BF16X6)
+
+
+def _time(fn, stream, reps):
+    """Median CUDA-event time (ms) of fn() on ``stream`` after one warm call."""
+    fn()
+    out = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return statistics.median(out)
+
+
+def _pick(ctx, knob, values, fn, stream, reps):
+    times = {}
+    for v in values:
+        B.sky_tune_set(ctx, knob, v)
+        times[v] = _time(fn, stream, reps)
+    best = min(times, key=times.get)
+    B.sky_tune_set(ctx, knob, best)
+    return best, times
+
+
+def _key(solver):
+    name = torch.cuda.get_device_name(solver.device)
+    return f"{name}|{'x'.join(map(str, solver.w.grid))}|{solver.I[0]}n{solver.I[1]}p|prec{solver.prec}"
+
+
+def tune_box(solver, reps=5, cache=None):
+    """Tune the line-pass and overlap knobs of ``solver`` on its species with
+    the most states (its psi must hold loaded states).  Returns
+    {knob name: (chosen value, {value: ms})}."""
+    key = _key(solver)
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            got = json.load(f).get(key)
+        if got:
+            apply(solver.ctx, got)
+            return {k: (v, None) for k, v in got.items()}
+    q = 0 if solver.I[0] >= solver.I[1] else 1
+    I, ctx, st = solver.I[q], solver.ctx, solver.stream
+    h = lambda: B.sky_apply_h(ctx, solver.U[q], solver.Bf[q], solver.W[q], solver.psi[q], solver.h[q], I)
+    ov = lambda: B.sky_overlap(ctx, solver.psi[q], solver.h[q], I, solver.H[q])
+    res = {}
+    for knob in (B.SKY_KNOB_LINE_YZ, B.SKY_KNOB_LINE_X):
+        res[NAMES[knob]] = _pick(ctx, knob, CANDIDATES[knob], h, st, reps)
+    knob = B.SKY_KNOB_TC_WAVES if solver.prec in TC_FORMS else B.SKY_KNOB_OVERLAP_WAVES
+    res[NAMES[knob]] = _pick(ctx, knob, CANDIDATES[knob], ov, st, reps)
+    torch.cuda.synchronize(solver.device)
+    if cache:
+        data = {}
+        if os.path.exists(cache):
+            with open(cache) as f:
+                data = json.load(f)
+        data[key] = {k: v[0] for k, v in res.items()}
+        with open(cache, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+    return res
+
+
+def apply(ctx, settings):
+    """Set knob values from {knob name: value}."""
+    by_name = {v: k for k, v in NAMES.items()}
+    for name, value in settings.items():
+        B.sky_tune_set(ctx, by_name[name], value)
+
+
+def tune_eigensolver(eig_ctx, run_solve, stream, reps=3):
+    """Tune the block count of the cooperative eigensolver of ``eig_ctx`` by
+    timing ``run_solve()`` (a batched solve on that context)."""
+    top = B.sky_tune_get(eig_ctx, B.SKY_KNOB_JACOBI_BLOCKS_MAX)
+    values = sorted({max(1, top // 4), max(1, top // 2), top})
+    return _pick(eig_ctx, B.SKY_KNOB_JACOBI_BLOCKS, values, run_solve, stream, reps)
+
+
+def tune_batch(bs, reps=5, cache=None):
+    """Tune a BatchSolver: the box knobs once per distinct box shape (grid,
+    particle numbers, precision), applied to every box of that shape, then the
+    shared eigensolver's block count on the whole batch (needs one iteration
+    done, so that its matrices are valid).  Returns the choices."""
+    shapes = {}
+    for s in bs.boxes:
+        shapes.setdefault((tuple(s.w.grid), s.I, s.prec), []).append(s)
+    out = {}
+    for shape, boxes in shapes.items():
+        res = tune_box(boxes[0], reps, cache)
+        settings = {k: v[0] for k, v in res.items()}
+        for s in boxes[1:]:
+            apply(s.ctx, settings)
+        out[str(shape)] = res
+    main = torch.cuda.current_stream(bs.device)
+    out["jacobi_blocks"] = tune_eigensolver(bs.eig, bs.eigensolve, main, reps=max(1, reps // 2))
+    return out

@@ -70,15 +70,7 @@ class BatchSolver:
             for q in s._species():
                 s.species_step(q)
         self._join(main)
-        S = [self.boxes[i].S[q] for i, q in self.problems]
-        H = [self.boxes[i].H[q] for i, q in self.problems]
-        C = [self.boxes[i].C[q] for i, q in self.problems]
-        M = [self.boxes[i].M[q] for i, q in self.problems]
-        I = [self.boxes[i].I[q] for i, q in self.problems]
-        lam = [self.boxes[i].lam[self.boxes[i].off[q]:self.boxes[i].off[q] + self.boxes[i].I[q]]
-               for i, q in self.problems]
-        B.sky_orthonormalize_batched(self.eig, S, I, C)
-        B.sky_subspace_diag_batched(self.eig, H, C, I, M, lam)
+        self.eigensolve()
         self._fork(main)
         for s in self.boxes:
             for q in s._species():
@@ -88,6 +80,29 @@ class BatchSolver:
             B.sky_mean_fields(s.ctx, s.rho, s.tau, s.divJ, s.U, s.Bf, s.W)
             B.sky_energy(s.ctx, s.rho, s.tau, s.divJ, s.eout)
         self._join(main)
+
+    def eigensolve(self):
+        """Loewdin factors and Rayleigh-Ritz of every species of every box in
+        one batched solve on the shared context (its stream)."""
+        S = [self.boxes[i].S[q] for i, q in self.problems]
+        H = [self.boxes[i].H[q] for i, q in self.problems]
+        C = [self.boxes[i].C[q] for i, q in self.problems]
+        M = [self.boxes[i].M[q] for i, q in self.problems]
+        I = [self.boxes[i].I[q] for i, q in self.problems]
+        lam = [self.boxes[i].lam[self.boxes[i].off[q]:self.boxes[i].off[q] + self.boxes[i].I[q]]
+               for i, q in self.problems]
+        B.sky_orthonormalize_batched(self.eig, S, I, C)
+        B.sky_subspace_diag_batched(self.eig, H, C, I, M, lam)
+
+    def tune(self, reps=5, cache=None):
+        """Autotune the launch shapes (one box per distinct shape, then the
+        shared eigensolver); call after at least one iteration and before
+        ``capture()``."""
+        from . import autotune
+        torch.cuda.synchronize(self.device)
+        res = autotune.tune_batch(self, reps, cache)
+        torch.cuda.synchronize(self.device)
+        return res
 
     def step_eager(self):
         """One iteration of every box, enqueued without a graph."""

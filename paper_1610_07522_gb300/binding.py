@@ -17,6 +17,8 @@ SKY_OK, SKY_EINVAL, SKY_ENOMEM, SKY_ECUDA, SKY_ENOTPD, SKY_ENOCONV, SKY_ETIMEOUT
 STATUS_NAMES = ["SKY_OK", "SKY_EINVAL", "SKY_ENOMEM", "SKY_ECUDA", "SKY_ENOTPD",
                 "SKY_ENOCONV", "SKY_ETIMEOUT", "SKY_ENAN", "SKY_EUNSUPPORTED"]
 SKY_F64, SKY_F32, SKY_F32_BF16X3, SKY_F32_BF16X6 = 0, 1, 2, 3
+(SKY_KNOB_LINE_YZ, SKY_KNOB_LINE_X, SKY_KNOB_OVERLAP_WAVES, SKY_KNOB_TC_WAVES,
+ SKY_KNOB_JACOBI_BLOCKS, SKY_KNOB_JACOBI_BLOCKS_MAX) = range(6)
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -61,6 +63,8 @@ _SIGNATURES = {
     "sky_subspace_diag_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I),
                                        ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "sky_reserve_batch": (_I, [_P, _I]),
+    "sky_tune_set": (_I, [_P, _I, _I]),
+    "sky_tune_get": (_I, [_P, _I]),
     "sky_net_forward": (_I, [_P, _I, _P, _P, _P, _P, _D, _P, _P]),
     "sky_net_backward": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "sky_net_adam": (_I, [_P, _P, _P, _P, _P, _I, _D, _D, _D, _D]),
@@ -198,6 +202,14 @@ def sky_subspace_diag_batched(ctx, H, C, I, M, eps):
     n = len(I)
     _check(ctx, lib().sky_subspace_diag_batched(ctx, n, _ptrs(H), _ptrs(C), (_I * n)(*I), _ptrs(M),
                                                 _ptrs(eps)))
+
+
+def sky_tune_set(ctx, knob, value):
+    _check(ctx, lib().sky_tune_set(ctx, int(knob), int(value)))
+
+
+def sky_tune_get(ctx, knob):
+    return int(lib().sky_tune_get(ctx, int(knob)))
 
 
 def sky_reserve_batch(ctx, nb):

@@ -161,8 +161,10 @@ struct LineGeom {
   long long nlines;   // nbatch * G / N
 };
 
-constexpr int kLineThreads = 128;   // threads (= lines) per block along y, z
-constexpr int kLinesX = 64;         // lines per block along x (smem staged)
+constexpr int kLineThreads = 128;   // most threads (= lines) per block along y, z
+constexpr int kLinesX = 64;         // most lines per block along x (smem staged)
+// The block shapes actually launched come from the context (tunable):
+// Ctx::line_yz in {32, 64, 128}, Ctx::line_x in {16, 32, 64}.
 
 // An Op provides:
 //   static constexpr bool kFwd, kInv;
@@ -207,23 +209,25 @@ __global__ void __launch_bounds__(kLineThreads) k_line_yz(Op op, LineGeom g) {
   for (int m = 0; m < N; ++m) op.store(b, base + m * stride, v[m]);
 }
 
-// Lines along x: a block stages kLinesX contiguous lines through shared memory.
+// Lines along x: a block stages blockDim.x (<= kLinesX) contiguous lines
+// through shared memory.
 template <typename T, int N, class Op>
 __global__ void __launch_bounds__(kLinesX) k_line_x(Op op, LineGeom g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw);   // [kLinesX][N + 1]
+  cx<T>* tile = reinterpret_cast<cx<T>*>(smem_raw);   // [lx][N + 1]
   __shared__ long long s_b[kLinesX];
   __shared__ int s_r[kLinesX];
-  const long long l0 = (long long)blockIdx.x * kLinesX;
+  const int lx = blockDim.x;
+  const long long l0 = (long long)blockIdx.x * lx;
   const int rows = g.ny * g.nz;
-  const int nl = (int)((g.nlines - l0) < kLinesX ? (g.nlines - l0) : kLinesX);
+  const int nl = (int)((g.nlines - l0) < lx ? (g.nlines - l0) : lx);
   if ((int)threadIdx.x < nl) {
     const long long l = l0 + threadIdx.x;
     s_b[threadIdx.x] = l / rows;
     s_r[threadIdx.x] = (int)(l % rows);
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < nl * N; e += kLinesX) {
+  for (int e = threadIdx.x; e < nl * N; e += lx) {
     const int ll = e / N, m = e % N;
     tile[ll * (N + 1) + m] = op.load(s_b[ll], s_r[ll] * N + m);
   }
@@ -238,32 +242,44 @@ __global__ void __launch_bounds__(kLinesX) k_line_x(Op op, LineGeom g) {
     for (int m = 0; m < N; ++m) tile[ll * (N + 1) + m] = v[m];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < nl * N; e += kLinesX) {
+  for (int e = threadIdx.x; e < nl * N; e += lx) {
     const int ll = e / N, m = e % N;
     op.store(s_b[ll], s_r[ll] * N + m, tile[ll * (N + 1) + m]);
   }
 }
 
-// Launch one pass along `axis` over `nbatch` arrays.
+// Launch one pass along `axis` over `nbatch` arrays on the context's stream,
+// with the context's block shapes.
 template <typename T, int N, int AXIS, class Op>
 inline cudaError_t launch_line(const Op& op, int nx, int ny, int nz, long long nbatch,
-                               cudaStream_t s) {
+                               const Ctx* c) {
   LineGeom g;
   g.nx = nx; g.ny = ny; g.nz = nz;
   const long long G = (long long)nx * ny * nz;
   g.nlines = nbatch * (G / N);
   if (g.nlines == 0) return cudaSuccess;
   if constexpr (AXIS == 0) {
-    const size_t smem = (size_t)kLinesX * (N + 1) * sizeof(cx<T>);
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k_line_x<T, N, Op>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+    const int lx = c->line_x;
+    const size_t smem = (size_t)lx * (N + 1) * sizeof(cx<T>);
+    constexpr size_t kSmemMax = (size_t)kLinesX * (N + 1) * sizeof(cx<T>);
+    if constexpr (kSmemMax > 48 * 1024) {
+      // opt in above 48 KB once per device (before any stream capture)
+      static bool opted[64] = {false};
+      int dev = 0;
+      cudaError_t e = cudaGetDevice(&dev);
       if (e != cudaSuccess) return e;
+      if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+      if (!opted[dev]) {
+        e = cudaFuncSetAttribute(k_line_x<T, N, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmemMax);
+        if (e != cudaSuccess) return e;
+        opted[dev] = true;
+      }
     }
-    k_line_x<T, N, Op><<<div_up(g.nlines, kLinesX), kLinesX, smem, s>>>(op, g); note_launch();
+    k_line_x<T, N, Op><<<div_up(g.nlines, lx), lx, smem, c->stream>>>(op, g); note_launch();
   } else {
-    k_line_yz<T, N, AXIS, Op><<<div_up(g.nlines, kLineThreads), kLineThreads, 0, s>>>(op, g); note_launch();
+    const int ly = c->line_yz;
+    k_line_yz<T, N, AXIS, Op><<<div_up(g.nlines, ly), ly, 0, c->stream>>>(op, g); note_launch();
   }
   return cudaGetLastError();
 }

@@ -69,9 +69,9 @@ static cudaError_t run_pass(Ctx* c, int axis, const Op& op, long long nb) {
   const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
   return dispatch_n<true>(c->n[axis], [&](auto NC) -> cudaError_t {
     constexpr int N = decltype(NC)::value;
-    if (axis == 0) return launch_line<double, N, 0>(op, nx, ny, nz, nb, c->stream);
-    if (axis == 1) return launch_line<double, N, 1>(op, nx, ny, nz, nb, c->stream);
-    return launch_line<double, N, 2>(op, nx, ny, nz, nb, c->stream);
+    if (axis == 0) return launch_line<double, N, 0>(op, nx, ny, nz, nb, c);
+    if (axis == 1) return launch_line<double, N, 1>(op, nx, ny, nz, nb, c);
+    return launch_line<double, N, 2>(op, nx, ny, nz, nb, c);
   });
 }
 
@@ -91,7 +91,9 @@ sky_status field_divergence(Ctx* c, const double* J, double* divJ) {
   for (int ax = 0; ax < 3; ++ax) {
     OpRealD op{J + ax * G, divJ, c->d_kp[ax], 1.0 / c->n[ax], 0, ax > 0, G};
     cudaError_t e = run_pass(c, ax, op, 1);
-    if (e != cudaSuccess) return cuda_check(c, e, "divergence");
+    if (e != cudaSuccess)
+      return set_err(c, SKY_ECUDA, "divergence (axis %d, n %d, blocks %d/%d): %s", ax, c->n[ax],
+                     c->line_x, c->line_yz, cudaGetErrorString(e));
   }
   return SKY_OK;
 }

@@ -35,7 +35,7 @@ sky_status overlap_impl(Ctx* c, const void* a, const void* b, int I, double2* X)
   if (is_tc(c->prec)) return tc_overlap(c, a, b, I, X);
   const long long V = 2LL * c->G;
   int ntiles;
-  const int nsplit = overlap_splits(I, V, c->ov_slots, &ntiles);
+  const int nsplit = overlap_splits(I, V, c->ov_waves * c->ov_slots, &ntiles);
   const long long kblocks = (V + BK - 1) / BK;
   const long long kchunk = ((kblocks + nsplit - 1) / nsplit) * BK;
   const int nsplit_eff = (int)((V + kchunk - 1) / kchunk);

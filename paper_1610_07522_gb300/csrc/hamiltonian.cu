@@ -91,9 +91,9 @@ static cudaError_t gradient_passes(Ctx* c, const cx<T>* src, cx<T>* const dst[3]
     OpDeriv<T> op{src, dst[ax], kt_of<T>(c, ax), (T)(1.0 / c->n[ax]), G};
     auto go = [&](auto NC) -> cudaError_t {
       constexpr int N = decltype(NC)::value;
-      if (ax == 0) return launch_line<T, N, 0>(op, nx, ny, nz, nb, c->stream);
-      if (ax == 1) return launch_line<T, N, 1>(op, nx, ny, nz, nb, c->stream);
-      return launch_line<T, N, 2>(op, nx, ny, nz, nb, c->stream);
+      if (ax == 0) return launch_line<T, N, 0>(op, nx, ny, nz, nb, c);
+      if (ax == 1) return launch_line<T, N, 1>(op, nx, ny, nz, nb, c);
+      return launch_line<T, N, 2>(op, nx, ny, nz, nb, c);
     };
     e = dispatch_n<std::is_same<T, float>::value>(c->n[ax], go);
     if (e != cudaSuccess) return e;
@@ -235,9 +235,9 @@ static sky_status apply_h_t(Ctx* c, const double* U, const double* B, const doub
       OpDeriv<T> op{g[ax], g[ax], kt_of<T>(c, ax), (T)(1.0 / c->n[ax]), G};
       auto go = [&](auto NC) -> cudaError_t {
         constexpr int N = decltype(NC)::value;
-        if (ax == 0) return launch_line<T, N, 0>(op, nx, ny, nz, 2LL * ns, c->stream);
-        if (ax == 1) return launch_line<T, N, 1>(op, nx, ny, nz, 2LL * ns, c->stream);
-        return launch_line<T, N, 2>(op, nx, ny, nz, 2LL * ns, c->stream);
+        if (ax == 0) return launch_line<T, N, 0>(op, nx, ny, nz, 2LL * ns, c);
+        if (ax == 1) return launch_line<T, N, 1>(op, nx, ny, nz, 2LL * ns, c);
+        return launch_line<T, N, 2>(op, nx, ny, nz, 2LL * ns, c);
       };
       e = dispatch_n<std::is_same<T, float>::value>(c->n[ax], go);
       if (e != cudaSuccess) return cuda_check(c, e, "apply_h divergence");
@@ -293,15 +293,15 @@ static sky_status damped_t(Ctx* c, int q, const cx<T>* psi, const cx<T>* hpsi,
   OpPass<T, true> o4{phi, G};
   OpDampZInv<T> o5{psi, phi, w, G};
   constexpr bool L = std::is_same<T, float>::value;
-  e = dispatch_n<L>(nz, [&](auto NC) { return launch_line<T, decltype(NC)::value, 2>(o1, nx, ny, nz, nb, c->stream); });
+  e = dispatch_n<L>(nz, [&](auto NC) { return launch_line<T, decltype(NC)::value, 2>(o1, nx, ny, nz, nb, c); });
   if (e == cudaSuccess)
-    e = dispatch_n<L>(ny, [&](auto NC) { return launch_line<T, decltype(NC)::value, 1>(o2, nx, ny, nz, nb, c->stream); });
+    e = dispatch_n<L>(ny, [&](auto NC) { return launch_line<T, decltype(NC)::value, 1>(o2, nx, ny, nz, nb, c); });
   if (e == cudaSuccess)
-    e = dispatch_n<L>(nx, [&](auto NC) { return launch_line<T, decltype(NC)::value, 0>(o3, nx, ny, nz, nb, c->stream); });
+    e = dispatch_n<L>(nx, [&](auto NC) { return launch_line<T, decltype(NC)::value, 0>(o3, nx, ny, nz, nb, c); });
   if (e == cudaSuccess)
-    e = dispatch_n<L>(ny, [&](auto NC) { return launch_line<T, decltype(NC)::value, 1>(o4, nx, ny, nz, nb, c->stream); });
+    e = dispatch_n<L>(ny, [&](auto NC) { return launch_line<T, decltype(NC)::value, 1>(o4, nx, ny, nz, nb, c); });
   if (e == cudaSuccess)
-    e = dispatch_n<L>(nz, [&](auto NC) { return launch_line<T, decltype(NC)::value, 2>(o5, nx, ny, nz, nb, c->stream); });
+    e = dispatch_n<L>(nz, [&](auto NC) { return launch_line<T, decltype(NC)::value, 2>(o5, nx, ny, nz, nb, c); });
   return e == cudaSuccess ? SKY_OK : cuda_check(c, e, "damped step");
 }
 

@@ -150,9 +150,13 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   if (c->red_nblk < 1) c->red_nblk = 1;
   if (c->red_nblk > 64) c->red_nblk = 64;
   c->ov_slots = overlap_slots(c->num_sms);
+  c->line_yz = 128;
+  c->line_x = 64;
+  c->ov_waves = 1;
+  c->tc_waves = 2;
   size_t gpart = 0;
-  for (int I = 1; I <= Imax; ++I) {
-    const size_t need = overlap_partial_elems(I, V, c->ov_slots);
+  for (int I = 1; I <= Imax; ++I) {   // room for the largest tunable split count
+    const size_t need = overlap_partial_elems(I, V, kMaxOverlapWaves * c->ov_slots);
     if (need > gpart) gpart = need;
   }
   c->gpart_elems = gpart;
@@ -214,7 +218,7 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   ALLOC(c->d_stats, 8);
   ALLOC(c->d_netpart, net_partial_elems(c->G));
   if (s == SKY_OK) {
-    c->eig_grid = jacobi_max_grid(c);
+    c->eig_grid = c->eig_grid_max = jacobi_max_grid(c);
     ALLOC(c->d_eigpart, (size_t)2 * c->eig_grid * kMaxBatch);
   }
 #undef ALLOC
@@ -410,6 +414,48 @@ sky_status sky_sp_spread(sky_ctx* c, const double* eps, const double* hnorm2, in
   if (!c) return SKY_EINVAL;
   if (A < 0 || (A > 0 && (!eps || !hnorm2)) || !out) return set_err(c, SKY_EINVAL, "sp_spread: bad arguments");
   return sp_spread_impl(c, eps, hnorm2, A, out);
+}
+
+sky_status sky_tune_set(sky_ctx* c, sky_knob knob, int value) {
+  if (!c) return SKY_EINVAL;
+  switch (knob) {
+    case SKY_KNOB_LINE_YZ:
+      if (value != 32 && value != 64 && value != 128) break;
+      c->line_yz = value;
+      return SKY_OK;
+    case SKY_KNOB_LINE_X:
+      if (value != 16 && value != 32 && value != 64) break;
+      c->line_x = value;
+      return SKY_OK;
+    case SKY_KNOB_OVERLAP_WAVES:
+      if (value < 1 || value > kMaxOverlapWaves) break;
+      c->ov_waves = value;
+      return SKY_OK;
+    case SKY_KNOB_TC_WAVES:
+      if (value != 1 && value != 2 && value != 4) break;
+      c->tc_waves = value;
+      return SKY_OK;
+    case SKY_KNOB_JACOBI_BLOCKS:
+      if (value < 1 || value > c->eig_grid_max) break;
+      c->eig_grid = value;
+      return SKY_OK;
+    default:
+      return set_err(c, SKY_EINVAL, "unknown knob %d", (int)knob);
+  }
+  return set_err(c, SKY_EINVAL, "value %d not allowed for knob %d", value, (int)knob);
+}
+
+int sky_tune_get(const sky_ctx* c, sky_knob knob) {
+  if (!c) return -1;
+  switch (knob) {
+    case SKY_KNOB_LINE_YZ: return c->line_yz;
+    case SKY_KNOB_LINE_X: return c->line_x;
+    case SKY_KNOB_OVERLAP_WAVES: return c->ov_waves;
+    case SKY_KNOB_TC_WAVES: return c->tc_waves;
+    case SKY_KNOB_JACOBI_BLOCKS: return c->eig_grid;
+    case SKY_KNOB_JACOBI_BLOCKS_MAX: return c->eig_grid_max;
+    default: return -1;
+  }
 }
 
 sky_status sky_reserve_batch(sky_ctx* c, int nb) {

@@ -56,6 +56,8 @@ struct Ctx;  // defined below; sky_ctx is an alias at the C boundary
 constexpr int kDensSplits = 8;     // state splits of the density accumulation
 constexpr int kMaxBatch = 128;     // problems per batched eigensolve / small GEMM
 constexpr int kRedBlock = 256;     // threads of the per-state reduction blocks
+constexpr int kMaxOverlapWaves = 2; // largest tunable K-split wave count of k_overlap
+constexpr int kMaxTcWaves = 4;      // largest tunable K-split wave count of the tcgen05 overlap
 
 struct Ctx {
   // geometry
@@ -98,7 +100,12 @@ struct Ctx {
   size_t eig_slot_rot;              // rotations per problem and round buffer
   size_t small_slot;                // elements per problem in each d_small buffer
   void* d_eigrot;                   // Jacobi rotations of two consecutive rounds
-  int eig_grid;                     // co-resident blocks of the Jacobi kernel
+  int eig_grid;                     // blocks of the Jacobi kernel (tunable, <= eig_grid_max)
+  int eig_grid_max;                 // co-resident blocks of the Jacobi kernel
+  int line_yz;                      // threads per block of the y/z line passes (tunable)
+  int line_x;                       // lines per block of the x line passes (tunable)
+  int ov_waves;                     // K-split waves of the FMA overlap (tunable)
+  int tc_waves;                     // K-split waves of the tensor-core overlap (tunable)
   double2* d_small[6];              // I x I temporaries
   void* d_tcA[3];                   // split-BF16 operand pieces (tensor-core forms)
   void* d_tcB[3];

@@ -146,7 +146,7 @@ void tc_scratch_sizes(int I, long long V, int num_sms, size_t* piece_a, size_t* 
   *piece_rot_a = (size_t)I * round8(2LL * I);
   const long long ldd = (2LL * I + 3) / 4 * 4;
   const int tiles = ((I + tc::BM - 1) / tc::BM) * ((2 * I + tc::BN - 1) / tc::BN);
-  int z = 2 * num_sms / (tiles > 0 ? tiles : 1);
+  int z = kMaxTcWaves * num_sms / (tiles > 0 ? tiles : 1);
   if (z < 1) z = 1;
   *partial = (size_t)z * I * ldd;
 }
@@ -168,7 +168,7 @@ sky_status tc_overlap(Ctx* c, const void* a, const void* b, int I, double2* X) {
   if (e != cudaSuccess) return cuda_check(c, e, "tc split");
   const long long ldd = (2LL * I + 3) / 4 * 4;
   const int tiles = ((I + tc::BM - 1) / tc::BM) * ((2 * I + tc::BN - 1) / tc::BN);
-  int z = 2 * c->num_sms / tiles;
+  int z = c->tc_waves * c->num_sms / tiles;
   if (z < 1) z = 1;
   const long long sstride = (long long)I * ldd;
   if ((size_t)z * sstride > c->tc_partial_elems) z = (int)(c->tc_partial_elems / sstride);
