@@ -219,14 +219,14 @@ def convergence_leg(dev, maxit=4000):
     w = IN.WORKLOADS[CONV_WORKLOAD]
     inp = IN.make_inputs(w)
 
-    def solve(prec, net=None):
+    def solve(prec, net=None, escalate=None):
         s = Solver(w, prec=prec, device=dev)
         if net is not None:
             s.set_damping(net)
         s.load(inp["psi0"], inp.get("rho0"), inp.get("tau0"))
         torch.cuda.synchronize(dev)
         t = time.perf_counter()
-        hist, conv = s.run(maxit=maxit, window=CONV_WINDOW)
+        hist, conv = s.run(maxit=maxit, window=CONV_WINDOW, escalate=escalate)
         dt = time.perf_counter() - t
         r = {"converged": conv, "iterations": len(hist), "seconds": round(dt, 4),
              "E_per_A": hist[-1]["E"] / s.A}
@@ -238,6 +238,8 @@ def convergence_leg(dev, maxit=4000):
     out = {"workload": CONV_WORKLOAD, "tol_MeV_per_A": w.tol, "window": CONV_WINDOW, "maxit": maxit}
     for name, prec in (("fp64", B.SKY_F64), ("fp32", B.SKY_F32), ("bf16x3", B.SKY_F32_BF16X3)):
         out[name] = solve(prec)
+    # split-BF16 far from convergence, FP32 GEMMs once |dE/A| < 2e-5
+    out["bf16x3_to_fp32"] = solve(B.SKY_F32_BF16X3, escalate=(2e-5, B.SKY_F32))
     t = time.perf_counter()
     s = Solver(w, prec=B.SKY_F64, device=dev)
     s.load(inp["psi0"], inp.get("rho0"), inp.get("tau0"))
@@ -248,13 +250,72 @@ def convergence_leg(dev, maxit=4000):
     s.close()
     out["learned_train_seconds"] = round(train_s, 3)
     out["learned_fp64"] = solve(B.SKY_F64, net)
-    out["learned_bf16x3"] = solve(B.SKY_F32_BF16X3, net)
+    out["learned_fp32"] = solve(B.SKY_F32, net)
+    out["learned_bf16x3_to_fp32"] = solve(B.SKY_F32_BF16X3, net, escalate=(2e-5, B.SKY_F32))
+    out["batched"] = batched_convergence(dev, net, maxit)
     base = out["fp64"]["seconds"]
-    forms = ("fp32", "bf16x3", "learned_fp64", "learned_bf16x3")
+    forms = ("fp32", "bf16x3", "bf16x3_to_fp32", "learned_fp64", "learned_fp32", "learned_bf16x3_to_fp32")
     for k in forms:
         out[k]["same_fixed_point"] = bool(out[k]["converged"] and
                                           abs(out[k]["E_per_A"] - out["fp64"]["E_per_A"]) < 1e-4)
     out["speedup_vs_fp64"] = {k: round(base / out[k]["seconds"], 3) for k in forms}
+    return out
+
+
+CONV_BOXES = 8
+
+
+def batched_convergence(dev, net, maxit):
+    """Eight 16^3, 16n+16p boxes with seeded Bloch twists: seconds until every
+    box meets the stop rule, plain FP64 one box at a time (the method without
+    batching) against the FP32 batch replayed as one CUDA graph, with and
+    without the learned weight."""
+    import numpy as np
+    import torch
+    from paper_1610_07522_gb300 import binding as B
+    from paper_1610_07522_gb300 import inputs as IN
+    from paper_1610_07522_gb300.batched import BatchSolver
+    from paper_1610_07522_gb300.solver import Solver
+
+    base = IN.WORKLOADS[CONV_WORKLOAD]
+    rng = np.random.default_rng(1005)
+    ws = [IN.Workload(**{**base.as_dict(), "name": f"conv_box_{i}", "seed": 1005 * 1000 + i,
+                         "twist": tuple(float(v) for v in rng.uniform(-np.pi, np.pi, 3))})
+          for i in range(CONV_BOXES)]
+    out = {"boxes": CONV_BOXES, "workload": f"{CONV_WORKLOAD} with seeded twists"}
+    t_all, its, E = 0.0, [], []
+    for w in ws:
+        inp = IN.make_inputs(w)
+        s = Solver(w, prec=B.SKY_F64, device=dev)
+        s.load(inp["psi0"], inp.get("rho0"), inp.get("tau0"))
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        hist, conv = s.run(maxit=maxit, window=CONV_WINDOW)
+        t_all += time.perf_counter() - t
+        its.append(len(hist) if conv else None)
+        E.append(hist[-1]["E"] / s.A)
+        s.close()
+    out["fp64_one_at_a_time"] = {"seconds": round(t_all, 3), "iterations": its,
+                                 "boxes_converged": sum(i is not None for i in its)}
+    for name, use_net in (("fp32_graph", False), ("learned_fp32_graph", True)):
+        bs = BatchSolver(ws, prec=B.SKY_F32, device=dev)
+        bs.load()
+        if use_net:
+            bs.set_damping(net)
+        bs.step_eager()
+        bs.capture()
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        done, EA = bs.run(maxit, window=CONV_WINDOW)
+        dt = time.perf_counter() - t
+        both = [b for b in range(len(ws)) if done[b] is not None and its[b] is not None]
+        out[name] = {"seconds": round(dt, 3), "iterations": done,
+                     "boxes_converged": sum(d is not None for d in done),
+                     "same_fixed_point_where_both_converged": bool(
+                         both and max(abs(EA[b] - E[b]) for b in both) < 1e-4)}
+        bs.close()
+    out["speedup_vs_fp64_one_at_a_time"] = {k: round(t_all / out[k]["seconds"], 3)
+                                            for k in ("fp32_graph", "learned_fp32_graph")}
     return out
 
 

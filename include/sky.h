@@ -208,6 +208,17 @@ sky_status sky_energy(sky_ctx* ctx, const double* rho, const double* tau,
 sky_status sky_sp_spread(sky_ctx* ctx, const double* eps, const double* hnorm2, int A,
                          double* out);
 
+/* ---- Precision form of a running context -------------------------------------
+ * Switch an FP32-spinor context among SKY_F32, SKY_F32_BF16X3 and
+ * SKY_F32_BF16X6 (the spinor storage stays complex FP32; only the overlap and
+ * recombination change).  A solver may run the cheap split-BF16 form while
+ * far from convergence and finish in a more accurate one, since the BF16
+ * forms' orthonormality error (about 1e-5 for x3) bounds how close they can
+ * get to the FP64 fixed point.  Switching to a split-BF16 form may allocate
+ * its operand pieces (and synchronises the context stream): call it outside
+ * stream capture.  An FP64 context cannot switch (SKY_EUNSUPPORTED). */
+sky_status sky_set_prec(sky_ctx* ctx, sky_prec prec);
+
 /* ---- Tunable launch shapes ---------------------------------------------------
  * Launch-shape knobs of a context, for an autotuner that times the calls on
  * its own workload and keeps the fastest values.  Every value gives the same

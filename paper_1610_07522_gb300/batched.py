@@ -38,6 +38,7 @@ class BatchSolver:
                               B.SKY_F64, imax, main.cuda_stream)
         B.sky_reserve_batch(self.eig, len(self.problems))
         self.graph = None
+        self.graph_stale = False
         self.launches_per_step = None
         self.units = sum(2 * (w.N + w.Z) for w in self.workloads)
 
@@ -81,6 +82,17 @@ class BatchSolver:
             B.sky_energy(s.ctx, s.rho, s.tau, s.divJ, s.eout)
         self._join(main)
 
+    def set_damping(self, net, rise_tol=1e-5):
+        """Learned damping weight in every box (each with its own network
+        workspace, as the boxes run concurrently); the per-box fallback of
+        Solver.set_damping applies, and a fallback re-captures the graph."""
+        for s in self.boxes:
+            with torch.cuda.stream(s.stream):
+                v = net.view()
+                v.workspace(s.G)            # allocated now, not inside a capture
+                s.set_damping(v, rise_tol=rise_tol)
+        self.graph_stale = self.graph is not None
+
     def eigensolve(self):
         """Loewdin factors and Rayleigh-Ritz of every species of every box in
         one batched solve on the shared context (its stream)."""
@@ -122,11 +134,15 @@ class BatchSolver:
         torch.cuda.synchronize(self.device)
 
     def step(self):
-        """One iteration of every box: the captured graph if there is one."""
+        """One iteration of every box: the captured graph if there is one
+        (re-captured first if a box's launch sequence changed)."""
         if self.graph is None:
             self.step_eager()
-        else:
-            self.graph.replay()
+            return
+        if self.graph_stale:
+            self.capture()
+            self.graph_stale = False
+        self.graph.replay()
 
     def sync(self):
         torch.cuda.synchronize(self.device)
@@ -134,10 +150,15 @@ class BatchSolver:
             B.sky_sync(s.ctx)
         B.sky_sync(self.eig)
 
-    def energies(self):
-        """Per-box (E, delta_eps) after synchronising."""
-        self.sync()
-        return [(float(s.eout[0].item()), float(s.spread[0].item())) for s in self.boxes]
+    def energies(self, check_status=True):
+        """Per-box (E, delta_eps) after synchronising, read in one copy; with
+        check_status every box's device status word is checked too."""
+        if check_status:
+            self.sync()
+        else:
+            torch.cuda.synchronize(self.device)
+        v = torch.stack([torch.stack([s.eout[0], s.spread[0]]) for s in self.boxes]).cpu().numpy()
+        return [(float(e), float(d)) for e, d in v]
 
     def run(self, maxit, tol=1e-6, window=5):
         """Iterate every box until each has held |E_n/A - E_{n-1}/A| < tol for
@@ -149,19 +170,26 @@ class BatchSolver:
         done = [None] * len(self.boxes)
         for it in range(maxit):
             self.step()
-            en = self.energies()
+            en = self.energies(check_status=(it % 64 == 63))
             for b, (E, _) in enumerate(en):
-                A = self.boxes[b].A
+                s = self.boxes[b]
+                A = s.A
                 if prev[b] is not None and abs(E - prev[b]) / A < tol:
                     below[b] += 1
                     if below[b] >= window and done[b] is None:
                         done[b] = it + 1
                 else:
                     below[b] = 0
+                if s.damping_on and prev[b] is not None and (E - prev[b]) / A > s.rise_tol:
+                    s.damping_scale *= 0.5          # the fallback of Solver.run
+                    s.damping_fallbacks += 1
+                    if s.damping_scale < s.min_scale:
+                        s.damping_on = False
+                    self.graph_stale = self.graph is not None
                 prev[b] = E
             if all(d is not None for d in done):
                 break
-        return done, [E / s.A for (E, _), s in zip(self.energies(), self.boxes)]
+        return done, [E / s.A for (E, _), s in zip(self.energies(check_status=True), self.boxes)]
 
     def close(self):
         self.graph = None

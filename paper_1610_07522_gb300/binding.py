@@ -63,6 +63,7 @@ _SIGNATURES = {
     "sky_subspace_diag_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I),
                                        ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "sky_reserve_batch": (_I, [_P, _I]),
+    "sky_set_prec": (_I, [_P, _I]),
     "sky_tune_set": (_I, [_P, _I, _I]),
     "sky_tune_get": (_I, [_P, _I]),
     "sky_net_forward": (_I, [_P, _I, _P, _P, _P, _P, _D, _P, _P]),
@@ -202,6 +203,10 @@ def sky_subspace_diag_batched(ctx, H, C, I, M, eps):
     n = len(I)
     _check(ctx, lib().sky_subspace_diag_batched(ctx, n, _ptrs(H), _ptrs(C), (_I * n)(*I), _ptrs(M),
                                                 _ptrs(eps)))
+
+
+def sky_set_prec(ctx, prec):
+    _check(ctx, lib().sky_set_prec(ctx, int(prec)))
 
 
 def sky_tune_set(ctx, knob, value):

@@ -83,6 +83,37 @@ static void free_all(Ctx* c) {
     if (p) cudaFree(p);
 }
 
+// BF16 operand pieces (up to `pieces`) and the FP32 split-K partials of the
+// tensor-core forms; pieces already present are kept.
+static sky_status alloc_tc_scratch(Ctx* c, int pieces) {
+  const int Imax = c->max_states > 0 ? c->max_states : 1;
+  const long long V = 2LL * c->G;
+  size_t pa, pb, pra, part;
+  tc_scratch_sizes(Imax, V, c->num_sms, &pa, &pb, &pra, &part);
+  sky_status s = SKY_OK;
+  for (int k = 0; k < pieces && s == SKY_OK; ++k) {
+    if (c->d_tcA[k]) continue;
+    unsigned short *x = nullptr, *y = nullptr, *z = nullptr;
+    s = dalloc(c, &x, pa);
+    if (s == SKY_OK) s = dalloc(c, &y, pb);
+    if (s == SKY_OK) s = dalloc(c, &z, pra);
+    if (s != SKY_OK) {
+      if (x) cudaFree(x);
+      if (y) cudaFree(y);
+      if (z) cudaFree(z);
+      return s;
+    }
+    c->d_tcA[k] = x; c->d_tcB[k] = y; c->d_tcRotA[k] = z;
+  }
+  if (s == SKY_OK && !c->d_tcPart) {
+    float* p = nullptr;
+    s = dalloc(c, &p, part);
+    c->d_tcPart = p;
+    c->tc_partial_elems = part;
+  }
+  return s;
+}
+
 static size_t scratch_budget() {
   const char* s = getenv("SKY_SCRATCH_MB");
   if (s && atol(s) > 0) return (size_t)atol(s) << 20;
@@ -201,20 +232,7 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   }
   for (int k = 0; k < 6; ++k) ALLOC(c->d_small[k], c->small_slot * c->eig_batch);
   ALLOC(c->d_gate, 8 * kMaxBatch);
-  if (s == SKY_OK && is_tc(prec)) {
-    size_t pa, pb, pra, part;
-    tc_scratch_sizes(Imax, V, c->num_sms, &pa, &pb, &pra, &part);
-    const int n = tc_nsplit(prec);
-    for (int k = 0; k < n && s == SKY_OK; ++k) {
-      unsigned short *x = nullptr, *y = nullptr, *z = nullptr;
-      s = dalloc(c, &x, pa);
-      if (s == SKY_OK) s = dalloc(c, &y, pb);
-      if (s == SKY_OK) s = dalloc(c, &z, pra);
-      c->d_tcA[k] = x; c->d_tcB[k] = y; c->d_tcRotA[k] = z;
-    }
-    ALLOC(c->d_tcPart, part);
-    c->tc_partial_elems = part;
-  }
+  if (s == SKY_OK && is_tc(prec)) s = alloc_tc_scratch(c, tc_nsplit(prec));
   ALLOC(c->d_stats, 8);
   ALLOC(c->d_netpart, net_partial_elems(c->G));
   if (s == SKY_OK) {
@@ -414,6 +432,22 @@ sky_status sky_sp_spread(sky_ctx* c, const double* eps, const double* hnorm2, in
   if (!c) return SKY_EINVAL;
   if (A < 0 || (A > 0 && (!eps || !hnorm2)) || !out) return set_err(c, SKY_EINVAL, "sp_spread: bad arguments");
   return sp_spread_impl(c, eps, hnorm2, A, out);
+}
+
+sky_status sky_set_prec(sky_ctx* c, sky_prec prec) {
+  if (!c) return SKY_EINVAL;
+  if (prec == c->prec) return SKY_OK;
+  if (prec != SKY_F32 && !is_tc(prec)) return set_err(c, SKY_EINVAL, "unknown precision form %d", (int)prec);
+  if (c->prec == SKY_F64)
+    return set_err(c, SKY_EUNSUPPORTED, "an FP64 context keeps FP64 spinors; create an FP32 one");
+  if (is_tc(prec)) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "set_prec sync");
+    const sky_status s = alloc_tc_scratch(c, tc_nsplit(prec));
+    if (s != SKY_OK) return s;
+  }
+  c->prec = prec;
+  return SKY_OK;
 }
 
 sky_status sky_tune_set(sky_ctx* c, sky_knob knob, int value) {

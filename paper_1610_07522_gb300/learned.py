@@ -66,6 +66,14 @@ class DampingNet:
                            torch.zeros(G, dtype=torch.float32, device=self.device))
         return self._ws[G]
 
+    def view(self):
+        """A handle on the same parameters with workspaces of its own, for
+        solvers that run the network concurrently on different streams."""
+        v = object.__new__(DampingNet)
+        v.__dict__.update(self.__dict__)
+        v._ws = {}
+        return v
+
     def weights(self, ctx, G, q, U, Bf, W, out, scale=1.0):
         """w_q(r) = 1 + scale (w_net - 1) into ``out`` [G] float from the mean
         field of species q."""

@@ -182,21 +182,36 @@ class Solver:
         e = self.eout.cpu().numpy()
         return float(e[0]), float(self.spread[0].item()), e
 
-    def run(self, maxit=None, tol=None, callback=None, window=1):
+    def set_prec(self, prec):
+        """Switch the GEMM form of an FP32-spinor solver (sky_set_prec)."""
+        B.sky_set_prec(self.ctx, prec)
+        self.prec = prec
+
+    def run(self, maxit=None, tol=None, callback=None, window=1, escalate=None):
         """Iterate until |E_n/A - E_{n-1}/A| < tol for ``window`` consecutive
         iterations (1: the plain rule) or maxit; returns (history, converged).
         A window > 1 keeps a single small change, e.g. rounding noise of an
-        FP32 form on a flat stretch of the path, from ending the run."""
+        FP32 form on a flat stretch of the path, from ending the run.
+        ``escalate = (tol_switch, prec)`` switches the GEMM form to ``prec``
+        once the change has stayed below tol_switch for ``window`` iterations
+        (e.g. split-BF16 far from convergence, then FP32)."""
         maxit = self.w.maxit if maxit is None else maxit
         tol = self.w.tol if tol is None else tol
-        hist, E_prev, below = [], None, 0
+        hist, E_prev, below, below_sw = [], None, 0, 0
         for it in range(maxit):
             self.step()
             E, de, _ = self.energy()
             hist.append({"it": it, "E": E, "delta_eps": de})
             if callback:
                 callback(it, hist[-1])
-            if E_prev is not None and abs(E - E_prev) / self.A < tol:
+            dE = abs(E - E_prev) / self.A if E_prev is not None else None
+            if escalate is not None and dE is not None:
+                below_sw = below_sw + 1 if dE < escalate[0] else 0
+                if below_sw >= window:
+                    self.set_prec(escalate[1])
+                    hist[-1]["escalated"] = escalate[1]
+                    escalate, below = None, 0
+            if dE is not None and dE < tol and escalate is None:
                 below += 1
                 if below >= window:
                     return hist, True
