@@ -4,16 +4,24 @@
 // split-BF16 products (hi*hi + hi*lo + lo*hi for a 2-way split, six products
 // for a 3-way split) accumulate in one tile.
 //
-// One CTA computes one 128 x 128 output tile over a range of K (split-K via
-// blockIdx.z writes separate partial tiles).  Warp roles:
+// Persistent kernel, one CTA per SM: CTA b computes the 128 x 128 output tiles
+// b, b + gridDim.x, ... (m fastest, then n, then the K split; split z writes
+// partial tile z).  Each ring stage holds one 64-wide K block of every operand
+// piece in use (A_0..A_{n-1}, B_0..B_{n-1}), so a piece is loaded once per K
+// block and all products of that block are issued from the same stage.  Two
+// TMEM accumulators alternate between tiles, so the epilogue of one tile runs
+// while the MMAs of the next are issued.  Warp roles:
 //   warp 0     TMA producer: cp.async.bulk.tensor loads of 128 x 64 bf16
-//              A and B boxes (128-byte swizzle) into a STAGES-deep ring;
-//   warp 1     owns the TMEM accumulator (128 lanes x 128 fp32 columns) and one
-//              elected lane issues tcgen05.mma (M = 128, N = 128, K = 16 each);
-//              tcgen05.commit frees ring stages and finally signals the epilogue;
-//   warps 2-5  epilogue: tcgen05.ld of their TMEM lane quadrant -> global fp32.
+//              A and B boxes (128-byte swizzle) into a ring of a.stages stages,
+//              running ahead across tile boundaries;
+//   warp 1     owns TMEM (2 x 128 fp32 columns) and one elected lane issues
+//              tcgen05.mma (M = 128, N = 128, K = 16 each); tcgen05.commit frees
+//              ring stages and signals the epilogue when a tile is complete;
+//   warps 2-5  epilogue: tcgen05.ld of their TMEM lane quadrant -> global fp32,
+//              then hand the accumulator back (one mbarrier arrival per warp).
 // Every mbarrier wait is bounded; a timeout sets SKY_ETIMEOUT in the status
-// word, the kernel still drains the MMAs it issued, frees TMEM and returns.
+// word, the kernel waits (bounded) for the MMAs it issued, frees TMEM and
+// returns.
 #pragma once
 
 #include <cuda.h>
@@ -25,12 +33,12 @@ namespace sky {
 namespace tc {
 
 constexpr int BM = 128, BN = 128, BK = 64;         // BK bf16 = one 128-byte swizzle row
-constexpr int STAGES = 5;
 constexpr int TILE_BYTES = BM * BK * 2;            // 16 KiB per operand tile
-constexpr int STAGE_BYTES = 2 * TILE_BYTES;        // A + B
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int kMaxStages = 8;
+constexpr int kRingBytes = 200 * 1024;             // ring budget (of 227 KB)
+constexpr int SMEM_BYTES = kRingBytes + 1024 + 256;
 constexpr int THREADS = 192;
-constexpr uint32_t TMEM_COLS = 128;
+constexpr uint32_t TMEM_COLS = 2 * BN;              // two accumulators (double buffer)
 constexpr long long kSpin = 1LL << 24;             // x >= 64 ns per try: bounded waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -126,6 +134,9 @@ struct GemmArgs {
   int kb_per_split;         // 64-wide K blocks per split (blockIdx.z)
   int nphase;               // phases: sum_p A[pa[p]] B[pb[p]]^T
   int pa[kMaxPhase], pb[kMaxPhase];
+  int npiece;               // pieces of each operand loaded per stage
+  int stages;               // ring depth (stage = 2 npiece tiles)
+  int nsplit;               // K splits (tiles are m x n x split)
   float* D;                 // D[z][m][n], row stride ldd, split stride sstride
   long long ldd, sstride;
   int* status;
@@ -139,27 +150,41 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       (unsigned char*)(((unsigned long long)smem_raw + 1023ull) & ~1023ull);
-  unsigned long long* bars = (unsigned long long*)(base + STAGES * STAGE_BYTES);
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+  const int np = a.npiece, stages = a.stages;
+  const int stage_bytes = 2 * np * TILE_BYTES;
+  unsigned long long* bars = (unsigned long long*)(base + kRingBytes);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kMaxStages + 5);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // persistent: CTA b takes tiles b, b + gridDim.x, ...; tile t -> (m fastest, n, split)
+  const int mt = (a.M + BM - 1) / BM, nt = (a.N + BN - 1) / BN;
+  const int ntiles = mt * nt * a.nsplit;
   const int nkb_total = (a.K + BK - 1) / BK;
-  const int kb0 = blockIdx.z * a.kb_per_split;
-  int my_nkb = nkb_total - kb0;
-  if (my_nkb > a.kb_per_split) my_nkb = a.kb_per_split;
-  if (my_nkb < 0) my_nkb = 0;
-  const int iters = my_nkb * a.nphase;
+  auto tile_kb = [&](int t, int& m0, int& n0, int& kb0, int& nkb, int& z) {
+    m0 = (t % mt) * BM;
+    n0 = ((t / mt) % nt) * BN;
+    z = t / (mt * nt);
+    kb0 = z * a.kb_per_split;
+    nkb = nkb_total - kb0;
+    if (nkb > a.kb_per_split) nkb = a.kb_per_split;
+    if (nkb < 0) nkb = 0;
+  };
   const uint32_t bar0 = smem_u32(bars);
   auto full = [&](int s) { return bar0 + 8u * s; };
-  auto empty = [&](int s) { return bar0 + 8u * (STAGES + s); };
-  const uint32_t done = bar0 + 8u * (2 * STAGES);
+  auto empty = [&](int s) { return bar0 + 8u * (kMaxStages + s); };
+  auto acc_full = [&](int b) { return bar0 + 8u * (2 * kMaxStages + b); };
+  auto acc_empty = [&](int b) { return bar0 + 8u * (2 * kMaxStages + 2 + b); };
+  const uint32_t drain = bar0 + 8u * (2 * kMaxStages + 4);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(full(s), 1);
       mbar_init(empty(s), 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full(b), 1);
+      mbar_init(acc_empty(b), 4);   // one arrival per epilogue warp
+    }
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -177,70 +202,115 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int it = 0; it < iters; ++it) {
-        const int s = it % STAGES, u = it / STAGES;
-        if (u > 0 && !mbar_wait(empty(s), (u - 1) & 1)) {
-          flag_status(a.status, SKY_ETIMEOUT);
-          break;
+      // stage layout: A_0 .. A_{np-1}, B_0 .. B_{np-1}, one 16 KiB tile each
+      long long g = 0;   // ring position across all tiles of this CTA
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int m0, n0, kb0, nkb, z;
+        tile_kb(t, m0, n0, kb0, nkb, z);
+        for (int it = 0; it < nkb; ++it, ++g) {
+          const int s = (int)(g % stages);
+          const long long u = g / stages;
+          if (u > 0 && !mbar_wait(empty(s), (uint32_t)((u - 1) & 1))) {
+            flag_status(a.status, SKY_ETIMEOUT);
+            ok = false;
+            break;
+          }
+          const int kb = kb0 + it;
+          const uint32_t sa = smem_u32(base + s * stage_bytes);
+          mbar_expect_tx(full(s), stage_bytes);
+          for (int i = 0; i < np; ++i) {
+            const CUtensorMap* mapA = i == 0 ? &mA0 : (i == 1 ? &mA1 : &mA2);
+            const CUtensorMap* mapB = i == 0 ? &mB0 : (i == 1 ? &mB1 : &mB2);
+            tma_load_2d(sa + i * TILE_BYTES, mapA, kb * BK, m0, full(s));
+            tma_load_2d(sa + (np + i) * TILE_BYTES, mapB, kb * BK, n0, full(s));
+          }
         }
-        const int ph = it / my_nkb, kb = kb0 + it % my_nkb;
-        const int ia = a.pa[ph], ib = a.pb[ph];
-        const CUtensorMap* mapA = ia == 0 ? &mA0 : (ia == 1 ? &mA1 : &mA2);
-        const CUtensorMap* mapB = ib == 0 ? &mB0 : (ib == 1 ? &mB1 : &mB2);
-        const uint32_t sa = smem_u32(base + s * STAGE_BYTES);
-        mbar_expect_tx(full(s), STAGE_BYTES);
-        tma_load_2d(sa, mapA, kb * BK, m0, full(s));
-        tma_load_2d(sa + TILE_BYTES, mapB, kb * BK, n0, full(s));
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(BM, BN);
-      int issued = 0;
-      for (int it = 0; it < iters; ++it) {
-        const int s = it % STAGES, u = it / STAGES;
-        if (!mbar_wait(full(s), u & 1)) {
+      long long g = 0;
+      int j = 0;   // tiles done by this CTA
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
+        int m0, n0, kb0, nkb, z;
+        tile_kb(t, m0, n0, kb0, nkb, z);
+        const int b = j & 1, use = j >> 1;
+        // the epilogue must have drained this accumulator's previous tile
+        if (use > 0 && !mbar_wait(acc_empty(b), (uint32_t)((use - 1) & 1))) {
           flag_status(a.status, SKY_ETIMEOUT);
           break;
         }
         fence_after();
-        const uint32_t sa = smem_u32(base + s * STAGE_BYTES);
-        const uint64_t da = sw128_desc(sa), db = sw128_desc(sa + TILE_BYTES);
+        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        for (int it = 0; it < nkb; ++it, ++g) {
+          const int s = (int)(g % stages);
+          const long long u = g / stages;
+          if (!mbar_wait(full(s), (uint32_t)(u & 1))) {
+            flag_status(a.status, SKY_ETIMEOUT);
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t sa = smem_u32(base + s * stage_bytes);
+          for (int p = 0; p < a.nphase; ++p) {
+            const uint64_t da = sw128_desc(sa + a.pa[p] * TILE_BYTES);
+            const uint64_t db = sw128_desc(sa + (np + a.pb[p]) * TILE_BYTES);
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k)   // +32 bytes along K = +2 in the encoded address
-          mma_bf16(tmem, da + 2ull * k, db + 2ull * k, idesc, (it > 0 || k > 0) ? 1u : 0u);
-        mma_commit(empty(s));
-        ++issued;
+            for (int k = 0; k < BK / 16; ++k)   // +32 bytes along K = +2 in the encoded address
+              mma_bf16(acc, da + 2ull * k, db + 2ull * k, idesc,
+                       (it > 0 || p > 0 || k > 0) ? 1u : 0u);
+          }
+          mma_commit(empty(s));
+        }
+        mma_commit(acc_full(b));   // arrives when this tile's MMAs have completed
       }
-      (void)issued;
-      mma_commit(done);   // arrives when every MMA issued above has completed
+      // every MMA issued by this thread completes before TMEM is freed
+      mma_commit(drain);
+      if (!mbar_wait(drain, 0)) flag_status(a.status, SKY_ETIMEOUT);
     }
   } else {
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of the tile's accumulator
     const int q = warp & 3;
-    const bool ok = mbar_wait(done, 0);
-    if (!ok && lane == 0) flag_status(a.status, SKY_ETIMEOUT);
-    fence_after();
-    const int row = m0 + q * 32 + lane;
-    float* drow = a.D + (long long)blockIdx.z * a.sstride + (long long)row * a.ldd;
-#pragma unroll 1
-    for (int c = 0; c < BN; c += 32) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
-      if (iters == 0) {
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = 0.0f;
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      int m0, n0, kb0, nkb, z;
+      tile_kb(t, m0, n0, kb0, nkb, z);
+      const int b = j & 1, use = j >> 1;
+      const bool ok = mbar_wait(acc_full(b), (uint32_t)(use & 1));
+      if (!ok) {
+        if (lane == 0) flag_status(a.status, SKY_ETIMEOUT);
+        break;
       }
-      const int col = n0 + c;
-      if (ok && row < a.M) {
-        if (col + 32 <= a.N) {
+      fence_after();
+      const int row = m0 + q * 32 + lane;
+      float* drow = a.D + (long long)z * a.sstride + (long long)row * a.ldd;
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c), v);
+        if (nkb == 0) {
 #pragma unroll
-          for (int i = 0; i < 32; i += 4)
-            *reinterpret_cast<float4*>(drow + col + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-        } else {
-          for (int i = 0; i < 32 && col + i < a.N; ++i) drow[col + i] = v[i];
+          for (int i = 0; i < 32; ++i) v[i] = 0.0f;
+        }
+        const int col = n0 + c;
+        if (row < a.M) {
+          if (col + 32 <= a.N) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<float4*>(drow + col + i) =
+                  make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+          } else {
+            for (int i = 0; i < 32 && col + i < a.N; ++i) drow[col + i] = v[i];
+          }
         }
       }
+      // this warp's lanes of the accumulator are read: hand it back to the MMA warp
+      fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acc_empty(b)) : "memory");
     }
   }
   fence_before();
@@ -320,6 +390,8 @@ inline cudaError_t gemm_bf16(const void* const* A, long long lda, const void* co
   }
   const Phases ph = phases_for_split(nsplit);
   const int nkb = (K + BK - 1) / BK;
+  int stages = kRingBytes / (2 * nsplit * TILE_BYTES);
+  if (stages > kMaxStages) stages = kMaxStages;
   int z = *splits < 1 ? 1 : *splits;
   if (z > nkb) z = nkb;
   GemmArgs g;
@@ -327,6 +399,8 @@ inline cudaError_t gemm_bf16(const void* const* A, long long lda, const void* co
   g.kb_per_split = (nkb + z - 1) / z;
   z = (nkb + g.kb_per_split - 1) / g.kb_per_split;
   g.nphase = ph.n;
+  g.npiece = nsplit;
+  g.stages = stages;
   for (int i = 0; i < kMaxPhase; ++i) {
     g.pa[i] = i < ph.n ? ph.pa[i] : 0;
     g.pb[i] = i < ph.n ? ph.pb[i] : 0;
@@ -342,7 +416,11 @@ inline cudaError_t gemm_bf16(const void* const* A, long long lda, const void* co
     if (e != cudaSuccess) return e;
     smem_set[dev] = true;
   }
-  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, z);
+  g.nsplit = z;
+  const long long ntiles = (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN) * z;
+  int nsm = 0;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int grid = (int)(ntiles < nsm ? ntiles : nsm);   // persistent: one CTA per SM
   k_gemm_bf16<<<grid, THREADS, SMEM_BYTES, s>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], g);
   note_launch();
   *splits = z;
