@@ -194,6 +194,11 @@ ZJobs zjobs(int np, bool ah, bool bh, const double2* const* A, const double2* co
   return j;
 }
 
+// Three real products per complex multiply-add (Gauss), as in k_overlap:
+//   P1 = sum a.x b.x,  P2 = sum a.y b.y,  P3 = sum (a.x + a.y)(b.x + b.y),
+//   Re = P1 - P2,  Im = P3 - P1 - P2;
+// the sums a.x + a.y and b.x + b.y are formed once when staging the tiles
+// (after the conjugation of a conjugate-transposed operand).
 template <bool AH, bool BH, int TS>
 __global__ void __launch_bounds__(TS * TS / 4) k_zgemm(ZJobs j) {
   const int b = blockIdx.z, n = j.n[b];
@@ -205,12 +210,14 @@ __global__ void __launch_bounds__(TS * TS / 4) k_zgemm(ZJobs j) {
   constexpr int NT = TS * TS / 4, TH = TS / 2;
   __shared__ double2 As[BK][TS + 1];
   __shared__ double2 Bs[BK][TS + 1];
+  __shared__ double Ad[BK][TS + 1];
+  __shared__ double Bd[BK][TS + 1];
   const int tid = threadIdx.x, ty = tid / TH, tx = tid % TH;
-  double2 acc[2][2];
+  double p1[2][2], p2[2][2], p3[2][2];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int k = 0; k < 2; ++k) acc[i][k] = make_double2(0.0, 0.0);
+    for (int k = 0; k < 2; ++k) p1[i][k] = p2[i][k] = p3[i][k] = 0.0;
   for (int k0 = 0; k0 < n; k0 += BK) {
     for (int e = tid; e < BK * TS; e += NT) {
       const int kk = e / TS, col = e % TS;
@@ -219,17 +226,30 @@ __global__ void __launch_bounds__(TS * TS / 4) k_zgemm(ZJobs j) {
       if (k < n && r < n) av = AH ? conjx(A[(long long)k * n + r]) : A[(long long)r * n + k];
       if (k < n && cc < n) bv = BH ? conjx(B[(long long)cc * n + k]) : B[(long long)k * n + cc];
       As[kk][col] = av;
+      Ad[kk][col] = av.x + av.y;
       Bs[kk][col] = bv;
+      Bd[kk][col] = bv.x + bv.y;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      const double2 a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
-      const double2 b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-      cfma(acc[0][0], a0, b0);
-      cfma(acc[0][1], a0, b1);
-      cfma(acc[1][0], a1, b0);
-      cfma(acc[1][1], a1, b1);
+      double2 a[2], bb[2];
+      double ad[2], bd[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        a[i] = As[kk][ty * 2 + i];
+        ad[i] = Ad[kk][ty * 2 + i];
+        bb[i] = Bs[kk][tx * 2 + i];
+        bd[i] = Bd[kk][tx * 2 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          p1[i][k] = fma(a[i].x, bb[k].x, p1[i][k]);
+          p2[i][k] = fma(a[i].y, bb[k].y, p2[i][k]);
+          p3[i][k] = fma(ad[i], bd[k], p3[i][k]);
+        }
     }
     __syncthreads();
   }
@@ -239,7 +259,8 @@ __global__ void __launch_bounds__(TS * TS / 4) k_zgemm(ZJobs j) {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const int r = r0 + ty * 2 + i, cc = c0 + tx * 2 + k;
-      if (r < n && cc < n) C[(long long)r * n + cc] = acc[i][k];
+      if (r < n && cc < n)
+        C[(long long)r * n + cc] = make_double2(p1[i][k] - p2[i][k], p3[i][k] - p1[i][k] - p2[i][k]);
     }
 }
 
