@@ -397,6 +397,7 @@ def run_gpu(args):
     ov_events = []
     s.overlap_events = ov_events      # CUDA events around each overlap call, on the ctx stream
     sampler = ClockSampler(_gpu_smi_id(local))
+    B.sky_stats(s.ctx, reset=True)
     _barrier(dist)
     torch.cuda.synchronize()
     sampler.start()
@@ -409,6 +410,7 @@ def run_gpu(args):
     t1.record(s.stream)
     torch.cuda.synchronize()
     launches = B.sky_kernel_launches() - launches0
+    solver_stats = B.sky_stats(s.ctx)
     _barrier(dist)
     clocks = sampler.stop()
     s.overlap_events = None
@@ -496,6 +498,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": "spinor-applies/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
+        "solver_stats_timed_steps": solver_stats,
         "clocks": clocks,
         "convergence": conv,
         "batched": batched,

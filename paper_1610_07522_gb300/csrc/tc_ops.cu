@@ -135,6 +135,13 @@ static inline long long round8(long long x) { return (x + 7) / 8 * 8; }
 
 int tc_nsplit(sky_prec p) { return p == SKY_F32_BF16X6 ? 3 : 2; }
 
+// FP32 accumulation in TMEM loses accuracy over long K (its rounding error
+// grows like sqrt(K) 2^-24 of the partial sums): every split-K partial of the
+// overlap covers at most kMaxAccK values of K, and the partials are summed in
+// FP64 by the reduce.
+constexpr long long kMaxAccK = 2048;
+int tc_min_splits(long long K) { return (int)((K + kMaxAccK - 1) / kMaxAccK); }
+
 // Scratch (bf16 elements per piece / fp32 partials) for I states of V complex.
 void tc_scratch_sizes(int I, long long V, int num_sms, size_t* piece_a, size_t* piece_b,
                       size_t* piece_rot_a, size_t* partial) {
@@ -147,6 +154,8 @@ void tc_scratch_sizes(int I, long long V, int num_sms, size_t* piece_a, size_t* 
   const long long ldd = (2LL * I + 3) / 4 * 4;
   const int tiles = ((I + tc::BM - 1) / tc::BM) * ((2 * I + tc::BN - 1) / tc::BN);
   int z = kMaxTcWaves * num_sms / (tiles > 0 ? tiles : 1);
+  const int zacc = tc_min_splits(K);
+  if (z < zacc) z = zacc;
   if (z < 1) z = 1;
   *partial = (size_t)z * I * ldd;
 }
@@ -169,6 +178,7 @@ sky_status tc_overlap(Ctx* c, const void* a, const void* b, int I, double2* X) {
   const long long ldd = (2LL * I + 3) / 4 * 4;
   const int tiles = ((I + tc::BM - 1) / tc::BM) * ((2 * I + tc::BN - 1) / tc::BN);
   int z = c->tc_waves * c->num_sms / tiles;
+  if (z < tc_min_splits(K)) z = tc_min_splits(K);   // bounded FP32 accumulation length
   if (z < 1) z = 1;
   const long long sstride = (long long)I * ldd;
   if ((size_t)z * sstride > c->tc_partial_elems) z = (int)(c->tc_partial_elems / sstride);

@@ -85,6 +85,14 @@ WORKLOADS = {
     "sly4_32cubed_700n300p": Workload(
         name="sly4_32cubed_700n300p", grid=(32, 32, 32), dx=(1.0, 1.0, 1.0),
         N=700, Z=300, coulomb=True, maxit=500, init="blobs", seed=1003),
+    # The paper's production shapes (Sec. 5, Tables 2-3): A = 6000 (3000 n +
+    # 3000 p) in a 32^3 or 48^3 box, dx = 1 fm.
+    "sly4_32cubed_3000n3000p": Workload(
+        name="sly4_32cubed_3000n3000p", grid=(32, 32, 32), dx=(1.0, 1.0, 1.0),
+        N=3000, Z=3000, coulomb=True, maxit=500, init="blobs", seed=1006),
+    "sly4_48cubed_3000n3000p": Workload(
+        name="sly4_48cubed_3000n3000p", grid=(48, 48, 48), dx=(1.0, 1.0, 1.0),
+        N=3000, Z=3000, coulomb=True, maxit=500, init="blobs", seed=1007),
     # Small 8^3 case for the brute-force pins.
     "sly4_8cubed_4n4p": Workload(
         name="sly4_8cubed_4n4p", grid=(8, 8, 8), dx=(1.0, 1.0, 1.0),
@@ -165,10 +173,17 @@ def noisy_plane_waves(grid, dx, I, amp, rng):
 
 def random_superpositions(grid, dx, I, rng):
     """Each state a seeded complex-normal combination of the 2I lowest spin
-    plane waves.  Not orthonormal."""
-    basis = plane_wave_states(grid, dx, plane_wave_labels(grid, dx, 2 * I))
+    plane waves e^{i k.r}/sqrt(L^3) (the same functions as plane_wave_states),
+    synthesised by one inverse FFT per state from its coefficients placed on
+    the FFT grid.  Not orthonormal."""
+    labels = plane_wave_labels(grid, dx, 2 * I)
     c = rng.standard_normal((I, 2 * I)) + 1j * rng.standard_normal((I, 2 * I))
-    return np.tensordot(c, basis, axes=(1, 0))
+    nx, ny, nz = grid
+    L3 = float(np.prod([grid[i] * dx[i] for i in range(3)]))
+    spec = np.zeros((I, 2, nz, ny, nx), dtype=np.complex128)
+    for j, (mx, my, mz, s) in enumerate(labels):
+        spec[:, s, mz % nz, my % ny, mx % nx] += c[:, j]
+    return np.fft.ifftn(spec, axes=(2, 3, 4)) * (nx * ny * nz / np.sqrt(L3))
 
 
 # --------------------------------------------------------------------------

@@ -172,3 +172,17 @@ def test_self_consistent_aufbau():
         occ = np.sort(rec["lam"][q])
         assert np.max(np.abs(occ - ev[:occ.size])) < 1e-4
         assert ev[occ.size] > occ[-1] + 1.0    # no empty level below the Fermi level
+
+
+def test_random_superpositions_are_plane_wave_sums():
+    """The k-space synthesis equals the explicit sum of the 2I lowest spin
+    plane waves with the same seeded coefficients."""
+    import numpy as np
+    from paper_1610_07522_gb300 import inputs as IN
+    grid, dx, I = (8, 12, 10), (1.0, 0.9, 1.1), 9
+    got = IN.random_superpositions(grid, dx, I, np.random.default_rng(5))
+    rng = np.random.default_rng(5)
+    basis = IN.plane_wave_states(grid, dx, IN.plane_wave_labels(grid, dx, 2 * I))
+    c = rng.standard_normal((I, 2 * I)) + 1j * rng.standard_normal((I, 2 * I))
+    want = np.tensordot(c, basis, axes=(1, 0))
+    assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want))
