@@ -332,6 +332,24 @@ def rayleigh_ritz(S, H):
     return C @ Z, lam
 
 
+def combined_literal(S, H):
+    """The paper's combined form (Sec. 3.3.3, Fig. step67): Z from the
+    eigendecomposition of H itself (the non-orthonormal basis, H = Z Lambda
+    Z^H, ascending), C = S^{-1/2} from the overlap of the same states, and the
+    two applied one after the other as one matrix: first the diagonalising
+    combination chi_alpha = sum_beta Z_{beta alpha} phi_beta, then Eq.
+    orthmatvec with C, psi_alpha = sum_gamma C_{gamma alpha} chi_gamma, i.e.
+    M = Z C.  (Reading: the paper's Z^H and C^T act on the column of states;
+    with H_ij = <phi_i|h|phi_j> the combination that diagonalises h is Z's
+    columns, and C is applied as in Eq. orthmatvec.)  Equal to the exact
+    Rayleigh-Ritz step when S = I; otherwise the new states are neither exactly
+    orthonormal nor exact Ritz vectors, and the difference vanishes at
+    convergence.  Returns (M, Lambda)."""
+    Hh = 0.5 * (H + np.conj(H).T)
+    lam, Z = np.linalg.eigh(Hh)
+    return Z @ loewdin(S), lam
+
+
 def rotate(phi, M):
     """psi_alpha = sum_beta M_{beta alpha} phi_beta (Eq. orthmatvec form)."""
     return np.tensordot(M, phi, axes=(0, 0))
@@ -370,11 +388,13 @@ def initial_state(psi0, grid, p, coulomb, rho0=None, tau0=None):
     return State(psi, U, B, W)
 
 
-def iterate(st, grid, p, coulomb, x0, E0, frozen=False, damping=None):
+def iterate(st, grid, p, coulomb, x0, E0, frozen=False, damping=None, variant="exact"):
     """One damped-gradient iteration.  Mutates ``st`` and returns a record
     with the Ritz values, convergence measure and energy.  ``damping``, if
     given, is a callable (q, U_q, B_q, W_q) -> w [nz,ny,nx] that scales the
     update of the damped step voxel by voxel (phi = psi - w (psi - phi)).
+    ``variant`` "exact" (Rayleigh-Ritz in the Loewdin basis) or
+    "paper_literal" (the combined form of Sec. 3.3.3, ``combined_literal``).
 
     Step 2: h psi with h^(n); eps = <psi|h|psi>; phi = psi - x0/(T+E0)(h-eps)psi;
             h phi with the same h^(n).
@@ -395,7 +415,7 @@ def iterate(st, grid, p, coulomb, x0, E0, frozen=False, damping=None):
         hphi = apply_h(phi, st.U[q], st.B[q], st.W[q], grid)
         S = overlap(phi, phi, grid)
         H = overlap(phi, hphi, grid)
-        M, lam = rayleigh_ritz(S, H)
+        M, lam = rayleigh_ritz(S, H) if variant == "exact" else combined_literal(S, H)
         st.psi[q] = rotate(phi, M)
         lam_l.append(lam)
     d = [densities(st.psi[q], grid) for q in range(2)]
@@ -410,14 +430,15 @@ def iterate(st, grid, p, coulomb, x0, E0, frozen=False, damping=None):
 
 
 def solve(psi0, grid, p, coulomb, x0, E0, maxit, tol, rho0=None, tau0=None,
-          frozen=False, callback=None, damping=None):
+          frozen=False, callback=None, damping=None, variant="exact"):
     """Iterate until |E_n/A - E_{n-1}/A| < tol (MeV) or maxit iterations."""
     st = initial_state(psi0, grid, p, coulomb, rho0, tau0)
     A = st.psi[0].shape[0] + st.psi[1].shape[0]
     hist = []
     E_prev = None
     for it in range(maxit):
-        rec = iterate(st, grid, p, coulomb, x0, E0, frozen=frozen, damping=damping)
+        rec = iterate(st, grid, p, coulomb, x0, E0, frozen=frozen, damping=damping,
+                      variant=variant)
         rec["it"] = it
         hist.append({k: rec[k] for k in ("it", "E", "delta_eps")})
         if callback is not None:

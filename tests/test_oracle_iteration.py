@@ -186,3 +186,68 @@ def test_random_superpositions_are_plane_wave_sums():
     c = rng.standard_normal((I, 2 * I)) + 1j * rng.standard_normal((I, 2 * I))
     want = np.tensordot(c, basis, axes=(1, 0))
     assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want))
+
+
+def _herm(rng, n, scale=1.0):
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    return scale * (A + A.conj().T) / 2
+
+
+def test_combined_literal_equals_exact_ritz_for_orthonormal_states():
+    import numpy as np
+    from oracle import sky_oracle as O
+    rng = np.random.default_rng(31)
+    n = 9
+    H = _herm(rng, n, 10.0)
+    M1, l1 = O.combined_literal(np.eye(n), H)
+    M2, l2 = O.rayleigh_ritz(np.eye(n), H)
+    assert np.max(np.abs(l1 - l2)) < 1e-12
+    # same vectors up to a phase per column (distinct eigenvalues)
+    ov = np.abs(np.sum(np.conj(M1) * M2, axis=0))
+    assert np.max(np.abs(ov - 1.0)) < 1e-12
+
+
+def test_combined_literal_differs_at_first_order_in_the_overlap():
+    """With S = I + eps E the literal form is neither orthonormal nor exact:
+    both defects are first order in eps (and vanish with it)."""
+    import numpy as np
+    from oracle import sky_oracle as O
+    rng = np.random.default_rng(32)
+    n = 8
+    H = np.diag(np.arange(n) * 3.0) + _herm(rng, n, 0.5)
+    E = _herm(rng, n, 1.0)
+    defects = []
+    for eps in (1e-2, 1e-3):
+        S = np.eye(n) + eps * E
+        M, lam = O.combined_literal(S, H)
+        Mx, lx = O.rayleigh_ritz(S, H)
+        ortho = np.max(np.abs(M.conj().T @ S @ M - np.eye(n)))
+        assert np.max(np.abs(Mx.conj().T @ S @ Mx - np.eye(n))) < 1e-12
+        defects.append((ortho, np.max(np.abs(lam - lx))))
+    for k in range(2):
+        assert defects[0][k] > 1e-6
+        ratio = defects[0][k] / defects[1][k]
+        assert 5.0 < ratio < 20.0          # linear in eps
+
+
+def test_literal_iteration_keeps_the_fixed_point():
+    """Exact eigenstates of a frozen h are a fixed point of the literal variant."""
+    import numpy as np
+    from oracle import sky_oracle as O
+    from paper_1610_07522_gb300 import inputs as IN
+    rng = np.random.default_rng(33)
+    g = O.Grid((4, 4, 4), (1.0, 1.0, 1.0))
+    p = dict(IN.SLY4)
+    U = np.stack([rng.uniform(-40, 0, g.shape) for _ in range(2)])
+    Bf = np.stack([20.7 + rng.uniform(0, 3, g.shape) for _ in range(2)])
+    Wf = np.stack([rng.uniform(-1, 1, (3,) + g.shape) for _ in range(2)])
+    psi, lams = [], []
+    for q in range(2):
+        Hd = O.dense_h(U[q], Bf[q], Wf[q], g)
+        lam, vec = np.linalg.eigh(0.5 * (Hd + Hd.conj().T))
+        psi.append((vec[:, :4].T / np.sqrt(g.dV)).reshape((4, 2) + g.shape))
+        lams.append(lam[:4])
+    st = O.State(psi, U, Bf, Wf)
+    rec = O.iterate(st, g, p, False, 0.45, 100.0, frozen=True, variant="paper_literal")
+    for q in range(2):
+        assert np.max(np.abs(rec["lam"][q] - lams[q])) < 1e-9
