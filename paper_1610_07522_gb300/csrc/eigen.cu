@@ -618,15 +618,18 @@ __global__ void k_hermitize(HermJobs h) {
 // eigenvalue it is z <- z (3 - l z^2)/2 from z = 1, which converges to
 // l^{-1/2} for 0 < l < 3 (quadratically once l z^2 is near 1).  It is used when
 // the Gershgorin bound max_i sum_j |S_ij| is below kNsSwitch (|S_ij| bounded
-// by |Re| + |Im|), which holds for the overlaps of damped orthonormal states.
+// by |Re| + |Im|) or when ||S - I||_F < kNsFrob (then every eigenvalue lies
+// within kNsFrob of 1); one of them holds for the overlaps of damped
+// orthonormal states, the Frobenius test being the sharper one at large I.
 // Otherwise, or if it has not converged after kNsMaxIter steps, C is
 // X Lambda^{-1/2} X^H from the Jacobi eigendecomposition of S, as the paper
 // describes.  Device gates per problem b at gate[8 b + k]: [0] Newton-Schulz
 // running, [1] eigendecomposition needed, [2] Newton-Schulz converged (one
 // final update pending or done), [3] Newton-Schulz chosen; [4..5] the row-sum
-// bound as integer bits.
+// bound as integer bits; [6..7] ||S - I||_F^2 as a double.
 constexpr int kNsMaxIter = 14;
 constexpr double kNsSwitch = 2.5;      // spectral bound for the Newton-Schulz route
+constexpr double kNsFrob = 0.9;        // ||S - I||_F bound for the same route
 constexpr double kNsConv = 1e-10;      // ||I - Z Y||_F after which one more update suffices
 
 struct NsJobs {
@@ -644,38 +647,50 @@ __global__ void k_ns_reset(int* gate) {
   int* g = gate + 8 * threadIdx.x;
   g[0] = g[1] = g[2] = g[3] = 0;
   *reinterpret_cast<unsigned long long*>(g + 4) = 0ull;
+  *reinterpret_cast<double*>(g + 6) = 0.0;
 }
 
-// Row sums of |S| (bounded by |Re| + |Im|) -> max into gate[4..5]; Y = S, Z = I.
+// Row sums of |S| (bounded by |Re| + |Im|) -> max into gate[4..5];
+// sum of |S - I|^2 -> gate[6..7]; Y = S, Z = I.
 __global__ void __launch_bounds__(256) k_ns_rows(NsJobs j, int* gate) {
-  __shared__ double red[8];
+  __shared__ double red[8], red2[8];
   const int b = blockIdx.y, n = j.n[b], i = blockIdx.x;
   if (i >= n) return;
-  double acc = 0.0;
+  double acc = 0.0, fro = 0.0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const long long e = (long long)i * n + k;
     const double2 v = j.S[b][e];
     acc += fabs(v.x) + fabs(v.y);
+    const double dr = v.x - (i == k ? 1.0 : 0.0);
+    fro += dr * dr + v.y * v.y;
     j.Y[b][e] = v;
     j.Z[b][e] = make_double2(i == k ? 1.0 : 0.0, 0.0);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  for (int o = 16; o > 0; o >>= 1) {
+    acc += __shfl_down_sync(0xffffffffu, acc, o);
+    fro += __shfl_down_sync(0xffffffffu, fro, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = acc;
+    red2[threadIdx.x >> 5] = fro;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    double t = 0.0, f = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t += red[w]; f += red2[w]; }
     // non-negative doubles order like their bit patterns
     atomicMax(reinterpret_cast<unsigned long long*>(gate + 8 * b + 4),
               (unsigned long long)__double_as_longlong(t));
+    atomicAdd(reinterpret_cast<double*>(gate + 8 * b + 6), f);
   }
 }
 
 __global__ void k_ns_choose(int* gate) {
   int* g = gate + 8 * threadIdx.x;
   const double R = __longlong_as_double(*reinterpret_cast<long long*>(g + 4));
-  const int ns = R < kNsSwitch;
+  const double F = *reinterpret_cast<const double*>(g + 6);
+  const int ns = R < kNsSwitch || F < kNsFrob * kNsFrob;
   g[3] = ns;
   g[0] = ns;
   g[1] = !ns;
@@ -837,6 +852,21 @@ sky_status subspace_batch(Ctx* c, int np, const double2* const* H, const double2
   st = eigh_batch(c, np, (const double2* const*)Hp, I, eps, Z, nullptr, 0);
   if (st != SKY_OK) return st;
   return zgemm_batch(c, zjobs(np, false, false, C, (const double2* const*)Z, M, I, none, none));   // M = C Z
+}
+
+// The paper's combined form (Sec. 3.3.3): Z from H itself (the non-orthonormal
+// basis), M = Z C, eps = the eigenvalues of H.
+sky_status subspace_literal_batch(Ctx* c, int np, const double2* const* H,
+                                  const double2* const* C, const int* I, double2* const* M,
+                                  double* const* eps) {
+  if (np < 1) return SKY_OK;
+  if (np > c->eig_batch) return set_err(c, SKY_EINVAL, "subspace batch %d > %d", np, c->eig_batch);
+  double2* Z[kMaxBatch];
+  for (int b = 0; b < np; ++b) Z[b] = c->d_small[2] + (size_t)b * c->small_slot;
+  const int* none[kMaxBatch] = {nullptr};
+  sky_status st = eigh_batch(c, np, H, I, eps, Z, nullptr, 0);
+  if (st != SKY_OK) return st;
+  return zgemm_batch(c, zjobs(np, false, false, (const double2* const*)Z, C, M, I, none, none));
 }
 
 sky_status subspace_impl(Ctx* c, const double2* H, const double2* C, int I, double2* M,
