@@ -344,9 +344,17 @@ def combined_literal(S, H):
     columns, and C is applied as in Eq. orthmatvec.)  Equal to the exact
     Rayleigh-Ritz step when S = I; otherwise the new states are neither exactly
     orthonormal nor exact Ritz vectors, and the difference vanishes at
-    convergence.  Returns (M, Lambda)."""
+    convergence.  The result depends on the phases of Z's columns (fixed as
+    below) and, for degenerate eigenvalues of H, on the basis chosen in each
+    degenerate space.  Returns (M, Lambda)."""
     Hh = 0.5 * (H + np.conj(H).T)
     lam, Z = np.linalg.eigh(Hh)
+    # M = Z C mixes the columns of Z, so the result depends on their phases,
+    # which the paper leaves open.  Reading: each eigenvector's largest
+    # component (the first one of largest modulus) is made real and positive.
+    for k in range(Z.shape[1]):
+        i = int(np.argmax(np.abs(Z[:, k])))
+        Z[:, k] *= np.conj(Z[i, k]) / abs(Z[i, k])
     return Z @ loewdin(S), lam
 
 

@@ -205,6 +205,10 @@ def test_combined_literal_equals_exact_ritz_for_orthonormal_states():
     # same vectors up to a phase per column (distinct eigenvalues)
     ov = np.abs(np.sum(np.conj(M1) * M2, axis=0))
     assert np.max(np.abs(ov - 1.0)) < 1e-12
+    # the phase convention: largest component of each column real and positive
+    for k in range(n):
+        i = int(np.argmax(np.abs(M1[:, k])))
+        assert abs(M1[i, k].imag) < 1e-14 and M1[i, k].real > 0
 
 
 def test_combined_literal_differs_at_first_order_in_the_overlap():
