@@ -164,6 +164,21 @@ sky_status sky_subspace_diag(sky_ctx* ctx, const double* H, const double* C, int
 sky_status sky_orthonormalize_batched(sky_ctx* ctx, int nb, const double* const* S, const int* I,
                                       double* const* C);
 
+/* The paper's combined form of steps 3b-3e (Sec. 3.3.3, Fig. step67), a
+ * selectable variant: Z diagonalises H itself (the matrix of the
+ * non-orthonormal states, H = Z Lambda Z^H, Lambda ascending into eps), and
+ * the Loewdin factor C of the same states (from sky_orthonormalize*) is
+ * applied after it, M = Z C, so that psi_a = sum_b M[b*I + a] phi_b
+ * (sky_rotate).  M depends on the phases of Z's columns, which the paper
+ * leaves open: each column's first component of largest modulus is made real
+ * and positive (and for degenerate eigenvalues on the eigensolver's basis).  Equal to sky_subspace_diag when the states are orthonormal;
+ * otherwise the new states are neither exactly orthonormal nor exact Ritz
+ * vectors, a difference the paper notes vanishes at convergence.  Arguments
+ * as sky_subspace_diag_batched. */
+sky_status sky_subspace_diag_literal_batched(sky_ctx* ctx, int nb, const double* const* H,
+                                             const double* const* C, const int* I,
+                                             double* const* M, double* const* eps);
+
 /* Raise the batch capacity of the batched calls to nb problems of up to
  * max_states each (1 <= nb <= 128).  Allocates device memory (about
  * 13 max_states^2 complex doubles per problem) and synchronises the context

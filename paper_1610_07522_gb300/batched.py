@@ -164,10 +164,12 @@ class BatchSolver:
         """Iterate every box until each has held |E_n/A - E_{n-1}/A| < tol for
         ``window`` consecutive iterations (boxes that are done keep iterating
         inside the batch) or maxit.  Returns per-box iterations to convergence
-        (None if not reached) and the last energies per nucleon."""
+        (None if not reached) and the energy per nucleon of each box at the
+        iteration it converged (its last one otherwise)."""
         prev = [None] * len(self.boxes)
         below = [0] * len(self.boxes)
         done = [None] * len(self.boxes)
+        E_done = [None] * len(self.boxes)
         for it in range(maxit):
             self.step()
             en = self.energies(check_status=(it % 64 == 63))
@@ -178,6 +180,7 @@ class BatchSolver:
                     below[b] += 1
                     if below[b] >= window and done[b] is None:
                         done[b] = it + 1
+                        E_done[b] = E / A
                 else:
                     below[b] = 0
                 if s.damping_on and prev[b] is not None and (E - prev[b]) / A > s.rise_tol:
@@ -189,7 +192,8 @@ class BatchSolver:
                 prev[b] = E
             if all(d is not None for d in done):
                 break
-        return done, [E / s.A for (E, _), s in zip(self.energies(check_status=True), self.boxes)]
+        last = [E / s.A for (E, _), s in zip(self.energies(check_status=True), self.boxes)]
+        return done, [e if e is not None else l for e, l in zip(E_done, last)]
 
     def close(self):
         self.graph = None

@@ -63,6 +63,8 @@ _SIGNATURES = {
     "sky_subspace_diag_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_I),
                                        ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "sky_reserve_batch": (_I, [_P, _I]),
+    "sky_subspace_diag_literal_batched": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                               ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "sky_set_prec": (_I, [_P, _I]),
     "sky_tune_set": (_I, [_P, _I, _I]),
     "sky_tune_get": (_I, [_P, _I]),
@@ -219,6 +221,12 @@ def sky_tune_get(ctx, knob):
 
 def sky_reserve_batch(ctx, nb):
     _check(ctx, lib().sky_reserve_batch(ctx, int(nb)))
+
+
+def sky_subspace_diag_literal_batched(ctx, H, C, I, M, eps):
+    n = len(I)
+    _check(ctx, lib().sky_subspace_diag_literal_batched(ctx, n, _ptrs(H), _ptrs(C), (_I * n)(*I),
+                                                        _ptrs(M), _ptrs(eps)))
 
 
 def sky_rotate(ctx, phi, M, I, psi_out):

@@ -854,8 +854,35 @@ sky_status subspace_batch(Ctx* c, int np, const double2* const* H, const double2
   return zgemm_batch(c, zjobs(np, false, false, C, (const double2* const*)Z, M, I, none, none));   // M = C Z
 }
 
+// Phase convention of the combined form: column k of Z is multiplied by the
+// phase that makes its first component of largest modulus real and positive.
+struct PhaseJobs {
+  double2* Z[kMaxBatch];
+  int n[kMaxBatch];
+};
+__global__ void k_fix_phase(PhaseJobs j) {
+  const int b = blockIdx.y, n = j.n[b];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double2* Z = j.Z[b];
+  int imax = 0;
+  double amax = -1.0;
+  for (int i = 0; i < n; ++i) {
+    const double2 v = Z[(long long)i * n + k];
+    const double a = v.x * v.x + v.y * v.y;
+    if (a > amax) { amax = a; imax = i; }
+  }
+  const double2 z = Z[(long long)imax * n + k];
+  const double r = sqrt(z.x * z.x + z.y * z.y);
+  const double2 ph = make_double2(z.x / r, -z.y / r);   // conj(z) / |z|
+  for (int i = 0; i < n; ++i) {
+    const long long e = (long long)i * n + k;
+    Z[e] = cmul(Z[e], ph);
+  }
+}
+
 // The paper's combined form (Sec. 3.3.3): Z from H itself (the non-orthonormal
-// basis), M = Z C, eps = the eigenvalues of H.
+// basis, phases as above), M = Z C, eps = the eigenvalues of H.
 sky_status subspace_literal_batch(Ctx* c, int np, const double2* const* H,
                                   const double2* const* C, const int* I, double2* const* M,
                                   double* const* eps) {
@@ -866,6 +893,17 @@ sky_status subspace_literal_batch(Ctx* c, int np, const double2* const* H,
   const int* none[kMaxBatch] = {nullptr};
   sky_status st = eigh_batch(c, np, H, I, eps, Z, nullptr, 0);
   if (st != SKY_OK) return st;
+  PhaseJobs pj;
+  int nmax = 1;
+  for (int b = 0; b < np; ++b) {
+    pj.Z[b] = Z[b];
+    pj.n[b] = I[b];
+    if (I[b] > nmax) nmax = I[b];
+  }
+  k_fix_phase<<<dim3(div_up(nmax, 128), np), 128, 0, c->stream>>>(pj);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(c, e, "fix phase");
   return zgemm_batch(c, zjobs(np, false, false, (const double2* const*)Z, C, M, I, none, none));
 }
 

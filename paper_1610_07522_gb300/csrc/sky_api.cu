@@ -399,6 +399,20 @@ sky_status sky_subspace_diag_batched(sky_ctx* c, int nb, const double* const* H,
                         reinterpret_cast<double2* const*>(M), eps);
 }
 
+sky_status sky_subspace_diag_literal_batched(sky_ctx* c, int nb, const double* const* H,
+                                             const double* const* C, const int* I,
+                                             double* const* M, double* const* eps) {
+  if (!c) return SKY_EINVAL;
+  sky_status st = check_batch(c, nb, I);
+  if (st != SKY_OK) return st;
+  if (!H || !C || !M || !eps) return set_err(c, SKY_EINVAL, "subspace_diag_literal: null pointer");
+  for (int b = 0; b < nb; ++b)
+    if (!H[b] || !C[b] || !M[b] || !eps[b]) return set_err(c, SKY_EINVAL, "subspace_diag_literal: null pointer");
+  return subspace_literal_batch(c, nb, reinterpret_cast<const double2* const*>(H),
+                                reinterpret_cast<const double2* const*>(C), I,
+                                reinterpret_cast<double2* const*>(M), eps);
+}
+
 sky_status sky_rotate(sky_ctx* c, const void* phi, const double* M, int I, void* psi_out) {
   CHECK_CTX();
   if (I == 0) return SKY_OK;

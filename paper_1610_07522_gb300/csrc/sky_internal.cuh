@@ -180,6 +180,9 @@ sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, dou
 sky_status lowdin_batch(Ctx* c, int np, const double2* const* S, const int* I, double2* const* C);
 sky_status subspace_batch(Ctx* c, int np, const double2* const* H, const double2* const* C,
                           const int* I, double2* const* M, double* const* eps);
+sky_status subspace_literal_batch(Ctx* c, int np, const double2* const* H,
+                                  const double2* const* C, const int* I, double2* const* M,
+                                  double* const* eps);
 sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z,
                      const int* run = nullptr);
 sky_status lowdin_impl(Ctx* c, const double2* S, int I, double2* C);

@@ -19,9 +19,13 @@ from . import binding as B
 
 
 class Solver:
-    def __init__(self, workload, prec=B.SKY_F64, device="cuda:0", max_states=None, stream=None):
+    def __init__(self, workload, prec=B.SKY_F64, device="cuda:0", max_states=None, stream=None,
+                 variant="exact"):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (there is no CPU path)")
+        if variant not in ("exact", "paper_literal"):
+            raise ValueError(variant)
+        self.variant = variant      # steps 3b-3e: exact Rayleigh-Ritz or the paper's combined form
         self.w = workload
         self.device = torch.device(device)
         self.prec = prec
@@ -143,9 +147,10 @@ class Solver:
         qs = self._species()
         I = [self.I[q] for q in qs]
         B.sky_orthonormalize_batched(self.ctx, [self.S[q] for q in qs], I, [self.C[q] for q in qs])
-        B.sky_subspace_diag_batched(self.ctx, [self.H[q] for q in qs], [self.C[q] for q in qs], I,
-                                    [self.M[q] for q in qs],
-                                    [self.lam[self.off[q]:self.off[q] + self.I[q]] for q in qs])
+        diag = (B.sky_subspace_diag_batched if self.variant == "exact"
+                else B.sky_subspace_diag_literal_batched)
+        diag(self.ctx, [self.H[q] for q in qs], [self.C[q] for q in qs], I, [self.M[q] for q in qs],
+             [self.lam[self.off[q]:self.off[q] + self.I[q]] for q in qs])
         for q in qs:
             B.sky_rotate(self.ctx, self.phi[q], self.M[q], self.I[q], self.psi[q])
 
