@@ -4,7 +4,7 @@
 // split-BF16 products (hi*hi + hi*lo + lo*hi for a 2-way split, six products
 // for a 3-way split) accumulate in one tile.
 //
-// Persistent kernel, one CTA per SM: CTA b computes the 128 x 128 output tiles
+// Persistent kernel, one CTA per SM: CTA b computes the 128 x BNT output tiles
 // b, b + gridDim.x, ... (m fastest, then n, then the K split; split z writes
 // partial tile z).  Each ring stage holds one 64-wide K block of every operand
 // piece in use (A_0..A_{n-1}, B_0..B_{n-1}), so a piece is loaded once per K
@@ -14,8 +14,8 @@
 //   warp 0     TMA producer: cp.async.bulk.tensor loads of 128 x 64 bf16
 //              A and B boxes (128-byte swizzle) into a ring of a.stages stages,
 //              running ahead across tile boundaries;
-//   warp 1     owns TMEM (2 x 128 fp32 columns) and one elected lane issues
-//              tcgen05.mma (M = 128, N = 128, K = 16 each); tcgen05.commit frees
+//   warp 1     owns TMEM (2 x BNT fp32 columns) and one elected lane issues
+//              tcgen05.mma (M = 128, N = BNT, K = 16 each); tcgen05.commit frees
 //              ring stages and signals the epilogue when a tile is complete;
 //   warps 2-5  epilogue: tcgen05.ld of their TMEM lane quadrant -> global fp32,
 //              then hand the accumulator back (one mbarrier arrival per warp).
@@ -33,12 +33,14 @@ namespace sky {
 namespace tc {
 
 constexpr int BM = 128, BN = 128, BK = 64;         // BK bf16 = one 128-byte swizzle row
-constexpr int TILE_BYTES = BM * BK * 2;            // 16 KiB per operand tile
+constexpr int TILE_BYTES = BM * BK * 2;            // 16 KiB per 128-row operand tile
+// BN: the 128-column tile used for sizing (partial tiles, tile counts of callers);
+// the kernel also runs with 256-column tiles (template BNT), see gemm_bf16.
 constexpr int kMaxStages = 8;
 constexpr int kRingBytes = 200 * 1024;             // ring budget (of 227 KB)
 constexpr int SMEM_BYTES = kRingBytes + 1024 + 256;
 constexpr int THREADS = 192;
-constexpr uint32_t TMEM_COLS = 2 * BN;              // two accumulators (double buffer)
+// TMEM: two accumulators (double buffer) of BNT fp32 columns each
 constexpr long long kSpin = 1LL << 24;             // x >= 64 ns per try: bounded waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -142,6 +144,7 @@ struct GemmArgs {
   int* status;
 };
 
+template <int BNT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                 const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
@@ -150,18 +153,20 @@ __global__ void __launch_bounds__(THREADS, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       (unsigned char*)(((unsigned long long)smem_raw + 1023ull) & ~1023ull);
+  constexpr int TILE_B = BNT * BK * 2;              // bytes of one B piece tile
+  constexpr uint32_t TMEM_COLS = 2 * BNT;
   const int np = a.npiece, stages = a.stages;
-  const int stage_bytes = 2 * np * TILE_BYTES;
+  const int stage_bytes = np * (TILE_BYTES + TILE_B);
   unsigned long long* bars = (unsigned long long*)(base + kRingBytes);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kMaxStages + 5);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // persistent: CTA b takes tiles b, b + gridDim.x, ...; tile t -> (m fastest, n, split)
-  const int mt = (a.M + BM - 1) / BM, nt = (a.N + BN - 1) / BN;
+  const int mt = (a.M + BM - 1) / BM, nt = (a.N + BNT - 1) / BNT;
   const int ntiles = mt * nt * a.nsplit;
   const int nkb_total = (a.K + BK - 1) / BK;
   auto tile_kb = [&](int t, int& m0, int& n0, int& kb0, int& nkb, int& z) {
     m0 = (t % mt) * BM;
-    n0 = ((t / mt) % nt) * BN;
+    n0 = ((t / mt) % nt) * BNT;
     z = t / (mt * nt);
     kb0 = z * a.kb_per_split;
     nkb = nkb_total - kb0;
@@ -223,14 +228,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             const CUtensorMap* mapA = i == 0 ? &mA0 : (i == 1 ? &mA1 : &mA2);
             const CUtensorMap* mapB = i == 0 ? &mB0 : (i == 1 ? &mB1 : &mB2);
             tma_load_2d(sa + i * TILE_BYTES, mapA, kb * BK, m0, full(s));
-            tma_load_2d(sa + (np + i) * TILE_BYTES, mapB, kb * BK, n0, full(s));
+            tma_load_2d(sa + np * TILE_BYTES + i * TILE_B, mapB, kb * BK, n0, full(s));
           }
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(BM, BN);
+      const uint32_t idesc = idesc_bf16(BM, BNT);
       long long g = 0;
       int j = 0;   // tiles done by this CTA
       bool ok = true;
@@ -244,7 +249,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         fence_after();
-        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        const uint32_t acc = tmem + (uint32_t)(b * BNT);
         for (int it = 0; it < nkb; ++it, ++g) {
           const int s = (int)(g % stages);
           const long long u = g / stages;
@@ -257,7 +262,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t sa = smem_u32(base + s * stage_bytes);
           for (int p = 0; p < a.nphase; ++p) {
             const uint64_t da = sw128_desc(sa + a.pa[p] * TILE_BYTES);
-            const uint64_t db = sw128_desc(sa + (np + a.pb[p]) * TILE_BYTES);
+            const uint64_t db = sw128_desc(sa + np * TILE_BYTES + a.pb[p] * TILE_B);
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k)   // +32 bytes along K = +2 in the encoded address
               mma_bf16(acc, da + 2ull * k, db + 2ull * k, idesc,
@@ -288,9 +293,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int row = m0 + q * 32 + lane;
       float* drow = a.D + (long long)z * a.sstride + (long long)row * a.ldd;
 #pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
+      for (int c = 0; c < BNT; c += 32) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c), v);
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BNT + c), v);
         if (nkb == 0) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = 0.0f;
@@ -325,7 +330,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 // ---------------------------------------------------------------- host side
 // bf16 matrix [rows][K] with row stride ld (elements, multiple of 8), K-major.
-inline cudaError_t make_map(CUtensorMap* map, const void* ptr, int rows, int K, long long ld) {
+inline cudaError_t make_map(CUtensorMap* map, const void* ptr, int rows, int K, long long ld,
+                            int box_rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -337,7 +343,7 @@ inline cudaError_t make_map(CUtensorMap* map, const void* ptr, int rows, int K, 
   }
   const cuuint64_t gdim[2] = {(cuuint64_t)K, (cuuint64_t)rows};
   const cuuint64_t gstride[1] = {(cuuint64_t)ld * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   const cuuint32_t estride[2] = {1, 1};
   CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), gdim,
                       gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -381,16 +387,19 @@ inline cudaError_t gemm_bf16(const void* const* A, long long lda, const void* co
   // TMA needs 16-byte row strides; columns past K read as zeros
   if ((lda & 7) || (ldb & 7) || (ldd & 3) || lda < K || ldb < K || nsplit < 1 || nsplit > 3)
     return cudaErrorInvalidValue;
+  // 128 x 256 tiles when the pieces of one K block still fit twice in the ring
+  // (x3: 96 KiB per stage), else 128 x 128 (x6: 96 KiB per stage)
+  const int bnt = (nsplit <= 2 && (long long)N >= 256) ? 256 : 128;
   CUtensorMap ma[3], mb[3];
   cudaError_t e;
   for (int i = 0; i < 3; ++i) {
     const int j = i < nsplit ? i : 0;
-    if ((e = make_map(&ma[i], A[j], M, K, lda)) != cudaSuccess) return e;
-    if ((e = make_map(&mb[i], B[j], N, K, ldb)) != cudaSuccess) return e;
+    if ((e = make_map(&ma[i], A[j], M, K, lda, BM)) != cudaSuccess) return e;
+    if ((e = make_map(&mb[i], B[j], N, K, ldb, bnt)) != cudaSuccess) return e;
   }
   const Phases ph = phases_for_split(nsplit);
   const int nkb = (K + BK - 1) / BK;
-  int stages = kRingBytes / (2 * nsplit * TILE_BYTES);
+  int stages = kRingBytes / (nsplit * (TILE_BYTES + bnt * BK * 2));
   if (stages > kMaxStages) stages = kMaxStages;
   int z = *splits < 1 ? 1 : *splits;
   if (z > nkb) z = nkb;
@@ -406,22 +415,27 @@ inline cudaError_t gemm_bf16(const void* const* A, long long lda, const void* co
     g.pb[i] = i < ph.n ? ph.pb[i] : 0;
   }
   g.D = D; g.ldd = ldd; g.sstride = sstride; g.status = status;
-  // the shared-memory opt-in is set once per device (before any stream capture)
+  // the shared-memory opt-ins are set once per device (before any stream capture)
   static bool smem_set[64] = {false};
   int dev = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!smem_set[dev]) {
-    e = cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    e = cudaFuncSetAttribute(k_gemm_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_gemm_bf16<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     smem_set[dev] = true;
   }
   g.nsplit = z;
-  const long long ntiles = (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN) * z;
+  const long long ntiles = (long long)((M + BM - 1) / BM) * ((N + bnt - 1) / bnt) * z;
   int nsm = 0;
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   const int grid = (int)(ntiles < nsm ? ntiles : nsm);   // persistent: one CTA per SM
-  k_gemm_bf16<<<grid, THREADS, SMEM_BYTES, s>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], g);
+  if (bnt == 256)
+    k_gemm_bf16<256><<<grid, THREADS, SMEM_BYTES, s>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], g);
+  else
+    k_gemm_bf16<128><<<grid, THREADS, SMEM_BYTES, s>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], g);
   note_launch();
   *splits = z;
   return cudaGetLastError();
