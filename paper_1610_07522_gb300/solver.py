@@ -20,7 +20,7 @@ from . import binding as B
 
 class Solver:
     def __init__(self, workload, prec=B.SKY_F64, device="cuda:0", max_states=None, stream=None,
-                 variant="exact"):
+                 variant="exact", concurrent_species=False):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (there is no CPU path)")
         if variant not in ("exact", "paper_literal"):
@@ -40,6 +40,17 @@ class Solver:
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             self.ctx = B.sky_init(workload.grid, workload.dx, workload.params, workload.coulomb,
                                   workload.twist, prec, Imax, self.stream.cuda_stream)
+            # species contexts: the same one, or (concurrent_species) the protons
+            # on a second context and stream, so that the work of the two species
+            # overlaps; both join for the batched eigensolve and the mean field
+            self.ctxq = [self.ctx, self.ctx]
+            self.streamq = [self.stream, self.stream]
+            if concurrent_species and workload.Z > 0:
+                self.streamq[1] = torch.cuda.Stream(device=self.device)
+                self.ctxq[1] = B.sky_init(workload.grid, workload.dx, workload.params,
+                                          workload.coulomb, workload.twist, prec, workload.Z,
+                                          self.streamq[1].cuda_stream)
+        self.concurrent = self.ctxq[1] is not self.ctx
         dev, G = self.device, self.G
         f64 = dict(dtype=torch.float64, device=dev)
         self.psi = [torch.zeros((I, 2) + self.shape, dtype=self.cdtype, device=dev) for I in self.I]
@@ -83,6 +94,13 @@ class Solver:
         self.min_scale = min_scale
         if net is not None and self.wq is None:
             self.wq = torch.zeros((2, self.G), dtype=torch.float32, device=self.device)
+        # with concurrent species the proton stream runs the network on its own workspace
+        self.dampq = [net, net]
+        if net is not None and self.concurrent:
+            self.dampq[1] = net.view()
+            self.dampq[1].workspace(self.G)
+        if net is not None:
+            net.workspace(self.G)
 
     # ------------------------------------------------------------ set-up
     def _species(self):
@@ -101,7 +119,9 @@ class Solver:
         for q in qs:
             B.sky_rotate(self.ctx, self.phi[q], self.C[q], self.I[q], self.psi[q])
         if rho0 is None:
+            self._fork()
             self.densities()
+            self._join()
         else:
             self.rho.copy_(torch.from_numpy(np.asarray(rho0).reshape(2, -1)))
             self.tau.copy_(torch.from_numpy(np.asarray(tau0).reshape(2, -1)))
@@ -112,18 +132,18 @@ class Solver:
     # ------------------------------------------------------------ iteration
     def densities(self):
         for q in range(2):   # I = 0 gives zero densities
-            B.sky_densities(self.ctx, self.psi[q], self.I[q], self.rho[q], self.tau[q], self.J[q],
+            B.sky_densities(self.ctxq[q], self.psi[q], self.I[q], self.rho[q], self.tau[q], self.J[q],
                             self.divJ[q])
 
     def species_step(self, q):
         """Step 2 and 3a for species q: h psi, damped step, h phi, S and H."""
         I, o = self.I[q], self.off[q]
-        ctx = self.ctx
+        ctx = self.ctxq[q]
         B.sky_apply_h(ctx, self.U[q], self.Bf[q], self.W[q], self.psi[q], self.h[q], I,
                       self.eps[o:o + I], self.hn2[o:o + I])
         w = None
         if self.damping_on:
-            self.damping.weights(ctx, self.G, q, self.U[q], self.Bf[q], self.W[q], self.wq[q],
+            self.dampq[q].weights(ctx, self.G, q, self.U[q], self.Bf[q], self.W[q], self.wq[q],
                                  self.damping_scale)
             w = self.wq[q]
         B.sky_damped_step(ctx, q, self.psi[q], self.h[q], self.eps[o:o + I], self.phi[q], I,
@@ -151,16 +171,34 @@ class Solver:
                 else B.sky_subspace_diag_literal_batched)
         diag(self.ctx, [self.H[q] for q in qs], [self.C[q] for q in qs], I, [self.M[q] for q in qs],
              [self.lam[self.off[q]:self.off[q] + self.I[q]] for q in qs])
+        self._fork()
         for q in qs:
-            B.sky_rotate(self.ctx, self.phi[q], self.M[q], self.I[q], self.psi[q])
+            B.sky_rotate(self.ctxq[q], self.phi[q], self.M[q], self.I[q], self.psi[q])
+
+    def _fork(self):
+        """Let the proton stream start after the work enqueued so far."""
+        if self.concurrent:
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+            self.streamq[1].wait_event(ev)
+
+    def _join(self):
+        """Let the main stream continue after the proton stream's work."""
+        if self.concurrent:
+            ev = torch.cuda.Event()
+            ev.record(self.streamq[1])
+            self.stream.wait_event(ev)
 
     def step(self, frozen=False):
         """One full iteration (Fig. 1 steps 2-5); enqueued, not synchronised."""
+        self._fork()
         for q in self._species():
             self.species_step(q)
-        self.ritz_step()
+        self._join()
+        self.ritz_step()          # batched eigensolve on the main stream; rotations forked
         B.sky_sp_spread(self.ctx, self.eps, self.hn2, self.A, self.spread)
         self.densities()
+        self._join()
         if not frozen:
             B.sky_mean_fields(self.ctx, self.rho, self.tau, self.divJ, self.U, self.Bf, self.W)
         B.sky_energy(self.ctx, self.rho, self.tau, self.divJ, self.eout)
@@ -180,6 +218,8 @@ class Solver:
 
     def sync(self):
         B.sky_sync(self.ctx)
+        if self.concurrent:
+            B.sky_sync(self.ctxq[1])
 
     def energy(self):
         """Host copy of (E, delta_eps) after synchronising."""
@@ -190,6 +230,8 @@ class Solver:
     def set_prec(self, prec):
         """Switch the GEMM form of an FP32-spinor solver (sky_set_prec)."""
         B.sky_set_prec(self.ctx, prec)
+        if self.concurrent:
+            B.sky_set_prec(self.ctxq[1], prec)
         self.prec = prec
 
     def run(self, maxit=None, tol=None, callback=None, window=1, escalate=None):
@@ -233,6 +275,9 @@ class Solver:
 
     def close(self):
         if self.ctx:
+            if getattr(self, "concurrent", False) and self.ctxq[1]:
+                B.sky_destroy(self.ctxq[1])
+                self.ctxq[1] = None
             B.sky_destroy(self.ctx)
             self.ctx = None
 

@@ -69,3 +69,24 @@ def test_escalated_split_bf16_run_reaches_the_fp64_fixed_point():
     assert res["fp64"][0] and res["x3_to_f32"][0]
     assert res["x3_to_f32"][2]
     assert abs(res["x3_to_f32"][1] - res["fp64"][1]) < 1e-4
+
+
+@pytest.mark.parametrize("prec", [B.SKY_F64, B.SKY_F32_BF16X3])
+def test_concurrent_species_streams_give_the_same_iteration(prec):
+    """Neutrons and protons on separate contexts and streams (joined for the
+    batched eigensolve and the mean field): bit-identical to one stream."""
+    w = IN.WORKLOADS["sly4_24cubed_280n120p_coulomb_fp64"]
+    inp = IN.make_inputs(w)
+    a = Solver(w, prec=prec)
+    b = Solver(w, prec=prec, concurrent_species=True)
+    assert b.concurrent and not a.concurrent
+    for s in (a, b):
+        s.load(inp["psi0"], inp["rho0"], inp["tau0"])
+    for _ in range(3):
+        a.step()
+        b.step()
+    Ea, Eb = a.energy(), b.energy()
+    assert Ea[0] == Eb[0] and Ea[1] == Eb[1]
+    assert torch.equal(a.psi[1], b.psi[1]) and torch.equal(a.rho, b.rho)
+    a.close()
+    b.close()
