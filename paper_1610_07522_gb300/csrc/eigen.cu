@@ -630,7 +630,8 @@ __global__ void k_hermitize(HermJobs h) {
 constexpr int kNsMaxIter = 14;
 constexpr double kNsSwitch = 2.5;      // spectral bound for the Newton-Schulz route
 constexpr double kNsFrob = 0.9;        // ||S - I||_F bound for the same route
-constexpr double kNsConv = 1e-10;      // ||I - Z Y||_F after which one more update suffices
+constexpr double kNsConv = 1e-7;       // ||I - Z Y||_F after which one more update suffices
+                                       // (it squares the residual: ~1e-14)
 
 struct NsJobs {
   const double2* S[kMaxBatch];
