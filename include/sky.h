@@ -245,6 +245,7 @@ sky_status sky_set_prec(sky_ctx* ctx, sky_prec prec);
  *   SKY_KNOB_OVERLAP_WAVES  FMA overlap: K splits filling 1 or 2 waves of blocks
  *   SKY_KNOB_TC_WAVES       split-BF16 overlap: K splits filling 1, 2 or 4 waves of SMs
  *   SKY_KNOB_JACOBI_BLOCKS  blocks of the cooperative eigensolver: 1..JACOBI_BLOCKS_MAX
+ *                           (until set: one per SM, two per SM for problems >= 512)
  *   SKY_KNOB_JACOBI_BLOCKS_MAX  (read only) co-resident blocks of that kernel
  * sky_tune_set returns SKY_EINVAL for a value outside these sets; sky_tune_get
  * returns the current value (-1 for an unknown knob or a NULL context). */

@@ -501,11 +501,13 @@ __global__ void k_jacobi_finish(EigJobs j, const int* result) {
   for (int i = 0; i < n; ++i) j.Z[b][(long long)i * n + rank] = j.V[b][(long long)i * m + c];
 }
 
+constexpr int kJacobiLarge = 512;   // problem size from which the untuned Jacobi uses 2 blocks/SM
+
 int jacobi_max_grid(Ctx* c) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, kJacThreads, 0);
   if (per_sm < 1) per_sm = 1;
-  if (per_sm > 1) per_sm = 1;   // one block per SM keeps the barrier short
+  if (per_sm > 2) per_sm = 2;   // the tunable maximum; the default is one block per SM
   return per_sm * c->num_sms;
 }
 
@@ -549,7 +551,11 @@ sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, dou
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "jacobi init");
   (void)items;
-  const int grid = c->eig_grid;   // every SM's FP64 units share each round
+  // every SM's FP64 units share each round; until tuned, two blocks per SM for
+  // large problems (FP64 bound: more warps hide latency) and one for small ones
+  // (barrier bound: fewer blocks make the barrier cheaper), measured on GB300
+  int grid = c->eig_grid;
+  if (c->eig_grid_auto && nmax >= kJacobiLarge) grid = c->eig_grid_max;
   a.tol = 1e-14;
   a.max_sweeps = 60;
   a.part = c->d_eigpart; a.bar = c->d_bar; a.status = c->d_status; a.result = c->d_eigres;

@@ -236,8 +236,10 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   ALLOC(c->d_stats, 8);
   ALLOC(c->d_netpart, net_partial_elems(c->G));
   if (s == SKY_OK) {
-    c->eig_grid = c->eig_grid_max = jacobi_max_grid(c);
-    ALLOC(c->d_eigpart, (size_t)2 * c->eig_grid * kMaxBatch);
+    c->eig_grid_max = jacobi_max_grid(c);
+    c->eig_grid = c->eig_grid_max < c->num_sms ? c->eig_grid_max : c->num_sms;   // one per SM
+    c->eig_grid_auto = true;
+    ALLOC(c->d_eigpart, (size_t)2 * c->eig_grid_max * kMaxBatch);
   }
 #undef ALLOC
   if (s == SKY_OK) {
@@ -486,6 +488,7 @@ sky_status sky_tune_set(sky_ctx* c, sky_knob knob, int value) {
     case SKY_KNOB_JACOBI_BLOCKS:
       if (value < 1 || value > c->eig_grid_max) break;
       c->eig_grid = value;
+      c->eig_grid_auto = false;
       return SKY_OK;
     default:
       return set_err(c, SKY_EINVAL, "unknown knob %d", (int)knob);

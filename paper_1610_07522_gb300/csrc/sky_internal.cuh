@@ -102,6 +102,7 @@ struct Ctx {
   void* d_eigrot;                   // Jacobi rotations of two consecutive rounds
   int eig_grid;                     // blocks of the Jacobi kernel (tunable, <= eig_grid_max)
   int eig_grid_max;                 // co-resident blocks of the Jacobi kernel
+  bool eig_grid_auto;               // eig_grid not tuned: chosen per solve from the size
   int line_yz;                      // threads per block of the y/z line passes (tunable)
   int line_x;                       // lines per block of the x line passes (tunable)
   int ov_waves;                     // K-split waves of the FMA overlap (tunable)
