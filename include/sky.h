@@ -236,7 +236,8 @@ sky_status sky_set_prec(sky_ctx* ctx, sky_prec prec);
 
 /* ---- Tunable launch shapes ---------------------------------------------------
  * Launch-shape knobs of a context, for an autotuner that times the calls on
- * its own workload and keeps the fastest values.  Every value gives the same
+ * its own workload and keeps the fastest values, and two limits of the
+ * device-side waits and iterations.  Every value gives the same
  * result except for the order of floating-point sums (split counts, eigensolver
  * blocks), so results may change in the last bits.  The paper has no
  * counterpart (its tuning is the MPI/OpenMP layout, Sec. 5).
@@ -247,6 +248,11 @@ sky_status sky_set_prec(sky_ctx* ctx, sky_prec prec);
  *   SKY_KNOB_JACOBI_BLOCKS  blocks of the cooperative eigensolver: 1..JACOBI_BLOCKS_MAX
  *                           (until set: one per SM, two per SM for problems >= 512)
  *   SKY_KNOB_JACOBI_BLOCKS_MAX  (read only) co-resident blocks of that kernel
+ *   SKY_KNOB_WAIT_SPINS     spin budget of each grid-barrier wait of the eigensolver, in
+ *                           thousands of tries (default 40000, i.e. about a second); a wait
+ *                           that runs out sets SKY_ETIMEOUT and the kernel returns, leaving
+ *                           the context usable (0 makes every wait give up at once)
+ *   SKY_KNOB_JACOBI_MAX_SWEEPS  Jacobi sweeps before SKY_ENOCONV (1..1000, default 60)
  * sky_tune_set returns SKY_EINVAL for a value outside these sets; sky_tune_get
  * returns the current value (-1 for an unknown knob or a NULL context). */
 typedef enum {
@@ -255,7 +261,9 @@ typedef enum {
   SKY_KNOB_OVERLAP_WAVES = 2,
   SKY_KNOB_TC_WAVES = 3,
   SKY_KNOB_JACOBI_BLOCKS = 4,
-  SKY_KNOB_JACOBI_BLOCKS_MAX = 5
+  SKY_KNOB_JACOBI_BLOCKS_MAX = 5,
+  SKY_KNOB_WAIT_SPINS = 6,
+  SKY_KNOB_JACOBI_MAX_SWEEPS = 7
 } sky_knob;
 sky_status sky_tune_set(sky_ctx* ctx, sky_knob knob, int value);
 int sky_tune_get(const sky_ctx* ctx, sky_knob knob);

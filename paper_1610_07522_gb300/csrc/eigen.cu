@@ -17,7 +17,6 @@
 namespace sky {
 
 constexpr int kJacThreads = 512;
-constexpr long long kBarrierSpins = 40000000; // x ~32 ns: bounded wait per barrier
 
 // Rotation of one index pair (p, q) in one round.  J = D R with D removing the
 // phase of A_pq and R the real Jacobi rotation:
@@ -147,7 +146,8 @@ __device__ __forceinline__ double2 left_row(const JRot& R1, int row, double2 t0,
 // counter (reset before the launch); barrier number e completes when it
 // reaches e * gridDim.x.  Release-add to arrive, acquire loads to wait, with
 // a bounded spin: on timeout it flags SKY_ETIMEOUT and returns false.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, int* status) {
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, int* status,
+                                             long long max_spins) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -160,7 +160,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, int
       unsigned v;
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
       if ((int)(v - target) >= 0) break;
-      if (++spins > kBarrierSpins || (*(volatile int*)status & SKY_STATUS_BIT(SKY_ETIMEOUT))) {
+      if (++spins > max_spins || (*(volatile int*)status & SKY_STATUS_BIT(SKY_ETIMEOUT))) {
         flag_status(status, SKY_ETIMEOUT);
         ok = 0;
         break;
@@ -192,6 +192,7 @@ struct JacBatch {
   int np;
   double tol;
   int max_sweeps;
+  long long spins;      // spin budget of each grid-barrier wait
   double* part;         // [np][gridDim.x][2] partial norms
   unsigned* bar;
   int* status;
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
     }
     block_norms(off, tot, a.part + (long long)b * 2 * gridDim.x);
   }
-  if (!grid_barrier(a.bar, epoch, a.status)) return;
+  if (!grid_barrier(a.bar, epoch, a.status, a.spins)) return;
   // per-problem bookkeeping: thread b of every block serves problem b (the same
   // sums in the same order in every block, so every block decides alike)
   int act = 0;
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
                          P.A0[(long long)p * P.m + q], p, q, P.n, s_thr[b]);
     }
   }
-  if (!grid_barrier(a.bar, epoch, a.status)) return;
+  if (!grid_barrier(a.bar, epoch, a.status, a.spins)) return;
   for (int t = 0; active; ++t) {
     // One item per thread.  Work is dealt out in 32-item warp chunks round-robin
     // over the blocks, so every SM gets an even share of each kind of item (the
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
       part[2 * blockIdx.x + 1] = s_acc[b][1];
       s_acc[b][0] = s_acc[b][1] = 0.0;
     }
-    if (!grid_barrier(a.bar, epoch, a.status)) return;
+    if (!grid_barrier(a.bar, epoch, a.status, a.spins)) return;
     act = 0;
     for (int b = threadIdx.x; b < np; b += blockDim.x) {
       if (s_done[b]) continue;
@@ -557,7 +558,8 @@ sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, dou
   int grid = c->eig_grid;
   if (c->eig_grid_auto && nmax >= kJacobiLarge) grid = c->eig_grid_max;
   a.tol = 1e-14;
-  a.max_sweeps = 60;
+  a.max_sweeps = c->jac_max_sweeps;
+  a.spins = c->wait_spins;
   a.part = c->d_eigpart; a.bar = c->d_bar; a.status = c->d_status; a.result = c->d_eigres;
   a.run = run; a.run_stride = run_stride;
   a.stats = c->d_stats;

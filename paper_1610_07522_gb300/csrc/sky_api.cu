@@ -185,6 +185,8 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   c->line_x = 64;
   c->ov_waves = 1;
   c->tc_waves = 2;
+  c->wait_spins = kBarrierSpins;
+  c->jac_max_sweeps = kJacMaxSweeps;
   size_t gpart = 0;
   for (int I = 1; I <= Imax; ++I) {   // room for the largest tunable split count
     const size_t need = overlap_partial_elems(I, V, kMaxOverlapWaves * c->ov_slots);
@@ -490,6 +492,14 @@ sky_status sky_tune_set(sky_ctx* c, sky_knob knob, int value) {
       c->eig_grid = value;
       c->eig_grid_auto = false;
       return SKY_OK;
+    case SKY_KNOB_WAIT_SPINS:
+      if (value < 0) break;
+      c->wait_spins = value == 0 ? 0 : (long long)value * 1000;
+      return SKY_OK;
+    case SKY_KNOB_JACOBI_MAX_SWEEPS:
+      if (value < 1 || value > 1000) break;
+      c->jac_max_sweeps = value;
+      return SKY_OK;
     default:
       return set_err(c, SKY_EINVAL, "unknown knob %d", (int)knob);
   }
@@ -505,6 +515,8 @@ int sky_tune_get(const sky_ctx* c, sky_knob knob) {
     case SKY_KNOB_TC_WAVES: return c->tc_waves;
     case SKY_KNOB_JACOBI_BLOCKS: return c->eig_grid;
     case SKY_KNOB_JACOBI_BLOCKS_MAX: return c->eig_grid_max;
+    case SKY_KNOB_WAIT_SPINS: return (int)(c->wait_spins / 1000);
+    case SKY_KNOB_JACOBI_MAX_SWEEPS: return c->jac_max_sweeps;
     default: return -1;
   }
 }

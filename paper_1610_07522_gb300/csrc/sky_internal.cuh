@@ -57,6 +57,8 @@ constexpr int kDensSplits = 8;     // state splits of the density accumulation
 constexpr int kMaxBatch = 128;     // problems per batched eigensolve / small GEMM
 constexpr int kRedBlock = 256;     // threads of the per-state reduction blocks
 constexpr int kMaxOverlapWaves = 2; // largest tunable K-split wave count of k_overlap
+constexpr long long kBarrierSpins = 40000000;  // default spins (~32 ns each) per barrier wait
+constexpr int kJacMaxSweeps = 60;   // default Jacobi sweep cap
 constexpr int kMaxTcWaves = 4;      // largest tunable K-split wave count of the tcgen05 overlap
 
 struct Ctx {
@@ -106,6 +108,8 @@ struct Ctx {
   int line_yz;                      // threads per block of the y/z line passes (tunable)
   int line_x;                       // lines per block of the x line passes (tunable)
   int ov_waves;                     // K-split waves of the FMA overlap (tunable)
+  long long wait_spins;             // spin budget of the eigensolver's grid-barrier waits
+  int jac_max_sweeps;               // Jacobi sweeps before SKY_ENOCONV
   int tc_waves;                     // K-split waves of the tensor-core overlap (tunable)
   double2* d_small[6];              // I x I temporaries
   void* d_tcA[3];                   // split-BF16 operand pieces (tensor-core forms)
