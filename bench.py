@@ -208,7 +208,7 @@ def convergence_leg(dev, maxit=4000):
     16^3, 16n+16p workload for each form: plain FP64, FP32, split-BF16 (x3),
     the paper's combined recombination, and the learned damping weight
     (trained here, on the GPU, by the library's kernels from plain
-    trajectories; its training time is reported apart).  The judge is the
+    trajectories; its training time is reported apart).  The reference is the
     plain method's fixed point (FP64 iterated to |dE/A| < 1e-8): a form
     reaches it when its stop point is as close as the plain FP64 stop point,
     within 1e-4 MeV per nucleon."""

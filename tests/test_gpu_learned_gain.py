@@ -5,7 +5,7 @@ Adam kernels, on samples from a plain FP64 trajectory of the 16^3, 16n+16p
 workload (one weighted step trained to reach where four plain steps go).
 Then the plain step and the learned step each run to |dE/A| < 1e-6 MeV from
 the same initial state.  The learned run must take clearly fewer iterations
-and reach the same fixed point: the plain converged state is the judge.
+and reach the same fixed point: the plain converged state is the reference.
 The stopping rule |dE/A| < 1e-6 per iteration leaves each run short of the
 exact fixed point by an amount that scales with its step size, so the two
 final energies are compared at 1e-4 MeV per nucleon.
