@@ -11,7 +11,8 @@
 //           b' = (Im b, -Re b) per entry, so D = a_r [b_r; b'_r]^T holds Re | Im;
 //   psi_a = sum_b M[b][a] phi_b:  psi_r = [M_re^T | M_im^T] [phi_r; (i phi)_r],
 //           i phi = (-Im phi, Re phi), with the phi operand stored transposed
-//           (K = 2I contiguous) so that D = psi_r directly.
+//           (K contiguous: the two halves padded with zeros to a multiple of 32
+//           states each) so that D = psi_r directly.
 #include <cuda_bf16.h>
 
 #include "tc_gemm.cuh"
@@ -54,10 +55,11 @@ __global__ void k_split_rows(const float* __restrict__ src, long long rows, long
 }
 
 // Transposed operand of the recombination: dst[i][v'][beta'] (row stride ld)
-// from phi_r[beta][v'] (beta' = beta) and (i phi)_r (beta' = I + beta).
-// 32 x 32 tiles through shared memory (coalesced on both sides).
+// from phi_r[beta][v'] (beta' = beta) and (i phi)_r (beta' = Ipad + beta), with
+// zeros for beta in [I, Ipad); Ipad a multiple of 32.  32 x 32 tiles through
+// shared memory (coalesced on both sides, whole 32-byte sectors written).
 __global__ void __launch_bounds__(256) k_split_rot_b(const float* __restrict__ phi, int I,
-                                                     long long K2V, long long ld, int n,
+                                                     int Ipad, long long K2V, long long ld, int n,
                                                      __nv_bfloat16* d0, __nv_bfloat16* d1,
                                                      __nv_bfloat16* d2) {
   __shared__ float t[32][65];    // [beta][v' (32 complex = 64 reals)]
@@ -76,8 +78,8 @@ __global__ void __launch_bounds__(256) k_split_rot_b(const float* __restrict__ p
     const int vl = idx >> 5, bl = idx & 31;
     const long long v = v0 + vl;
     const int b = b0 + bl;
-    if (v >= K2V || b >= I) continue;
-    const float x = t[bl][vl];
+    if (v >= K2V) continue;
+    const float x = t[bl][vl];            // zero for b >= I
     // (i phi)_r: even v' (re slot) takes -Im, odd v' (im slot) takes +Re
     const float y = (vl & 1) ? t[bl][vl - 1] : -t[bl][vl + 1];
     __nv_bfloat16 sx[3], sy[3];
@@ -85,21 +87,25 @@ __global__ void __launch_bounds__(256) k_split_rot_b(const float* __restrict__ p
     split3(y, n, sy);
     for (int i = 0; i < n; ++i) {
       d[i][v * ld + b] = sx[i];
-      d[i][v * ld + I + b] = sy[i];
+      d[i][v * ld + Ipad + b] = sy[i];
     }
   }
 }
 
 // Row operand of the recombination: A[alpha][beta'] = M_re[beta'][alpha]
 // (beta' < I) or M_im[beta' - I][alpha], split into bf16 pieces.
-__global__ void k_split_rot_a(const double2* __restrict__ M, int I, long long ld, int n,
+__global__ void k_split_rot_a(const double2* __restrict__ M, int I, int Ipad, long long ld, int n,
                               __nv_bfloat16* d0, __nv_bfloat16* d1, __nv_bfloat16* d2) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)I * 2 * I) return;
-  const int a = (int)(e / (2 * I)), bp = (int)(e % (2 * I));
-  const double2 m = M[(long long)(bp < I ? bp : bp - I) * I + a];
-  // the FP64 value keeps its residual in the lower pieces
-  const double xd = bp < I ? m.x : m.y;
+  if (e >= (long long)I * 2 * Ipad) return;
+  const int a = (int)(e / (2 * Ipad)), bp = (int)(e % (2 * Ipad));
+  const int beta = bp < Ipad ? bp : bp - Ipad;
+  // row a: [Re M[beta][a] for beta < I | zeros | Im M[beta][a] | zeros]
+  double xd = 0.0;
+  if (beta < I) {
+    const double2 m = M[(long long)beta * I + a];
+    xd = bp < Ipad ? m.x : m.y;   // the FP64 value keeps its residual in the lower pieces
+  }
   __nv_bfloat16 s[3];
   const __nv_bfloat16 h = __double2bfloat16(xd);
   s[0] = h;
@@ -131,7 +137,10 @@ __global__ void k_tc_overlap_reduce(const float* __restrict__ D, int nz, long lo
   if (a != b) X[(long long)b * I + a] = conjx(s);
 }
 
-static inline long long round8(long long x) { return (x + 7) / 8 * 8; }
+// K layout of the recombination: [re | zeros | im | zeros] in halves of
+// round32(I), so that both halves of each row start on a 64-byte boundary and
+// every 32-byte sector of the transposed operand is written whole.
+static inline long long round32(long long x) { return (x + 31) / 32 * 32; }
 
 int tc_nsplit(sky_prec p) { return p == SKY_F32_BF16X6 ? 3 : 2; }
 
@@ -148,9 +157,9 @@ void tc_scratch_sizes(int I, long long V, int num_sms, size_t* piece_a, size_t* 
   const long long K = 2 * V;
   *piece_a = (size_t)I * K;
   const size_t ov_b = (size_t)2 * I * K;
-  const size_t rot_b = (size_t)K * round8(2LL * I);
+  const size_t rot_b = (size_t)K * 2 * round32(I);
   *piece_b = ov_b > rot_b ? ov_b : rot_b;
-  *piece_rot_a = (size_t)I * round8(2LL * I);
+  *piece_rot_a = (size_t)I * 2 * round32(I);
   const long long ldd = (2LL * I + 3) / 4 * 4;
   const int tiles = ((I + tc::BM - 1) / tc::BM) * ((2 * I + tc::BN - 1) / tc::BN);
   int z = kMaxTcWaves * num_sms / (tiles > 0 ? tiles : 1);
@@ -196,22 +205,24 @@ sky_status tc_overlap(Ctx* c, const void* a, const void* b, int I, double2* X) {
 sky_status tc_rotate(Ctx* c, const void* phi, const double2* M, int I, void* out) {
   const long long V = 2LL * c->G, K2V = 2 * V;
   const int n = tc_nsplit(c->prec);
-  const long long ldk = round8(2LL * I);
+  const int Ipad = (int)round32(I);
+  const long long ldk = 2LL * Ipad;
   __nv_bfloat16* Ra[3] = {(__nv_bfloat16*)c->d_tcRotA[0], (__nv_bfloat16*)c->d_tcRotA[1],
                           (__nv_bfloat16*)c->d_tcRotA[2]};
   __nv_bfloat16* Bp[3] = {(__nv_bfloat16*)c->d_tcB[0], (__nv_bfloat16*)c->d_tcB[1],
                           (__nv_bfloat16*)c->d_tcB[2]};
-  k_split_rot_a<<<div_up((long long)I * 2 * I, 256), 256, 0, c->stream>>>(M, I, ldk, n, Ra[0],
-                                                                         Ra[1], Ra[2]);
-  dim3 g2(div_up(K2V, 64), div_up(I, 32));
-  k_split_rot_b<<<g2, 256, 0, c->stream>>>((const float*)phi, I, K2V, ldk, n, Bp[0], Bp[1], Bp[2]);
+  k_split_rot_a<<<div_up((long long)I * 2 * Ipad, 256), 256, 0, c->stream>>>(M, I, Ipad, ldk, n,
+                                                                            Ra[0], Ra[1], Ra[2]);
+  dim3 g2(div_up(K2V, 64), Ipad / 32);
+  k_split_rot_b<<<g2, 256, 0, c->stream>>>((const float*)phi, I, Ipad, K2V, ldk, n, Bp[0], Bp[1],
+                                           Bp[2]);
   note_launch(2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(c, e, "tc rotate split");
   int z = 1;
   const void* pa[3] = {Ra[0], Ra[1], Ra[2]};
   const void* pb[3] = {Bp[0], Bp[1], Bp[2]};
-  e = tc::gemm_bf16(pa, ldk, pb, ldk, n, I, (int)K2V, 2 * I, &z, (float*)out, K2V, 0,
+  e = tc::gemm_bf16(pa, ldk, pb, ldk, n, I, (int)K2V, 2 * Ipad, &z, (float*)out, K2V, 0,
                     c->d_status, c->stream);
   return cuda_check(c, e, "tc rotate gemm");
 }
