@@ -93,8 +93,9 @@ sky_status sky_sync(sky_ctx* ctx);
 /* Solver counters of the context (waits for its stream): out[0] Jacobi
  * eigensolves run, out[1] Jacobi sweeps in total, out[2] sweeps of the last
  * eigensolve, out[3] Loewdin factors computed, out[4] of them by the
- * Newton-Schulz route, out[5] Newton-Schulz iterations in total, out[6..7]
- * reserved (0).  reset != 0 clears them afterwards. */
+ * Newton-Schulz route, out[5] Newton-Schulz iterations in total, out[6]
+ * eigensolves by the tridiagonal route, out[7] reserved (0).  reset != 0
+ * clears them afterwards. */
 sky_status sky_stats(sky_ctx* ctx, long long out[8], int reset);
 
 /* Human-readable text of the last error the context saw (never NULL). */
@@ -253,6 +254,14 @@ sky_status sky_set_prec(sky_ctx* ctx, sky_prec prec);
  *                           that runs out sets SKY_ETIMEOUT and the kernel returns, leaving
  *                           the context usable (0 makes every wait give up at once)
  *   SKY_KNOB_JACOBI_MAX_SWEEPS  Jacobi sweeps before SKY_ENOCONV (1..1000, default 60)
+ *   SKY_KNOB_EIGEN_METHOD   the FP64 eigensolver behind every diagonalisation:
+ *                           SKY_EIG_JACOBI (parallel cyclic Jacobi), SKY_EIG_TRIDIAGONAL
+ *                           (Householder reduction to real tridiagonal form, bisection,
+ *                           inverse iteration, back-transformation: the paper's route
+ *                           through ScaLAPACK, Sec. 3.3.2) or SKY_EIG_AUTO (default:
+ *                           tridiagonal for batches of at most 8 problems of 64 states or
+ *                           more, Jacobi otherwise; the tridiagonal route falls back to
+ *                           Jacobi when its work vectors exceed shared memory)
  * sky_tune_set returns SKY_EINVAL for a value outside these sets; sky_tune_get
  * returns the current value (-1 for an unknown knob or a NULL context). */
 typedef enum {
@@ -263,8 +272,10 @@ typedef enum {
   SKY_KNOB_JACOBI_BLOCKS = 4,
   SKY_KNOB_JACOBI_BLOCKS_MAX = 5,
   SKY_KNOB_WAIT_SPINS = 6,
-  SKY_KNOB_JACOBI_MAX_SWEEPS = 7
+  SKY_KNOB_JACOBI_MAX_SWEEPS = 7,
+  SKY_KNOB_EIGEN_METHOD = 8
 } sky_knob;
+enum { SKY_EIG_AUTO = 0, SKY_EIG_JACOBI = 1, SKY_EIG_TRIDIAGONAL = 2 };
 sky_status sky_tune_set(sky_ctx* ctx, sky_knob knob, int value);
 int sky_tune_get(const sky_ctx* ctx, sky_knob knob);
 

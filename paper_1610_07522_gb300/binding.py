@@ -19,7 +19,8 @@ STATUS_NAMES = ["SKY_OK", "SKY_EINVAL", "SKY_ENOMEM", "SKY_ECUDA", "SKY_ENOTPD",
 SKY_F64, SKY_F32, SKY_F32_BF16X3, SKY_F32_BF16X6 = 0, 1, 2, 3
 (SKY_KNOB_LINE_YZ, SKY_KNOB_LINE_X, SKY_KNOB_OVERLAP_WAVES, SKY_KNOB_TC_WAVES,
  SKY_KNOB_JACOBI_BLOCKS, SKY_KNOB_JACOBI_BLOCKS_MAX, SKY_KNOB_WAIT_SPINS,
- SKY_KNOB_JACOBI_MAX_SWEEPS) = range(8)
+ SKY_KNOB_JACOBI_MAX_SWEEPS, SKY_KNOB_EIGEN_METHOD) = range(9)
+SKY_EIG_AUTO, SKY_EIG_JACOBI, SKY_EIG_TRIDIAGONAL = range(3)
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -159,11 +160,12 @@ def sky_supported_size(n, prec):
 
 
 def sky_stats(ctx, reset=False):
-    """Solver counters: dict of Jacobi solves / sweeps and Loewdin routes."""
+    """Solver counters: dict of Jacobi solves / sweeps, Loewdin routes and
+    tridiagonal-route eigensolves."""
     buf = (ctypes.c_longlong * 8)()
     _check(ctx, lib().sky_stats(ctx, buf, 1 if reset else 0))
     keys = ("jacobi_solves", "jacobi_sweeps", "jacobi_last_sweeps", "loewdin_calls",
-            "loewdin_newton_schulz", "newton_schulz_iters")
+            "loewdin_newton_schulz", "newton_schulz_iters", "tridiagonal_solves")
     return {k: int(buf[i]) for i, k in enumerate(keys)}
 
 

@@ -12,7 +12,7 @@
 // one cooperative kernel whose rounds are separated by a grid barrier with a
 // bounded wait.  Near convergence the matrices are close to diagonal and a
 // sweep or two suffices.
-#include "sky_internal.cuh"
+#include "eig_common.cuh"
 
 namespace sky {
 
@@ -63,24 +63,6 @@ __device__ __forceinline__ int pair_index(int i, int r, int m) {
   if (i == 0) return 0;
   const int pos = ((i - 1 - r) % (m - 1) + (m - 1)) % (m - 1) + 1;
   return pos < m / 2 ? pos : m - 1 - pos;
-}
-
-// x^{-1/2} from an FP32 seed and two Newton steps in FP64, r <- r (3 - x r^2)/2
-// (relative error 1e-7 -> 1e-14 -> rounding); x must lie in the FP32 range.
-__device__ __forceinline__ double rsqrt_refined(double x) {
-  double r = (double)rsqrtf((float)x);
-  r = r * fma(-0.5 * x, r * r, 1.5);
-  r = r * fma(-0.5 * x, r * r, 1.5);
-  return r;
-}
-
-// 1/x from an FP32 seed and two Newton steps in FP64, r <- r (2 - x r);
-// x must lie in the FP32 range.
-__device__ __forceinline__ double rcp_refined(double x) {
-  double r = (double)__frcp_rn((float)x);
-  r = r * fma(-x, r, 2.0);
-  r = r * fma(-x, r, 2.0);
-  return r;
 }
 
 // Jacobi rotation of B = [[app, z], [z*, aqq]] to FP64 accuracy without the
@@ -142,37 +124,6 @@ __device__ __forceinline__ double2 left_row(const JRot& R1, int row, double2 t0,
   return row ? rx_plus_conjcy(R1.s, t0, R1.j11, t1) : rx_plus_conjcy(R1.c, t0, R1.j10, t1);
 }
 
-// Grid barrier over all blocks of a cooperative launch: a monotonic arrival
-// counter (reset before the launch); barrier number e completes when it
-// reaches e * gridDim.x.  Release-add to arrive, acquire loads to wait, with
-// a bounded spin: on timeout it flags SKY_ETIMEOUT and returns false.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, int* status,
-                                             long long max_spins) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ++epoch;
-    const unsigned target = epoch * gridDim.x;
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
-    int ok = 1;
-    long long spins = 0;
-    for (;;) {
-      unsigned v;
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
-      if ((int)(v - target) >= 0) break;
-      if (++spins > max_spins || (*(volatile int*)status & SKY_STATUS_BIT(SKY_ETIMEOUT))) {
-        flag_status(status, SKY_ETIMEOUT);
-        ok = 0;
-        break;
-      }
-      if (spins > 64) __nanosleep(32);
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 // ---- batched solve -----------------------------------------------------------
 // Up to kMaxBatch independent Hermitian problems share one cooperative launch:
 // every round serves all unfinished problems, so the fixed cost of a round
@@ -229,16 +180,6 @@ __device__ __forceinline__ void sum_parts(const double* part, double& off, doubl
   off = 0.0;
   tot = 0.0;
   for (int b = 0; b < (int)gridDim.x; ++b) { off += part[2 * b]; tot += part[2 * b + 1]; }
-}
-
-// Problem of item w: the last b with off[b] <= w (off ascending, off[np] > w).
-__device__ __forceinline__ int find_prob(const int* off, int np, int w) {
-  int lo = 0, hi = np - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= w) lo = mid; else hi = mid - 1;
-  }
-  return lo;
 }
 
 __global__ void __launch_bounds__(kJacThreads) k_jacobi(JacBatch a) {
@@ -514,12 +455,12 @@ int jacobi_max_grid(Ctx* c) {
 
 size_t jacobi_rot_bytes(int m) { return (size_t)2 * (m / 2 + 1) * sizeof(JRot); }
 
-// Eigendecomposition of np Hermitian matrices A[b] (n[b] x n[b]) into ascending
-// w[b] and eigenvector columns Z[b]; problem b is skipped when run[b*stride] == 0.
-sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, double* const* w,
-                      double2* const* Z, const int* run, int run_stride) {
-  if (np < 1) return SKY_OK;
-  if (np > c->eig_batch) return set_err(c, SKY_EINVAL, "eigensolver batch %d > %d", np, c->eig_batch);
+// Jacobi eigendecomposition of np Hermitian matrices A[b] (n[b] x n[b]) into
+// ascending w[b] and eigenvector columns Z[b]; problem b is skipped when
+// run[b*stride] == 0.
+static sky_status eigh_batch_jacobi(Ctx* c, int np, const double2* const* A, const int* n,
+                                    double* const* w, double2* const* Z, const int* run,
+                                    int run_stride) {
   EigJobs j;
   JacBatch a;
   long long items = 0;
@@ -571,6 +512,30 @@ sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, dou
   k_jacobi_finish<<<dim3(div_up(nmax, 128), np), 128, 0, c->stream>>>(j, c->d_eigres);
   note_launch();
   return cuda_check(c, cudaGetLastError(), "jacobi finish");
+}
+
+// Until the method is set, problems of kTriAutoMin states and more in batches of
+// at most kTriAutoBatch take the tridiagonal route (O(n^3) once instead of per
+// Jacobi sweep); many small problems stay with the batched Jacobi solver,
+// whose rounds serve the whole batch at once.
+constexpr int kTriAutoMin = 64;
+constexpr int kTriAutoBatch = 8;
+
+// Eigendecomposition of np Hermitian matrices A[b] (n[b] x n[b]) into ascending
+// w[b] and eigenvector columns Z[b]; problem b is skipped when run[b*stride] == 0.
+sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, double* const* w,
+                      double2* const* Z, const int* run, int run_stride) {
+  if (np < 1) return SKY_OK;
+  if (np > c->eig_batch) return set_err(c, SKY_EINVAL, "eigensolver batch %d > %d", np, c->eig_batch);
+  int nmax = 0;
+  for (int b = 0; b < np; ++b) nmax = n[b] > nmax ? n[b] : nmax;
+  const bool tri = c->eig_method == SKY_EIG_TRIDIAGONAL ||
+                   (c->eig_method == SKY_EIG_AUTO && nmax >= kTriAutoMin && np <= kTriAutoBatch);
+  if (tri) {
+    const sky_status s = eigh_batch_tri(c, np, A, n, w, Z, run, run_stride);
+    if (s != SKY_EUNSUPPORTED) return s;
+  }
+  return eigh_batch_jacobi(c, np, A, n, w, Z, run, run_stride);
 }
 
 sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z, const int* run) {

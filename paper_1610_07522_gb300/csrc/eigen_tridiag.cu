@@ -1,0 +1,844 @@
+// FP64 Hermitian eigensolver by reduction to real tridiagonal form, for the
+// diagonalisations of steps 3b-3c (Sec. 3.3.2) at the sizes where the cyclic
+// Jacobi method's O(I^3) work per sweep dominates an iteration.
+//
+// The paper hands these to ScaLAPACK's Hermitian tridiagonal reduction with
+// the MRRR tridiagonal solver.  Here the same three stages are GPU kernels:
+//
+//  1. k_hh_tridiag: A = Q T Q^H with Q = H_0 H_1 ... H_{n-2}, each reflector
+//     H_t = I - tau_t v_t v_t^H chosen so that H_t^H maps column t below the
+//     diagonal onto beta_t e_1 with beta_t real (T is real symmetric).  One
+//     cooperative kernel: block g keeps the columns j = g, g + G, ... of the
+//     (full, Hermitian) trailing matrix in shared memory.  The update by H_t is
+//     A <- A - v w^H - w v^H with p = A v, w = tau p - (|tau|^2 v^H p / 2) v.
+//     Each owner forms p_j = col_j^H v_t for its own columns, fused with that
+//     column's update by the previous reflector, and publishes p and the next
+//     column; after one grid barrier every block recomputes the next column
+//     and reflector itself (the same arithmetic in every block), so each step
+//     costs one barrier.
+//  2. k_tri_bisect: eigenvalues of T by Sturm-count multisection (sign
+//     changes of the leading minors of T - x I, no divisions), kBisLanes
+//     points per eigenvalue and round.
+//  3. k_tri_vectors: eigenvectors of T by inverse iteration (Gaussian
+//     elimination with partial pivoting of T - lambda I, factored once, then
+//     kInvIters solves from a counter-based random start); eigenvalues closer
+//     than kTightRel ||T||
+//     are handled by one thread in order, each new vector orthogonalised
+//     against the cluster's earlier ones after every solve (as LAPACK's
+//     dstein does).  k_tri_window then applies first-order Loewdin steps
+//     Y <- Y (3 I - Y^T Y) / 2, with Y^T Y formed only between eigenvalues
+//     within kWinRel ||T|| of each other (the inverse-iteration vectors'
+//     mutual overlaps fall off like eps ||T|| / gap).  k_hh_back forms
+//     Z = Q Y, one warp per column, the reflectors applied in reverse order.
+//
+// Eigenvalues come out ascending, eigenvectors as the columns of Z.
+#include "eig_common.cuh"
+
+namespace sky {
+
+constexpr int kTriThreads = 512;
+constexpr int kTriWarps = kTriThreads / 32;
+constexpr int kBisLanes = 16;           // bisection points per eigenvalue and round
+constexpr int kBisMaxRounds = 96;       // ample for 2 eps ||T|| at 17x per round
+constexpr int kInvIters = 3;            // inverse-iteration solves per vector
+constexpr int kVecThreads = 8;          // eigenvectors per block of k_tri_vectors
+constexpr double kTightRel = 1e-9;      // cluster threshold relative to ||T||
+constexpr double kWinRel = 0.05;        // Loewdin window relative to ||T||
+constexpr int kWinMax = 128;            // neighbours per side in the window at most
+constexpr int kWinThreads = 128;
+constexpr int kWinChunks = (2 * kWinMax + 1 + 31) / 32;
+constexpr int kBackWarps = 16;
+constexpr size_t kTriSmemMax = 200 * 1024;   // dynamic shared memory of k_hh_tridiag / k_hh_back
+constexpr double kEps = 2.220446049250313e-16;
+
+struct TriBatch {
+  const double2* A[kMaxBatch];   // input matrices, row-major n x n
+  double* w[kMaxBatch];          // eigenvalues out (ascending)
+  double2* Z[kMaxBatch];         // eigenvectors out, Z[i * n + k] = component i of vector k
+  int n[kMaxBatch];
+  int rot[kMaxBatch];            // column j of problem b lives in block (j + rot) mod G
+  int soff[kMaxBatch];           // own columns' offset in dynamic shared memory, -1: global
+  int voff[kMaxBatch];           // offset of the block's three work vectors
+  int coff;                      // offset of the per-column partials (doubles) in shared memory
+  int off[kMaxBatch + 1];        // prefix sums of n: eigenvalue / column items
+  int sid[kMaxBatch];            // workspace slot of each problem
+  int np;
+  double2* S0;                   // per problem: own columns (global home), later U0, U1
+  double2* S1;                   // per problem: reflectors V[t * n + i]
+  double2* S2;                   // per problem: Y and its Loewdin ping-pong buffer
+  size_t slot;                   // double2 per problem in S0, S1, S2
+  double* T;                     // per problem: U2, published vectors, tau, d, e, e^2, lambda
+  size_t tslot;                  // doubles per problem in T
+  int m;                         // stride of the vectors in T (even, >= every n)
+  const int* run;                // problem b runs iff run == null or run[b * run_stride] != 0
+  int run_stride;
+  double* sp;                    // per problem slot: [2][gridDim.x] partials of Re(v^H p)
+  size_t sp_stride;
+  unsigned* bar;
+  int* status;
+  long long spins;
+  long long* stats;
+};
+
+struct TriPtrs {
+  double2* cols;                 // own columns, global home: column j at cols + j * n
+  double2* V;
+  double *Y, *Y2, *U0, *U1, *U2;
+  double2 *P0, *P1, *C0, *C1, *tau;
+  double *d, *e, *e2, *lam;
+};
+
+__device__ __forceinline__ TriPtrs tri_ptrs(const TriBatch& a, int b) {
+  TriPtrs p;
+  const size_t n = (size_t)a.n[b], m = (size_t)a.m, k = (size_t)a.sid[b];
+  p.cols = a.S0 + k * a.slot;
+  p.U0 = reinterpret_cast<double*>(p.cols);
+  p.U1 = p.U0 + n * n;
+  p.V = a.S1 + k * a.slot;
+  p.Y = reinterpret_cast<double*>(a.S2 + k * a.slot);
+  p.Y2 = p.Y + n * n;
+  double* t = a.T + k * a.tslot;
+  p.U2 = t;
+  double2* vecs = reinterpret_cast<double2*>(t + m * m);   // m even: 16-byte aligned
+  p.P0 = vecs; p.P1 = vecs + m; p.C0 = vecs + 2 * m; p.C1 = vecs + 3 * m; p.tau = vecs + 4 * m;
+  double* s = reinterpret_cast<double*>(vecs + 5 * m);
+  p.d = s; p.e = s + m; p.e2 = s + 2 * m; p.lam = s + 3 * m;
+  return p;
+}
+
+__device__ __forceinline__ bool tri_run(const TriBatch& a, int b) {
+  return a.n[b] > 0 && (!a.run || a.run[b * a.run_stride] != 0);
+}
+
+// Warp sum by butterfly: every lane ends with the same total.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---- stage 1: Householder reduction ------------------------------------------
+// The per-step vectors of a problem are short (n - t entries): its head work
+// runs on one group of kHeadWarps warps, and the heads of up to kHeadGroups
+// problems run side by side (one set of __syncthreads for all of them).
+constexpr int kHeadWarps = 4;
+constexpr int kHeadThreads = kHeadWarps * 32;
+constexpr int kHeadGroups = kTriWarps / kHeadWarps;
+
+// First own column of block g for problem b and the number of own columns.
+__device__ __forceinline__ void own_range(const TriBatch& a, int b, int& j0, int& ns) {
+  const int G = gridDim.x, n = a.n[b];
+  j0 = (((int)blockIdx.x - a.rot[b]) % G + G) % G;
+  ns = j0 < n ? (n - 1 - j0) / G + 1 : 0;
+}
+
+__device__ __forceinline__ double2* own_col(const TriBatch& a, int b, double2* dsm, int j, int s) {
+  const int n = a.n[b];
+  return a.soff[b] >= 0 ? dsm + a.soff[b] + (size_t)s * n
+                        : a.S0 + (size_t)a.sid[b] * a.slot + (size_t)j * n;
+}
+
+// Per-block partials of Re(v_t^H p_t) of problem b, parity t & 1.
+__device__ __forceinline__ double* sp_row(const TriBatch& a, int b, int t) {
+  return a.sp + (size_t)a.sid[b] * a.sp_stride + (size_t)(t & 1) * gridDim.x;
+}
+
+struct HeadShared {
+  double red[kHeadGroups][kHeadWarps + 1];
+  double2 sc[kHeadGroups][2];
+};
+
+// Step t of the problems b0 .. b0 + kHeadGroups - 1 (group q serves b0 + q),
+// every block alike: column t of the trailing matrix (updated by reflector
+// t-1 from the published copy), d_t, and reflector t.  Work vectors: vn = v_t
+// (built in place from the column), vo = v_{t-1}, w.  v_{t-1}^H p_{t-1} is the
+// sum of the owners' published per-block partials (the same order in every
+// block); beta, tau and 1/(alpha - beta) are formed once per problem by the
+// group's first thread and passed on in shared memory.  The published p and
+// column are loaded in one pass (one L2 round trip per step).
+__device__ void tri_heads(const TriBatch& a, int b0, int t, double2* dsm, HeadShared& hs,
+                          double2* s_tau, const unsigned char* s_run) {
+  const int q = threadIdx.x / kHeadThreads, ht = threadIdx.x % kHeadThreads;
+  const int b = b0 + q, lane = threadIdx.x & 31, hwarp = ht >> 5;
+  const bool on = b < a.np && s_run[b] && t <= a.n[b] - 1;
+  const int n = on ? a.n[b] : 0;
+  double2* vb = dsm + (on ? a.voff[b] : 0);
+  double2* vn = vb + (size_t)(t & 1) * n;
+  const double2* vo = vb + (size_t)((t + 1) & 1) * n;
+  double2* w = vb + 2 * (size_t)n;
+  TriPtrs p;
+  if (on) p = tri_ptrs(a, b);
+  double sg = 0.0;                           // |column|^2 below the subdiagonal
+  if (t == 0) {
+    if (on) {
+      const double2* A = a.A[b];
+      for (int i = ht; i < n; i += kHeadThreads) {
+        double2 x = A[i];
+        x.y = i == 0 ? 0.0 : -x.y;         // column 0 = conj(row 0)
+        vn[i] = x;
+        if (i >= 2) sg = fma(x.x, x.x, fma(x.y, x.y, sg));
+      }
+    }
+  } else {
+    if (on) {
+      const double2* Pp = ((t - 1) & 1) ? p.P1 : p.P0;
+      const double2* Cp = ((t - 1) & 1) ? p.C1 : p.C0;
+      for (int i = t + ht; i < n; i += kHeadThreads) {
+        w[i] = __ldcg(Pp + i);
+        vn[i] = __ldcg(Cp + i);            // the column after step t-2's update, for now
+      }
+      if (hwarp == 0) {
+        const double* ps = sp_row(a, b, t - 1);
+        double S = 0.0;
+        for (int g = lane; g < (int)gridDim.x; g += 32) S += __ldcg(ps + g);
+        S = warp_sum(S);
+        if (lane == 0) {
+          const double2 tau = s_tau[b];
+          hs.red[q][kHeadWarps] = 0.5 * (tau.x * tau.x + tau.y * tau.y) * S;
+        }
+      }
+    }
+    __syncthreads();
+    if (on) {
+      const double c = hs.red[q][kHeadWarps];
+      const double2 tau = s_tau[b];
+      for (int i = t + ht; i < n; i += kHeadThreads) {
+        const double2 x = w[i], v = vo[i];
+        w[i] = make_double2(fma(tau.x, x.x, fma(-tau.y, x.y, -c * v.x)),
+                            fma(tau.x, x.y, fma(tau.y, x.x, -c * v.y)));
+      }
+    }
+    __syncthreads();
+    if (on) {
+      const double2 wt = w[t];             // v_{t-1}[t] = 1; col = Cb - v conj(w_t) - w
+      for (int i = t + ht; i < n; i += kHeadThreads) {
+        const double2 cb = vn[i], v = vo[i], x = w[i];
+        const double2 y = make_double2(fma(-v.x, wt.x, fma(-v.y, wt.y, cb.x - x.x)),
+                                       fma(-v.y, wt.x, fma(v.x, wt.y, cb.y - x.y)));
+        vn[i] = y;
+        if (i >= t + 2) sg = fma(y.x, y.x, fma(y.y, y.y, sg));
+      }
+    }
+  }
+  const bool refl = on && t <= n - 2;
+  if (refl) {
+    sg = warp_sum(sg);
+    if (lane == 0) hs.red[q][hwarp] = sg;
+  }
+  __syncthreads();
+  if (refl && ht == 0) {
+    double sig = hs.red[q][0];
+    for (int k = 1; k < kHeadWarps; ++k) sig += hs.red[q][k];
+    const double2 al = vn[t + 1];
+    double beta;
+    double2 tn, sc;
+    if (sig == 0.0 && al.y == 0.0) {
+      beta = al.x;                          // already real: H_t = I
+      tn = make_double2(0.0, 0.0);
+      sc = make_double2(1.0, 0.0);
+    } else {
+      const double nr = sqrt(al.x * al.x + al.y * al.y + sig);
+      beta = al.x >= 0.0 ? -nr : nr;
+      const double rb = 1.0 / beta;
+      tn = make_double2((beta - al.x) * rb, -al.y * rb);
+      const double dx = al.x - beta;        // |Re alpha| + nr: no cancellation
+      const double r = 1.0 / fma(dx, dx, al.y * al.y);
+      sc = make_double2(dx * r, -al.y * r);  // 1 / (alpha - beta)
+    }
+    s_tau[b] = tn;
+    hs.sc[q][0] = sc;
+    hs.sc[q][1] = make_double2(beta, vn[t].x);
+    vn[t + 1] = make_double2(1.0, 0.0);
+  }
+  __syncthreads();
+  if (refl) {
+    const double2 sc = hs.sc[q][0];
+    for (int i = t + 2 + ht; i < n; i += kHeadThreads) {
+      const double2 x = vn[i];
+      vn[i] = make_double2(fma(x.x, sc.x, -x.y * sc.y), fma(x.x, sc.y, x.y * sc.x));
+    }
+  }
+  __syncthreads();
+  if (on && blockIdx.x == 0) {
+    if (refl) {
+      if (ht == 0) {
+        const double2 bd = hs.sc[q][1];
+        p.d[t] = bd.y;
+        p.e[t] = bd.x;
+        p.e2[t] = bd.x * bd.x;
+        p.tau[t] = s_tau[b];
+      }
+      double2* Vt = p.V + (size_t)t * n;
+      for (int i = t + 1 + ht; i < n; i += kHeadThreads) Vt[i] = vn[i];
+    } else if (ht == 0) {
+      p.d[t] = vn[t].x;                     // t = n - 1
+    }
+  }
+}
+
+// Own columns of problem b active at step t (j >= t+1): first slot and count.
+__device__ __forceinline__ void active_own(const TriBatch& a, int b, int t, int& j0, int& smin,
+                                           int& cb) {
+  const int G = gridDim.x;
+  int ns;
+  own_range(a, b, j0, ns);
+  smin = t + 1 > j0 ? (t + 1 - j0 + G - 1) / G : 0;
+  cb = ns > smin ? ns - smin : 0;
+}
+
+// Own columns j >= t+1, one warp per column: update by reflector t-1 (rows
+// > t), p_j = col_j^H v_t, publication of p_j and of column t+1, and the
+// block's partial of Re(v_t^H p_t) per problem (over its own columns, in
+// column order).
+__device__ void tri_body(const TriBatch& a, int t, double2* dsm, double* contrib,
+                         const unsigned char* s_run) {
+  const int G = gridDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int C = 0;
+  for (int b = 0; b < a.np; ++b) {
+    if (!s_run[b] || t > a.n[b] - 2) continue;
+    int j0, smin, cb;
+    active_own(a, b, t, j0, smin, cb);
+    C += cb;
+  }
+  for (int ci = wid; ci < C; ci += kTriWarps) {
+    // column ci -> problem b, column j, slot s
+    int b = 0, j = 0, s = 0, rest = ci;
+    for (; b < a.np; ++b) {
+      if (!s_run[b] || t > a.n[b] - 2) continue;
+      int j0, smin, cb;
+      active_own(a, b, t, j0, smin, cb);
+      if (rest < cb) {
+        s = smin + rest;
+        j = j0 + s * G;
+        break;
+      }
+      rest -= cb;
+    }
+    const int n = a.n[b];
+    double2* col = own_col(a, b, dsm, j, s);
+    const double2* vb = dsm + a.voff[b];
+    const double2* vn = vb + (size_t)(t & 1) * n;
+    const double2* vo = vb + (size_t)((t + 1) & 1) * n;
+    const double2* w = vb + 2 * (size_t)n;
+    const TriPtrs p = tri_ptrs(a, b);
+    double2* Cb = (t & 1) ? p.C1 : p.C0;
+    const bool upd = t >= 1, pub = (j == t + 1);
+    const double2 wj = upd ? conjx(w[j]) : make_double2(0.0, 0.0);
+    const double2 vj = upd ? conjx(vo[j]) : make_double2(0.0, 0.0);
+    double ax = 0.0, ay = 0.0;
+    for (int i = t + 1 + lane; i < n; i += 32) {
+      double2 x = col[i];
+      if (upd) {                            // x -= vo_i conj(w_j) + w_i conj(vo_j)
+        const double2 v = vo[i], u = w[i];
+        x.x = fma(-v.x, wj.x, fma(v.y, wj.y, fma(-u.x, vj.x, fma(u.y, vj.y, x.x))));
+        x.y = fma(-v.x, wj.y, fma(-v.y, wj.x, fma(-u.x, vj.y, fma(-u.y, vj.x, x.y))));
+        col[i] = x;
+      }
+      const double2 v = vn[i];
+      ax = fma(x.x, v.x, fma(x.y, v.y, ax));      // conj(x) v
+      ay = fma(x.x, v.y, fma(-x.y, v.x, ay));
+      if (pub) Cb[i] = x;
+    }
+    ax = warp_sum(ax);
+    ay = warp_sum(ay);
+    if (lane == 0) {
+      ((t & 1) ? p.P1 : p.P0)[j] = make_double2(ax, ay);
+      const double2 vnj = vn[j];
+      contrib[ci] = fma(vnj.x, ax, vnj.y * ay);   // Re(conj(v_t[j]) p_j)
+    }
+  }
+  __syncthreads();
+  // per-problem partials, one thread per problem, own columns in order
+  for (int b = threadIdx.x; b < a.np; b += blockDim.x) {
+    if (!s_run[b] || t > a.n[b] - 2) continue;
+    int first = 0;
+    for (int q = 0; q < b; ++q) {
+      if (!s_run[q] || t > a.n[q] - 2) continue;
+      int j0, smin, cb;
+      active_own(a, q, t, j0, smin, cb);
+      first += cb;
+    }
+    int j0, smin, cb;
+    active_own(a, b, t, j0, smin, cb);
+    double acc = 0.0;
+    for (int k = 0; k < cb; ++k) acc += contrib[first + k];
+    sp_row(a, b, t)[blockIdx.x] = acc;
+  }
+}
+
+__global__ void __launch_bounds__(kTriThreads, 1) k_hh_tridiag(TriBatch a) {
+  extern __shared__ double2 dsm[];
+  __shared__ HeadShared hs;
+  __shared__ double2 s_tau[kMaxBatch];
+  __shared__ unsigned char s_run[kMaxBatch];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double* contrib = reinterpret_cast<double*>(dsm + a.coff);
+  unsigned epoch = 0;
+  int nrun = 0;
+  for (int b = 0; b < a.np; ++b) {
+    const bool r = tri_run(a, b);
+    if (tid == 0) {
+      s_run[b] = r;
+      s_tau[b] = make_double2(0.0, 0.0);
+    }
+    if (r && a.n[b] > nrun) nrun = a.n[b];
+  }
+  __syncthreads();
+  // own columns: column j = conj(row j) of the Hermitian input
+  for (int b = 0; b < a.np; ++b) {
+    if (!s_run[b]) continue;
+    int j0, ns;
+    own_range(a, b, j0, ns);
+    const int n = a.n[b];
+    const double2* A = a.A[b];
+    for (int s = 0; s < ns; ++s) {
+      const int j = j0 + s * (int)gridDim.x;
+      double2* col = own_col(a, b, dsm, j, s);
+      for (int i = tid; i < n; i += nt) {
+        double2 x = A[(size_t)j * n + i];
+        x.y = i == j ? 0.0 : -x.y;
+        col[i] = x;
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = 0; t < nrun; ++t) {
+    for (int b0 = 0; b0 < a.np; b0 += kHeadGroups) tri_heads(a, b0, t, dsm, hs, s_tau, s_run);
+    tri_body(a, t, dsm, contrib, s_run);
+    if (t + 1 < nrun && !grid_barrier(a.bar, epoch, a.status, a.spins)) return;
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    long long k = 0;
+    for (int b = 0; b < a.np; ++b) k += s_run[b];
+    a.stats[6] += k;
+  }
+}
+
+// ---- stage 2: eigenvalues of T -------------------------------------------------
+// Number of eigenvalues of T below x: the sign changes of the Sturm sequence
+// p_0 = 1, p_k = (d_k - x) p_{k-1} - e_{k-1}^2 p_{k-2} (leading minors of
+// T - x I), which equals the number of negative pivots of its LDL^T
+// factorisation.  Every computed p_k is exact for T with d_k - x and e_{k-1}^2
+// perturbed by a few ulps, so the count is backward stable like the pivot
+// recurrence, and needs no division.  The pair (p_k, p_{k-1}) is rescaled by a
+// power of two (exact) whenever it leaves [2^-500, 2^500]; an exact zero p_k
+// takes the sign opposite to p_{k-1}.
+__device__ __forceinline__ int exp_of(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+__device__ __forceinline__ int sturm_count(const double* __restrict__ d,
+                                           const double* __restrict__ e2, int n, double x) {
+  double p2 = 1.0, p1 = __ldg(d) - x;
+  if ((__double_as_longlong(p1) << 1) == 0) p1 = -0x1p-600;
+  long long b1 = __double_as_longlong(p1);
+  int cnt = (int)((unsigned long long)b1 >> 63);
+#pragma unroll 2
+  for (int i = 1; i < n; ++i) {
+    double p = fma(__ldg(d + i) - x, p1, -(__ldg(e2 + i - 1) * p2));
+    long long bp = __double_as_longlong(p);
+    if ((bp << 1) == 0) {                      // exact zero: opposite sign to p_{k-1}
+      p = b1 < 0 ? 0x1p-600 * -p1 : -0x1p-600 * p1;
+      bp = __double_as_longlong(p);
+    }
+    cnt += (int)((unsigned long long)(bp ^ b1) >> 63);
+    p2 = p1;
+    p1 = p;
+    b1 = bp;
+    const int ex = max(exp_of(p1), exp_of(p2));
+    if ((ex > 1023 + 500 && ex < 2047) || ex < 1023 - 500) {
+      const double sc = __longlong_as_double((long long)(2046 - ex) << 52);   // 2^(1023 - ex)
+      p1 *= sc;
+      p2 *= sc;
+      b1 = __double_as_longlong(p1);
+    }
+  }
+  return cnt;
+}
+
+// kBisLanes lanes per eigenvalue; 32-thread blocks spread the work over the SMs.
+__global__ void __launch_bounds__(32) k_tri_bisect(TriBatch a) {
+  constexpr int L = kBisLanes;
+  const int grp = threadIdx.x / L, l = threadIdx.x % L;
+  const unsigned mask = ((1u << L) - 1u) << (grp * L);
+  const int item = blockIdx.x * (32 / L) + grp;
+  if (item >= a.off[a.np]) return;          // whole groups leave together
+  const int b = find_prob(a.off, a.np, item);
+  if (!tri_run(a, b)) return;
+  const int n = a.n[b], j = item - a.off[b];
+  const TriPtrs p = tri_ptrs(a, b);
+  // Gershgorin interval
+  double lo = INFINITY, hi = -INFINITY;
+  for (int i = l; i < n; i += L) {
+    const double r = (i > 0 ? fabs(p.e[i - 1]) : 0.0) + (i < n - 1 ? fabs(p.e[i]) : 0.0);
+    lo = fmin(lo, p.d[i] - r);
+    hi = fmax(hi, p.d[i] + r);
+  }
+#pragma unroll
+  for (int o = 1; o < L; o <<= 1) {
+    lo = fmin(lo, __shfl_xor_sync(mask, lo, o, L));
+    hi = fmax(hi, __shfl_xor_sync(mask, hi, o, L));
+  }
+  const double nrm = fmax(fabs(lo), fabs(hi));
+  const double pad = 2.0 * kEps * nrm + 1e-290;
+  lo -= pad;
+  hi += pad;
+  const double tol = 2.5 * kEps * nrm;
+  for (int round = 0; round < kBisMaxRounds; ++round) {
+    if (!(hi - lo > tol)) break;
+    const double x = lo + (hi - lo) * ((double)(l + 1) / (double)(L + 1));
+    const int cnt = sturm_count(p.d, p.e2, n, x);
+    double nlo = lo, nhi = hi;
+    bool above = false;
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+      const double xk = __shfl_sync(mask, x, k, L);
+      const int ck = __shfl_sync(mask, cnt, k, L);
+      if (!above) {
+        if (ck <= j) nlo = xk;
+        else { nhi = xk; above = true; }
+      }
+    }
+    lo = nlo;
+    hi = nhi;
+  }
+  if (l == 0) {
+    const double lam = 0.5 * (lo + hi);
+    p.lam[j] = lam;
+    a.w[b][j] = lam;
+  }
+}
+
+// ---- stage 3: eigenvectors of T ---------------------------------------------------
+// Uniform in [-1, 1) from (k, i): the splitmix64 finaliser of a Weyl sequence.
+__device__ __forceinline__ double start_entry(unsigned long long k, unsigned long long i) {
+  unsigned long long x = k * 0x9E3779B97F4A7C15ull + (i + 1) * 0xD1B54A32D192ED03ull;
+  x ^= x >> 30; x *= 0xBF58476D1CE4E5B9ull;
+  x ^= x >> 27; x *= 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return (double)(x >> 11) * (1.0 / 4503599627370496.0) - 1.0;
+}
+
+// LU factors with partial pivoting of T - lam I for column k (row stride n):
+// U0 = 1 / (pivot), U1 = first superdiagonal of U, U2 = the multiplier of
+// the row operation, its lowest mantissa bit set when rows i and i+1 were
+// swapped (then U's second superdiagonal is e_{i+1}, else 0).  One
+// reciprocal per row; a zero pivot is replaced by pert.
+__device__ __forceinline__ double pack_piv(double l, bool piv) {
+  return __longlong_as_double((__double_as_longlong(l) & ~1ll) | (long long)piv);
+}
+__device__ __forceinline__ bool piv_of(double l) { return (__double_as_longlong(l) & 1ll) != 0; }
+
+__device__ __forceinline__ void tri_factor(const TriPtrs& p, int n, int k, double lam, double pert) {
+  const size_t sn = (size_t)n;
+  double cur0 = p.d[0] - lam, cur1 = n > 1 ? p.e[0] : 0.0;
+  for (int i = 0; i < n - 1; ++i) {
+    const double sub = p.e[i], nd = p.d[i + 1] - lam;
+    const double nsup = i + 1 < n - 1 ? p.e[i + 1] : 0.0;
+    const bool piv = fabs(sub) > fabs(cur0);
+    const double c0 = cur0 == 0.0 ? pert : cur0;
+    const double r = 1.0 / (piv ? sub : c0);
+    const double l = (piv ? cur0 : sub) * r;
+    const size_t e = (size_t)i * sn + k;
+    p.U0[e] = r;
+    p.U1[e] = piv ? nd : cur1;
+    p.U2[e] = pack_piv(l, piv);
+    const double n0 = piv ? fma(-l, nd, cur1) : fma(-l, cur1, nd);
+    cur1 = piv ? -l * nsup : nsup;
+    cur0 = n0;
+  }
+  p.U0[(size_t)(n - 1) * sn + k] = 1.0 / (cur0 == 0.0 ? pert : cur0);
+}
+
+// y <- (T - lam I)^{-1} y on column k of Y with the stored factors.
+__device__ __forceinline__ void tri_solve(const TriPtrs& p, int n, int k) {
+  double* Y = p.Y;
+  const size_t sn = (size_t)n;
+  double rc = Y[k];
+  for (int i = 0; i < n - 1; ++i) {
+    const size_t e = (size_t)i * sn + k;
+    const double lv = p.U2[e], rn = Y[e + sn];
+    if (piv_of(lv)) {
+      Y[e] = rn;
+      rc = fma(-lv, rn, rc);
+    } else {
+      Y[e] = rc;
+      rc = fma(-lv, rc, rn);
+    }
+  }
+  Y[(size_t)(n - 1) * sn + k] = rc;
+  double y1 = 0.0, y2 = 0.0;                // y[i+1], y[i+2]
+  for (int i = n - 1; i >= 0; --i) {
+    const size_t e = (size_t)i * sn + k;
+    const double u2 = (i + 2 < n && piv_of(p.U2[e])) ? p.e[i + 1] : 0.0;
+    const double yi = (Y[e] - p.U1[e] * y1 - u2 * y2) * p.U0[e];
+    Y[e] = yi;
+    y2 = y1;
+    y1 = yi;
+  }
+}
+
+// One thread per eigenvalue; the first of a cluster does the whole cluster.
+// Blocks of kVecThreads spread the serial work over the SMs.
+__global__ void __launch_bounds__(kVecThreads, 1) k_tri_vectors(TriBatch a) {
+  const int item = blockIdx.x * kVecThreads + threadIdx.x;
+  if (item >= a.off[a.np]) return;
+  const int b = find_prob(a.off, a.np, item);
+  if (!tri_run(a, b)) return;
+  const int n = a.n[b], j = item - a.off[b];
+  const TriPtrs p = tri_ptrs(a, b);
+  const double* lam = p.lam;
+  const double nrm = fmax(fmax(fabs(lam[0]), fabs(lam[n - 1])), 1e-300);
+  const double tight = kTightRel * nrm;
+  if (j > 0 && lam[j] - lam[j - 1] <= tight) return;   // not the first of its cluster
+  int end = j + 1;
+  while (end < n && lam[end] - lam[end - 1] <= tight) ++end;
+  const double pert = kEps * nrm;
+  const size_t sn = (size_t)n;
+  double* Y = p.Y;
+  for (int k = j; k < end; ++k) {
+    for (int i = 0; i < n; ++i) Y[(size_t)i * sn + k] = start_entry((unsigned long long)k, i);
+    tri_factor(p, n, k, lam[k], pert);
+    for (int it = 0; it < kInvIters; ++it) {
+      tri_solve(p, n, k);
+      for (int c = j; c < k; ++c) {          // against the cluster's earlier vectors
+        double dot = 0.0;
+        for (int i = 0; i < n; ++i) dot = fma(Y[(size_t)i * sn + c], Y[(size_t)i * sn + k], dot);
+        for (int i = 0; i < n; ++i) Y[(size_t)i * sn + k] = fma(-dot, Y[(size_t)i * sn + c], Y[(size_t)i * sn + k]);
+      }
+      double s = 0.0;
+      if (it + 1 < kInvIters) {
+        for (int i = 0; i < n; ++i) s = fmax(s, fabs(Y[(size_t)i * sn + k]));
+      } else {
+        for (int i = 0; i < n; ++i) s = fma(Y[(size_t)i * sn + k], Y[(size_t)i * sn + k], s);
+        s = sqrt(s);
+      }
+      if (!(s > 0.0) || !isfinite(s)) {
+        flag_status(a.status, SKY_ENOCONV);
+        s = 1.0;
+      }
+      const double r = 1.0 / s;
+      for (int i = 0; i < n; ++i) Y[(size_t)i * sn + k] *= r;
+    }
+  }
+}
+
+// One first-order Loewdin step on the columns of Y within each eigenvalue's
+// window: Yout[:, j] = Yin[:, j] (3 - G_jj)/2 - sum_{k != j} G_kj Yin[:, k] / 2.
+__global__ void __launch_bounds__(kWinThreads) k_tri_window(TriBatch a, int pass) {
+  __shared__ double gpart[kWinThreads / 32][2 * kWinMax + 1];
+  __shared__ double coef[2 * kWinMax + 1];
+  const int item = blockIdx.x;
+  const int b = find_prob(a.off, a.np, item);
+  if (!tri_run(a, b)) return;
+  const int n = a.n[b], j = item - a.off[b];
+  const TriPtrs p = tri_ptrs(a, b);
+  const double* Yin = pass ? p.Y2 : p.Y;
+  double* Yout = pass ? p.Y : p.Y2;
+  const double* lam = p.lam;
+  const double gw = kWinRel * fmax(fabs(lam[0]), fabs(lam[n - 1]));
+  int lo = j, hi = j;
+  while (lo > 0 && j - lo < kWinMax && lam[j] - lam[lo - 1] <= gw) --lo;
+  while (hi < n - 1 && hi - j < kWinMax && lam[hi + 1] - lam[j] <= gw) ++hi;
+  const int K = hi - lo + 1;
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const size_t sn = (size_t)n;
+  double acc[kWinChunks];
+#pragma unroll
+  for (int c = 0; c < kWinChunks; ++c) acc[c] = 0.0;
+  for (int i = wq; i < n; i += kWinThreads / 32) {
+    const double* row = Yin + (size_t)i * sn;
+    const double yj = row[j];
+#pragma unroll
+    for (int c = 0; c < kWinChunks; ++c) {
+      const int t = lane + 32 * c;
+      if (t < K) acc[c] = fma(row[lo + t], yj, acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kWinChunks; ++c) {
+    const int t = lane + 32 * c;
+    if (t < K) gpart[wq][t] = acc[c];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < K; t += kWinThreads) {
+    double g = gpart[0][t];
+    for (int q = 1; q < kWinThreads / 32; ++q) g += gpart[q][t];
+    coef[t] = (lo + t == j) ? 1.5 - 0.5 * g : -0.5 * g;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += kWinThreads) {
+    const double* row = Yin + (size_t)i * sn + lo;
+    double s = 0.0;
+    for (int t = 0; t < K; ++t) s = fma(coef[t], row[t], s);
+    Yout[(size_t)i * sn + j] = s;
+  }
+}
+
+// ---- back-transformation: Z = H_0 H_1 ... H_{n-2} Y, one warp per column ----------
+__global__ void __launch_bounds__(kBackWarps * 32) k_hh_back(TriBatch a, int zstride) {
+  extern __shared__ double2 dsm[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double2* z = dsm + (size_t)wid * zstride;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  const int total = a.off[a.np];
+  for (int it = wid * gridDim.x + blockIdx.x; it < total; it += nw) {
+    const int b = find_prob(a.off, a.np, it);
+    if (!tri_run(a, b)) continue;
+    const int n = a.n[b], col = it - a.off[b];
+    const TriPtrs p = tri_ptrs(a, b);
+    for (int i = lane; i < n; i += 32) z[i] = make_double2(p.Y[(size_t)i * n + col], 0.0);
+    for (int k = n - 2; k >= 0; --k) {
+      const double2 tau = p.tau[k];
+      if (tau.x == 0.0 && tau.y == 0.0) continue;
+      const double2* v = p.V + (size_t)k * n;
+      const int i0 = ((k + 1) >> 5) * 32 + lane;
+      double sx = 0.0, sy = 0.0;
+      for (int i = i0; i < n; i += 32) {
+        if (i <= k) continue;
+        const double2 vi = v[i], zi = z[i];
+        sx = fma(vi.x, zi.x, fma(vi.y, zi.y, sx));     // conj(v) z
+        sy = fma(vi.x, zi.y, fma(-vi.y, zi.x, sy));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      }
+      const double2 f = cmul(tau, make_double2(sx, sy));
+      for (int i = i0; i < n; i += 32) {
+        if (i <= k) continue;
+        const double2 vi = v[i];
+        double2 zi = z[i];
+        zi.x = fma(-vi.x, f.x, fma(vi.y, f.y, zi.x));     // z -= v f
+        zi.y = fma(-vi.x, f.y, fma(-vi.y, f.x, zi.y));
+        z[i] = zi;
+      }
+    }
+    double2* Z = a.Z[b];
+    for (int i = lane; i < n; i += 32) Z[(size_t)i * n + col] = z[i];
+    __syncwarp();
+  }
+}
+
+__global__ void k_tri_reset(unsigned* bar) { bar[0] = 0u; }
+
+// Shared-memory opt-in of the two kernels that take more than 48 KB (once per
+// context, outside any stream capture).
+sky_status tri_init(Ctx* c) {
+  cudaError_t e = cudaFuncSetAttribute(k_hh_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kTriSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_hh_back, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTriSmemMax);
+  return cuda_check(c, e, "tridiagonal solver attributes");
+}
+
+// One launch sequence for the problems idx[0..np) of a batch (their vectors fit).
+static sky_status tri_group(Ctx* c, int np, const int* idx, const double2* const* A, const int* n,
+                            double* const* w, double2* const* Z, const int* run, int run_stride) {
+  TriBatch a;
+  a.np = np;
+  a.off[0] = 0;
+  long long ntot = 0;
+  int nmax = 1;
+  for (int q = 0; q < np; ++q) {
+    const int b = idx[q];
+    a.A[q] = A[b]; a.w[q] = w[b]; a.Z[q] = Z[b]; a.n[q] = n[b]; a.sid[q] = b;
+    a.off[q + 1] = a.off[q] + n[b];
+    ntot += n[b];
+    if (n[b] > nmax) nmax = n[b];
+  }
+  if (ntot == 0) return SKY_OK;
+  const int G = (int)(ntot < c->num_sms ? ntot : c->num_sms);
+  // shared memory: three work vectors per problem, then own columns while they fit
+  size_t used = 0;
+  int maxown = 0;
+  for (int q = 0; q < np; ++q) {
+    a.voff[q] = (int)used;
+    used += 3 * (size_t)a.n[q];
+    maxown += (a.n[q] + G - 1) / G;
+  }
+  a.coff = (int)used;
+  used += (size_t)(maxown + 1) / 2;
+  int rot = 0;
+  for (int q = 0; q < np; ++q) {
+    const size_t need = (size_t)((a.n[q] + G - 1) / G) * a.n[q];
+    if ((used + need) * sizeof(double2) <= kTriSmemMax) {
+      a.soff[q] = (int)used;
+      used += need;
+    } else {
+      a.soff[q] = -1;
+    }
+    a.rot[q] = rot;
+    rot = (rot + a.n[q]) % G;
+  }
+  const int zstride = nmax + (nmax & 1);
+  int back_warps = kBackWarps;
+  while (back_warps > 1 && (size_t)back_warps * zstride * sizeof(double2) > kTriSmemMax) back_warps >>= 1;
+  a.S0 = c->d_eigA[0]; a.S1 = c->d_eigA[1]; a.S2 = c->d_eigV; a.slot = c->eig_slot;
+  a.T = c->d_trid; a.tslot = c->tri_slot; a.m = c->tri_m;
+  a.sp = c->d_eigpart; a.sp_stride = (size_t)2 * c->eig_grid_max;
+  a.run = run; a.run_stride = run_stride;
+  a.bar = c->d_bar; a.status = c->d_status; a.spins = c->wait_spins; a.stats = c->d_stats;
+  // run flags are indexed by the batch position of each problem
+  if (run) {
+    bool ident = true;
+    for (int q = 0; q < np; ++q) ident = ident && idx[q] == q;
+    if (!ident) return SKY_EUNSUPPORTED;
+  }
+  cudaError_t e;
+  k_tri_reset<<<1, 1, 0, c->stream>>>(c->d_bar);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "tridiagonal reset");
+  void* args[] = {&a};
+  note_launch();
+  e = cudaLaunchCooperativeKernel((const void*)k_hh_tridiag, dim3(G), dim3(kTriThreads), args,
+                                  used * sizeof(double2), c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "householder tridiagonalisation");
+  const int per = 32 / kBisLanes;
+  k_tri_bisect<<<div_up(ntot, per), 32, 0, c->stream>>>(a);
+  k_tri_vectors<<<div_up(ntot, kVecThreads), kVecThreads, 0, c->stream>>>(a);
+  k_tri_window<<<(unsigned)ntot, kWinThreads, 0, c->stream>>>(a, 0);
+  k_tri_window<<<(unsigned)ntot, kWinThreads, 0, c->stream>>>(a, 1);
+  // columns spread over all SMs first (consecutive items go to different blocks)
+  const int back_blocks = (int)(ntot < c->num_sms ? ntot : c->num_sms);
+  const int need_warps = (int)div_up(ntot, back_blocks);
+  if (need_warps < back_warps) back_warps = need_warps;
+  k_hh_back<<<back_blocks, back_warps * 32, (size_t)back_warps * zstride * sizeof(double2),
+              c->stream>>>(a, zstride);
+  note_launch(5);
+  return cuda_check(c, cudaGetLastError(), "tridiagonal eigensolver");
+}
+
+// Eigendecomposition of np Hermitian matrices by the tridiagonal route, in
+// groups whose work vectors fit in shared memory (problems of one group share
+// every launch).  Returns SKY_EUNSUPPORTED, with nothing enqueued, when a
+// single problem's vectors do not fit (or a device-gated batch would need more
+// than one group); the caller then uses the Jacobi solver.
+sky_status eigh_batch_tri(Ctx* c, int np, const double2* const* A, const int* n,
+                          double* const* w, double2* const* Z, const int* run, int run_stride) {
+  int groups[kMaxBatch + 1], order[kMaxBatch];
+  int ng = 0;
+  size_t used = 0;
+  groups[0] = 0;
+  for (int b = 0; b < np; ++b) {
+    const size_t need = (3 * (size_t)n[b] + (n[b] + 1) / 2 + 1) * sizeof(double2);
+    const size_t zneed = (size_t)(n[b] + (n[b] & 1)) * sizeof(double2);
+    if (need > kTriSmemMax || zneed > kTriSmemMax) return SKY_EUNSUPPORTED;
+    if (used + need > kTriSmemMax) {
+      groups[++ng] = b;
+      used = 0;
+    }
+    used += need;
+    order[b] = b;
+  }
+  groups[++ng] = np;
+  if (run && ng > 1) return SKY_EUNSUPPORTED;
+  for (int g = 0; g < ng; ++g) {
+    const sky_status s = tri_group(c, groups[g + 1] - groups[g], order + groups[g], A, n, w, Z,
+                                   run, run_stride);
+    if (s != SKY_OK) return s;
+  }
+  return SKY_OK;
+}
+
+}  // namespace sky

@@ -78,7 +78,7 @@ static void free_all(Ctx* c) {
                   c->d_small[3], c->d_small[4], c->d_small[5], c->d_gate,
                   c->d_stats, c->d_tcA[0], c->d_tcA[1], c->d_tcA[2], c->d_tcB[0],
                   c->d_tcB[1], c->d_tcB[2], c->d_tcRotA[0], c->d_tcRotA[1], c->d_tcRotA[2],
-                  c->d_tcPart, c->d_netpart};
+                  c->d_tcPart, c->d_netpart, c->d_trid};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -187,6 +187,7 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   c->tc_waves = 2;
   c->wait_spins = kBarrierSpins;
   c->jac_max_sweeps = kJacMaxSweeps;
+  c->eig_method = SKY_EIG_AUTO;
   size_t gpart = 0;
   for (int I = 1; I <= Imax; ++I) {   // room for the largest tunable split count
     const size_t need = overlap_partial_elems(I, V, kMaxOverlapWaves * c->ov_slots);
@@ -233,6 +234,9 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
     c->d_eigrot = p;
   }
   for (int k = 0; k < 6; ++k) ALLOC(c->d_small[k], c->small_slot * c->eig_batch);
+  c->tri_m = m;
+  c->tri_slot = tri_slot_doubles(m);
+  ALLOC(c->d_trid, c->tri_slot * c->eig_batch);
   ALLOC(c->d_gate, 8 * kMaxBatch);
   if (s == SKY_OK && is_tc(prec)) s = alloc_tc_scratch(c, tc_nsplit(prec));
   ALLOC(c->d_stats, 8);
@@ -267,6 +271,7 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   if (s == SKY_OK) s = cuda_check(c, cudaMemset(c->d_status, 0, sizeof(int)), "status reset");
   if (s == SKY_OK) s = cuda_check(c, cudaMemset(c->d_stats, 0, 8 * sizeof(long long)), "stats reset");
   if (s == SKY_OK) s = cuda_check(c, cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned)), "barrier reset");
+  if (s == SKY_OK) s = tri_init(c);
   if (s == SKY_OK) s = upload_twiddles_hamiltonian(c);
   if (s == SKY_OK) s = upload_twiddles_fields(c);
   if (s == SKY_OK) s = build_coulomb_table(c);
@@ -500,6 +505,10 @@ sky_status sky_tune_set(sky_ctx* c, sky_knob knob, int value) {
       if (value < 1 || value > 1000) break;
       c->jac_max_sweeps = value;
       return SKY_OK;
+    case SKY_KNOB_EIGEN_METHOD:
+      if (value != SKY_EIG_AUTO && value != SKY_EIG_JACOBI && value != SKY_EIG_TRIDIAGONAL) break;
+      c->eig_method = value;
+      return SKY_OK;
     default:
       return set_err(c, SKY_EINVAL, "unknown knob %d", (int)knob);
   }
@@ -517,6 +526,7 @@ int sky_tune_get(const sky_ctx* c, sky_knob knob) {
     case SKY_KNOB_JACOBI_BLOCKS_MAX: return c->eig_grid_max;
     case SKY_KNOB_WAIT_SPINS: return (int)(c->wait_spins / 1000);
     case SKY_KNOB_JACOBI_MAX_SWEEPS: return c->jac_max_sweeps;
+    case SKY_KNOB_EIGEN_METHOD: return c->eig_method;
     default: return -1;
   }
 }
@@ -536,19 +546,23 @@ sky_status sky_reserve_batch(sky_ctx* c, int nb) {
   if (s == SKY_OK) s = dalloc(c, &w, (2 * c->eig_slot_rot + 2) * nb);
   if (s == SKY_OK) s = dalloc(c, &rot, jacobi_rot_bytes(m) * nb);
   for (int k = 0; k < 6 && s == SKY_OK; ++k) s = dalloc(c, &sm[k], c->small_slot * nb);
+  double* trid = nullptr;
+  if (s == SKY_OK) s = dalloc(c, &trid, c->tri_slot * nb);
   if (s != SKY_OK) {
-    void* ptrs[] = {a0, a1, v, w, rot, sm[0], sm[1], sm[2], sm[3], sm[4], sm[5]};
+    void* ptrs[] = {a0, a1, v, w, rot, sm[0], sm[1], sm[2], sm[3], sm[4], sm[5], trid};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     return s;
   }
   cudaStreamSynchronize(c->stream);   // no queued work may still use the old buffers
   void* old[] = {c->d_eigA[0], c->d_eigA[1], c->d_eigV, c->d_eigw, c->d_eigrot, c->d_small[0],
-                 c->d_small[1], c->d_small[2], c->d_small[3], c->d_small[4], c->d_small[5]};
+                 c->d_small[1], c->d_small[2], c->d_small[3], c->d_small[4], c->d_small[5],
+                 c->d_trid};
   for (void* p : old)
     if (p) cudaFree(p);
   c->d_eigA[0] = a0; c->d_eigA[1] = a1; c->d_eigV = v; c->d_eigw = w; c->d_eigrot = rot;
   for (int k = 0; k < 6; ++k) c->d_small[k] = sm[k];
+  c->d_trid = trid;
   c->eig_batch = nb;
   return SKY_OK;
 }

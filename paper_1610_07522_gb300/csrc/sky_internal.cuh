@@ -120,6 +120,10 @@ struct Ctx {
   int* d_gate;                      // device-side gates of the Loewdin paths [8]
   long long* d_stats;               // solver counters reported by sky_stats [8]
   double* d_netpart;                // partial sums of the damping-network kernels
+  int eig_method;                   // SKY_EIG_AUTO / SKY_EIG_JACOBI / SKY_EIG_TRIDIAGONAL
+  double* d_trid;                   // tridiagonal solver vectors and LU rows [tri_slot] per problem
+  size_t tri_slot;                  // doubles per problem in d_trid
+  int tri_m;                        // vector stride inside a d_trid slot (even)
   char err[256];
 };
 
@@ -188,6 +192,10 @@ sky_status subspace_batch(Ctx* c, int np, const double2* const* H, const double2
 sky_status subspace_literal_batch(Ctx* c, int np, const double2* const* H,
                                   const double2* const* C, const int* I, double2* const* M,
                                   double* const* eps);
+sky_status eigh_batch_tri(Ctx* c, int np, const double2* const* A, const int* n,
+                          double* const* w, double2* const* Z, const int* run, int run_stride);
+sky_status tri_init(Ctx* c);
+inline size_t tri_slot_doubles(int m) { return (size_t)m * m + 16 * (size_t)m; }
 sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z,
                      const int* run = nullptr);
 sky_status lowdin_impl(Ctx* c, const double2* S, int I, double2* C);

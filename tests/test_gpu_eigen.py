@@ -1,0 +1,168 @@
+"""The two FP64 eigensolvers behind every diagonalisation (GPU): the parallel
+cyclic Jacobi method and the tridiagonal route (Householder reduction to real
+tridiagonal form, Sturm bisection, inverse iteration, back-transformation),
+selected with SKY_KNOB_EIGEN_METHOD.  Each is driven through
+sky_subspace_diag with C = I (so H' = H and M holds the eigenvectors) on
+seeded Hermitian matrices with random, near-degenerate (pairs split by
+1e-12..1e-3, as Kramers pairs are near convergence) and exactly degenerate
+spectra, and compared with the oracle's Rayleigh-Ritz (Sec. 3.3.2):
+eigenvalues, orthonormality, residuals and, where the eigenvalue is isolated,
+the eigenvector itself up to its phase."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_1610_07522_gb300 import binding as B
+from paper_1610_07522_gb300 import inputs as IN
+
+pytestmark = pytest.mark.gpu
+
+METHODS = {"jacobi": B.SKY_EIG_JACOBI, "tridiagonal": B.SKY_EIG_TRIDIAGONAL}
+
+
+def _ctx(nmax):
+    return B.sky_init((8, 8, 8), (1.0, 1.0, 1.0), dict(IN.SLY4), True, (0.0, 0.0, 0.0),
+                      B.SKY_F64, nmax, torch.cuda.current_stream().cuda_stream)
+
+
+def _unitary(rng, n):
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    return q
+
+
+def _matrix(kind, n, rng):
+    if kind == "random":
+        a = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        return 10.0 * (a + a.conj().T)
+    U = _unitary(rng, n)
+    c = np.sort(rng.uniform(-60.0, 40.0, (n + 1) // 2))
+    if kind == "pairs":
+        sp = 10.0 ** rng.uniform(-12.0, -3.0, c.size)
+        ev = np.concatenate([c - sp / 2, c + sp / 2])[:n]
+    else:   # exactly degenerate: pairs and a 4-fold level
+        ev = np.repeat(c, 2)[:n]
+        ev[: min(4, n)] = c[0]
+    H = (U * ev) @ U.conj().T
+    return 0.5 * (H + H.conj().T)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def _solve(ctx, H):
+    n = H.shape[0]
+    C = _dev(np.eye(n, dtype=np.complex128))
+    M = torch.zeros((n, n), dtype=torch.complex128, device="cuda:0")
+    lam = torch.zeros(n, dtype=torch.float64, device="cuda:0")
+    B.sky_subspace_diag(ctx, _dev(H), C, n, M, lam)
+    B.sky_sync(ctx)
+    return M.cpu().numpy(), lam.cpu().numpy()
+
+
+def _check(H, M, lam, label):
+    n = H.shape[0]
+    Mw, lw = O.rayleigh_ritz(np.eye(n, dtype=np.complex128), H)
+    nrm = max(1.0, float(np.max(np.abs(lw))))
+    de = float(np.max(np.abs(lam - lw)))
+    orth = float(np.max(np.abs(M.conj().T @ M - np.eye(n))))
+    res = float(np.max(np.abs(H @ M - M * lam)))
+    print(f"{label}: |d lambda| {de:.1e}, ||M^H M - I|| {orth:.1e}, residual {res:.1e} (||H|| {nrm:.0f})")
+    assert de < 1e-12 * nrm * max(1, n // 100)
+    assert orth < 1e-12
+    assert res < 1e-12 * nrm
+    gaps = np.minimum(np.diff(lw, prepend=-np.inf), np.diff(lw, append=np.inf))
+    for j in np.flatnonzero(gaps > 1e-6 * nrm):
+        k = int(np.argmax(np.abs(Mw[:, j])))
+        ph = M[k, j] / Mw[k, j]
+        assert abs(abs(ph) - 1.0) < 1e-8
+        assert np.max(np.abs(M[:, j] - ph * Mw[:, j])) < 1e-8
+
+
+@pytest.mark.parametrize("method", list(METHODS))
+@pytest.mark.parametrize("kind", ["random", "pairs", "degenerate"])
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 64, 130, 300])
+def test_eigensolver_against_oracle(method, kind, n):
+    rng = np.random.default_rng(1000 * n + len(kind))
+    H = _matrix(kind, n, rng)
+    c = _ctx(max(n, 2))
+    B.sky_tune_set(c, B.SKY_KNOB_EIGEN_METHOD, METHODS[method])
+    B.sky_stats(c, reset=True)
+    M, lam = _solve(c, H)
+    st = B.sky_stats(c)
+    B.sky_destroy(c)
+    if method == "tridiagonal":
+        assert st["tridiagonal_solves"] == 1 and st["jacobi_solves"] == 0
+    else:
+        assert st["jacobi_solves"] == 1 and st["tridiagonal_solves"] == 0
+    _check(H, M, lam, f"{method} {kind} n={n}")
+
+
+def test_auto_method_picks_the_tridiagonal_route_for_large_problems():
+    rng = np.random.default_rng(5)
+    c = _ctx(96)
+    assert B.sky_tune_get(c, B.SKY_KNOB_EIGEN_METHOD) == B.SKY_EIG_AUTO
+    B.sky_stats(c, reset=True)
+    _solve(c, _matrix("random", 40, rng))
+    _solve(c, _matrix("random", 96, rng))
+    st = B.sky_stats(c)
+    B.sky_destroy(c)
+    assert st["jacobi_solves"] == 1 and st["tridiagonal_solves"] == 1
+
+
+def test_batched_tridiagonal_route_uneven_sizes():
+    """Two problems of different sizes (the neutron / proton pair of one box)
+    in one batched launch sequence, each against the oracle."""
+    rng = np.random.default_rng(9)
+    sizes = [300, 130]
+    Hs = [_matrix("pairs", sizes[0], rng), _matrix("random", sizes[1], rng)]
+    c = _ctx(300)
+    B.sky_tune_set(c, B.SKY_KNOB_EIGEN_METHOD, B.SKY_EIG_TRIDIAGONAL)
+    dH = [_dev(h) for h in Hs]
+    dC = [_dev(np.eye(n, dtype=np.complex128)) for n in sizes]
+    M = [torch.zeros((n, n), dtype=torch.complex128, device="cuda:0") for n in sizes]
+    lam = [torch.zeros(n, dtype=torch.float64, device="cuda:0") for n in sizes]
+    B.sky_subspace_diag_batched(c, dH, dC, sizes, M, lam)
+    B.sky_sync(c)
+    B.sky_destroy(c)
+    for b in range(2):
+        _check(Hs[b], M[b].cpu().numpy(), lam[b].cpu().numpy(), f"batched b={b} n={sizes[b]}")
+
+
+def test_loewdin_eigen_route_by_tridiagonal_solver():
+    """An overlap far from the identity (S^{-1/2} from the eigendecomposition,
+    Eq. Loewedin) at a size the tridiagonal route serves."""
+    rng = np.random.default_rng(13)
+    n = 150
+    a = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    S = 3.0 * np.eye(n) + (a @ a.conj().T) / n
+    c = _ctx(n)
+    B.sky_stats(c, reset=True)
+    C = torch.zeros((n, n), dtype=torch.complex128, device="cuda:0")
+    B.sky_orthonormalize(c, _dev(S), n, C)
+    B.sky_sync(c)
+    st = B.sky_stats(c)
+    B.sky_destroy(c)
+    Cg = C.cpu().numpy()
+    assert st["loewdin_newton_schulz"] == 0 and st["tridiagonal_solves"] == 1
+    Cw = O.loewdin(S)
+    assert np.max(np.abs(Cg - Cw)) / np.max(np.abs(Cw)) < 1e-11
+    assert np.max(np.abs(Cg.conj().T @ S @ Cg - np.eye(n))) < 1e-11
+
+
+def test_tridiagonal_wait_budget_runs_out_with_etimeout_and_recovers():
+    rng = np.random.default_rng(17)
+    H = _matrix("random", 96, rng)
+    c = _ctx(96)
+    B.sky_tune_set(c, B.SKY_KNOB_EIGEN_METHOD, B.SKY_EIG_TRIDIAGONAL)
+    default = B.sky_tune_get(c, B.SKY_KNOB_WAIT_SPINS)
+    B.sky_tune_set(c, B.SKY_KNOB_WAIT_SPINS, 0)
+    with pytest.raises(B.SkyError) as ei:
+        _solve(c, H)
+    assert ei.value.status == B.SKY_ETIMEOUT
+    B.sky_tune_set(c, B.SKY_KNOB_WAIT_SPINS, default)
+    M, lam = _solve(c, H)
+    B.sky_destroy(c)
+    _check(H, M, lam, "tridiagonal after a timeout")
