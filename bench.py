@@ -30,6 +30,7 @@ if ROOT not in sys.path:
 WORKLOAD = "sly4_24cubed_280n120p_coulomb_fp64"
 FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of GB300 (CUDA cores; FP64 tensor is no faster)
 FORMS = {"fp64": 0, "f32": 1, "bf16x3": 2, "bf16x6": 3}     # sky_prec values
+EIGEN = {"auto": 0, "jacobi": 1, "tridiagonal": 2}        # SKY_KNOB_EIGEN_METHOD values
 DTYPES = {"fp64": "f64", "f32": "f32", "bf16x3": "f32+bf16x3", "bf16x6": "f32+bf16x6"}
 
 
@@ -449,6 +450,7 @@ def run_gpu(args):
     # neutrons and protons on separate contexts and streams (bit-identical to one
     # stream; the single-stream step is reported beside it)
     s = Solver(w, prec=prec, device=dev, concurrent_species=True)
+    s.set_eigen_method(EIGEN[args.eigen])
     s.load(inp["psi0"], inp.get("rho0"), inp.get("tau0"))
     units = 2 * (w.N + w.Z)
 
@@ -514,6 +516,7 @@ def run_gpu(args):
 
     # the same step with both species on one context and stream
     sc = Solver(w, prec=prec, device=dev)
+    sc.set_eigen_method(EIGEN[args.eigen])
     sc.load(inp["psi0"], inp.get("rho0"), inp.get("tau0"))
     for _ in range(args.warmup):
         sc.step()
@@ -568,6 +571,7 @@ def run_gpu(args):
         "dtype": DTYPES[args.form], "data": "synthetic",
         "config": {"workload": args.workload, "grid": list(w.grid), "dx_fm": list(w.dx),
                    "N": w.N, "Z": w.Z, "coulomb": w.coulomb, "precision": args.form,
+                   "eigensolver": args.eigen,
                    "parallelism": f"replicas x{ws}",
                    "l2": f"working set (psi, phi, h psi: {3 * s.psi[0].element_size() * V * (w.N + w.Z) / 1e9:.2f} GB) exceeds L2 (129 MB), no flush"},
         "roofline": roof,
@@ -605,6 +609,9 @@ def main():
                     help="skip the 64-box batched (CUDA graph) form")
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the time-to-convergence comparison of the forms")
+    ap.add_argument("--eigen", default="auto", choices=sorted(EIGEN),
+                    help="FP64 eigensolver of the timed steps (auto: tridiagonal route for "
+                         "large species, batched Jacobi for many small problems)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -1,8 +1,10 @@
 // FP64 Hermitian eigensolver for steps 3b-3c (Sec. 3.3.2) and the Loewdin /
 // Rayleigh-Ritz factors built on it.
 //
-// The paper diagonalises with ScaLAPACK's tridiagonal + MRRR solver.  Here
-// the solver is a parallel cyclic Jacobi method: in each round the indices
+// The paper diagonalises with ScaLAPACK's tridiagonal + MRRR solver; its
+// GPU counterpart is in eigen_tridiag.cu, and eigh_batch below picks between
+// it and the solver of this file, a parallel cyclic Jacobi method (one launch
+// for a whole batch of small problems): in each round the indices
 // are paired by a round-robin tournament, every pair (p, q) gets the 2x2
 // unitary J = D R (D removes the phase of A_pq, R is the real Jacobi
 // rotation), and all (I/2)^2 2x2 blocks are updated at once as

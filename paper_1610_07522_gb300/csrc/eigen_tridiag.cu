@@ -184,8 +184,10 @@ __device__ void tri_heads(const TriBatch& a, int b0, int t, double2* dsm, HeadSh
       const double2* Pp = ((t - 1) & 1) ? p.P1 : p.P0;
       const double2* Cp = ((t - 1) & 1) ? p.C1 : p.C0;
       for (int i = t + ht; i < n; i += kHeadThreads) {
-        w[i] = __ldcg(Pp + i);
+        const double2 x = __ldcg(Pp + i);
+        w[i] = x;
         vn[i] = __ldcg(Cp + i);            // the column after step t-2's update, for now
+        if (i == t) hs.sc[q][0] = x;       // p_{t-1}[t], for w_t in every thread
       }
       if (hwarp == 0) {
         const double* ps = sp_row(a, b, t - 1);
@@ -200,21 +202,20 @@ __device__ void tri_heads(const TriBatch& a, int b0, int t, double2* dsm, HeadSh
     }
     __syncthreads();
     if (on) {
+      // w = tau p - c v_{t-1}; w_t (v_{t-1}[t] = 1) the same bits in every thread;
+      // then column t = Cb - v_{t-1} conj(w_t) - w
       const double c = hs.red[q][kHeadWarps];
       const double2 tau = s_tau[b];
+      const double2 pt = hs.sc[q][0], vt = vo[t];
+      const double2 wt = make_double2(fma(tau.x, pt.x, fma(-tau.y, pt.y, -c * vt.x)),
+                                      fma(tau.x, pt.y, fma(tau.y, pt.x, -c * vt.y)));
       for (int i = t + ht; i < n; i += kHeadThreads) {
-        const double2 x = w[i], v = vo[i];
-        w[i] = make_double2(fma(tau.x, x.x, fma(-tau.y, x.y, -c * v.x)),
-                            fma(tau.x, x.y, fma(tau.y, x.x, -c * v.y)));
-      }
-    }
-    __syncthreads();
-    if (on) {
-      const double2 wt = w[t];             // v_{t-1}[t] = 1; col = Cb - v conj(w_t) - w
-      for (int i = t + ht; i < n; i += kHeadThreads) {
-        const double2 cb = vn[i], v = vo[i], x = w[i];
-        const double2 y = make_double2(fma(-v.x, wt.x, fma(-v.y, wt.y, cb.x - x.x)),
-                                       fma(-v.y, wt.x, fma(v.x, wt.y, cb.y - x.y)));
+        const double2 x = w[i], v = vo[i], cb = vn[i];
+        const double2 u = make_double2(fma(tau.x, x.x, fma(-tau.y, x.y, -c * v.x)),
+                                       fma(tau.x, x.y, fma(tau.y, x.x, -c * v.y)));
+        w[i] = u;
+        const double2 y = make_double2(fma(-v.x, wt.x, fma(-v.y, wt.y, cb.x - u.x)),
+                                       fma(-v.y, wt.x, fma(v.x, wt.y, cb.y - u.y)));
         vn[i] = y;
         if (i >= t + 2) sg = fma(y.x, y.x, fma(y.y, y.y, sg));
       }

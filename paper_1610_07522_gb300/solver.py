@@ -234,6 +234,12 @@ class Solver:
             B.sky_set_prec(self.ctxq[1], prec)
         self.prec = prec
 
+    def set_eigen_method(self, method):
+        """Choose the FP64 eigensolver of the diagonalisations
+        (B.SKY_EIG_AUTO, B.SKY_EIG_JACOBI or B.SKY_EIG_TRIDIAGONAL)."""
+        for c in {id(x): x for x in self.ctxq}.values():
+            B.sky_tune_set(c, B.SKY_KNOB_EIGEN_METHOD, method)
+
     def run(self, maxit=None, tol=None, callback=None, window=1, escalate=None):
         """Iterate until |E_n/A - E_{n-1}/A| < tol for ``window`` consecutive
         iterations (1: the plain rule) or maxit; returns (history, converged).

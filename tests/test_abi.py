@@ -80,3 +80,33 @@ def test_binding_net_constants_match_header():
     assert binding.SKY_NET_NPARAM == P.NPARAM
     assert binding.SKY_NET_WMAX == P.WMAX and binding.SKY_NET_HIDDEN == P.HIDDEN
     assert binding.SKY_NET_USCALE == P.U_SCALE and binding.SKY_NET_WSCALE == P.W_SCALE
+
+
+def test_binding_eigen_knob_matches_header():
+    from paper_1610_07522_gb300 import binding
+    src = open(os.path.join(ROOT, "include", "sky.h")).read()
+    assert re.search(r"SKY_KNOB_EIGEN_METHOD\s*=\s*(\d+)", src).group(1) == str(binding.SKY_KNOB_EIGEN_METHOD)
+    enum = re.search(r"enum\s*\{\s*SKY_EIG_AUTO\s*=\s*(\d+),\s*SKY_EIG_JACOBI\s*=\s*(\d+),\s*"
+                     r"SKY_EIG_TRIDIAGONAL\s*=\s*(\d+)\s*\}", src)
+    assert tuple(int(x) for x in enum.groups()) == (binding.SKY_EIG_AUTO, binding.SKY_EIG_JACOBI,
+                                                     binding.SKY_EIG_TRIDIAGONAL)
+
+
+def test_solver_eigen_method_sets_every_context(monkeypatch):
+    """Solver.set_eigen_method and bench.py --eigen set the knob once on each
+    distinct context (host logic only: the contexts are stand-ins)."""
+    from paper_1610_07522_gb300 import binding
+    from paper_1610_07522_gb300.solver import Solver
+    import bench
+    calls = []
+    monkeypatch.setattr(binding, "sky_tune_set", lambda c, k, v: calls.append((c, k, v)))
+    s = object.__new__(Solver)
+    a, b = object(), object()
+    for ctxq, want in (([a, a], [a]), ([a, b], [a, b])):
+        calls.clear()
+        s.ctxq = ctxq
+        s.set_eigen_method(bench.EIGEN["jacobi"])
+        assert [c for c, _, _ in calls] == want
+        assert all(k == binding.SKY_KNOB_EIGEN_METHOD and v == binding.SKY_EIG_JACOBI for _, k, v in calls)
+    assert bench.EIGEN == {"auto": binding.SKY_EIG_AUTO, "jacobi": binding.SKY_EIG_JACOBI,
+                           "tridiagonal": binding.SKY_EIG_TRIDIAGONAL}
