@@ -182,7 +182,7 @@ sky_status sky_subspace_diag_literal_batched(sky_ctx* ctx, int nb, const double*
 
 /* Raise the batch capacity of the batched calls to nb problems of up to
  * max_states each (1 <= nb <= 128).  Allocates device memory (about
- * 13 max_states^2 complex doubles per problem) and synchronises the context
+ * 9.5 max_states^2 complex doubles per problem) and synchronises the context
  * stream; call it outside stream capture.  SKY_ENOMEM leaves the context as
  * it was. */
 sky_status sky_reserve_batch(sky_ctx* ctx, int nb);

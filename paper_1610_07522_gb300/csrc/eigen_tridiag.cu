@@ -8,28 +8,29 @@
 //  1. k_hh_tridiag: A = Q T Q^H with Q = H_0 H_1 ... H_{n-2}, each reflector
 //     H_t = I - tau_t v_t v_t^H chosen so that H_t^H maps column t below the
 //     diagonal onto beta_t e_1 with beta_t real (T is real symmetric).  One
-//     cooperative kernel: block g keeps the columns j = g, g + G, ... of the
-//     (full, Hermitian) trailing matrix in shared memory.  The update by H_t is
+//     cooperative kernel: the blocks keep the columns of the (full, Hermitian)
+//     trailing matrix cyclically in shared memory.  The update by H_t is
 //     A <- A - v w^H - w v^H with p = A v, w = tau p - (|tau|^2 v^H p / 2) v.
 //     Each owner forms p_j = col_j^H v_t for its own columns, fused with that
-//     column's update by the previous reflector, and publishes p and the next
-//     column; after one grid barrier every block recomputes the next column
-//     and reflector itself (the same arithmetic in every block), so each step
-//     costs one barrier.
+//     column's update by the previous reflector, and publishes p, the next
+//     column and its block's partial of v^H p; after one grid barrier every
+//     block recomputes the next column and reflector itself (the same
+//     arithmetic in every block), so each step costs one barrier.  The heads
+//     of up to four problems run side by side on separate warp groups.
 //  2. k_tri_bisect: eigenvalues of T by Sturm-count multisection (sign
 //     changes of the leading minors of T - x I, no divisions), kBisLanes
 //     points per eigenvalue and round.
 //  3. k_tri_vectors: eigenvectors of T by inverse iteration (Gaussian
 //     elimination with partial pivoting of T - lambda I, factored once, then
 //     kInvIters solves from a counter-based random start); eigenvalues closer
-//     than kTightRel ||T||
-//     are handled by one thread in order, each new vector orthogonalised
-//     against the cluster's earlier ones after every solve (as LAPACK's
-//     dstein does).  k_tri_window then applies first-order Loewdin steps
-//     Y <- Y (3 I - Y^T Y) / 2, with Y^T Y formed only between eigenvalues
-//     within kWinRel ||T|| of each other (the inverse-iteration vectors'
-//     mutual overlaps fall off like eps ||T|| / gap).  k_hh_back forms
-//     Z = Q Y, one warp per column, the reflectors applied in reverse order.
+//     than kTightRel ||T|| are handled by one thread in order, each new vector
+//     orthogonalised against the cluster's earlier ones after every solve (as
+//     LAPACK's dstein does).  k_tri_window then applies first-order Loewdin
+//     steps Y <- Y (3 I - Y^T Y) / 2, with Y^T Y formed only between
+//     eigenvalues within kWinRel ||T|| of each other (the inverse-iteration
+//     vectors' mutual overlaps fall off like eps ||T|| / gap).  k_hh_back
+//     forms Z = Q Y, one warp per column, the reflectors applied in reverse
+//     order.
 //
 // Eigenvalues come out ascending, eigenvectors as the columns of Z.
 #include "eig_common.cuh"
