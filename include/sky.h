@@ -262,6 +262,16 @@ sky_status sky_set_prec(sky_ctx* ctx, sky_prec prec);
  *                           tridiagonal for batches of at most 8 problems of 64 states or
  *                           more, Jacobi otherwise; the tridiagonal route falls back to
  *                           Jacobi when its work vectors exceed shared memory)
+ *   SKY_KNOB_SPLIT_GEMM     FP64 and FP32 forms: 1 (default) computes sky_overlap and
+ *                           sky_rotate on the tensor cores as exact-integer split products
+ *                           (each row scaled by a power of two and cut into signed 8-bit
+ *                           digits held exactly in bf16: 6 digits and 21 digit products for
+ *                           SKY_F64, 4 and 10 for SKY_F32; every digit product summed
+ *                           exactly in FP32 over segments of 128 values of K, the segments
+ *                           added in pairs of FP32 by error-free transformations), about
+ *                           1e-14 (FP64) and 1e-9 (FP32) of the largest result; 0 runs the
+ *                           FP64 FMA kernels on the CUDA cores.  Switching to 1 may allocate
+ *                           the digit buffers; not allowed for the split-BF16 forms
  * sky_tune_set returns SKY_EINVAL for a value outside these sets; sky_tune_get
  * returns the current value (-1 for an unknown knob or a NULL context). */
 typedef enum {
@@ -273,7 +283,8 @@ typedef enum {
   SKY_KNOB_JACOBI_BLOCKS_MAX = 5,
   SKY_KNOB_WAIT_SPINS = 6,
   SKY_KNOB_JACOBI_MAX_SWEEPS = 7,
-  SKY_KNOB_EIGEN_METHOD = 8
+  SKY_KNOB_EIGEN_METHOD = 8,
+  SKY_KNOB_SPLIT_GEMM = 9
 } sky_knob;
 enum { SKY_EIG_AUTO = 0, SKY_EIG_JACOBI = 1, SKY_EIG_TRIDIAGONAL = 2 };
 sky_status sky_tune_set(sky_ctx* ctx, sky_knob knob, int value);
@@ -350,9 +361,13 @@ sky_status sky_precond_stats(sky_ctx* ctx, const void* psi, const void* phi, con
  * state; dV the volume element; stream a cudaStream_t (NULL = default).
  * Its scratch is one fixed 16 MiB device array inside the library, held by
  * every GPU that loads it until exit; I is limited to 1024 (SKY_EINVAL
- * above).  The first call on a device looks up that array's address and
- * should come before any stream capture.  Calls share the array: calls that
- * overlap in time on the GPU race.  Calls no cudaMalloc or cudaFree. */
+ * above).  Every call looks the array's address up in the CUDA context
+ * current at the call (so a device reset or another context on the device
+ * gets its own copy); the first call in a context loads the library's device
+ * code there and should come before any stream capture.  Calls share the
+ * array: calls that overlap in time on the GPU race.  If a CUDA error is
+ * already pending when the call starts, it returns SKY_ECUDA without work and
+ * leaves that error for the caller.  Calls no cudaMalloc or cudaFree. */
 sky_status sky_overlap_noalloc(const void* a, const void* b, int I, long long V, double dV,
                                sky_prec prec, double* X, void* stream);
 

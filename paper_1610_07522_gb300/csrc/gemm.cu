@@ -2,7 +2,9 @@
 // matrices X = <a|b> (Eqs. normmatrix, hammatrix; lower triangle only, as in
 // Fig. 3), the recombination psi = phi M (Sec. 3.3.3) and small I x I
 // products for the Loewdin and Rayleigh-Ritz factors.  FP64 FMA on the CUDA
-// cores; FP32 spinors are widened on load.
+// cores; FP32 spinors are widened on load.  The FP64 and FP32 forms send the
+// overlap and the recombination to the tensor-core split GEMMs of oz_ops.cu
+// unless SKY_KNOB_SPLIT_GEMM is 0.
 #include "overlap_kernels.cuh"
 
 namespace sky {
@@ -33,6 +35,7 @@ size_t overlap_partial_elems(int I, long long V, int slots) {
 
 sky_status overlap_impl(Ctx* c, const void* a, const void* b, int I, double2* X) {
   if (is_tc(c->prec)) return tc_overlap(c, a, b, I, X);
+  if (c->oz_on) return oz_overlap(c, a, b, I, X);
   const long long V = 2LL * c->G;
   int ntiles;
   const int nsplit = overlap_splits(I, V, c->ov_waves * c->ov_slots, &ntiles);
@@ -162,6 +165,7 @@ __global__ void __launch_bounds__(256) k_rotate(const S* __restrict__ phi, const
 
 sky_status rotate_impl(Ctx* c, const void* phi, const double2* M, int I, void* out) {
   if (is_tc(c->prec)) return tc_rotate(c, phi, M, I, out);
+  if (c->oz_on) return oz_rotate(c, phi, M, I, out);
   const long long V = 2LL * c->G;
   dim3 grid(div_up(V, BN), div_up(I, BM));
   if (c->prec == SKY_F64)

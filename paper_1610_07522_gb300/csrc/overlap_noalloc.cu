@@ -9,12 +9,15 @@
 // (kNoallocElems complex doubles = 16 MiB).  Every GPU that loads the library
 // holds this array until the process exits.  Host code cannot pass the
 // array's name to a kernel (on the host it names a stand-in, not the device
-// address), so the device address is looked up once per device with
-// cudaGetSymbolAddress, with that device current, on the first call made
-// on it; that first call should therefore happen before any stream capture.
-// All calls share the array: calls whose work overlaps on the GPU (for
-// example on two streams at once) race on it.  Each call writes every
-// partial entry it later reads, so nothing has to be cleared between calls.
+// address), and the device address belongs to the CUDA context current at
+// the call (a device reset or another context on the same device gives
+// another address), so every call looks it up with cudaGetSymbolAddress in
+// the current context.  The first call in a context loads the library's
+// device code there and should therefore happen before any stream capture;
+// later lookups are host-side table reads.  All calls share the array: calls
+// whose work overlaps on the GPU (for example on two streams at once) race on
+// it.  Each call writes every partial entry it later reads, so nothing has to
+// be cleared between calls.
 #include <mutex>
 
 #include "overlap_kernels.cuh"
@@ -28,25 +31,18 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double2 g_noalloc_partial[kNoallocElems];
 
-std::mutex g_setup_mutex;
-double2* g_partial_ptr[kMaxDevices] = {};
+std::mutex g_sms_mutex;
 int g_num_sms[kMaxDevices] = {};
 
-// Device address of the scratch array and the SM count of the current device,
-// looked up on the first call on that device.
-cudaError_t device_setup(int dev, double2** ptr, int* sms) {
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_partial_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
-    if (e != cudaSuccess) return e;
+// SM count of device dev (a device property: cached per device number).
+cudaError_t device_sms(int dev, int* sms) {
+  std::lock_guard<std::mutex> lock(g_sms_mutex);
+  if (!g_num_sms[dev]) {
     int n = 0;
-    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    const cudaError_t e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    g_partial_ptr[dev] = static_cast<double2*>(p);
     g_num_sms[dev] = n;
   }
-  *ptr = g_partial_ptr[dev];
   *sms = g_num_sms[dev];
   return cudaSuccess;
 }
@@ -62,15 +58,18 @@ extern "C" sky_status sky_overlap_noalloc(const void* a, const void* b, int I, l
   if (!a || !b || !X || I < 0 || V <= 0) return SKY_EINVAL;
   if (I > kNoallocMaxI) return SKY_EINVAL;   // the partial tile would not fit the scratch
   if (prec != SKY_F64 && prec != SKY_F32) return SKY_EUNSUPPORTED;
+  // an error left pending by the caller's earlier work is not this call's:
+  // leave it for the caller's own checks and do nothing
+  if (cudaPeekAtLastError() != cudaSuccess) return SKY_ECUDA;
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SKY_ECUDA;
-  double2* part = nullptr;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SKY_ECUDA;
   int sms = 0;
-  if (device_setup(dev, &part, &sms) != cudaSuccess) {
-    cudaGetLastError();
+  void* p = nullptr;
+  if (device_sms(dev, &sms) != cudaSuccess || cudaGetSymbolAddress(&p, g_noalloc_partial) != cudaSuccess) {
+    cudaGetLastError();   // the error just raised is this call's own
     return SKY_ECUDA;
   }
+  double2* part = static_cast<double2*>(p);
   const int nt = (I + BM - 1) / BM;
   const int ntiles = nt * (nt + 1) / 2;
   const long long kblocks = (V + BK - 1) / BK;
@@ -88,6 +87,7 @@ extern "C" sky_status sky_overlap_noalloc(const void* a, const void* b, int I, l
   else
     k_overlap<float2><<<grid, 256, 0, s>>>((const float2*)a, (const float2*)b, I, V, kchunk, part);
   note_launch();
+  if (cudaGetLastError() != cudaSuccess) return SKY_ECUDA;
   k_overlap_reduce<<<div_up((long long)I * I, 256), 256, 0, s>>>(part, nsplit_eff, I, dV,
                                                                 (double2*)X);
   note_launch();

@@ -1,0 +1,452 @@
+// FP64 and FP32 forms of the overlap / Hamiltonian matrices (Eqs. normmatrix,
+// hammatrix) and of the recombination psi = phi M (Sec. 3.3.3) on the tensor
+// cores through the exact-integer split GEMM of oz_gemm.cuh.
+//
+// The split kernels work on the bit patterns only (integer exponent, mantissa
+// and shifts; no FP64 arithmetic, which runs at 1/64 of the FP32 rate on this
+// chip): each value x of a row with exponent E (|x| < 2^E over the row) is
+// rounded to the integer X = round(|x| 2^{8S - E}) < 2^{8S} + 1 and written as
+// balanced base-256 digits alpha_0 .. alpha_{S-1} (alpha_0 in [0, 256],
+// the others in [-128, 127]), with the sign of x.
+//
+// Complex contractions are real GEMMs over the interleaved (re, im) storage,
+// as in the split-BF16 forms:
+//   <a|b>:  Re = sum_k a_r[k] b_r[k],  Im = sum_k a_r[k] b'_r[k],
+//           b' = (Im b, -Re b): D = a_r [b_r; b'_r]^T holds Re | Im;
+//   psi_a = sum_b M[b][a] phi_b:  psi_r = [M_re^T | M_im^T] [phi_r; (i phi)_r],
+//           the phi operand transposed (K = state index contiguous), rows v'
+//           of the real view, both halves of K padded to round32(I).
+#include <climits>
+#include <cstdlib>
+
+#include "oz_gemm.cuh"
+
+namespace sky {
+
+namespace {
+
+__device__ __forceinline__ int exp_of(double x) {   // e with |x| < 2^e, INT_MIN for 0
+  const int ef = (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+  return ef == 0 ? INT_MIN : ef - 1022;
+}
+__device__ __forceinline__ int exp_of(float x) {
+  const int ef = (int)((__float_as_uint(x) >> 23) & 0xFF);
+  return ef == 0 ? INT_MIN : ef - 126;
+}
+
+// |x| 2^{8S - E} rounded to an integer (denormals and zero give 0).
+template <int S>
+__device__ __forceinline__ unsigned long long fixed_of(double x, int E) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int ef = (int)((bits >> 52) & 0x7FF);
+  if (ef == 0) return 0ull;
+  const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = ef - 1075 + 8 * S - E;
+  if (sh >= 0) return sh < 11 ? mant << sh : 0ull;   // |x| < 2^E keeps sh < 0 for S <= 6
+  const int r = -sh;
+  if (r >= 64) return 0ull;
+  return (mant + (1ull << (r - 1))) >> r;
+}
+template <int S>
+__device__ __forceinline__ unsigned long long fixed_of(float x, int E) {
+  const unsigned bits = __float_as_uint(x);
+  const int ef = (int)((bits >> 23) & 0xFF);
+  if (ef == 0) return 0ull;
+  const unsigned long long mant = (bits & 0x7FFFFFu) | 0x800000u;
+  const int sh = ef - 150 + 8 * S - E;
+  if (sh >= 0) return sh < 40 ? mant << sh : 0ull;
+  const int r = -sh;
+  if (r >= 64) return 0ull;
+  return (mant + (1ull << (r - 1))) >> r;
+}
+__device__ __forceinline__ bool sign_of(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ bool sign_of(float x) { return (int)__float_as_uint(x) < 0; }
+
+// Balanced base-256 digits of x relative to 2^E, as bf16 bit patterns.
+__device__ __forceinline__ unsigned short bf16_of_int(int d) {   // |d| <= 256: exact
+  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+  return (unsigned short)(__float_as_uint(f) >> 16);
+}
+template <int S, typename R>
+__device__ __forceinline__ void digits(R x, int E, unsigned short* out) {
+  long long X = (long long)fixed_of<S>(x, E);
+  const bool neg = sign_of(x);
+  int d[S];
+#pragma unroll
+  for (int s = S - 1; s >= 1; --s) {
+    int v = (int)(X & 255);
+    X >>= 8;
+    if (v >= 128) { v -= 256; ++X; }
+    d[s] = v;
+  }
+  d[0] = (int)X;
+#pragma unroll
+  for (int s = 0; s < S; ++s) out[s] = bf16_of_int(neg ? -d[s] : d[s]);
+}
+__device__ __forceinline__ unsigned short neg_bf16(unsigned short h) { return h ^ 0x8000u; }
+__device__ __forceinline__ unsigned pack2(unsigned short lo, unsigned short hi) {
+  return (unsigned)lo | ((unsigned)hi << 16);
+}
+
+template <typename R>
+__device__ __forceinline__ int block_max(int v) {
+  __shared__ int red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : INT_MIN;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const int r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// E[r] = exponent bound of row r of a [R][V] complex array (0 for a zero row).
+template <typename T>
+__global__ void __launch_bounds__(256) k_oz_rowexp(const T* __restrict__ src, long long V, int* E) {
+  using R = decltype(T().x);
+  const T* row = src + (long long)blockIdx.x * V;
+  int m = INT_MIN;
+  for (long long k = threadIdx.x; k < V; k += blockDim.x) {
+    const T v = row[k];
+    m = max(m, max(exp_of((R)v.x), exp_of((R)v.y)));
+  }
+  m = block_max<R>(m);
+  if (threadIdx.x == 0) E[blockIdx.x] = m == INT_MIN ? 0 : m;
+}
+
+// Slices of rows [0, R) of a [R][V] complex array over complex columns
+// [c0, c0 + nc): dst[s][r][2 (c - c0) + {0, 1}]; with prime_off >= 0 also
+// rows prime_off + r = (Im, -Re).
+template <typename T, int S>
+__global__ void __launch_bounds__(256) k_oz_split_rows(const T* __restrict__ src, int R, long long V,
+                                                       long long c0, long long nc,
+                                                       const int* __restrict__ E,
+                                                       unsigned short* dst, long long ld,
+                                                       long long ss, int prime_off) {
+  using RT = decltype(T().x);
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)R * nc) return;
+  const int r = (int)(e / nc);
+  const long long c = e - (long long)r * nc;
+  const T v = src[(long long)r * V + c0 + c];
+  const int Er = E[r];
+  unsigned short dr[S], di[S];
+  digits<S>((RT)v.x, Er, dr);
+  digits<S>((RT)v.y, Er, di);
+  unsigned* d32 = reinterpret_cast<unsigned*>(dst);
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    d32[(s * ss + (long long)r * ld) / 2 + c] = pack2(dr[s], di[s]);
+    if (prime_off >= 0)
+      d32[(s * ss + (long long)(prime_off + r) * ld) / 2 + c] = pack2(di[s], neg_bf16(dr[s]));
+  }
+}
+
+// Row operand of the recombination: row a = [Re M[b][a] (b < I) | 0 | Im M[b][a] | 0],
+// halves of Ipad; Ea[a] its exponent.  One block per row a.
+template <int S>
+__global__ void __launch_bounds__(256) k_oz_rot_a(const double2* __restrict__ M, int I, int Ipad,
+                                                  unsigned short* dst, long long ld, long long ss,
+                                                  int* Ea) {
+  const int a = blockIdx.x;
+  int m = INT_MIN;
+  for (int b = threadIdx.x; b < I; b += blockDim.x) {
+    const double2 v = M[(long long)b * I + a];
+    m = max(m, max(exp_of(v.x), exp_of(v.y)));
+  }
+  m = block_max<double>(m);
+  const int E = m == INT_MIN ? 0 : m;
+  if (threadIdx.x == 0) Ea[a] = E;
+  for (int b = threadIdx.x; b < Ipad; b += blockDim.x) {
+    unsigned short dr[S], di[S];
+    const double2 v = b < I ? M[(long long)b * I + a] : make_double2(0.0, 0.0);
+    digits<S>(v.x, E, dr);
+    digits<S>(v.y, E, di);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      dst[s * ss + (long long)a * ld + b] = dr[s];
+      dst[s * ss + (long long)a * ld + Ipad + b] = di[s];
+    }
+  }
+}
+
+// F[v] = exponent bound over the states of entry v (both parts) of [I][V].
+template <typename T>
+__global__ void __launch_bounds__(256) k_oz_colexp(const T* __restrict__ phi, int I, long long V,
+                                                   int* F) {
+  using R = decltype(T().x);
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  int m = INT_MIN;
+  for (int b = 0; b < I; ++b) {
+    const T x = phi[(long long)b * V + v];
+    m = max(m, max(exp_of((R)x.x), exp_of((R)x.y)));
+  }
+  F[v] = m == INT_MIN ? 0 : m;
+}
+
+// Transposed operand of the recombination for complex columns [v0, v0 + nv):
+// rows v' = 2 (v - v0) (+1), K index b' = b (phi_r) and Ipad + b ((i phi)_r):
+//   row 2v:   Re phi_b[v],  -Im phi_b[v];   row 2v+1: Im phi_b[v],  Re phi_b[v];
+// zeros for b in [I, Ipad).  32 states x 32 entries per block through shared
+// memory (coalesced reads along v, writes along b).
+template <typename T, int S>
+__global__ void __launch_bounds__(256) k_oz_split_rot_b(const T* __restrict__ phi, int I, int Ipad,
+                                                        long long V, long long v0, long long nv,
+                                                        const int* __restrict__ F,
+                                                        unsigned short* dst, long long ld,
+                                                        long long ss) {
+  using R = decltype(T().x);
+  __shared__ T t[32][33];
+  const int b0 = blockIdx.y * 32;
+  const long long vb = (long long)blockIdx.x * 32;   // relative to v0
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int b = b0 + r;
+    const long long v = vb + tx;
+    T z;
+    z.x = 0; z.y = 0;
+    t[r][tx] = (b < I && v < nv) ? phi[(long long)b * V + v0 + v] : z;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const long long v = vb + r;   // entry handled by this warp; lanes run over states
+    if (v >= nv) continue;
+    const int b = b0 + tx;
+    const T x = t[tx][r];
+    const int Fv = F[v0 + v];
+    unsigned short dr[S], di[S];
+    digits<S>((R)x.x, Fv, dr);
+    digits<S>((R)x.y, Fv, di);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      unsigned short* row0 = dst + s * ss + (2 * v) * ld;
+      unsigned short* row1 = row0 + ld;
+      row0[b] = dr[s];
+      row0[Ipad + b] = neg_bf16(di[s]);
+      row1[b] = di[s];
+      row1[Ipad + b] = dr[s];
+    }
+  }
+}
+
+// X[a][b] (+)= dV 2^{Ea[a] + Eb[b] - 16} sum_z (P_z[a][b] + i P_z[a][I + b]) for a >= b
+// (each P entry an unevaluated pair hi + lo), mirrored.
+__global__ void k_oz_overlap_reduce(const float2* __restrict__ P, int nz, long long sp,
+                                    long long ldp, int I, const int* __restrict__ Ea,
+                                    const int* __restrict__ Eb, double dV, double2* X,
+                                    int accumulate) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)I * I) return;
+  const int a = (int)(e / I), b = (int)(e % I);
+  if (a < b) return;
+  double re = 0.0, im = 0.0;
+  for (int z = 0; z < nz; ++z) {
+    const float2* Pz = P + z * sp + (long long)a * ldp;
+    const float2 r = Pz[b], i = Pz[I + b];
+    re += (double)r.x + (double)r.y;
+    im += (double)i.x + (double)i.y;
+  }
+  const double sc = dV * oz::pow2d(Ea[a] + Eb[b] - 16);
+  double2 s = make_double2(sc * re, sc * im);
+  if (accumulate) s = s + X[(long long)a * I + b];
+  X[(long long)a * I + b] = s;
+  if (a != b) X[(long long)b * I + a] = conjx(s);
+}
+
+inline int oz_slices(sky_prec p) { return p == SKY_F64 ? oz::kS64 : oz::kS32; }
+inline int oz_bn(sky_prec p) { return p == SKY_F64 ? oz::kBN64 : oz::kBN32; }
+inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+
+// K splits of the overlap GEMM: about one wave of items over the SMs, each
+// split at least 8 K blocks (two exact segments).
+int oz_overlap_splits(int I, long long K, int bn, int nsm) {
+  const int tiles = oz::count_tiles(I, 2 * I, bn, true, I);
+  const long long nkb = (K + oz::BK - 1) / oz::BK;
+  long long z = (nsm + tiles - 1) / (tiles > 0 ? tiles : 1);
+  const long long zmax = nkb / 8 > 0 ? nkb / 8 : 1;
+  if (z > zmax) z = zmax;
+  if (z < 1) z = 1;
+  return (int)z;
+}
+
+template <int S, int BN>
+sky_status oz_overlap_t(Ctx* c, const void* a, const void* b, int I, double2* X) {
+  const long long V = 2LL * c->G;             // complex entries per state
+  const bool f64 = c->prec == SKY_F64;
+  int* Ea = c->d_ozE;
+  int* Eb = c->d_ozE + c->max_states;
+  cudaStream_t st = c->stream;
+  // exponents over whole rows (shared by every K chunk)
+  if (f64) {
+    k_oz_rowexp<double2><<<I, 256, 0, st>>>((const double2*)a, V, Ea);
+    if (b != a) k_oz_rowexp<double2><<<I, 256, 0, st>>>((const double2*)b, V, Eb);
+  } else {
+    k_oz_rowexp<float2><<<I, 256, 0, st>>>((const float2*)a, V, Ea);
+    if (b != a) k_oz_rowexp<float2><<<I, 256, 0, st>>>((const float2*)b, V, Eb);
+  }
+  note_launch(b != a ? 2 : 1);
+  if (b == a) Eb = Ea;
+  // K chunk (complex entries) so that S slices of the 2I B rows fit the buffer
+  long long nc = c->oz_b_elems / ((long long)S * 2 * I) / 2;
+  nc = nc / 64 * 64;   // whole 128-value segments
+  if (nc > V) nc = V;
+  if (nc < 64 && nc < V) return set_err(c, SKY_EINVAL, "overlap: split buffer too small for I=%d", I);
+  const long long ldp = 2LL * I;
+  bool first = true;
+  for (long long c0 = 0; c0 < V; c0 += nc) {
+    const long long n = (V - c0) < nc ? (V - c0) : nc;
+    const long long K = 2 * n, ld = round_up(K, 8);
+    unsigned short* Bp = (unsigned short*)c->d_ozB;
+    unsigned short* Ap = (unsigned short*)c->d_ozA;
+    const long long sb = (long long)2 * I * ld, sa = (long long)I * ld;
+    const long long tot = (long long)I * n;
+    if (f64) {
+      k_oz_split_rows<double2, S><<<div_up(tot, 256), 256, 0, st>>>(
+          (const double2*)b, I, V, c0, n, Eb, Bp, ld, sb, I);
+      if (b != a)
+        k_oz_split_rows<double2, S><<<div_up(tot, 256), 256, 0, st>>>(
+            (const double2*)a, I, V, c0, n, Ea, Ap, ld, sa, -1);
+    } else {
+      k_oz_split_rows<float2, S><<<div_up(tot, 256), 256, 0, st>>>(
+          (const float2*)b, I, V, c0, n, Eb, Bp, ld, sb, I);
+      if (b != a)
+        k_oz_split_rows<float2, S><<<div_up(tot, 256), 256, 0, st>>>(
+            (const float2*)a, I, V, c0, n, Ea, Ap, ld, sa, -1);
+    }
+    note_launch(b != a ? 2 : 1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(c, e, "oz split");
+    int z = oz_overlap_splits(I, K, BN, c->num_sms);
+    const long long spart = (long long)I * ldp;
+    if ((size_t)z * spart > c->oz_p_elems) z = (int)(c->oz_p_elems / spart);
+    if (z < 1) return set_err(c, SKY_EINVAL, "overlap: partial buffer too small for I=%d", I);
+    oz::OzArgs g{};
+    g.mode = 0;
+    g.P = c->d_ozP;
+    g.ldp = ldp;
+    g.sp = spart;
+    g.status = c->d_status;
+    const void* Aop = b != a ? (const void*)Ap : (const void*)Bp;
+    const long long lda = ld, sA = b != a ? sa : sb;
+    e = oz::oz_gemm<S, BN>(Aop, lda, sA, I, Bp, ld, sb, 2 * I, (int)K, true, I, g, &z, st);
+    if (e != cudaSuccess) return cuda_check(c, e, "oz overlap gemm");
+    k_oz_overlap_reduce<<<div_up((long long)I * I, 256), 256, 0, st>>>(
+        c->d_ozP, z, spart, ldp, I, Ea, Eb, c->dV, X, first ? 0 : 1);
+    note_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(c, e, "oz overlap reduce");
+    first = false;
+  }
+  return SKY_OK;
+}
+
+template <int S, int BN>
+sky_status oz_rotate_t(Ctx* c, const void* phi, const double2* M, int I, void* out) {
+  const long long V = 2LL * c->G;
+  const bool f64 = c->prec == SKY_F64;
+  const int Ipad = (int)round_up(I, 32);
+  const long long ldk = 2LL * Ipad;
+  cudaStream_t st = c->stream;
+  int* Ea = c->d_ozE;
+  int* F = c->d_ozE + c->max_states;
+  unsigned short* Ap = (unsigned short*)c->d_ozA;
+  unsigned short* Bp = (unsigned short*)c->d_ozB;
+  const long long sa = (long long)I * ldk;
+  if ((long long)S * sa > (long long)c->oz_a_elems)
+    return set_err(c, SKY_EINVAL, "rotate: split buffer too small for I=%d", I);
+  k_oz_rot_a<S><<<I, 256, 0, st>>>(M, I, Ipad, Ap, ldk, sa, Ea);
+  if (f64) k_oz_colexp<double2><<<div_up(V, 256), 256, 0, st>>>((const double2*)phi, I, V, F);
+  else k_oz_colexp<float2><<<div_up(V, 256), 256, 0, st>>>((const float2*)phi, I, V, F);
+  note_launch(2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(c, e, "oz rotate split a");
+  // complex columns per chunk so that S slices of 2 nv rows fit the buffer
+  long long nv = c->oz_b_elems / ((long long)S * 2 * ldk);
+  nv = nv / 480 * 480;   // 2 nv rows: a multiple of both tile widths
+  if (nv > V) nv = V;
+  if (nv < 480 && nv < V) return set_err(c, SKY_EINVAL, "rotate: split buffer too small for I=%d", I);
+  for (long long v0 = 0; v0 < V; v0 += nv) {
+    const long long n = (V - v0) < nv ? (V - v0) : nv;
+    const long long sb = 2 * n * ldk;
+    dim3 g2(div_up(n, 32), Ipad / 32);
+    if (f64)
+      k_oz_split_rot_b<double2, S><<<g2, 256, 0, st>>>((const double2*)phi, I, Ipad, V, v0, n, F,
+                                                       Bp, ldk, sb);
+    else
+      k_oz_split_rot_b<float2, S><<<g2, 256, 0, st>>>((const float2*)phi, I, Ipad, V, v0, n, F, Bp,
+                                                      ldk, sb);
+    note_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(c, e, "oz rotate split b");
+    oz::OzArgs g{};
+    g.mode = 1;
+    g.out = f64 ? (void*)((double*)out + 2 * v0) : (void*)((float*)out + 2 * v0);
+    g.ldo = 2 * V;
+    g.out_f32 = f64 ? 0 : 1;
+    g.ea = Ea;
+    g.eb = F + v0;
+    g.eb_shift = 1;
+    g.status = c->d_status;
+    int z = 1;
+    e = oz::oz_gemm<S, BN>(Ap, ldk, sa, I, Bp, ldk, sb, (int)(2 * n), (int)ldk, false, I, g, &z,
+                           st);
+    if (e != cudaSuccess) return cuda_check(c, e, "oz rotate gemm");
+  }
+  return SKY_OK;
+}
+
+}  // namespace
+
+sky_status oz_overlap(Ctx* c, const void* a, const void* b, int I, double2* X) {
+  if (c->prec == SKY_F64) return oz_overlap_t<oz::kS64, oz::kBN64>(c, a, b, I, X);
+  return oz_overlap_t<oz::kS32, oz::kBN32>(c, a, b, I, X);
+}
+
+sky_status oz_rotate(Ctx* c, const void* phi, const double2* M, int I, void* out) {
+  if (c->prec == SKY_F64) return oz_rotate_t<oz::kS64, oz::kBN64>(c, phi, M, I, out);
+  return oz_rotate_t<oz::kS32, oz::kBN32>(c, phi, M, I, out);
+}
+
+// Slice buffers (bf16 elements over all slices), exponents and partials of
+// the split GEMMs for up to Imax states of V complex entries.  The B buffer
+// holds the [b; b'] overlap operand (or a K chunk of it) and the transposed
+// recombination operand (or a chunk of its rows); its size is capped by
+// SKY_OZ_MB (default 4096 MiB).
+void oz_scratch_sizes(sky_prec prec, int Imax, long long V, int nsm, size_t* a_elems,
+                      size_t* b_elems, size_t* e_elems, size_t* p_elems) {
+  const int S = oz_slices(prec), bn = oz_bn(prec);
+  const long long Ipad = round_up(Imax, 32);
+  const long long ov_b = (long long)S * 2 * Imax * round_up(2 * V, 8);
+  const long long rot_b = (long long)S * 2 * V * 2 * Ipad;
+  long long need_b = ov_b > rot_b ? ov_b : rot_b;
+  long long cap = 4096;
+  if (const char* s = getenv("SKY_OZ_MB"))
+    if (atol(s) > 0) cap = atol(s);
+  cap = (cap << 20) / 2;
+  // at least one chunk of 64 complex columns (overlap) / 480 (recombination)
+  const long long min_b = (long long)S * 2 * Imax * 128 > (long long)S * 960 * 2 * Ipad
+                              ? (long long)S * 2 * Imax * 128
+                              : (long long)S * 960 * 2 * Ipad;
+  if (need_b > cap) need_b = cap > min_b ? cap : min_b;
+  *b_elems = (size_t)need_b;
+  // A: the a rows of an overlap chunk (at most half of B) or the rotation rows
+  const long long rot_a = (long long)S * Imax * 2 * Ipad;
+  *a_elems = (size_t)(need_b / 2 > rot_a ? need_b / 2 : rot_a);
+  *e_elems = (size_t)(2 * Imax + V + 64);
+  size_t pmax = 1;
+  for (int I = 1; I <= Imax; ++I) {
+    const size_t p = (size_t)oz_overlap_splits(I, 2 * V, bn, nsm) * I * 2 * I;
+    if (p > pmax) pmax = p;
+  }
+  *p_elems = pmax;
+}
+
+}  // namespace sky

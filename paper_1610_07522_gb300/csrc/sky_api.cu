@@ -78,7 +78,8 @@ static void free_all(Ctx* c) {
                   c->d_small[3], c->d_small[4], c->d_small[5], c->d_gate,
                   c->d_stats, c->d_tcA[0], c->d_tcA[1], c->d_tcA[2], c->d_tcB[0],
                   c->d_tcB[1], c->d_tcB[2], c->d_tcRotA[0], c->d_tcRotA[1], c->d_tcRotA[2],
-                  c->d_tcPart, c->d_netpart, c->d_trid};
+                  c->d_tcPart, c->d_netpart, c->d_trid, c->d_ozA, c->d_ozB, c->d_ozE,
+                  c->d_ozP};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -112,6 +113,31 @@ static sky_status alloc_tc_scratch(Ctx* c, int pieces) {
     c->tc_partial_elems = part;
   }
   return s;
+}
+
+// Slice buffers, exponents and partials of the tensor-core split GEMMs of the
+// FP64 and FP32 forms; kept if already present.
+static sky_status alloc_oz_scratch(Ctx* c) {
+  if (c->d_ozB) return SKY_OK;
+  const int Imax = c->max_states > 0 ? c->max_states : 1;
+  size_t ae, be, ee, pe;
+  oz_scratch_sizes(c->prec, Imax, 2LL * c->G, c->num_sms, &ae, &be, &ee, &pe);
+  unsigned short *A = nullptr, *Bp = nullptr;
+  int* E = nullptr;
+  float2* P = nullptr;
+  sky_status s = dalloc(c, &A, ae);
+  if (s == SKY_OK) s = dalloc(c, &Bp, be);
+  if (s == SKY_OK) s = dalloc(c, &E, ee);
+  if (s == SKY_OK) s = dalloc(c, &P, pe);
+  if (s != SKY_OK) {
+    void* ptrs[] = {A, Bp, E, P};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    return s;
+  }
+  c->d_ozA = A; c->d_ozB = Bp; c->d_ozE = E; c->d_ozP = P;
+  c->oz_a_elems = ae; c->oz_b_elems = be; c->oz_p_elems = pe;
+  return SKY_OK;
 }
 
 static size_t scratch_budget() {
@@ -239,6 +265,8 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   ALLOC(c->d_trid, c->tri_slot * c->eig_batch);
   ALLOC(c->d_gate, 8 * kMaxBatch);
   if (s == SKY_OK && is_tc(prec)) s = alloc_tc_scratch(c, tc_nsplit(prec));
+  c->oz_on = is_tc(prec) ? 0 : 1;
+  if (s == SKY_OK && c->oz_on) s = alloc_oz_scratch(c);
   ALLOC(c->d_stats, 8);
   ALLOC(c->d_netpart, net_partial_elems(c->G));
   if (s == SKY_OK) {
@@ -463,13 +491,16 @@ sky_status sky_set_prec(sky_ctx* c, sky_prec prec) {
   if (prec != SKY_F32 && !is_tc(prec)) return set_err(c, SKY_EINVAL, "unknown precision form %d", (int)prec);
   if (c->prec == SKY_F64)
     return set_err(c, SKY_EUNSUPPORTED, "an FP64 context keeps FP64 spinors; create an FP32 one");
-  if (is_tc(prec)) {
-    cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return cuda_check(c, e, "set_prec sync");
-    const sky_status s = alloc_tc_scratch(c, tc_nsplit(prec));
-    if (s != SKY_OK) return s;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "set_prec sync");
+  const sky_prec old = c->prec;
+  c->prec = prec;   // the scratch sizes depend on the form
+  const sky_status s = is_tc(prec) ? alloc_tc_scratch(c, tc_nsplit(prec)) : alloc_oz_scratch(c);
+  if (s != SKY_OK) {
+    c->prec = old;
+    return s;
   }
-  c->prec = prec;
+  if (!is_tc(prec)) c->oz_on = 1;
   return SKY_OK;
 }
 
@@ -509,6 +540,15 @@ sky_status sky_tune_set(sky_ctx* c, sky_knob knob, int value) {
       if (value != SKY_EIG_AUTO && value != SKY_EIG_JACOBI && value != SKY_EIG_TRIDIAGONAL) break;
       c->eig_method = value;
       return SKY_OK;
+    case SKY_KNOB_SPLIT_GEMM:
+      if (value != 0 && value != 1) break;
+      if (value == 1 && is_tc(c->prec)) break;
+      if (value == 1) {
+        const sky_status s = alloc_oz_scratch(c);
+        if (s != SKY_OK) return s;
+      }
+      c->oz_on = value;
+      return SKY_OK;
     default:
       return set_err(c, SKY_EINVAL, "unknown knob %d", (int)knob);
   }
@@ -527,6 +567,7 @@ int sky_tune_get(const sky_ctx* c, sky_knob knob) {
     case SKY_KNOB_WAIT_SPINS: return (int)(c->wait_spins / 1000);
     case SKY_KNOB_JACOBI_MAX_SWEEPS: return c->jac_max_sweeps;
     case SKY_KNOB_EIGEN_METHOD: return c->eig_method;
+    case SKY_KNOB_SPLIT_GEMM: return c->oz_on;
     default: return -1;
   }
 }

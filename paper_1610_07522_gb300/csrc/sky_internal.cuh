@@ -124,6 +124,13 @@ struct Ctx {
   double* d_trid;                   // tridiagonal solver vectors and LU rows [tri_slot] per problem
   size_t tri_slot;                  // doubles per problem in d_trid
   int tri_m;                        // vector stride inside a d_trid slot (even)
+  // exact-integer split GEMMs of the FP64 and FP32 forms (oz_ops.cu)
+  int oz_on;                        // 1: tensor-core split GEMMs, 0: FP64 FMA kernels
+  void* d_ozA;                      // bf16 slices of the row operand
+  void* d_ozB;                      // bf16 slices of the column operand
+  int* d_ozE;                       // row exponents
+  float2* d_ozP;                    // split-K partials (hi, lo)
+  size_t oz_a_elems, oz_b_elems, oz_p_elems;
   char err[256];
 };
 
@@ -206,6 +213,10 @@ int tc_nsplit(sky_prec p);
 void tc_scratch_sizes(int I, long long V, int num_sms, size_t* piece_a, size_t* piece_b,
                       size_t* piece_rot_a, size_t* partial);
 sky_status tc_overlap(Ctx* c, const void* a, const void* b, int I, double2* X);
+void oz_scratch_sizes(sky_prec prec, int Imax, long long V, int nsm, size_t* a_elems,
+                      size_t* b_elems, size_t* e_elems, size_t* p_elems);
+sky_status oz_overlap(Ctx* c, const void* a, const void* b, int I, double2* X);
+sky_status oz_rotate(Ctx* c, const void* phi, const double2* M, int I, void* out);
 sky_status tc_rotate(Ctx* c, const void* phi, const double2* M, int I, void* out);
 inline bool is_tc(sky_prec p) { return p == SKY_F32_BF16X3 || p == SKY_F32_BF16X6; }
 size_t jacobi_rot_bytes(int m);

@@ -53,7 +53,8 @@ def test_set_prec_matches_a_context_made_in_that_form():
     want = O.overlap(a.cpu().numpy().astype(np.complex128), b.cpu().numpy().astype(np.complex128), g)
     # full products in the split forms vs the lower-triangle mirror of the oracle
     err = {p: np.max(np.abs(np.tril(out[p]) - np.tril(want))) / np.max(np.abs(want)) for p in out}
-    assert err[B.SKY_F32] < 1e-12 and err[B.SKY_F32_BF16X6] < 2e-5 and err[B.SKY_F32_BF16X3] < 4e-5
+    # SKY_F32: 4-digit exact split products, digits to 2^-32 of each row's scale
+    assert err[B.SKY_F32] < 1e-8 and err[B.SKY_F32_BF16X6] < 2e-5 and err[B.SKY_F32_BF16X3] < 4e-5
 
 
 def test_escalated_split_bf16_run_reaches_the_fp64_fixed_point():
