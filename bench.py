@@ -28,7 +28,6 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOAD = "sly4_24cubed_280n120p_coulomb_fp64"
-FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of GB300 (CUDA cores; FP64 tensor is no faster)
 FORMS = {"fp64": 0, "f32": 1, "bf16x3": 2, "bf16x6": 3}     # sky_prec values
 EIGEN = {"auto": 0, "jacobi": 1, "tridiagonal": 2}        # SKY_KNOB_EIGEN_METHOD values
 DTYPES = {"fp64": "f64", "f32": "f32", "bf16x3": "f32+bf16x3", "bf16x6": "f32+bf16x6"}
@@ -432,6 +431,146 @@ def batched_leg(dev, form="bf16x3", count=64, steps=10):
     return out
 
 
+# ---------------------------------------------------------------- rooflines
+# digit (or bf16 piece) products of each form's tensor-core contractions
+NPROD = {0: 21, 1: 10, 2: 3, 3: 6}
+# DRAM bytes per spinor of one sky_apply_h call: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum summed over the call's kernels (bench.py --probe-call
+# apply_h; profiles/), divided by its I.  Keyed by (workload, form); absent
+# until captured for the current kernels.
+HPSI_TRAFFIC_PER_SPINOR = {
+    # 2.780 GB over the 8 kernels of one I = 280 call (profiles/sky_apply_h_sly4_24cubed_280n_fp64.md)
+    ("sly4_24cubed_280n120p_coulomb_fp64", "fp64"): 2780380928.0 / 280,
+}
+
+
+def fma_peaks(dev):
+    """FP64 and FP32 FMA rates of this GPU (TFLOP/s), measured with the
+    library's FMA-chain probe kernel (best of 5 launches after 2 warm-ups,
+    CUDA events on the launching stream)."""
+    import torch
+    from paper_1610_07522_gb300 import binding as B
+    st = torch.cuda.current_stream(dev)
+    out = {}
+    for name, fp64, iters in (("fp64", 1, 4000), ("fp32", 0, 100000)):
+        for _ in range(2):
+            B.sky_fma_probe(fp64, 4, iters, st.cuda_stream)
+        best = 0.0
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fl = B.sky_fma_probe(fp64, 4, iters, st.cuda_stream)
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+            best = max(best, fl / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        out[name] = best
+    return out
+
+
+def hpsi_work(grid, csize):
+    """Algorithmic work of one spinor h.psi (sky_apply_h): per spatial axis j a
+    gradient and a divergence sweep over both spin components (2G points),
+    each a forward and an inverse 1D FFT along j at 5 n log2 n flops per
+    transform of n points, plus about 150 G pointwise flops; bytes: read psi
+    and write h psi once (2 x 2G complex values)."""
+    import math
+    G = grid[0] * grid[1] * grid[2]
+    flops = sum(2 * 2 * G * 2 * 5 * math.log2(n) for n in grid) + 150 * G
+    return flops, 2 * 2 * G * csize
+
+
+def call_rooflines(events, grid, prec, peaks, csize):
+    """Per-call rooflines from CUDA-event durations of the single-stream step:
+    sky_apply_h against the FP64 (FP32) FMA pipe and HBM, the overlap and the
+    recombination against the tensor pipe (their digit or piece products)."""
+    G = grid[0] * grid[1] * grid[2]
+    V = 2 * G
+    out = {}
+
+    def mean_ms(kind):
+        ev = events.get(kind, [])
+        return sum(e0.elapsed_time(e1) for _, e0, e1 in ev) / max(1, len(ev)), ev
+
+    ms, ev = mean_ms("apply_h")
+    if ev:
+        f1, b1 = hpsi_work(grid, csize)
+        fl = sum(I for I, _, _ in ev) * f1 / len(ev)
+        by = sum(I for I, _, _ in ev) * b1 / len(ev)
+        pk = peaks["fp64" if prec == 0 else "fp32"]
+        out["apply_h"] = {
+            "kernel": "sky_apply_h (line-pass FFTs, k_h_local, k_h_sum)",
+            "bound": "alu", "unit": "TFLOP/s", "avg_call_ms": ms,
+            "mean_I": sum(I for I, _, _ in ev) / len(ev),
+            "achieved": fl / (ms / 1e3) / 1e12, "peak": pk,
+            "frac": fl / (ms / 1e3) / 1e12 / pk,
+            "peak_source": f"measured {'FP64' if prec == 0 else 'FP32'} FMA rate (sky_fma_probe, this run)",
+            "hbm_algorithmic_GBps": by / (ms / 1e3) / 1e9,
+            "hbm_frac": by / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+            "work": "per spinor: 40 G sum_j log2 n_j + 150 G flops, 2 x 2G complex values moved"}
+    for kind, tri in (("overlap", True), ("rotate", False)):
+        ms, ev = mean_ms(kind)
+        if not ev:
+            continue
+        n = NPROD[prec]
+        full = prec in (2, 3)   # the split-BF16 forms compute the whole product
+        f64eq = sum((8.0 * V * I * (I + 1) / 2) if (tri and not full) else 8.0 * V * I * I
+                    for I, _, _ in ev) / len(ev)
+        ach = n * f64eq / (ms / 1e3) / 1e12
+        out[kind] = {
+            "kernel": f"sky_{kind} (digit split + k_oz_gemm tcgen05 + reduce)" if prec in (0, 1)
+                      else f"sky_{kind} (bf16 split + k_gemm_bf16 tcgen05)",
+            "bound": "tensor", "unit": "TFLOP/s", "avg_call_ms": ms,
+            "achieved": ach, "peak": peaks["bf16_tflops"], "frac": ach / peaks["bf16_tflops"],
+            "peak_source": "measured dense BF16 burst (MEASURED_PEAKS.json)",
+            "products": n,
+            "fp64_equivalent_tflops": f64eq / (ms / 1e3) / 1e12,
+            "work": ("products x 8 V I(I+1)/2 (lower triangle)" if (tri and not full)
+                     else "products x 8 V I^2")}
+    return out
+
+
+def probe_call(args):
+    """One library call on the workload's shapes (random states), for an ncu
+    capture of exactly that call's kernels; prints the number of library
+    launches the call made (the last ones of the capture)."""
+    import torch
+    from paper_1610_07522_gb300 import binding as B
+    from paper_1610_07522_gb300 import inputs as IN
+    w = IN.WORKLOADS[args.workload]
+    prec = FORMS[args.form]
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream(dev)
+    I = w.N
+    ctx = B.sky_init(w.grid, w.dx, w.params, w.coulomb, w.twist, prec, I, st.cuda_stream)
+    nx, ny, nz = w.grid
+    G = nx * ny * nz
+    cd = torch.complex128 if prec == 0 else torch.complex64
+    gen = torch.Generator(device=dev).manual_seed(1)
+    psi = torch.randn((I, 2, nz, ny, nx), dtype=cd, device=dev, generator=gen) / G ** 0.5
+    out = torch.zeros_like(psi)
+    f64 = dict(dtype=torch.float64, device=dev)
+    U = torch.full((G,), -40.0, **f64)
+    Bf = torch.full((G,), 20.0, **f64)
+    W = torch.zeros((3, G), **f64)
+    X = torch.zeros((I, I), dtype=torch.complex128, device=dev)
+    M = torch.eye(I, dtype=torch.complex128, device=dev)
+    torch.cuda.synchronize(dev)
+    n0 = B.sky_kernel_launches()
+    if args.probe_call == "apply_h":
+        B.sky_apply_h(ctx, U, Bf, W, psi, out, I)
+    elif args.probe_call == "overlap":
+        B.sky_overlap(ctx, psi, psi, I, X)
+    elif args.probe_call == "rotate":
+        B.sky_rotate(ctx, psi, M, I, out)
+    B.sky_sync(ctx)
+    print(json.dumps({"probe_call": args.probe_call, "workload": args.workload, "form": args.form,
+                      "I": I, "launches": B.sky_kernel_launches() - n0}))
+    B.sky_destroy(ctx)
+    return 0
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import numpy as np
@@ -457,8 +596,6 @@ def run_gpu(args):
     for _ in range(args.warmup):
         s.step()
     s.sync()
-    ov_events = []
-    s.overlap_events = ov_events      # CUDA events around each overlap call, on the ctx stream
     sampler = ClockSampler(_gpu_smi_id(local))
     B.sky_stats(s.ctx, reset=True)
     _barrier(dist)
@@ -476,45 +613,21 @@ def run_gpu(args):
     solver_stats = B.sky_stats(s.ctx)
     _barrier(dist)
     clocks = sampler.stop()
-    s.overlap_events = None
     s.sync()
     ms = t0.elapsed_time(t1) / args.steps
     ms_max = _max_over_ranks(ms, dist, dev)
     value = ws * units / (ms_max / 1e3)
 
-    # roofline of the overlap / Hamiltonian matrix call (the largest kernel of
-    # the FP64 step).  FP64 and FP32 forms: k_overlap, FP64 FMA on the lower
-    # triangle, 8 algorithmic flops per complex multiply-add (the 3M form
-    # executes 6).  Split-BF16 forms: the tcgen05 GEMM over the full complex
-    # product, counted as executed BF16 tensor flops (products x 8 I^2 V).
     V = 2 * s.G
-    ov_ms, ov_flops, ov_bytes = 0.0, 0.0, 0.0
-    nprod = {2: 3, 3: 6}.get(prec, 0)
     csize = s.psi[0].element_size()
-    for I, e0, e1, same in ov_events:
-        ov_ms += e0.elapsed_time(e1)
-        ov_flops += (8.0 * V * I * (I + 1) / 2) if nprod == 0 else nprod * 8.0 * V * I * I
-        ov_bytes += (1 if same else 2) * csize * V * I
-    ov_launch_ms = ov_ms / max(1, len(ov_events))
-    achieved = ov_flops / (ov_ms / 1e3) / 1e12 if ov_ms > 0 else None
     peaks, peak_src = _measured_peaks()
-    if nprod == 0:
-        roof = {"kernel": "sky_overlap (k_overlap + split-K reduce), FP64 FMA", "bound": "alu",
-                "peak": FP64_PEAK_TFLOPS,
-                "peak_source": "nominal dense FP64 of GB300 (profiling recipe table)",
-                "traffic": ov_bytes / max(1, len(ov_events)),
-                "traffic_source": "ncu dram__bytes_read+write of one k_overlap launch (I = 120) equals "
-                                  "one read of each distinct operand; scaled to the mean launch of this run"}
-    else:
-        roof = {"kernel": "sky_overlap, split-BF16 (split + tcgen05 GEMM + reduce)", "bound": "tensor",
-                "peak": peaks["bf16_tflops"],
-                "peak_source": f"{peak_src} dense BF16 burst (MEASURED_PEAKS.json)"}
-    roof.setdefault("traffic", None)
-    roof.update({"achieved": achieved, "unit": "TFLOP/s",
-                 "frac": (achieved / roof["peak"]) if achieved else None,
-                 "avg_launch_ms": ov_launch_ms})
+    peaks = dict(peaks)
+    probe = fma_peaks(dev)
+    peaks.update(probe)
 
-    # the same step with both species on one context and stream
+    # the same step with both species on one context and stream; then the same
+    # steps again with CUDA events around every sky_apply_h, sky_overlap and
+    # sky_rotate call (per-call rooflines; the events sit between the calls)
     sc = Solver(w, prec=prec, device=dev)
     sc.set_eigen_method(EIGEN[args.eigen])
     sc.load(inp["psi0"], inp.get("rho0"), inp.get("tau0"))
@@ -529,7 +642,24 @@ def run_gpu(args):
     c1.record(sc.stream)
     torch.cuda.synchronize()
     conc_ms = c0.elapsed_time(c1) / args.steps
+    sc.call_events = {}
+    for _ in range(args.steps):
+        sc.step()
+    sc.sync()
+    torch.cuda.synchronize()
+    calls = call_rooflines(sc.call_events, w.grid, prec, peaks, csize)
+    sc.call_events = None
     sc.close()
+    # the line's roofline: the h.psi call, the largest call of the step (the
+    # FP64 FFT line passes are FP64-pipe work); the contractions beside it
+    roof = dict(calls.get("apply_h", {}))
+    tps = HPSI_TRAFFIC_PER_SPINOR.get((args.workload, args.form))
+    roof["traffic"] = tps * roof["mean_I"] if (tps and roof) else None
+    roof["traffic_source"] = (
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum over the kernels of one sky_apply_h "
+        "call (bench.py --probe-call apply_h) per spinor, times this run's mean I per call"
+        if roof["traffic"] is not None else "not captured for this workload and form")
+    roof["fma_peaks_tflops"] = probe
 
     # end to end through the public API with pinned host buffers
     host = {
@@ -575,6 +705,7 @@ def run_gpu(args):
                    "parallelism": f"replicas x{ws}",
                    "l2": f"working set (psi, phi, h psi: {3 * s.psi[0].element_size() * V * (w.N + w.Z) / 1e9:.2f} GB) exceeds L2 (129 MB), no flush"},
         "roofline": roof,
+        "roofline_calls": {k: v for k, v in calls.items() if k != "apply_h"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "spinor-applies/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -609,12 +740,16 @@ def main():
                     help="skip the 64-box batched (CUDA graph) form")
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the time-to-convergence comparison of the forms")
+    ap.add_argument("--probe-call", default=None, choices=["apply_h", "overlap", "rotate"],
+                    help="run one library call on the workload's shapes and exit (for ncu)")
     ap.add_argument("--eigen", default="auto", choices=sorted(EIGEN),
                     help="FP64 eigensolver of the timed steps (auto: tridiagonal route for "
                          "large species, batched Jacobi for many small problems)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.probe_call:
+        return probe_call(args)
     return run_gpu(args)
 
 

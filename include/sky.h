@@ -30,6 +30,8 @@
 #ifndef SKY_H
 #define SKY_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -76,7 +78,10 @@ typedef struct {
  * memory the context owns; stream is a cudaStream_t (NULL = legacy default
  * stream).  The device is the current CUDA device.  On success *out owns
  * device memory until sky_destroy.  Returns SKY_EINVAL / SKY_EUNSUPPORTED /
- * SKY_ENOMEM / SKY_ECUDA on failure with *out = NULL. */
+ * SKY_ENOMEM / SKY_ECUDA on failure with *out = NULL.  With the environment
+ * variable SKY_FILL_SCRATCH_NAN=1, every device buffer a context allocates
+ * (here or later) starts filled with 0xFF bytes, NaN in every floating-point
+ * format: a check that no kernel reads scratch it has not written. */
 sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3],
                     const sky_skyrme* params, const double twist[3],
                     sky_prec prec, int max_states, void* stream);
@@ -100,6 +105,17 @@ sky_status sky_stats(sky_ctx* ctx, long long out[8], int reset);
 
 /* Human-readable text of the last error the context saw (never NULL). */
 const char* sky_last_error(const sky_ctx* ctx);
+
+/* Host <-> device copies on the context's stream, for callers whose state
+ * lives in host memory (the paper's code keeps psi in host memory, Sec. 3.1):
+ * sky_memcpy_h2d copies bytes from the HOST buffer src into the DEVICE buffer
+ * dst, sky_memcpy_d2h from the DEVICE buffer src into the HOST buffer dst.
+ * Enqueued (asynchronous with respect to the host for page-locked host
+ * memory; pageable host memory makes the call wait for the copy); both
+ * buffers stay owned by the caller and must stay valid until the stream has
+ * run the copy.  SKY_ECUDA if the runtime rejects the copy. */
+sky_status sky_memcpy_h2d(sky_ctx* ctx, void* dst, const void* src, size_t bytes);
+sky_status sky_memcpy_d2h(sky_ctx* ctx, void* dst, const void* src, size_t bytes);
 
 /* 1 if an axis of n points is built for precision prec, else 0. */
 int sky_supported_size(int n, sky_prec prec);
@@ -370,6 +386,16 @@ sky_status sky_precond_stats(sky_ctx* ctx, const void* psi, const void* phi, con
  * leaves that error for the caller.  Calls no cudaMalloc or cudaFree. */
 sky_status sky_overlap_noalloc(const void* a, const void* b, int I, long long V, double dV,
                                sky_prec prec, double* X, void* stream);
+
+/* ---- FMA-rate probe -----------------------------------------------------------
+ * The paper has no counterpart: a measurement aid for roofline fractions.
+ * Enqueues one kernel of blocks_per_sm (1..64) blocks of 256 threads per SM on
+ * stream, each thread running 8 independent FMA chains for iters (>= 1)
+ * iterations in FP64 (fp64 != 0) or FP32, and sets *flops (host) to the
+ * floating-point operations it executes (2 per FMA).  Time it with events on
+ * the same stream: flops / time is the device's FMA rate in that precision.
+ * Allocates nothing and writes no device memory. */
+sky_status sky_fma_probe(int fp64, int blocks_per_sm, int iters, void* stream, double* flops);
 
 #ifdef __cplusplus
 }

@@ -75,6 +75,9 @@ _SIGNATURES = {
     "sky_net_adam": (_I, [_P, _P, _P, _P, _P, _I, _D, _D, _D, _D]),
     "sky_cross_overlap": (_I, [_P, _P, _P, _I, _P]),
     "sky_precond_stats": (_I, [_P, _P, _P, _P, _I, _P, _P]),
+    "sky_fma_probe": (_I, [_I, _I, _I, _P, ctypes.POINTER(_D)]),
+    "sky_memcpy_h2d": (_I, [_P, _P, _P, ctypes.c_size_t]),
+    "sky_memcpy_d2h": (_I, [_P, _P, _P, ctypes.c_size_t]),
 }
 
 # Constants of the damping network (the #defines of include/sky.h).
@@ -282,3 +285,33 @@ def sky_cross_overlap(ctx, a, b, I, X):
 def sky_precond_stats(ctx, psi, phi, ppsi, I, abc, norm):
     _check(ctx, lib().sky_precond_stats(ctx, _ptr(psi), _ptr(phi), _ptr(ppsi), int(I), _ptr(abc),
                                         _ptr(norm)))
+
+
+def sky_fma_probe(fp64, blocks_per_sm, iters, stream=0):
+    """Enqueue the FMA-chain probe kernel; returns the flops it executes."""
+    f = _D(0.0)
+    st = lib().sky_fma_probe(int(bool(fp64)), int(blocks_per_sm), int(iters),
+                             _P(stream) if stream else None, ctypes.byref(f))
+    if st != SKY_OK:
+        raise SkyError(st, "sky_fma_probe failed")
+    return f.value
+
+
+def _nbytes(t):
+    return t.numel() * t.element_size()
+
+
+def sky_memcpy_h2d(ctx, dst, src):
+    """Copy the host tensor src into the device tensor dst on the context stream."""
+    n = _nbytes(src)
+    if _nbytes(dst) != n:
+        raise ValueError("sky_memcpy_h2d: size mismatch")
+    _check(ctx, lib().sky_memcpy_h2d(ctx, _ptr(dst), _ptr(src), n))
+
+
+def sky_memcpy_d2h(ctx, dst, src):
+    """Copy the device tensor src into the host tensor dst on the context stream."""
+    n = _nbytes(src)
+    if _nbytes(dst) != n:
+        raise ValueError("sky_memcpy_d2h: size mismatch")
+    _check(ctx, lib().sky_memcpy_d2h(ctx, _ptr(dst), _ptr(src), n))

@@ -571,8 +571,10 @@ __device__ __forceinline__ void tri_solve(const TriPtrs& p, int n, int k) {
   double y1 = 0.0, y2 = 0.0;                // y[i+1], y[i+2]
   for (int i = n - 1; i >= 0; --i) {
     const size_t e = (size_t)i * sn + k;
+    // the last row has no superdiagonal (its U1 and U2 entries are never formed)
+    const double u1 = i + 1 < n ? p.U1[e] : 0.0;
     const double u2 = (i + 2 < n && piv_of(p.U2[e])) ? p.e[i + 1] : 0.0;
-    const double yi = (Y[e] - p.U1[e] * y1 - u2 * y2) * p.U0[e];
+    const double yi = (Y[e] - u1 * y1 - u2 * y2) * p.U0[e];
     Y[e] = yi;
     y2 = y1;
     y1 = yi;

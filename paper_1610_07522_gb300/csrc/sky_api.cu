@@ -56,11 +56,20 @@ static Couplings couplings(const sky_skyrme& p) {
   return c;
 }
 
+// SKY_FILL_SCRATCH_NAN=1 in the environment: every buffer a context allocates
+// starts as 0xFF bytes (NaN in every floating-point format), so a kernel that
+// reads scratch it has not written shows up as NaN in the results.
+static bool fill_nan() {
+  const char* s = getenv("SKY_FILL_SCRATCH_NAN");
+  return s && s[0] == '1';
+}
+
 template <typename T>
 static sky_status dalloc(Ctx* c, T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaSuccess && fill_nan()) e = cudaMemset(*p, 0xFF, count * sizeof(T));
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();
@@ -235,6 +244,7 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   if (s == SKY_OK) {
     void* p = nullptr;
     e = cudaMalloc(&p, chunk * per_state);
+    if (e == cudaSuccess && fill_nan()) e = cudaMemset(p, 0xFF, chunk * per_state);
     if (e != cudaSuccess) { cudaGetLastError(); s = set_err(c, SKY_ENOMEM, "scratch allocation failed"); }
     c->d_gscr = p;
   }
@@ -345,6 +355,22 @@ sky_status sky_sync(sky_ctx* c) {
 }
 
 const char* sky_last_error(const sky_ctx* c) { return c ? c->err : "null context"; }
+
+sky_status sky_memcpy_h2d(sky_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (!c) return SKY_EINVAL;
+  if (bytes == 0) return SKY_OK;
+  if (!dst || !src) return set_err(c, SKY_EINVAL, "memcpy_h2d: null pointer");
+  return cuda_check(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream),
+                    "memcpy_h2d");
+}
+
+sky_status sky_memcpy_d2h(sky_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (!c) return SKY_EINVAL;
+  if (bytes == 0) return SKY_OK;
+  if (!dst || !src) return set_err(c, SKY_EINVAL, "memcpy_d2h: null pointer");
+  return cuda_check(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream),
+                    "memcpy_d2h");
+}
 
 sky_status sky_stats(sky_ctx* c, long long out[8], int reset) {
   if (!c || !out) return SKY_EINVAL;

@@ -75,6 +75,9 @@ class Solver:
         self.spread = torch.zeros(2, **f64)
         self.off = (0, workload.N)
         self.overlap_events = None   # list to collect (I, start, end, a is b) per overlap call, or None
+        # dict to collect (I, start, end) per call of sky_apply_h / sky_overlap / sky_rotate
+        # (keys "apply_h", "overlap", "rotate"), events on the species' stream, or None
+        self.call_events = None
         self.damping = None          # learned.DampingNet giving the per-voxel step weight, or None
         self.damping_on = False
         self.damping_fallbacks = 0
@@ -135,12 +138,25 @@ class Solver:
             B.sky_densities(self.ctxq[q], self.psi[q], self.I[q], self.rho[q], self.tau[q], self.J[q],
                             self.divJ[q])
 
+    def _timed(self, kind, q, fn):
+        """Run fn(); with call_events set, bracket it with CUDA events on the
+        stream species q's calls are enqueued on."""
+        if self.call_events is None:
+            return fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(self.streamq[q])
+        fn()
+        e1.record(self.streamq[q])
+        self.call_events.setdefault(kind, []).append((self.I[q], e0, e1))
+
     def species_step(self, q):
         """Step 2 and 3a for species q: h psi, damped step, h phi, S and H."""
         I, o = self.I[q], self.off[q]
         ctx = self.ctxq[q]
-        B.sky_apply_h(ctx, self.U[q], self.Bf[q], self.W[q], self.psi[q], self.h[q], I,
-                      self.eps[o:o + I], self.hn2[o:o + I])
+        self._timed("apply_h", q, lambda: B.sky_apply_h(
+            ctx, self.U[q], self.Bf[q], self.W[q], self.psi[q], self.h[q], I,
+            self.eps[o:o + I], self.hn2[o:o + I]))
         w = None
         if self.damping_on:
             self.dampq[q].weights(ctx, self.G, q, self.U[q], self.Bf[q], self.W[q], self.wq[q],
@@ -148,16 +164,17 @@ class Solver:
             w = self.wq[q]
         B.sky_damped_step(ctx, q, self.psi[q], self.h[q], self.eps[o:o + I], self.phi[q], I,
                           self.w.x0, self.w.E0, w)
-        B.sky_apply_h(ctx, self.U[q], self.Bf[q], self.W[q], self.phi[q], self.h[q], I)
+        self._timed("apply_h", q, lambda: B.sky_apply_h(
+            ctx, self.U[q], self.Bf[q], self.W[q], self.phi[q], self.h[q], I))
         for X, rhs in ((self.S[q], self.phi[q]), (self.H[q], self.h[q])):
             if self.overlap_events is None:
-                B.sky_overlap(ctx, self.phi[q], rhs, I, X)
+                self._timed("overlap", q, lambda: B.sky_overlap(ctx, self.phi[q], rhs, I, X))
             else:
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(self.stream)
+                e0.record(self.streamq[q])
                 B.sky_overlap(ctx, self.phi[q], rhs, I, X)
-                e1.record(self.stream)
+                e1.record(self.streamq[q])
                 self.overlap_events.append((I, e0, e1, rhs is self.phi[q]))
 
     def ritz_step(self):
@@ -173,7 +190,8 @@ class Solver:
              [self.lam[self.off[q]:self.off[q] + self.I[q]] for q in qs])
         self._fork()
         for q in qs:
-            B.sky_rotate(self.ctxq[q], self.phi[q], self.M[q], self.I[q], self.psi[q])
+            self._timed("rotate", q, lambda: B.sky_rotate(self.ctxq[q], self.phi[q], self.M[q],
+                                                          self.I[q], self.psi[q]))
 
     def _fork(self):
         """Let the proton stream start after the work enqueued so far."""
@@ -205,14 +223,16 @@ class Solver:
 
     def step_host(self, host, eout_host):
         """One iteration from host state: copy psi and the mean field in from
-        pinned host tensors, iterate, copy the energies back (end to end)."""
+        pinned host tensors through the library's copy calls (on the context
+        stream), iterate, copy the energies back (end to end)."""
         for q in range(2):
-            self.psi[q].copy_(host["psi"][q], non_blocking=True)
-        self.U.copy_(host["U"], non_blocking=True)
-        self.Bf.copy_(host["B"], non_blocking=True)
-        self.W.copy_(host["W"], non_blocking=True)
+            if self.I[q] > 0:
+                B.sky_memcpy_h2d(self.ctx, self.psi[q], host["psi"][q])
+        B.sky_memcpy_h2d(self.ctx, self.U, host["U"])
+        B.sky_memcpy_h2d(self.ctx, self.Bf, host["B"])
+        B.sky_memcpy_h2d(self.ctx, self.W, host["W"])
         self.step()
-        eout_host.copy_(self.eout, non_blocking=True)
+        B.sky_memcpy_d2h(self.ctx, eout_host, self.eout)
         self.sync()
         return eout_host
 
