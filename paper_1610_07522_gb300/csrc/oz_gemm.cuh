@@ -5,7 +5,7 @@
 // Each row r of an operand is scaled by a power of two 2^e[r] (|x| < 2^e[r])
 // and written as S signed base-256 digits,
 //     x = 2^e[r] sum_{s<S} alpha_s 2^{-8(s+1)}   (+ a remainder below 2^{-8S}),
-// alpha_0 in [-256, 256], alpha_s in [-128, 127]: small integers that bf16
+// |alpha_0| <= 256, |alpha_s| <= 128 (s >= 1): small integers that bf16
 // holds exactly ("slices", Ozaki, Ogita, Oishi and Rump 2012).  The product
 // keeps the slice pairs of total weight g = s + t <= S - 1:
 //     sum_k A[m][k] B[n][k] = 2^{e_m + f_n - 16} sum_g 2^{-8g} G_g[m][n],

@@ -7,7 +7,7 @@
 // chip): each value x of a row with exponent E (|x| < 2^E over the row) is
 // rounded to the integer X = round(|x| 2^{8S - E}) < 2^{8S} + 1 and written as
 // balanced base-256 digits alpha_0 .. alpha_{S-1} (alpha_0 in [0, 256],
-// the others in [-128, 127]), with the sign of x.
+// the others in [-128, 127]), then given the sign of x (|alpha_s| <= 128).
 //
 // Complex contractions are real GEMMs over the interleaved (re, im) storage,
 // as in the split-BF16 forms:
