@@ -681,6 +681,34 @@ def run_gpu(args):
     e2e_dt = _max_over_ranks(e2e_dt, dist, dev)
     e2e_value = ws * units / e2e_dt
 
+    # time-dependent stepping (predictor-corrector pairs of order-6 Taylor
+    # propagations) of the same states, FP64 or the chosen form
+    td = None
+    if not args.no_td:
+        from paper_1610_07522_gb300.td import TimeStepper
+        ts = TimeStepper(s, order=6)
+        ts.init_fields()
+        E0 = ts.energy()
+        for _ in range(2):
+            ts.step(0.1)
+        s.sync()
+        k = 5
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(s.stream)
+        for _ in range(k):
+            ts.step(0.1)
+        d1.record(s.stream)
+        torch.cuda.synchronize()
+        td_ms = d0.elapsed_time(d1) / k
+        E1 = ts.energy()
+        td = {"dt_fm_per_c": 0.1, "taylor_order": 6, "steps_timed": k, "ms_per_step": td_ms,
+              "spinor_applies_per_s": 2 * 6 * units / 2 / (td_ms / 1e3),
+              "energy_drift_rel_over_7_steps": abs(E1 - E0) / abs(E0),
+              "note": "each step: half step with h(t), midpoint mean field, full step with it "
+                      "(12 h.psi per state), densities, mean field, energy"}
+        del ts
+
     conv = None
     if rank == 0 and not args.no_convergence:
         conv = convergence_leg(dev)
@@ -715,6 +743,7 @@ def run_gpu(args):
                           "note": "both species on one context and stream (the main number "
                                   "runs them on two)"},
         "clocks": clocks,
+        "time_dependent": td,
         "convergence": conv,
         "batched": batched,
     }
@@ -738,6 +767,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-box batched (CUDA graph) form")
+    ap.add_argument("--no-td", action="store_true",
+                    help="skip the time-dependent stepping leg")
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the time-to-convergence comparison of the forms")
     ap.add_argument("--probe-call", default=None, choices=["apply_h", "overlap", "rotate"],

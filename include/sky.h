@@ -148,6 +148,22 @@ sky_status sky_damped_step(sky_ctx* ctx, int q, const void* psi, const void* hps
                            const double* eps, void* phi, int I, double x0, double E0,
                            const float* w);
 
+/* ---- Time-dependent stepping (Sec. 2.2, the unitary time evolution of
+ * Sky3D's time-dependent mode, Sec. 1) -----------------------------------------
+ * out = sum_{k=0}^{order} (-i tau h)^k / k! psi, the Taylor polynomial of
+ * the propagator exp(-i tau h) with tau = dt / hbar in MeV^-1 (dt in fm/c
+ * divided by hbar c = 197.327 MeV fm) and h the single-particle Hamiltonian
+ * of sky_apply_h with the mean field U, B, W of one species.  The states
+ * need no orthonormalisation: the exact propagator is unitary and the
+ * polynomial departs from it by the Taylor remainder |tau h|^(order+1) /
+ * (order+1)!.  psi, out: [I][2][G]; work: device scratch of 2 I V complex
+ * values in the context precision, owned by the caller and overwritten.
+ * psi, out and work must not overlap; 0 <= order <= 32 (order 0 copies psi).
+ * The mean field to pass (e.g. the one at the midpoint of the step) is the
+ * caller's choice. */
+sky_status sky_td_taylor(sky_ctx* ctx, const double* U, const double* B, const double* W,
+                         const void* psi, void* out, void* work, int I, double tau, int order);
+
 /* ---- Step 3a: overlap / Hamiltonian matrix (Eqs. normmatrix, hammatrix) ----
  * X[a*I + b] = <a_a | b_b> = dx^3 sum_v conj(a_a[v]) b_b[v] for a >= b, and
  * X[b*I + a] = conj(X[a*I + b]) (only the lower triangle is formed, Fig. 3).

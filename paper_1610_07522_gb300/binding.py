@@ -76,6 +76,7 @@ _SIGNATURES = {
     "sky_cross_overlap": (_I, [_P, _P, _P, _I, _P]),
     "sky_precond_stats": (_I, [_P, _P, _P, _P, _I, _P, _P]),
     "sky_fma_probe": (_I, [_I, _I, _I, _P, ctypes.POINTER(_D)]),
+    "sky_td_taylor": (_I, [_P, _P, _P, _P, _P, _P, _P, _I, _D, _I]),
     "sky_memcpy_h2d": (_I, [_P, _P, _P, ctypes.c_size_t]),
     "sky_memcpy_d2h": (_I, [_P, _P, _P, ctypes.c_size_t]),
 }
@@ -184,6 +185,11 @@ def sky_apply_h(ctx, U, B, W, psi, hpsi, I, eps=None, hnorm2=None):
 def sky_damped_step(ctx, q, psi, hpsi, eps, phi, I, x0, E0, w=None):
     _check(ctx, lib().sky_damped_step(ctx, int(q), _ptr(psi), _ptr(hpsi), _ptr(eps), _ptr(phi),
                                       int(I), float(x0), float(E0), _ptr(w)))
+
+
+def sky_td_taylor(ctx, U, B, W, psi, out, work, I, tau, order=6):
+    _check(ctx, lib().sky_td_taylor(ctx, _ptr(U), _ptr(B), _ptr(W), _ptr(psi), _ptr(out),
+                                    _ptr(work), int(I), float(tau), int(order)))
 
 
 def sky_overlap(ctx, a, b, I, X):

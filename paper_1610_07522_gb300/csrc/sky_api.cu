@@ -395,6 +395,19 @@ sky_status sky_apply_h(sky_ctx* c, const double* U, const double* B, const doubl
   return apply_h_impl(c, U, B, W, psi, hpsi, I, eps, hnorm2);
 }
 
+sky_status sky_td_taylor(sky_ctx* c, const double* U, const double* B, const double* W,
+                         const void* psi, void* out, void* work, int I, double tau, int order) {
+  CHECK_CTX();
+  if (I == 0) return SKY_OK;
+  if (!U || !B || !W || !psi || !out || (order > 0 && !work))
+    return set_err(c, SKY_EINVAL, "td_taylor: null pointer");
+  if (order < 0 || order > 32) return set_err(c, SKY_EINVAL, "td_taylor: order %d outside [0, 32]", order);
+  if (out == psi || work == psi || work == out)
+    return set_err(c, SKY_EINVAL, "td_taylor: psi, out and work must be separate buffers");
+  if (!(tau == tau) || tau > 1e300 || tau < -1e300) return set_err(c, SKY_EINVAL, "td_taylor: bad tau");
+  return td_taylor_impl(c, U, B, W, psi, out, work, I, tau, order);
+}
+
 sky_status sky_damped_step(sky_ctx* c, int q, const void* psi, const void* hpsi, const double* eps,
                            void* phi, int I, double x0, double E0, const float* w) {
   CHECK_CTX();

@@ -154,6 +154,8 @@ sky_status upload_twiddles_hamiltonian(Ctx* c);
 sky_status upload_twiddles_fields(Ctx* c);
 sky_status apply_h_impl(Ctx* c, const double* U, const double* B, const double* W,
                         const void* psi, void* hpsi, int I, double* eps, double* hn2);
+sky_status td_taylor_impl(Ctx* c, const double* U, const double* B, const double* W,
+                          const void* psi, void* out, void* work, int I, double tau, int order);
 sky_status damped_step_impl(Ctx* c, int q, const void* psi, const void* hpsi,
                             const double* eps, void* phi, int I, double x0, double E0,
                             const float* w);
