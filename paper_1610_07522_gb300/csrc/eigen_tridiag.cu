@@ -59,7 +59,9 @@ struct TriBatch {
   int n[kMaxBatch];
   int rot[kMaxBatch];            // column j of problem b lives in block (j + rot) mod G
   int soff[kMaxBatch];           // own columns' offset in dynamic shared memory, -1: global
-  int voff[kMaxBatch];           // offset of the block's three work vectors
+  int voff[kMaxBatch];           // offset of the block's three work vectors, -1: global
+  double2* gvec;                 // per (problem slot, block) work vectors when voff = -1
+  size_t gvec_stride;            // double2 per (problem slot, block) in gvec
   int coff;                      // offset of the per-column partials (doubles) in shared memory
   int off[kMaxBatch + 1];        // prefix sums of n: eigenvalue / column items
   int sid[kMaxBatch];            // workspace slot of each problem
@@ -105,6 +107,16 @@ __device__ __forceinline__ TriPtrs tri_ptrs(const TriBatch& a, int b) {
   double* s = reinterpret_cast<double*>(vecs + 5 * m);
   p.d = s; p.e = s + m; p.e2 = s + 2 * m; p.lam = s + 3 * m;
   return p;
+}
+
+// The block's three work vectors of problem b (v_t, v_{t-1}, w): in shared
+// memory, or, for problems too large for it, a private copy per block in
+// global memory (every block computes the same vectors itself, so the copies
+// must not be shared between blocks).
+__device__ __forceinline__ double2* vec_base(const TriBatch& a, int b, double2* dsm) {
+  return a.voff[b] >= 0
+             ? dsm + a.voff[b]
+             : a.gvec + ((size_t)a.sid[b] * gridDim.x + blockIdx.x) * a.gvec_stride;
 }
 
 __device__ __forceinline__ bool tri_run(const TriBatch& a, int b) {
@@ -163,7 +175,7 @@ __device__ void tri_heads(const TriBatch& a, int b0, int t, double2* dsm, HeadSh
   const int b = b0 + q, lane = threadIdx.x & 31, hwarp = ht >> 5;
   const bool on = b < a.np && s_run[b] && t <= a.n[b] - 1;
   const int n = on ? a.n[b] : 0;
-  double2* vb = dsm + (on ? a.voff[b] : 0);
+  double2* vb = on ? vec_base(a, b, dsm) : dsm;
   double2* vn = vb + (size_t)(t & 1) * n;
   const double2* vo = vb + (size_t)((t + 1) & 1) * n;
   double2* w = vb + 2 * (size_t)n;
@@ -318,7 +330,7 @@ __device__ void tri_body(const TriBatch& a, int t, double2* dsm, double* contrib
     }
     const int n = a.n[b];
     double2* col = own_col(a, b, dsm, j, s);
-    const double2* vb = dsm + a.voff[b];
+    const double2* vb = vec_base(a, b, dsm);
     const double2* vn = vb + (size_t)(t & 1) * n;
     const double2* vo = vb + (size_t)((t + 1) & 1) * n;
     const double2* w = vb + 2 * (size_t)n;
@@ -726,6 +738,18 @@ __global__ void __launch_bounds__(kBackWarps * 32) k_hh_back(TriBatch a, int zst
 
 __global__ void k_tri_reset(unsigned* bar) { bar[0] = 0u; }
 
+// A problem of n states keeps its work vectors in global memory when they
+// alone (with the per-column partials) exceed the shared-memory budget.
+bool tri_vectors_global(int n) {
+  return (3 * (size_t)n + (n + 1) / 2 + 1) * sizeof(double2) > kTriSmemMax;
+}
+
+// double2 elements of the global work vectors for nb problems of up to m
+// states on nsm blocks (0 when m fits in shared memory).
+size_t tri_vec_elems(int m, int nb, int nsm) {
+  return tri_vectors_global(m) ? (size_t)nb * nsm * 3 * (size_t)m : 0;
+}
+
 // Shared-memory opt-in of the two kernels that take more than 48 KB (once per
 // context, outside any stream capture).
 sky_status tri_init(Ctx* c) {
@@ -753,14 +777,21 @@ static sky_status tri_group(Ctx* c, int np, const int* idx, const double2* const
   }
   if (ntot == 0) return SKY_OK;
   const int G = (int)(ntot < c->num_sms ? ntot : c->num_sms);
-  // shared memory: three work vectors per problem, then own columns while they fit
+  // shared memory: three work vectors per problem (in global memory for a
+  // problem whose vectors alone exceed it), then own columns while they fit
   size_t used = 0;
   int maxown = 0;
   for (int q = 0; q < np; ++q) {
-    a.voff[q] = (int)used;
-    used += 3 * (size_t)a.n[q];
+    if (tri_vectors_global(a.n[q])) {
+      a.voff[q] = -1;
+    } else {
+      a.voff[q] = (int)used;
+      used += 3 * (size_t)a.n[q];
+    }
     maxown += (a.n[q] + G - 1) / G;
   }
+  a.gvec = c->d_trivec;
+  a.gvec_stride = 3 * (size_t)c->tri_m;
   a.coff = (int)used;
   used += (size_t)(maxown + 1) / 2;
   int rot = 0;
@@ -825,7 +856,9 @@ sky_status eigh_batch_tri(Ctx* c, int np, const double2* const* A, const int* n,
   size_t used = 0;
   groups[0] = 0;
   for (int b = 0; b < np; ++b) {
-    const size_t need = (3 * (size_t)n[b] + (n[b] + 1) / 2 + 1) * sizeof(double2);
+    const bool gv = tri_vectors_global(n[b]);
+    if (gv && (!c->d_trivec || b >= c->tri_vec_slots || n[b] > c->tri_m)) return SKY_EUNSUPPORTED;
+    const size_t need = ((gv ? 0 : 3 * (size_t)n[b]) + (n[b] + 1) / 2 + 1) * sizeof(double2);
     const size_t zneed = (size_t)(n[b] + (n[b] & 1)) * sizeof(double2);
     if (need > kTriSmemMax || zneed > kTriSmemMax) return SKY_EUNSUPPORTED;
     if (used + need > kTriSmemMax) {

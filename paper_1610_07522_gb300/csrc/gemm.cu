@@ -278,7 +278,19 @@ static void launch_zgemm(Ctx* c, const ZJobs& j, int nmax) {
   else k_zgemm<true, true, TS><<<grid, NT, 0, c->stream>>>(j);
 }
 
-sky_status zgemm_batch(Ctx* c, const ZJobs& j) {
+sky_status zgemm_batch(Ctx* c, const ZJobs& jin) {
+  // problems of kOzZgemmMin states or more: tensor-core digit-split products
+  // (one launch sequence each, gated like the rest); the others in one
+  // batched FP64 launch
+  ZJobs j = jin;
+  for (int b = 0; b < j.np; ++b) {
+    const bool gated = j.run[b] || j.stop[b];
+    if (j.n[b] >= (gated ? kOzZgemmGated : kOzZgemmMin) && oz_zgemm_fits(c, j.n[b])) {
+      const sky_status s = oz_zgemm(c, j.ah, j.bh, j.A[b], j.B[b], j.C[b], j.n[b], j.run[b], j.stop[b]);
+      if (s != SKY_OK) return s;
+      j.n[b] = 0;
+    }
+  }
   int nmax = 0;
   long long tiles32 = 0;
   for (int b = 0; b < j.np; ++b) {

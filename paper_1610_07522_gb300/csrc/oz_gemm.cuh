@@ -148,6 +148,8 @@ struct OzArgs {
   const int* eb;            // mode 1: row exponents of B, eb[n >> eb_shift]
   int eb_shift;
   int* status;
+  const int* run;           // device gate: the launch does nothing when *run == 0 or *stop != 0
+  const int* stop;
 };
 
 // First 128-row tile a column tile of the [b; b'] overlap layout needs
@@ -209,6 +211,7 @@ template <int S, int BNT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
               OzArgs a) {
+  if ((a.run && *a.run == 0) || (a.stop && *a.stop != 0)) return;   // uniform in the CTA
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((unsigned long long)smem_raw + 1023ull) & ~1023ull);
   constexpr int TILE_B = BNT * BK * 2;

@@ -87,6 +87,11 @@ __device__ __forceinline__ unsigned short neg_bf16(unsigned short h) { return h 
 __device__ __forceinline__ unsigned pack2(unsigned short lo, unsigned short hi) {
   return (unsigned)lo | ((unsigned)hi << 16);
 }
+// Device-side gate of a launch sequence (a problem whose iteration the device
+// has stopped): skip the work when run says 0 or stop says non-zero.
+__device__ __forceinline__ bool gated_off(const int* run, const int* stop) {
+  return (run && *run == 0) || (stop && *stop != 0);
+}
 
 template <typename R>
 __device__ __forceinline__ int block_max(int v) {
@@ -109,8 +114,10 @@ __device__ __forceinline__ int block_max(int v) {
 
 // E[r] = exponent bound of row r of a [R][V] complex array (0 for a zero row).
 template <typename T>
-__global__ void __launch_bounds__(256) k_oz_rowexp(const T* __restrict__ src, long long V, int* E) {
+__global__ void __launch_bounds__(256) k_oz_rowexp(const T* __restrict__ src, long long V, int* E,
+                                                   const int* run, const int* stop) {
   using R = decltype(T().x);
+  if (gated_off(run, stop)) return;
   const T* row = src + (long long)blockIdx.x * V;
   int m = INT_MIN;
   for (long long k = threadIdx.x; k < V; k += blockDim.x) {
@@ -129,8 +136,10 @@ __global__ void __launch_bounds__(256) k_oz_split_rows(const T* __restrict__ src
                                                        long long c0, long long nc,
                                                        const int* __restrict__ E,
                                                        unsigned short* dst, long long ld,
-                                                       long long ss, int prime_off) {
+                                                       long long ss, int prime_off,
+                                                       const int* run, const int* stop) {
   using RT = decltype(T().x);
+  if (gated_off(run, stop)) return;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)R * nc) return;
   const int r = (int)(e / nc);
@@ -237,6 +246,64 @@ __global__ void __launch_bounds__(256) k_oz_split_rot_b(const T* __restrict__ ph
   }
 }
 
+// Digits of the rows of an n x n complex matrix operand in one pass per row
+// (one block per row r): the operand row is row r of src, or with trans the
+// conjugate of column r (a conjugate transpose read in place).  Its exponent
+// goes to E[r]; digits to dst[s][r][2k + {0, 1}], and with prime_off >= 0
+// (Im, -Re) to row prime_off + r.
+template <int S>
+__global__ void __launch_bounds__(256) k_oz_split_mat(const double2* __restrict__ src, int n,
+                                                      int trans, int* E, unsigned short* dst,
+                                                      long long ld, long long ss, int prime_off,
+                                                      const int* run, const int* stop) {
+  if (gated_off(run, stop)) return;
+  const int r = blockIdx.x;
+  auto at = [&](int k) {
+    return trans ? conjx(src[(long long)k * n + r]) : src[(long long)r * n + k];
+  };
+  int m = INT_MIN;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double2 v = at(k);
+    m = max(m, max(exp_of(v.x), exp_of(v.y)));
+  }
+  m = block_max<double>(m);
+  const int Er = m == INT_MIN ? 0 : m;
+  if (threadIdx.x == 0) E[r] = Er;
+  unsigned* d32 = reinterpret_cast<unsigned*>(dst);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double2 v = at(k);
+    unsigned short dr[S], di[S];
+    digits<S>(v.x, Er, dr);
+    digits<S>(v.y, Er, di);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      d32[(s * ss + (long long)r * ld) / 2 + k] = pack2(dr[s], di[s]);
+      if (prime_off >= 0)
+        d32[(s * ss + (long long)(prime_off + r) * ld) / 2 + k] = pack2(di[s], neg_bf16(dr[s]));
+    }
+  }
+}
+
+// C[m][c] = conj(sum_z (P_z[m][c] + i P_z[m][n + c])) 2^{Ea[m] + Eb[c] - 16}: the
+// product X Y from the full overlap of X with Zt = conj(Y)^T.
+__global__ void k_oz_zgemm_reduce(const float2* __restrict__ P, int nz, long long sp, long long ldp,
+                                  int n, const int* __restrict__ Ea, const int* __restrict__ Eb,
+                                  double2* C, const int* run, const int* stop) {
+  if (gated_off(run, stop)) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int m = (int)(e / n), c = (int)(e % n);
+  double re = 0.0, im = 0.0;
+  for (int z = 0; z < nz; ++z) {
+    const float2* Pz = P + z * sp + (long long)m * ldp;
+    const float2 r = Pz[c], i = Pz[n + c];
+    re += (double)r.x + (double)r.y;
+    im += (double)i.x + (double)i.y;
+  }
+  const double sc = oz::pow2d(Ea[m] + Eb[c] - 16);
+  C[e] = make_double2(sc * re, -sc * im);
+}
+
 // X[a][b] (+)= dV 2^{Ea[a] + Eb[b] - 16} sum_z (P_z[a][b] + i P_z[a][I + b]) for a >= b
 // (each P entry an unevaluated pair hi + lo), mirrored.
 __global__ void k_oz_overlap_reduce(const float2* __restrict__ P, int nz, long long sp,
@@ -286,11 +353,11 @@ sky_status oz_overlap_t(Ctx* c, const void* a, const void* b, int I, double2* X)
   cudaStream_t st = c->stream;
   // exponents over whole rows (shared by every K chunk)
   if (f64) {
-    k_oz_rowexp<double2><<<I, 256, 0, st>>>((const double2*)a, V, Ea);
-    if (b != a) k_oz_rowexp<double2><<<I, 256, 0, st>>>((const double2*)b, V, Eb);
+    k_oz_rowexp<double2><<<I, 256, 0, st>>>((const double2*)a, V, Ea, nullptr, nullptr);
+    if (b != a) k_oz_rowexp<double2><<<I, 256, 0, st>>>((const double2*)b, V, Eb, nullptr, nullptr);
   } else {
-    k_oz_rowexp<float2><<<I, 256, 0, st>>>((const float2*)a, V, Ea);
-    if (b != a) k_oz_rowexp<float2><<<I, 256, 0, st>>>((const float2*)b, V, Eb);
+    k_oz_rowexp<float2><<<I, 256, 0, st>>>((const float2*)a, V, Ea, nullptr, nullptr);
+    if (b != a) k_oz_rowexp<float2><<<I, 256, 0, st>>>((const float2*)b, V, Eb, nullptr, nullptr);
   }
   note_launch(b != a ? 2 : 1);
   if (b == a) Eb = Ea;
@@ -310,16 +377,16 @@ sky_status oz_overlap_t(Ctx* c, const void* a, const void* b, int I, double2* X)
     const long long tot = (long long)I * n;
     if (f64) {
       k_oz_split_rows<double2, S><<<div_up(tot, 256), 256, 0, st>>>(
-          (const double2*)b, I, V, c0, n, Eb, Bp, ld, sb, I);
+          (const double2*)b, I, V, c0, n, Eb, Bp, ld, sb, I, nullptr, nullptr);
       if (b != a)
         k_oz_split_rows<double2, S><<<div_up(tot, 256), 256, 0, st>>>(
-            (const double2*)a, I, V, c0, n, Ea, Ap, ld, sa, -1);
+            (const double2*)a, I, V, c0, n, Ea, Ap, ld, sa, -1, nullptr, nullptr);
     } else {
       k_oz_split_rows<float2, S><<<div_up(tot, 256), 256, 0, st>>>(
-          (const float2*)b, I, V, c0, n, Eb, Bp, ld, sb, I);
+          (const float2*)b, I, V, c0, n, Eb, Bp, ld, sb, I, nullptr, nullptr);
       if (b != a)
         k_oz_split_rows<float2, S><<<div_up(tot, 256), 256, 0, st>>>(
-            (const float2*)a, I, V, c0, n, Ea, Ap, ld, sa, -1);
+            (const float2*)a, I, V, c0, n, Ea, Ap, ld, sa, -1, nullptr, nullptr);
     }
     note_launch(b != a ? 2 : 1);
     cudaError_t e = cudaGetLastError();
@@ -405,6 +472,61 @@ sky_status oz_rotate_t(Ctx* c, const void* phi, const double2* M, int I, void* o
 
 }  // namespace
 
+// C = opA(A) opB(B) for n x n complex FP64 matrices (op: identity or conjugate
+// transpose) on the tensor cores: with X = opA(A) and Zt = conj(opB(B))^T,
+// C[m][c] = conj(sum_k conj(X[m][k]) Zt[c][k]), the full digit-split overlap
+// of X's rows with Zt's rows (6 digits; about 1e-14 of the largest element).
+// Every kernel is skipped when the device gate (run, stop) says so.
+bool oz_zgemm_fits(const Ctx* c, int n) {
+  const long long K = 2LL * n;
+  return c->d_ozB && n <= c->max_states &&
+         (long long)oz::kS64 * 2 * n * K <= (long long)c->oz_b_elems &&
+         (long long)oz::kS64 * n * K <= (long long)c->oz_a_elems;
+}
+
+sky_status oz_zgemm(Ctx* c, bool ah, bool bh, const double2* A, const double2* B, double2* C,
+                    int n, const int* run, const int* stop) {
+  constexpr int S = oz::kS64, BN = oz::kBN64;
+  cudaStream_t st = c->stream;
+  int* Ea = c->d_ozE;
+  int* Eb = c->d_ozE + c->max_states;
+  const long long K = 2LL * n, ld = round_up(K, 8);
+  unsigned short* Bp = (unsigned short*)c->d_ozB;
+  unsigned short* Ap = (unsigned short*)c->d_ozA;
+  const long long sb = 2LL * n * ld, sa = (long long)n * ld;
+  const long long tot = (long long)n * n;
+  // X = opA(A): rows of A, or conjugated columns; Zt = conj(opB(B))^T: rows of
+  // B when opB is the conjugate transpose, else conjugated columns of B
+  k_oz_split_mat<S><<<n, 256, 0, st>>>(A, n, ah ? 1 : 0, Ea, Ap, ld, sa, -1, run, stop);
+  k_oz_split_mat<S><<<n, 256, 0, st>>>(B, n, bh ? 0 : 1, Eb, Bp, ld, sb, n, run, stop);
+  note_launch(2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(c, e, "oz zgemm split");
+  const int tiles = oz::count_tiles(n, 2 * n, BN, false, n);
+  const long long nkb = (K + oz::BK - 1) / oz::BK;
+  long long z = (c->num_sms + tiles - 1) / tiles;
+  if (z > nkb / 8) z = nkb / 8;
+  if (z < 1) z = 1;
+  const long long spart = 2LL * n * n;
+  if ((size_t)z * spart > c->oz_p_elems) z = (long long)(c->oz_p_elems / spart);
+  if (z < 1) return set_err(c, SKY_EINVAL, "zgemm: partial buffer too small for n=%d", n);
+  int zi = (int)z;
+  oz::OzArgs g{};
+  g.mode = 0;
+  g.P = c->d_ozP;
+  g.ldp = 2LL * n;
+  g.sp = spart;
+  g.status = c->d_status;
+  g.run = run;
+  g.stop = stop;
+  e = oz::oz_gemm<S, BN>(Ap, ld, sa, n, Bp, ld, sb, 2 * n, (int)K, false, n, g, &zi, st);
+  if (e != cudaSuccess) return cuda_check(c, e, "oz zgemm");
+  k_oz_zgemm_reduce<<<div_up(tot, 256), 256, 0, st>>>(c->d_ozP, zi, spart, 2LL * n, n, Ea, Eb, C,
+                                                      run, stop);
+  note_launch();
+  return cuda_check(c, cudaGetLastError(), "oz zgemm reduce");
+}
+
 sky_status oz_overlap(Ctx* c, const void* a, const void* b, int I, double2* X) {
   if (c->prec == SKY_F64) return oz_overlap_t<oz::kS64, oz::kBN64>(c, a, b, I, X);
   return oz_overlap_t<oz::kS32, oz::kBN32>(c, a, b, I, X);
@@ -422,6 +544,10 @@ sky_status oz_rotate(Ctx* c, const void* phi, const double2* M, int I, void* out
 // SKY_OZ_MB (default 4096 MiB).
 void oz_scratch_sizes(sky_prec prec, int Imax, long long V, int nsm, size_t* a_elems,
                       size_t* b_elems, size_t* e_elems, size_t* p_elems) {
+  if (Imax <= 0 || V <= 0) {
+    *a_elems = *b_elems = *e_elems = *p_elems = 1;
+    return;
+  }
   const int S = oz_slices(prec), bn = oz_bn(prec);
   const long long Ipad = round_up(Imax, 32);
   const long long ov_b = (long long)S * 2 * Imax * round_up(2 * V, 8);

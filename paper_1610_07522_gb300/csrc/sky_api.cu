@@ -88,7 +88,7 @@ static void free_all(Ctx* c) {
                   c->d_stats, c->d_tcA[0], c->d_tcA[1], c->d_tcA[2], c->d_tcB[0],
                   c->d_tcB[1], c->d_tcB[2], c->d_tcRotA[0], c->d_tcRotA[1], c->d_tcRotA[2],
                   c->d_tcPart, c->d_netpart, c->d_trid, c->d_ozA, c->d_ozB, c->d_ozE,
-                  c->d_ozP};
+                  c->d_ozP, c->d_trivec};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -124,13 +124,25 @@ static sky_status alloc_tc_scratch(Ctx* c, int pieces) {
   return s;
 }
 
-// Slice buffers, exponents and partials of the tensor-core split GEMMs of the
-// FP64 and FP32 forms; kept if already present.
-static sky_status alloc_oz_scratch(Ctx* c) {
-  if (c->d_ozB) return SKY_OK;
+// Digit buffers, exponents and partials of the tensor-core
+// split GEMMs: the overlap and recombination of the FP64 and FP32 forms
+// (when oz_on) and the eigensolver's I x I products (from kOzZgemmMin
+// states on, every form).  Buffers already present and large enough are kept;
+// smaller ones are replaced (callers synchronise the stream first).
+static sky_status alloc_oz_scratch(Ctx* c, bool overlap_too) {
   const int Imax = c->max_states > 0 ? c->max_states : 1;
   size_t ae, be, ee, pe;
-  oz_scratch_sizes(c->prec, Imax, 2LL * c->G, c->num_sms, &ae, &be, &ee, &pe);
+  oz_scratch_sizes(overlap_too ? c->prec : SKY_F64, overlap_too ? Imax : 0, overlap_too ? 2LL * c->G : 0,
+                   c->num_sms, &ae, &be, &ee, &pe);
+  if (Imax >= kOzZgemmMin) {   // the I x I products
+    const size_t zb = (size_t)6 * 2 * Imax * 2 * Imax;
+    if (zb > be) be = zb;
+    if (zb / 2 > ae) ae = zb / 2;
+    if ((size_t)2 * Imax * Imax > pe) pe = (size_t)2 * Imax * Imax;
+  }
+  if (ee < (size_t)(2 * Imax + 2LL * c->G + 64)) ee = (size_t)(2 * Imax + 2LL * c->G + 64);
+  if (c->d_ozB && c->oz_a_elems >= ae && c->oz_b_elems >= be && c->oz_p_elems >= pe)
+    return SKY_OK;
   unsigned short *A = nullptr, *Bp = nullptr;
   int* E = nullptr;
   float2* P = nullptr;
@@ -144,6 +156,9 @@ static sky_status alloc_oz_scratch(Ctx* c) {
       if (p) cudaFree(p);
     return s;
   }
+  void* old[] = {c->d_ozA, c->d_ozB, c->d_ozE, c->d_ozP};
+  for (void* p : old)
+    if (p) cudaFree(p);
   c->d_ozA = A; c->d_ozB = Bp; c->d_ozE = E; c->d_ozP = P;
   c->oz_a_elems = ae; c->oz_b_elems = be; c->oz_p_elems = pe;
   return SKY_OK;
@@ -273,10 +288,14 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   c->tri_m = m;
   c->tri_slot = tri_slot_doubles(m);
   ALLOC(c->d_trid, c->tri_slot * c->eig_batch);
+  if (s == SKY_OK && tri_vec_elems(m, c->eig_batch, c->num_sms) > 0) {
+    ALLOC(c->d_trivec, tri_vec_elems(m, c->eig_batch, c->num_sms));
+    c->tri_vec_slots = c->eig_batch;
+  }
   ALLOC(c->d_gate, 8 * kMaxBatch);
   if (s == SKY_OK && is_tc(prec)) s = alloc_tc_scratch(c, tc_nsplit(prec));
   c->oz_on = is_tc(prec) ? 0 : 1;
-  if (s == SKY_OK && c->oz_on) s = alloc_oz_scratch(c);
+  if (s == SKY_OK && (c->oz_on || Imax >= kOzZgemmMin)) s = alloc_oz_scratch(c, c->oz_on != 0);
   ALLOC(c->d_stats, 8);
   ALLOC(c->d_netpart, net_partial_elems(c->G));
   if (s == SKY_OK) {
@@ -534,7 +553,7 @@ sky_status sky_set_prec(sky_ctx* c, sky_prec prec) {
   if (e != cudaSuccess) return cuda_check(c, e, "set_prec sync");
   const sky_prec old = c->prec;
   c->prec = prec;   // the scratch sizes depend on the form
-  const sky_status s = is_tc(prec) ? alloc_tc_scratch(c, tc_nsplit(prec)) : alloc_oz_scratch(c);
+  const sky_status s = is_tc(prec) ? alloc_tc_scratch(c, tc_nsplit(prec)) : alloc_oz_scratch(c, true);
   if (s != SKY_OK) {
     c->prec = old;
     return s;
@@ -583,7 +602,9 @@ sky_status sky_tune_set(sky_ctx* c, sky_knob knob, int value) {
       if (value != 0 && value != 1) break;
       if (value == 1 && is_tc(c->prec)) break;
       if (value == 1) {
-        const sky_status s = alloc_oz_scratch(c);
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_check(c, e, "tune sync");
+        const sky_status s = alloc_oz_scratch(c, true);
         if (s != SKY_OK) return s;
       }
       c->oz_on = value;
@@ -627,9 +648,12 @@ sky_status sky_reserve_batch(sky_ctx* c, int nb) {
   if (s == SKY_OK) s = dalloc(c, &rot, jacobi_rot_bytes(m) * nb);
   for (int k = 0; k < 6 && s == SKY_OK; ++k) s = dalloc(c, &sm[k], c->small_slot * nb);
   double* trid = nullptr;
+  double2* tvec = nullptr;
   if (s == SKY_OK) s = dalloc(c, &trid, c->tri_slot * nb);
+  if (s == SKY_OK && tri_vec_elems(m, nb, c->num_sms) > 0)
+    s = dalloc(c, &tvec, tri_vec_elems(m, nb, c->num_sms));
   if (s != SKY_OK) {
-    void* ptrs[] = {a0, a1, v, w, rot, sm[0], sm[1], sm[2], sm[3], sm[4], sm[5], trid};
+    void* ptrs[] = {a0, a1, v, w, rot, sm[0], sm[1], sm[2], sm[3], sm[4], sm[5], trid, tvec};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     return s;
@@ -637,9 +661,11 @@ sky_status sky_reserve_batch(sky_ctx* c, int nb) {
   cudaStreamSynchronize(c->stream);   // no queued work may still use the old buffers
   void* old[] = {c->d_eigA[0], c->d_eigA[1], c->d_eigV, c->d_eigw, c->d_eigrot, c->d_small[0],
                  c->d_small[1], c->d_small[2], c->d_small[3], c->d_small[4], c->d_small[5],
-                 c->d_trid};
+                 c->d_trid, c->d_trivec};
   for (void* p : old)
     if (p) cudaFree(p);
+  c->d_trivec = tvec;
+  c->tri_vec_slots = tvec ? nb : 0;
   c->d_eigA[0] = a0; c->d_eigA[1] = a1; c->d_eigV = v; c->d_eigw = w; c->d_eigrot = rot;
   for (int k = 0; k < 6; ++k) c->d_small[k] = sm[k];
   c->d_trid = trid;

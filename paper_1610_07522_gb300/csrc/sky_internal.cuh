@@ -124,6 +124,8 @@ struct Ctx {
   double* d_trid;                   // tridiagonal solver vectors and LU rows [tri_slot] per problem
   size_t tri_slot;                  // doubles per problem in d_trid
   int tri_m;                        // vector stride inside a d_trid slot (even)
+  double2* d_trivec;                // per-block work vectors of problems too large for shared memory
+  int tri_vec_slots;                // problems d_trivec has room for
   // exact-integer split GEMMs of the FP64 and FP32 forms (oz_ops.cu)
   int oz_on;                        // 1: tensor-core split GEMMs, 0: FP64 FMA kernels
   void* d_ozA;                      // bf16 slices of the row operand
@@ -204,6 +206,8 @@ sky_status subspace_literal_batch(Ctx* c, int np, const double2* const* H,
 sky_status eigh_batch_tri(Ctx* c, int np, const double2* const* A, const int* n,
                           double* const* w, double2* const* Z, const int* run, int run_stride);
 sky_status tri_init(Ctx* c);
+bool tri_vectors_global(int n);
+size_t tri_vec_elems(int m, int nb, int nsm);
 inline size_t tri_slot_doubles(int m) { return (size_t)m * m + 16 * (size_t)m; }
 sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z,
                      const int* run = nullptr);
@@ -219,6 +223,15 @@ void oz_scratch_sizes(sky_prec prec, int Imax, long long V, int nsm, size_t* a_e
                       size_t* b_elems, size_t* e_elems, size_t* p_elems);
 sky_status oz_overlap(Ctx* c, const void* a, const void* b, int I, double2* X);
 sky_status oz_rotate(Ctx* c, const void* phi, const double2* M, int I, void* out);
+// I x I complex products from this many states on go to the tensor cores;
+// device-gated ones (the Newton-Schulz iterations, most of which the device
+// skips) from kOzZgemmGated on, below which one batched FP64 launch costs
+// less than the digit-split launch sequence a skipped product still enqueues
+constexpr int kOzZgemmMin = 192;
+constexpr int kOzZgemmGated = 768;
+bool oz_zgemm_fits(const Ctx* c, int n);
+sky_status oz_zgemm(Ctx* c, bool ah, bool bh, const double2* A, const double2* B, double2* C,
+                    int n, const int* run, const int* stop);
 sky_status tc_rotate(Ctx* c, const void* phi, const double2* M, int I, void* out);
 inline bool is_tc(sky_prec p) { return p == SKY_F32_BF16X3 || p == SKY_F32_BF16X6; }
 size_t jacobi_rot_bytes(int m);

@@ -166,3 +166,20 @@ def test_tridiagonal_wait_budget_runs_out_with_etimeout_and_recovers():
     M, lam = _solve(c, H)
     B.sky_destroy(c)
     _check(H, M, lam, "tridiagonal after a timeout")
+
+
+def test_tridiagonal_route_beyond_shared_memory():
+    """3700 states: the reduction's three work vectors per block no longer fit
+    in shared memory and live in a per-block global buffer; the route must
+    still be taken (no Jacobi fallback) and agree with the oracle."""
+    n = 3700
+    rng = np.random.default_rng(37)
+    H = _matrix("random", n, rng)
+    c = _ctx(n)
+    B.sky_tune_set(c, B.SKY_KNOB_EIGEN_METHOD, B.SKY_EIG_TRIDIAGONAL)
+    B.sky_stats(c, reset=True)
+    M, lam = _solve(c, H)
+    st = B.sky_stats(c)
+    B.sky_destroy(c)
+    assert st["tridiagonal_solves"] == 1 and st["jacobi_solves"] == 0
+    _check(H, M, lam, f"tridiagonal random n={n}")

@@ -180,3 +180,43 @@ def test_integer_operands_are_exact(grid, bits):
         assert np.array_equal(host(X), want)
     finally:
         B.sky_destroy(c)
+
+
+@pytest.mark.parametrize("I", [200, 413, 800])
+@pytest.mark.parametrize("near_identity", [True, False])
+def test_large_loewdin_and_ritz_products_on_the_tensor_cores(I, near_identity):
+    """From 192 states on, the I x I complex products of the Rayleigh-Ritz
+    step, and from 768 on also the device-gated ones of the Loewdin factor
+    (Newton-Schulz when S is near the identity, else the eigendecomposition
+    route, the Newton-Schulz products then gated off on the device), run as
+    digit-split tensor-core products; against the oracle's
+    eigendecomposition-based Loewdin and Ritz."""
+    rng = np.random.default_rng(300 + I + near_identity)
+    A = rng.standard_normal((I, I)) + 1j * rng.standard_normal((I, I))
+    Hm = A + A.conj().T
+    if near_identity:
+        S = np.eye(I) + 0.02 * Hm / np.sqrt(I)
+    else:
+        X = rng.standard_normal((I, I)) + 1j * rng.standard_normal((I, I))
+        S = X @ X.conj().T / I + 0.05 * np.eye(I)
+    H = 30.0 * Hm / np.sqrt(I)
+    H = S @ H @ S          # a Hamiltonian matrix in the non-orthonormal basis
+    H = 0.5 * (H + H.conj().T)
+    C_w = O.loewdin(S)
+    M_w, lam_w = O.rayleigh_ritz(S, H)
+    c = make_ctx((8, 8, 8), B.SKY_F64, I)
+    try:
+        dS, dH = dev(S), dev(H)
+        C = torch.zeros_like(dS)
+        M = torch.zeros_like(dS)
+        lam = torch.zeros(I, dtype=torch.float64, device="cuda:0")
+        B.sky_orthonormalize(c, dS, I, C)
+        B.sky_subspace_diag(c, dH, C, I, M, lam)
+        B.sky_sync(c)
+        Cg, Mg, lg = host(C), host(M), host(lam)
+        assert relerr(Cg, C_w) < 1e-10
+        nrm = max(1.0, float(np.max(np.abs(lam_w))))
+        assert np.max(np.abs(lg - lam_w)) < 1e-10 * nrm
+        assert np.max(np.abs(Mg.conj().T @ S @ Mg - np.eye(I))) < 1e-10
+    finally:
+        B.sky_destroy(c)
