@@ -378,6 +378,58 @@ def batched_convergence(dev, net, maxit):
     return out
 
 
+# ---------------------------------------------------------------- production shapes
+# The paper's production shapes (Sec. 5.1, Tables 2-3): A = 6000, 3000 n + 3000 p,
+# in 32^3 and 48^3 boxes (dx = 1 fm), blob starts; seconds per iteration on one
+# GB300 in the paper's FP64 form and the FP32-spinor form (context only: the
+# paper's figures are Cray XC40 seconds per iteration).
+PRODUCTION = [("sly4_32cubed_3000n3000p", "fp64"), ("sly4_32cubed_3000n3000p", "f32"),
+              ("sly4_48cubed_3000n3000p", "f32")]
+
+
+def production_leg(dev, iters=2):
+    """Seconds per full iteration (both species on two streams) of the A = 6000
+    shapes after one untimed iteration from the start; input generation (host,
+    NumPy) and the load are timed apart."""
+    import torch
+    from paper_1610_07522_gb300 import inputs as IN
+    from paper_1610_07522_gb300.solver import Solver
+    out = {"paper_context_s_per_iteration": {"32^3, 32 Haswell cores": 59.8,
+                                             "32^3, 1536 Haswell cores": 3.5}}
+    for name, form in PRODUCTION:
+        w = IN.WORKLOADS[name]
+        t = time.perf_counter()
+        inp = IN.make_inputs(w)
+        gen_s = time.perf_counter() - t
+        s = Solver(w, prec=FORMS[form], device=dev, concurrent_species=True)
+        t = time.perf_counter()
+        s.load(inp["psi0"], inp.get("rho0"), inp.get("tau0"))
+        del inp
+        s.step()
+        s.sync()
+        load_s = time.perf_counter() - t
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        for _ in range(iters):
+            s.step()
+        e1.record(s.stream)
+        torch.cuda.synchronize(dev)
+        E, de, _ = s.energy()
+        from paper_1610_07522_gb300 import binding as B
+        B_stats = B.sky_stats(s.ctx)
+        out[f"{name}_{form}"] = {"grid": list(w.grid), "N": w.N, "Z": w.Z, "form": form,
+                                 "s_per_iteration": e0.elapsed_time(e1) / 1e3 / iters,
+                                 "iterations_timed": iters, "input_generation_s": round(gen_s, 2),
+                                 "load_and_first_iteration_s": round(load_s, 2),
+                                 "E_per_A": E / (w.N + w.Z), "delta_eps": de,
+                                 "solver_stats": B_stats}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- batched form
 def batched_leg(dev, form="bf16x3", count=64, steps=10):
     """The 64 uneven, twisted boxes of inputs.batched_workloads() (grids 16^3,
@@ -715,6 +767,9 @@ def run_gpu(args):
     batched = None
     if rank == 0 and not args.no_batched:
         batched = batched_leg(dev)
+    production = None
+    if rank == 0 and not args.no_production:
+        production = production_leg(dev)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -746,6 +801,7 @@ def run_gpu(args):
         "time_dependent": td,
         "convergence": conv,
         "batched": batched,
+        "production_A6000": production,
     }
     s.close()
     if rank == 0:
@@ -767,6 +823,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-box batched (CUDA graph) form")
+    ap.add_argument("--no-production", action="store_true",
+                    help="skip the A = 6000 production shapes (32^3, 48^3)")
     ap.add_argument("--no-td", action="store_true",
                     help="skip the time-dependent stepping leg")
     ap.add_argument("--no-convergence", action="store_true",

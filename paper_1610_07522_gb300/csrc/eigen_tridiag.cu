@@ -744,10 +744,14 @@ bool tri_vectors_global(int n) {
   return (3 * (size_t)n + (n + 1) / 2 + 1) * sizeof(double2) > kTriSmemMax;
 }
 
-// double2 elements of the global work vectors for nb problems of up to m
-// states on nsm blocks (0 when m fits in shared memory).
+// double2 elements of the global work vectors for the problems of a batch
+// of nb problems of up to m states on nsm blocks: needed when one problem,
+// or the tridiagonal route's largest batch (8 problems) of them, does not fit
+// in shared memory (0 otherwise).
 size_t tri_vec_elems(int m, int nb, int nsm) {
-  return tri_vectors_global(m) ? (size_t)nb * nsm * 3 * (size_t)m : 0;
+  const int k = nb < 8 ? nb : 8;
+  const size_t one = (3 * (size_t)m + (m + 1) / 2 + 1) * sizeof(double2);
+  return (tri_vectors_global(m) || k * one > kTriSmemMax) ? (size_t)k * nsm * 3 * (size_t)m : 0;
 }
 
 // Shared-memory opt-in of the two kernels that take more than 48 KB (once per
@@ -762,7 +766,8 @@ sky_status tri_init(Ctx* c) {
 
 // One launch sequence for the problems idx[0..np) of a batch (their vectors fit).
 static sky_status tri_group(Ctx* c, int np, const int* idx, const double2* const* A, const int* n,
-                            double* const* w, double2* const* Z, const int* run, int run_stride) {
+                            double* const* w, double2* const* Z, const int* run, int run_stride,
+                            const bool* gvec) {
   TriBatch a;
   a.np = np;
   a.off[0] = 0;
@@ -782,7 +787,7 @@ static sky_status tri_group(Ctx* c, int np, const int* idx, const double2* const
   size_t used = 0;
   int maxown = 0;
   for (int q = 0; q < np; ++q) {
-    if (tri_vectors_global(a.n[q])) {
+    if (gvec[idx[q]]) {
       a.voff[q] = -1;
     } else {
       a.voff[q] = (int)used;
@@ -852,12 +857,31 @@ static sky_status tri_group(Ctx* c, int np, const int* idx, const double2* const
 sky_status eigh_batch_tri(Ctx* c, int np, const double2* const* A, const int* n,
                           double* const* w, double2* const* Z, const int* run, int run_stride) {
   int groups[kMaxBatch + 1], order[kMaxBatch];
+  bool gvec[kMaxBatch];
   int ng = 0;
   size_t used = 0;
   groups[0] = 0;
+  // work vectors in global memory for problems too large for shared memory,
+  // and, when the global buffer has room, for the largest problems until the
+  // whole batch fits one launch sequence (a device-gated batch must: it
+  // cannot be split)
+  const bool room = c->d_trivec && np <= c->tri_vec_slots;
+  size_t total = 0;
   for (int b = 0; b < np; ++b) {
-    const bool gv = tri_vectors_global(n[b]);
-    if (gv && (!c->d_trivec || b >= c->tri_vec_slots || n[b] > c->tri_m)) return SKY_EUNSUPPORTED;
+    gvec[b] = tri_vectors_global(n[b]);
+    total += ((gvec[b] ? 0 : 3 * (size_t)n[b]) + (n[b] + 1) / 2 + 1) * sizeof(double2);
+  }
+  while (room && total > kTriSmemMax) {
+    int big = -1;
+    for (int b = 0; b < np; ++b)
+      if (!gvec[b] && (big < 0 || n[b] > n[big])) big = b;
+    if (big < 0) break;
+    gvec[big] = true;
+    total -= 3 * (size_t)n[big] * sizeof(double2);
+  }
+  for (int b = 0; b < np; ++b) {
+    const bool gv = gvec[b];
+    if (gv && (!room || n[b] > c->tri_m)) return SKY_EUNSUPPORTED;
     const size_t need = ((gv ? 0 : 3 * (size_t)n[b]) + (n[b] + 1) / 2 + 1) * sizeof(double2);
     const size_t zneed = (size_t)(n[b] + (n[b] & 1)) * sizeof(double2);
     if (need > kTriSmemMax || zneed > kTriSmemMax) return SKY_EUNSUPPORTED;
@@ -872,7 +896,7 @@ sky_status eigh_batch_tri(Ctx* c, int np, const double2* const* A, const int* n,
   if (run && ng > 1) return SKY_EUNSUPPORTED;
   for (int g = 0; g < ng; ++g) {
     const sky_status s = tri_group(c, groups[g + 1] - groups[g], order + groups[g], A, n, w, Z,
-                                   run, run_stride);
+                                   run, run_stride, gvec);
     if (s != SKY_OK) return s;
   }
   return SKY_OK;

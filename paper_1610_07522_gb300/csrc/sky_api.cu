@@ -290,7 +290,7 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   ALLOC(c->d_trid, c->tri_slot * c->eig_batch);
   if (s == SKY_OK && tri_vec_elems(m, c->eig_batch, c->num_sms) > 0) {
     ALLOC(c->d_trivec, tri_vec_elems(m, c->eig_batch, c->num_sms));
-    c->tri_vec_slots = c->eig_batch;
+    c->tri_vec_slots = c->eig_batch < 8 ? c->eig_batch : 8;
   }
   ALLOC(c->d_gate, 8 * kMaxBatch);
   if (s == SKY_OK && is_tc(prec)) s = alloc_tc_scratch(c, tc_nsplit(prec));
@@ -665,7 +665,7 @@ sky_status sky_reserve_batch(sky_ctx* c, int nb) {
   for (void* p : old)
     if (p) cudaFree(p);
   c->d_trivec = tvec;
-  c->tri_vec_slots = tvec ? nb : 0;
+  c->tri_vec_slots = tvec ? (nb < 8 ? nb : 8) : 0;
   c->d_eigA[0] = a0; c->d_eigA[1] = a1; c->d_eigV = v; c->d_eigw = w; c->d_eigrot = rot;
   for (int k = 0; k < 6; ++k) c->d_small[k] = sm[k];
   c->d_trid = trid;

@@ -183,3 +183,30 @@ def test_tridiagonal_route_beyond_shared_memory():
     B.sky_destroy(c)
     assert st["tridiagonal_solves"] == 1 and st["jacobi_solves"] == 0
     _check(H, M, lam, f"tridiagonal random n={n}")
+
+
+def test_gated_loewdin_batch_too_large_for_one_shared_memory_stays_tridiagonal():
+    """Two 2000-state overlaps far from the identity (the eigendecomposition
+    route, gated on the device): their work vectors together exceed shared
+    memory, and a gated batch cannot be split into launch groups, so the
+    larger problems' vectors move to the global buffer and the batch stays on
+    the tridiagonal route (no Jacobi fallback)."""
+    n = 2000
+    rng = np.random.default_rng(41)
+    S = []
+    for _ in range(2):
+        X = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        S.append(X @ X.conj().T / n + 0.05 * np.eye(n))
+    c = _ctx(n)
+    B.sky_stats(c, reset=True)
+    dS = [_dev(s_) for s_ in S]
+    C = [torch.zeros((n, n), dtype=torch.complex128, device="cuda:0") for _ in range(2)]
+    B.sky_orthonormalize_batched(c, dS, [n, n], C)
+    B.sky_sync(c)
+    st = B.sky_stats(c)
+    B.sky_destroy(c)
+    assert st["tridiagonal_solves"] == 2 and st["jacobi_solves"] == 0
+    for b in range(2):
+        Cw = O.loewdin(S[b])
+        Cg = C[b].cpu().numpy()
+        assert np.max(np.abs(Cg - Cw)) < 1e-10 * np.max(np.abs(Cw))
