@@ -202,7 +202,7 @@ CONV_SNAPS = [0, 2, 5, 12, 25, 60, 120, 180, 240, 360, 480, 600, 720, 840, 960]
 CONV_WINDOW = 5
 
 
-def convergence_leg(dev, maxit=4000):
+def convergence_leg(dev, maxit=4000, nets_out=None):
     """Seconds and iterations to |E_n/A - E_{n-1}/A| < 1e-6 MeV (held for
     CONV_WINDOW consecutive iterations, the same rule for every form) on the
     16^3, 16n+16p workload for each form: plain FP64, FP32, split-BF16 (x3),
@@ -298,6 +298,8 @@ def convergence_leg(dev, maxit=4000):
         s.close()
     out["learned_configs123_train_seconds"] = round(time.perf_counter() - t, 3)
     out["learned_configs123_fp32"] = solve(B.SKY_F32, net3)
+    if nets_out is not None:
+        nets_out["net_configs123"] = net3
     out["batched"] = batched_convergence(dev, net, maxit)
     base = out["fp64"]["seconds"]
     forms = ("fp64_paper_literal", "fp32", "bf16x3", "bf16x3_to_fp32", "learned_fp64", "learned_fp32",
@@ -424,6 +426,56 @@ def production_leg(dev, iters=2):
                                  "load_and_first_iteration_s": round(load_s, 2),
                                  "E_per_A": E / (w.N + w.Z), "delta_eps": de,
                                  "solver_stats": B_stats}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    return out
+
+
+# ---------------------------------------------------------------- learned form at scale
+CONFIG5 = "sly4_64cubed_5600n2400p"
+
+
+def config5_leg(dev, net, iters=3):
+    """The learned-weight form at scale: 64^3, 5600 n + 2400 p, FP32 spinors
+    (the FP64 form has no 64-point FFT lines), blob densities and seeded noisy
+    plane-wave states made on the device; ``iters`` iterations (a labelled
+    cap: convergence at this size takes thousands) of the plain damped step
+    and of the learned per-voxel weight (the network trained on the 16^3,
+    24^3 and 32^3 trajectories), from the same start, with wall time per
+    iteration (each ends with the host reading the energy)."""
+    import numpy as np
+    import torch
+    from paper_1610_07522_gb300 import binding as B
+    from paper_1610_07522_gb300 import inputs as IN
+    from paper_1610_07522_gb300.solver import Solver
+    w = IN.WORKLOADS[CONFIG5]
+    rng = np.random.default_rng(w.seed)
+    rho0, tau0 = IN.blob_densities(w.grid, w.dx, w.N, w.Z, w.nblob, w.blob_sigma, rng)
+    out = {"workload": CONFIG5, "grid": list(w.grid), "N": w.N, "Z": w.Z, "form": "f32",
+           "iterations_capped": iters,
+           "start": "blob densities, noisy plane waves (noise 0.1) generated on the device"}
+    for name, use_net in (("plain", False), ("learned", True)):
+        if use_net and net is None:
+            continue
+        s = Solver(w, prec=B.SKY_F32, device=dev, concurrent_species=True)
+        t = time.perf_counter()
+        psi0 = [IN.noisy_plane_waves_device(w.grid, w.dx, I, w.noise, w.seed * 10 + q, dev,
+                                            torch.complex64) for q, I in enumerate((w.N, w.Z))]
+        s.load(psi0, rho0, tau0)
+        del psi0
+        torch.cuda.empty_cache()
+        s.sync()
+        load_s = time.perf_counter() - t
+        if use_net:
+            s.set_damping(net)
+        stamps = [time.perf_counter()]
+        hist, _ = s.run(maxit=iters, tol=-1.0, callback=lambda it, rec: stamps.append(time.perf_counter()))
+        dts = [b - a for a, b in zip(stamps, stamps[1:])]
+        out[name] = {"load_s": round(load_s, 2), "s_per_iteration": dts,
+                     "E_per_A": [h["E"] / (w.N + w.Z) for h in hist],
+                     "delta_eps": [h["delta_eps"] for h in hist],
+                     "fallbacks": s.damping_fallbacks if use_net else None}
         s.close()
         del s
         torch.cuda.empty_cache()
@@ -762,14 +814,18 @@ def run_gpu(args):
         del ts
 
     conv = None
+    nets = {}
     if rank == 0 and not args.no_convergence:
-        conv = convergence_leg(dev)
+        conv = convergence_leg(dev, nets_out=nets)
     batched = None
     if rank == 0 and not args.no_batched:
         batched = batched_leg(dev)
     production = None
     if rank == 0 and not args.no_production:
         production = production_leg(dev)
+    config5 = None
+    if rank == 0 and not args.no_config5:
+        config5 = config5_leg(dev, nets.get("net_configs123"))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -802,6 +858,7 @@ def run_gpu(args):
         "convergence": conv,
         "batched": batched,
         "production_A6000": production,
+        "learned_at_scale_64cubed": config5,
     }
     s.close()
     if rank == 0:
@@ -823,6 +880,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-box batched (CUDA graph) form")
+    ap.add_argument("--no-config5", action="store_true",
+                    help="skip the 64^3, 5600 n + 2400 p learned-form leg")
     ap.add_argument("--no-production", action="store_true",
                     help="skip the A = 6000 production shapes (32^3, 48^3)")
     ap.add_argument("--no-td", action="store_true",

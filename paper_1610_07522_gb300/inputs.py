@@ -93,6 +93,13 @@ WORKLOADS = {
     "sly4_48cubed_3000n3000p": Workload(
         name="sly4_48cubed_3000n3000p", grid=(48, 48, 48), dx=(1.0, 1.0, 1.0),
         N=3000, Z=3000, coulomb=True, maxit=500, init="blobs", seed=1007),
+    # Learned-form scale (64^3, 8000 nucleons at 0.03 fm^-3, proton fraction
+    # 0.3, FP32 spinors): blob densities; the states are seeded noisy plane
+    # waves made on the device (noisy_plane_waves_device), 47 GB of FP64 host
+    # arrays being too much to build and copy for a benchmark.
+    "sly4_64cubed_5600n2400p": Workload(
+        name="sly4_64cubed_5600n2400p", grid=(64, 64, 64), dx=(1.0, 1.0, 1.0),
+        N=5600, Z=2400, coulomb=True, maxit=500, init="blobs", noise=0.1, seed=1008),
     # Small 8^3 case for the brute-force pins.
     "sly4_8cubed_4n4p": Workload(
         name="sly4_8cubed_4n4p", grid=(8, 8, 8), dx=(1.0, 1.0, 1.0),
@@ -169,6 +176,42 @@ def noisy_plane_waves(grid, dx, I, amp, rng):
     vol = float(np.prod([grid[i] * dx[i] for i in range(3)]))
     noise = rng.standard_normal(psi.shape) + 1j * rng.standard_normal(psi.shape)
     return psi + amp * noise / math.sqrt(2.0 * vol)
+
+
+def noisy_plane_waves_device(grid, dx, I, amp, seed, device, dtype):
+    """The recipe of noisy_plane_waves (lowest I spin plane waves
+    e^{i k.r}/sqrt(L^3) plus amp (xi_re + i xi_im)/sqrt(2 L^3), xi standard
+    normal) built on a CUDA device with torch's generator seeded by ``seed``
+    (another random stream than NumPy's), in chunks of states; ``dtype``
+    torch.complex64 or complex128.  Not orthonormal."""
+    import torch
+    labels = plane_wave_labels(grid, dx, I)
+    nx, ny, nz = grid
+    L = [grid[i] * dx[i] for i in range(3)]
+    vol = L[0] * L[1] * L[2]
+    rdt = torch.float64
+    x = torch.arange(nx, device=device, dtype=rdt) * dx[0]
+    y = torch.arange(ny, device=device, dtype=rdt) * dx[1]
+    z = torch.arange(nz, device=device, dtype=rdt) * dx[2]
+    gen = torch.Generator(device=device).manual_seed(int(seed))
+    out = torch.empty((I, 2, nz, ny, nx), dtype=dtype, device=device)
+    chunk = 64
+    for a0 in range(0, I, chunk):
+        lab = labels[a0:a0 + chunk]
+        m = torch.tensor([[l[0], l[1], l[2]] for l in lab], device=device, dtype=rdt)
+        sp = torch.tensor([l[3] for l in lab], device=device)
+        phx = torch.exp(2j * math.pi * m[:, 0, None] * x[None, :] / L[0])
+        phy = torch.exp(2j * math.pi * m[:, 1, None] * y[None, :] / L[1])
+        phz = torch.exp(2j * math.pi * m[:, 2, None] * z[None, :] / L[2])
+        pw = (phz[:, :, None, None] * phy[:, None, :, None] * phx[:, None, None, :]) / math.sqrt(vol)
+        n = len(lab)
+        # complex normal with unit total variance = (xi_re + i xi_im) / sqrt(2)
+        noise = torch.randn((n, 2, nz, ny, nx), dtype=torch.complex128, device=device, generator=gen)
+        blk = amp * noise / math.sqrt(vol)
+        idx = torch.arange(n, device=device)
+        blk[idx, sp] += pw
+        out[a0:a0 + n] = blk.to(dtype)
+    return out
 
 
 def random_superpositions(grid, dx, I, rng):

@@ -110,12 +110,16 @@ class Solver:
         return [q for q in range(2) if self.I[q] > 0]
 
     def load(self, psi0, rho0=None, tau0=None):
-        """Fig. 1 step 1 from host arrays: orthonormalise the trial states
+        """Fig. 1 step 1 from host arrays (or device tensors): orthonormalise the trial states
         (psi = Loewdin(phi), Eqs. Loewedin, orthmatvec); the mean field from
         their densities or from given initial densities."""
         qs = self._species()
         for q in qs:
-            self.phi[q].copy_(torch.from_numpy(np.ascontiguousarray(psi0[q])).to(self.cdtype))
+            src = psi0[q]
+            if torch.is_tensor(src):      # already on the device (large workloads)
+                self.phi[q].copy_(src.reshape(self.phi[q].shape))
+            else:
+                self.phi[q].copy_(torch.from_numpy(np.ascontiguousarray(src)).to(self.cdtype))
             B.sky_overlap(self.ctx, self.phi[q], self.phi[q], self.I[q], self.S[q])
         B.sky_orthonormalize_batched(self.ctx, [self.S[q] for q in qs], [self.I[q] for q in qs],
                                      [self.C[q] for q in qs])
