@@ -432,6 +432,78 @@ def production_leg(dev, iters=2):
     return out
 
 
+# ---------------------------------------------------------------- forms at the precision config
+CONV3_WORKLOAD = "sly4_32cubed_700n300p"
+
+
+def convergence_config3_leg(dev, net, cap=300):
+    """The forms where they are defined: 32^3, 700 n + 300 p, Coulomb, blob start.
+    The stop rule (|dE/A| < 1e-6 MeV for 5 iterations) takes thousands of
+    iterations here, so the comparison is capped (labelled): the plain FP64
+    method runs ``cap`` iterations and reaches E_cap/A; every form then runs
+    until its E/A is at or below E_cap/A (or the stop rule holds, or 2 cap
+    iterations pass), and its wall time for that is compared with FP64's
+    (each form stops once it gets there).
+    Forms: FP32 spinors with the 4-digit tensor-core contractions,
+    split-BF16 x3 escalated to them once |dE/A| < 2e-5, and the learned
+    weight (FP32)."""
+    import torch
+    from paper_1610_07522_gb300 import binding as B
+    from paper_1610_07522_gb300 import inputs as IN
+    from paper_1610_07522_gb300.solver import Solver
+    w = IN.WORKLOADS[CONV3_WORKLOAD]
+    inp = IN.make_inputs(w)
+    A = w.N + w.Z
+    out = {"workload": CONV3_WORKLOAD, "cap_iterations": cap,
+           "rule": "time to E/A <= the plain FP64 method's E/A after the cap (or the stop rule)"}
+
+    def run(prec, target=None, net_=None, escalate=None, maxit=cap):
+        s = Solver(w, prec=prec, device=dev, concurrent_species=True)
+        if net_ is not None:
+            s.set_damping(net_)
+        s.load(inp["psi0"], inp.get("rho0"), inp.get("tau0"))
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        reached = {}
+
+        def cb(it, rec):
+            if target is not None and "t" not in reached and rec["E"] / A <= target:
+                reached["t"] = time.perf_counter() - t
+                reached["it"] = it + 1
+                return True             # the comparison needs no more
+        try:
+            hist, conv = s.run(maxit=maxit, window=CONV_WINDOW, callback=cb, escalate=escalate)
+        except B.SkyError as err:
+            s.close()
+            return {"error": str(err)}
+        dt = time.perf_counter() - t
+        r = {"iterations": len(hist), "seconds": round(dt, 3), "converged": conv,
+             "E_per_A": hist[-1]["E"] / A, "s_per_iteration": dt / len(hist)}
+        if target is not None:
+            r["reached_target"] = "t" in reached
+            r["seconds_to_target"] = round(reached["t"], 3) if "t" in reached else None
+            r["iterations_to_target"] = reached.get("it")
+        if net_ is not None:
+            r["fallbacks"] = s.damping_fallbacks
+        s.close()
+        torch.cuda.empty_cache()
+        return r
+
+    base = run(B.SKY_F64)
+    out["fp64"] = base
+    target = base["E_per_A"]
+    out["target_E_per_A"] = target
+    out["fp32"] = run(B.SKY_F32, target, maxit=2 * cap)
+    out["bf16x3_to_fp32"] = run(B.SKY_F32_BF16X3, target, escalate=(2e-5, B.SKY_F32), maxit=2 * cap)
+    if net is not None:
+        out["learned_fp32"] = run(B.SKY_F32, target, net_=net, maxit=2 * cap)
+    out["speedup_vs_fp64_to_target"] = {
+        k: (round(base["seconds"] / out[k]["seconds_to_target"], 3)
+            if out.get(k, {}).get("seconds_to_target") else None)
+        for k in ("fp32", "bf16x3_to_fp32", "learned_fp32") if k in out}
+    return out
+
+
 # ---------------------------------------------------------------- learned form at scale
 CONFIG5 = "sly4_64cubed_5600n2400p"
 
@@ -823,6 +895,9 @@ def run_gpu(args):
     production = None
     if rank == 0 and not args.no_production:
         production = production_leg(dev)
+    conv3 = None
+    if rank == 0 and not args.no_convergence:
+        conv3 = convergence_config3_leg(dev, nets.get("net_configs123"))
     config5 = None
     if rank == 0 and not args.no_config5:
         config5 = config5_leg(dev, nets.get("net_configs123"))
@@ -858,6 +933,7 @@ def run_gpu(args):
         "convergence": conv,
         "batched": batched,
         "production_A6000": production,
+        "convergence_32cubed_700n300p": conv3,
         "learned_at_scale_64cubed": config5,
     }
     s.close()

@@ -271,7 +271,8 @@ class Solver:
         FP32 form on a flat stretch of the path, from ending the run.
         ``escalate = (tol_switch, prec)`` switches the GEMM form to ``prec``
         once the change has stayed below tol_switch for ``window`` iterations
-        (e.g. split-BF16 far from convergence, then FP32)."""
+        (e.g. split-BF16 far from convergence, then FP32).  ``callback(it, record)``
+        returning True ends the run there (not converged)."""
         maxit = self.w.maxit if maxit is None else maxit
         tol = self.w.tol if tol is None else tol
         hist, E_prev, below, below_sw = [], None, 0, 0
@@ -279,8 +280,8 @@ class Solver:
             self.step()
             E, de, _ = self.energy()
             hist.append({"it": it, "E": E, "delta_eps": de})
-            if callback:
-                callback(it, hist[-1])
+            if callback and callback(it, hist[-1]) is True:
+                return hist, False          # the caller asked to stop here
             dE = abs(E - E_prev) / self.A if E_prev is not None else None
             if escalate is not None and dE is not None:
                 below_sw = below_sw + 1 if dE < escalate[0] else 0
