@@ -20,7 +20,7 @@ from . import binding as B
 
 class Solver:
     def __init__(self, workload, prec=B.SKY_F64, device="cuda:0", max_states=None, stream=None,
-                 variant="exact", concurrent_species=False):
+                 variant="exact", concurrent_species=False, split_eigensolve=False):
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (there is no CPU path)")
         if variant not in ("exact", "paper_literal"):
@@ -51,6 +51,10 @@ class Solver:
                                           workload.coulomb, workload.twist, prec, workload.Z,
                                           self.streamq[1].cuda_stream)
         self.concurrent = self.ctxq[1] is not self.ctx
+        # with concurrent species: each species' Loewdin and Rayleigh-Ritz solve on its
+        # own context and stream right after its matrices (the species couple only
+        # through the mean field), instead of one batched solve of both
+        self.split_eig = bool(split_eigensolve and self.concurrent)
         dev, G = self.device, self.G
         f64 = dict(dtype=torch.float64, device=dev)
         self.psi = [torch.zeros((I, 2) + self.shape, dtype=self.cdtype, device=dev) for I in self.I]
@@ -211,9 +215,33 @@ class Solver:
             ev.record(self.streamq[1])
             self.stream.wait_event(ev)
 
+    def species_ritz(self, q):
+        """Steps 3b-3e of species q alone on its own context and stream."""
+        I = self.I[q]
+        ctx = self.ctxq[q]
+        B.sky_orthonormalize_batched(ctx, [self.S[q]], [I], [self.C[q]])
+        diag = (B.sky_subspace_diag_batched if self.variant == "exact"
+                else B.sky_subspace_diag_literal_batched)
+        diag(ctx, [self.H[q]], [self.C[q]], [I], [self.M[q]],
+             [self.lam[self.off[q]:self.off[q] + I]])
+        self._timed("rotate", q, lambda: B.sky_rotate(ctx, self.phi[q], self.M[q], I, self.psi[q]))
+
     def step(self, frozen=False):
         """One full iteration (Fig. 1 steps 2-5); enqueued, not synchronised."""
         self._fork()
+        if self.split_eig:
+            # two independent chains (neutrons on the main stream, protons on the
+            # second) up to the densities; joined for the mean field
+            for q in self._species():
+                self.species_step(q)
+                self.species_ritz(q)
+            self.densities()
+            self._join()
+            B.sky_sp_spread(self.ctx, self.eps, self.hn2, self.A, self.spread)
+            if not frozen:
+                B.sky_mean_fields(self.ctx, self.rho, self.tau, self.divJ, self.U, self.Bf, self.W)
+            B.sky_energy(self.ctx, self.rho, self.tau, self.divJ, self.eout)
+            return
         for q in self._species():
             self.species_step(q)
         self._join()

@@ -91,3 +91,28 @@ def test_concurrent_species_streams_give_the_same_iteration(prec):
     assert torch.equal(a.psi[1], b.psi[1]) and torch.equal(a.rho, b.rho)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", [B.SKY_F64, B.SKY_F32])
+def test_split_eigensolve_chains_match_the_batched_solve(prec):
+    """Each species' Loewdin and Rayleigh-Ritz solve on its own context and
+    stream (two independent chains up to the densities) against the batched
+    solve of both: the same iteration up to the order of the eigensolver's
+    partial sums (its grid depends on the problems launched together)."""
+    w = IN.WORKLOADS["sly4_24cubed_280n120p_coulomb_fp64"]
+    inp = IN.make_inputs(w)
+    a = Solver(w, prec=prec, concurrent_species=True)
+    b = Solver(w, prec=prec, concurrent_species=True, split_eigensolve=True)
+    assert b.split_eig and not a.split_eig
+    for s in (a, b):
+        s.load(inp["psi0"], inp["rho0"], inp["tau0"])
+    for _ in range(3):
+        a.step()
+        b.step()
+    Ea, Eb = a.energy(), b.energy()
+    tol = 1e-11 if prec == B.SKY_F64 else 1e-6
+    assert abs(Ea[0] - Eb[0]) <= tol * abs(Ea[0])
+    la, lb = a.lam.cpu().numpy(), b.lam.cpu().numpy()
+    assert np.max(np.abs(la - lb)) < (1e-9 if prec == B.SKY_F64 else 1e-3)
+    a.close()
+    b.close()
