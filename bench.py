@@ -680,7 +680,9 @@ def call_rooflines(events, grid, prec, peaks, csize):
             "mean_I": sum(I for I, _, _ in ev) / len(ev),
             "achieved": fl / (ms / 1e3) / 1e12, "peak": pk,
             "frac": fl / (ms / 1e3) / 1e12 / pk,
-            "peak_source": f"measured {'FP64' if prec == 0 else 'FP32'} FMA rate (sky_fma_probe, this run)",
+            "peak_source": (f"measured {'FP64' if prec == 0 else 'FP32'} FMA rate (sky_fma_probe, this run)"
+                            + ("; the derivative line passes run in double-float arithmetic on the "
+                               "FP32 pipe, so this is an FP64-equivalent rate" if prec == 0 else "")),
             "hbm_algorithmic_GBps": by / (ms / 1e3) / 1e9,
             "hbm_frac": by / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
             "work": "per spinor: 40 G sum_j log2 n_j + 150 G flops, 2 x 2G complex values moved"}
@@ -720,6 +722,8 @@ def probe_call(args):
     st = torch.cuda.current_stream(dev)
     I = w.N
     ctx = B.sky_init(w.grid, w.dx, w.params, w.coulomb, w.twist, prec, I, st.cuda_stream)
+    if args.line_arith is not None:
+        B.sky_tune_set(ctx, B.SKY_KNOB_LINE_ARITH, args.line_arith)
     nx, ny, nz = w.grid
     G = nx * ny * nz
     cd = torch.complex128 if prec == 0 else torch.complex64
@@ -984,6 +988,9 @@ def main():
                     help="skip the time-to-convergence comparison of the forms")
     ap.add_argument("--probe-call", default=None, choices=["apply_h", "overlap", "rotate"],
                     help="run one library call on the workload's shapes and exit (for ncu)")
+    ap.add_argument("--line-arith", type=int, default=None, choices=[0, 1],
+                    help="--probe-call only: FP64 form's derivative line passes in FP64 (0) "
+                         "or double-float (1, the default)")
     ap.add_argument("--eigen", default="auto", choices=sorted(EIGEN),
                     help="FP64 eigensolver of the timed steps (auto: tridiagonal route for "
                          "large species, batched Jacobi for many small problems)")

@@ -304,6 +304,12 @@ sky_status sky_set_prec(sky_ctx* ctx, sky_prec prec);
  *                           1e-14 (FP64) and 1e-9 (FP32) of the largest result; 0 runs the
  *                           FP64 FMA kernels on the CUDA cores.  Switching to 1 may allocate
  *                           the digit buffers; not allowed for the split-BF16 forms
+ *   SKY_KNOB_LINE_ARITH     FP64 form: 1 (default) carries the spectral derivative line
+ *                           passes (of h psi and the densities) in double-float arithmetic,
+ *                           pairs of FP32 values (about 48 significant bits, FP64 loads and
+ *                           stores; GB300 issues FP32 operations at about 77x its FP64 rate),
+ *                           within a few 1e-15 of the FP64 transforms; 0 runs them in FP64.
+ *                           The FP32 forms accept 0 only
  * sky_tune_set returns SKY_EINVAL for a value outside these sets; sky_tune_get
  * returns the current value (-1 for an unknown knob or a NULL context). */
 typedef enum {
@@ -316,7 +322,8 @@ typedef enum {
   SKY_KNOB_WAIT_SPINS = 6,
   SKY_KNOB_JACOBI_MAX_SWEEPS = 7,
   SKY_KNOB_EIGEN_METHOD = 8,
-  SKY_KNOB_SPLIT_GEMM = 9
+  SKY_KNOB_SPLIT_GEMM = 9,
+  SKY_KNOB_LINE_ARITH = 10
 } sky_knob;
 enum { SKY_EIG_AUTO = 0, SKY_EIG_JACOBI = 1, SKY_EIG_TRIDIAGONAL = 2 };
 sky_status sky_tune_set(sky_ctx* ctx, sky_knob knob, int value);

@@ -11,7 +11,7 @@
 // through shared memory (rows padded to N+1 to avoid bank conflicts).
 #pragma once
 
-#include "sky_internal.cuh"
+#include "dd.cuh"
 
 namespace sky {
 
@@ -37,10 +37,12 @@ constexpr int kTwTotal = 6 + 8 + 10 + 12 + 16 + 20 + 24 + 32 + 40 + 48 + 64;
 // uploads its own copy for the current device at context creation.
 static __constant__ double2 c_tw_d[kTwTotal];
 static __constant__ float2 c_tw_f[kTwTotal];
+static __constant__ float4 c_tw_dd[kTwTotal];   // (cos hi, cos lo, sin hi, sin lo)
 
 static inline cudaError_t upload_twiddles_this_unit() {
   double2 hd[kTwTotal];
   float2 hf[kTwTotal];
+  float4 hdd[kTwTotal];
   const long double two_pi = 6.283185307179586476925286766559005768L;
   for (int i = 0; i < kNumTw; ++i) {
     const int N = tw_size(i), off = tw_offset(N);
@@ -48,9 +50,14 @@ static inline cudaError_t upload_twiddles_this_unit() {
       const long double a = two_pi * (long double)p / (long double)N;
       hd[off + p] = make_double2((double)cosl(a), (double)sinl(a));
       hf[off + p] = make_float2((float)cosl(a), (float)sinl(a));
+      const float ch = (float)cosl(a), sh = (float)sinl(a);
+      hdd[off + p] = make_float4(ch, (float)(cosl(a) - (long double)ch), sh,
+                                 (float)(sinl(a) - (long double)sh));
     }
   }
   cudaError_t e = cudaMemcpyToSymbol(c_tw_d, hd, sizeof(hd));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_tw_dd, hdd, sizeof(hdd));
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_tw_f, hf, sizeof(hf));
 }
@@ -58,6 +65,10 @@ static inline cudaError_t upload_twiddles_this_unit() {
 template <typename T> __device__ __forceinline__ cx<T> tw_entry(int i);
 template <> __device__ __forceinline__ double2 tw_entry<double>(int i) { return c_tw_d[i]; }
 template <> __device__ __forceinline__ float2 tw_entry<float>(int i) { return c_tw_f[i]; }
+template <> __device__ __forceinline__ ddc tw_entry<dd>(int i) {
+  const float4 w = c_tw_dd[i];
+  return ddc{dd(w.x, w.y), dd(w.z, w.w)};
+}
 
 // v * W_N^p with W_N = exp(-2 pi i / N) (forward) or exp(+2 pi i / N) (inverse).
 template <typename T, int N, bool INV>
@@ -96,9 +107,10 @@ template <typename T, bool INV> struct Dft<T, 4, INV> {
 template <typename T, bool INV> struct Dft<T, 3, INV> {
   // X1,2 = x0 - (x1+x2)/2 -/+ i (sqrt3/2)(x1 - x2) for the forward sign.
   static __device__ __forceinline__ void run(cx<T>* x) {
-    const T h = (T)0.866025403784438646763723170752936183;
+    constexpr T h = T(0.866025403784438646763723170752936183);
+    constexpr T half = T(0.5);
     const cx<T> s = x[1] + x[2], d = x[1] - x[2];
-    const cx<T> m = x[0] - (T)0.5 * s;
+    const cx<T> m = x[0] - half * s;
     const cx<T> r = h * (INV ? mul_i(d) : mul_mi(d));
     x[0] = x[0] + s; x[1] = m + r; x[2] = m - r;
   }
@@ -106,10 +118,10 @@ template <typename T, bool INV> struct Dft<T, 3, INV> {
 template <typename T, bool INV> struct Dft<T, 5, INV> {
   // c1 = cos(2pi/5), c2 = cos(4pi/5), s1 = sin(2pi/5), s2 = sin(4pi/5).
   static __device__ __forceinline__ void run(cx<T>* x) {
-    const T c1 = (T)0.309016994374947424102293417182819059;
-    const T c2 = (T)-0.809016994374947424102293417182819059;
-    const T s1 = (T)0.951056516295153572116439333379382143;
-    const T s2 = (T)0.587785252292473129181428776797681326;
+    constexpr T c1 = T(0.309016994374947424102293417182819059);
+    constexpr T c2 = T(-0.809016994374947424102293417182819059);
+    constexpr T s1 = T(0.951056516295153572116439333379382143);
+    constexpr T s2 = T(0.587785252292473129181428776797681326);
     const cx<T> a1 = x[1] + x[4], a2 = x[2] + x[3], b1 = x[1] - x[4], b2 = x[2] - x[3];
     const cx<T> m1 = x[0] + c1 * a1 + c2 * a2, m2 = x[0] + c2 * a1 + c1 * a2;
     const cx<T> n1 = s1 * b1 + s2 * b2, n2 = s2 * b1 - s1 * b2;

@@ -30,6 +30,21 @@ template <typename T> struct OpDeriv {
   __device__ __forceinline__ void store(long long b, int i, cx<T> v) const { out[b * G + i] = v; }
 };
 
+// The same derivative pass of FP64 arrays with the transform carried in
+// double-float arithmetic (dd.cuh): loads and stores FP64, k from a table of
+// float pairs of (k + theta/L) / N.
+struct OpDerivDD {
+  static constexpr bool kFwd = true, kInv = true;
+  const double2* in; double2* out; const float2* k; long long G;
+  __device__ __forceinline__ ddc load(long long b, int i) const { return ddc_of(in[b * G + i]); }
+  __device__ __forceinline__ void mid(ddc& v, long long, int, int m) const {
+    const float2 kk = k[m];
+    const dd kd(kk.x, kk.y);
+    v = ddc{-(kd * v.y), kd * v.x};
+  }
+  __device__ __forceinline__ void store(long long b, int i, ddc v) const { out[b * G + i] = dbl2_of(v); }
+};
+
 // Damped step, z pass: r = hpsi - eps psi, forward along z, into phi.
 template <typename T> struct OpDampZFwd {
   static constexpr bool kFwd = true, kInv = false;
@@ -82,20 +97,38 @@ template <> const double* kt_of<double>(const Ctx* c, int axis) { return c->d_kt
 template <> const float* kt_of<float>(const Ctx* c, int axis) { return c->d_ktf[axis]; }
 
 // G_j = d_j src for the three axes; nb = number of 3D arrays.
+// One derivative pass d_axis src -> dst over nb arrays: FP64 arrays in
+// double-float arithmetic when the context asks for it (SKY_KNOB_LINE_ARITH).
 template <typename T>
-static cudaError_t gradient_passes(Ctx* c, const cx<T>* src, cx<T>* const dst[3], long long nb) {
+static cudaError_t deriv_pass(Ctx* c, int ax, const cx<T>* src, cx<T>* dst, long long nb) {
   const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
   const long long G = c->G;
-  cudaError_t e;
+  if constexpr (std::is_same<T, double>::value) {
+    if (c->line_dd) {
+      OpDerivDD op{src, dst, c->d_ktdd[ax], G};
+      auto go = [&](auto NC) -> cudaError_t {
+        constexpr int N = decltype(NC)::value;
+        if (ax == 0) return launch_line<dd, N, 0>(op, nx, ny, nz, nb, c);
+        if (ax == 1) return launch_line<dd, N, 1>(op, nx, ny, nz, nb, c);
+        return launch_line<dd, N, 2>(op, nx, ny, nz, nb, c);
+      };
+      return dispatch_n<false>(c->n[ax], go);
+    }
+  }
+  OpDeriv<T> op{src, dst, kt_of<T>(c, ax), (T)(1.0 / c->n[ax]), G};
+  auto go = [&](auto NC) -> cudaError_t {
+    constexpr int N = decltype(NC)::value;
+    if (ax == 0) return launch_line<T, N, 0>(op, nx, ny, nz, nb, c);
+    if (ax == 1) return launch_line<T, N, 1>(op, nx, ny, nz, nb, c);
+    return launch_line<T, N, 2>(op, nx, ny, nz, nb, c);
+  };
+  return dispatch_n<std::is_same<T, float>::value>(c->n[ax], go);
+}
+
+template <typename T>
+static cudaError_t gradient_passes(Ctx* c, const cx<T>* src, cx<T>* const dst[3], long long nb) {
   for (int ax = 0; ax < 3; ++ax) {
-    OpDeriv<T> op{src, dst[ax], kt_of<T>(c, ax), (T)(1.0 / c->n[ax]), G};
-    auto go = [&](auto NC) -> cudaError_t {
-      constexpr int N = decltype(NC)::value;
-      if (ax == 0) return launch_line<T, N, 0>(op, nx, ny, nz, nb, c);
-      if (ax == 1) return launch_line<T, N, 1>(op, nx, ny, nz, nb, c);
-      return launch_line<T, N, 2>(op, nx, ny, nz, nb, c);
-    };
-    e = dispatch_n<std::is_same<T, float>::value>(c->n[ax], go);
+    const cudaError_t e = deriv_pass<T>(c, ax, src, dst[ax], nb);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -230,16 +263,8 @@ static sky_status apply_h_t(Ctx* c, const double* U, const double* B, const doub
     k_h_local<T><<<grid, 256, 0, c->stream>>>(ps, g[0], g[1], g[2], hs, U, B, W, (int)G); note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "apply_h local");
     // pass 3: F_j <- d_j F_j in place, one axis per array
-    const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
     for (int ax = 0; ax < 3; ++ax) {
-      OpDeriv<T> op{g[ax], g[ax], kt_of<T>(c, ax), (T)(1.0 / c->n[ax]), G};
-      auto go = [&](auto NC) -> cudaError_t {
-        constexpr int N = decltype(NC)::value;
-        if (ax == 0) return launch_line<T, N, 0>(op, nx, ny, nz, 2LL * ns, c);
-        if (ax == 1) return launch_line<T, N, 1>(op, nx, ny, nz, 2LL * ns, c);
-        return launch_line<T, N, 2>(op, nx, ny, nz, 2LL * ns, c);
-      };
-      e = dispatch_n<std::is_same<T, float>::value>(c->n[ax], go);
+      e = deriv_pass<T>(c, ax, g[ax], g[ax], 2LL * ns);
       if (e != cudaSuccess) return cuda_check(c, e, "apply_h divergence");
     }
     dim3 g4(c->red_nblk, ns);

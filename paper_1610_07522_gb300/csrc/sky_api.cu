@@ -79,7 +79,8 @@ static sky_status dalloc(Ctx* c, T** p, size_t count) {
 }
 
 static void free_all(Ctx* c) {
-  void* ptrs[] = {c->d_status, c->d_kt[0], c->d_kt[1], c->d_kt[2], c->d_ktf[0], c->d_ktf[1],
+  void* ptrs[] = {c->d_status, c->d_kt[0], c->d_kt[1], c->d_kt[2], c->d_ktdd[0], c->d_ktdd[1],
+                  c->d_ktdd[2], c->d_ktf[0], c->d_ktf[1],
                   c->d_ktf[2], c->d_kp[0], c->d_kp[1], c->d_kp[2], c->d_damp[0], c->d_damp[1],
                   c->d_coul, c->d_gscr, c->d_red, c->d_dpart, c->d_ftmp, c->d_fcx, c->d_gpart,
                   c->d_eigA[0], c->d_eigA[1], c->d_eigV, c->d_eigw, c->d_eigpart, c->d_bar,
@@ -238,6 +239,7 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   c->wait_spins = kBarrierSpins;
   c->jac_max_sweeps = kJacMaxSweeps;
   c->eig_method = SKY_EIG_AUTO;
+  c->line_dd = prec == SKY_F64 ? 1 : 0;
   size_t gpart = 0;
   for (int I = 1; I <= Imax; ++I) {   // room for the largest tunable split count
     const size_t need = overlap_partial_elems(I, V, kMaxOverlapWaves * c->ov_slots);
@@ -250,6 +252,7 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   ALLOC(c->d_status, 1);
   for (int j = 0; j < 3; ++j) {
     ALLOC(c->d_kt[j], grid[j]);
+    ALLOC(c->d_ktdd[j], grid[j]);
     ALLOC(c->d_ktf[j], grid[j]);
     ALLOC(c->d_kp[j], grid[j]);
   }
@@ -312,16 +315,23 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
       double* kt = new double[n];
       double* kp = new double[n];
       float* kf = new float[n];
+      float2* kdd = new float2[n];
       for (int a = 0; a < n; ++a) {
         const int mm = (a < (n + 1) / 2) ? a : a - n;
         kp[a] = 2.0 * M_PI * mm / c->L[j];
         kt[a] = kp[a] + c->theta[j] / c->L[j];
         kf[a] = (float)kt[a];
+        // (k + theta/L) / n as the nearest float pair, in long double
+        const long double kl = (2.0L * 3.141592653589793238462643383279502884L * mm +
+                                (long double)c->theta[j]) / ((long double)c->L[j] * n);
+        const float h = (float)kl;
+        kdd[a] = make_float2(h, (float)(kl - (long double)h));
       }
       e = cudaMemcpy(c->d_kt[j], kt, n * sizeof(double), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(c->d_ktdd[j], kdd, n * sizeof(float2), cudaMemcpyHostToDevice);
       if (e == cudaSuccess) e = cudaMemcpy(c->d_kp[j], kp, n * sizeof(double), cudaMemcpyHostToDevice);
       if (e == cudaSuccess) e = cudaMemcpy(c->d_ktf[j], kf, n * sizeof(float), cudaMemcpyHostToDevice);
-      delete[] kt; delete[] kp; delete[] kf;
+      delete[] kt; delete[] kp; delete[] kf; delete[] kdd;
       s = cuda_check(c, e, "wavenumber upload");
     }
   }
@@ -598,6 +608,11 @@ sky_status sky_tune_set(sky_ctx* c, sky_knob knob, int value) {
       if (value != SKY_EIG_AUTO && value != SKY_EIG_JACOBI && value != SKY_EIG_TRIDIAGONAL) break;
       c->eig_method = value;
       return SKY_OK;
+    case SKY_KNOB_LINE_ARITH:
+      if (value != 0 && value != 1) break;
+      if (value == 1 && c->prec != SKY_F64) break;
+      c->line_dd = value;
+      return SKY_OK;
     case SKY_KNOB_SPLIT_GEMM:
       if (value != 0 && value != 1) break;
       if (value == 1 && is_tc(c->prec)) break;
@@ -628,6 +643,7 @@ int sky_tune_get(const sky_ctx* c, sky_knob knob) {
     case SKY_KNOB_JACOBI_MAX_SWEEPS: return c->jac_max_sweeps;
     case SKY_KNOB_EIGEN_METHOD: return c->eig_method;
     case SKY_KNOB_SPLIT_GEMM: return c->oz_on;
+    case SKY_KNOB_LINE_ARITH: return c->line_dd;
     default: return -1;
   }
 }

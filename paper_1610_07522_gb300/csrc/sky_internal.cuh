@@ -78,6 +78,8 @@ struct Ctx {
   double* d_kt[3];                  // twisted wavenumbers k + theta/L (FP64)
   float* d_ktf[3];                  // the same in FP32
   double* d_kp[3];                  // plain wavenumbers (real fields)
+  float2* d_ktdd[3];                // (k + theta/L) / n as float pairs (double-float passes)
+  int line_dd;                      // 1: FP64 derivative passes in double-float arithmetic
   double* d_damp[2];                // 1 / (E0 + hb2m_q |k + theta/L|^2), [G]
   double damp_E0[2];                // E0 the tables were built for (NaN = none)
   double* d_coul;                   // 4 pi e^2 / |k|^2 (0 at k = 0), [G]

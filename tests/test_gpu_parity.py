@@ -512,3 +512,58 @@ def test_batched_loewdin_and_rayleigh_ritz():
             assert np.max(np.abs(host(lam[b]) - Lw[b])) < 1e-9
             Mg = host(M[b])
             assert np.max(np.abs(Mg.conj().T @ Ss[b] @ Mg - np.eye(I[b]))) < 1e-11
+
+
+@pytest.mark.parametrize("case", [CASES[2], CASES[3]])
+def test_apply_h_and_densities_in_both_line_arithmetics(case):
+    """The FP64 form's derivative line passes in double-float arithmetic (the
+    default, SKY_KNOB_LINE_ARITH = 1) and in FP64 (0): both within the FP64
+    per-call tolerance of the oracle; FP32 contexts accept only 0."""
+    rng = np.random.default_rng(77)
+    with Ctx(*case) as c:
+        g = c.grid
+        I = 4
+        psi = IN.random_spinors(g.n, I, rng)
+        U, Bf, W = _fields(g, rng)
+        want = O.apply_h(psi, U, Bf, W, g)
+        rho_w, tau_w, J_w, dJ_w = O.densities(psi, g)
+        assert B.sky_tune_get(c.ctx, B.SKY_KNOB_LINE_ARITH) == 1
+        for arith in (1, 0):
+            B.sky_tune_set(c.ctx, B.SKY_KNOB_LINE_ARITH, arith)
+            d_h = torch.zeros(psi.shape, dtype=torch.complex128, device="cuda:0")
+            B.sky_apply_h(c.ctx, dev(U), dev(Bf), dev(W), dev(psi), d_h, I)
+            assert relerr(host(d_h), want) < REL, arith
+            rho = torch.zeros(g.G, dtype=torch.float64, device="cuda:0")
+            tau, dJ = torch.zeros_like(rho), torch.zeros_like(rho)
+            J = torch.zeros(3 * g.G, dtype=torch.float64, device="cuda:0")
+            B.sky_densities(c.ctx, dev(psi), I, rho, tau, J, dJ)
+            assert relerr(host(tau), tau_w.ravel()) < REL, arith
+            assert relerr(host(J), J_w.ravel()) < REL, arith
+    with Ctx((16, 16, 16), prec=B.SKY_F32) as c32:
+        assert B.sky_tune_get(c32.ctx, B.SKY_KNOB_LINE_ARITH) == 0
+        with pytest.raises(B.SkyError):
+            B.sky_tune_set(c32.ctx, B.SKY_KNOB_LINE_ARITH, 1)
+
+
+def test_apply_h_across_magnitudes():
+    """Spinors scaled by 1e-28 ... 1e20 and one with exact zeros: the
+    double-float passes convert doubles by their bit patterns inside
+    2^-74 <= |x| < 2^127 and through FP64 conversions outside (zeros, smaller
+    values); h is linear, so each spinor is compared with the oracle relative
+    to its own largest value."""
+    rng = np.random.default_rng(91)
+    with Ctx((16, 16, 16), twist=(0.2, -0.4, 0.9)) as c:
+        g = c.grid
+        scales = [1e-28, 1e-21, 3e-9, 1.0, 7e5, 1e20]
+        psi = IN.random_spinors(g.n, len(scales) + 1, rng)
+        for a, s in enumerate(scales):
+            psi[a] *= s
+        psi[-1, 1] = 0.0                       # spin-down component identically zero
+        psi[-1, 0, :, 3:9] = 0.0               # and a slab of zeros in spin-up
+        U, Bf, W = _fields(g, rng)
+        want = O.apply_h(psi, U, Bf, W, g)
+        d_h = torch.zeros(psi.shape, dtype=torch.complex128, device="cuda:0")
+        B.sky_apply_h(c.ctx, dev(U), dev(Bf), dev(W), dev(psi), d_h, psi.shape[0])
+        got = host(d_h)
+        for a in range(psi.shape[0]):
+            assert relerr(got[a], want[a]) < REL, a
