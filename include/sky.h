@@ -304,12 +304,16 @@ sky_status sky_set_prec(sky_ctx* ctx, sky_prec prec);
  *                           1e-14 (FP64) and 1e-9 (FP32) of the largest result; 0 runs the
  *                           FP64 FMA kernels on the CUDA cores.  Switching to 1 may allocate
  *                           the digit buffers; not allowed for the split-BF16 forms
- *   SKY_KNOB_LINE_ARITH     FP64 form: 1 (default) carries the spectral derivative line
- *                           passes (of h psi and the densities) in double-float arithmetic,
- *                           pairs of FP32 values (about 48 significant bits, FP64 loads and
- *                           stores; GB300 issues FP32 operations at about 77x its FP64 rate),
- *                           within a few 1e-15 of the FP64 transforms; 0 runs them in FP64.
- *                           The FP32 forms accept 0 only
+ *   SKY_KNOB_LINE_ARITH     FP64 form, the spectral derivatives of h psi and the densities
+ *                           (Sec. 2.2): 2 (default) applies each axis's derivative as the
+ *                           dense circulant operator of the FFT form, a product of six-digit
+ *                           exact-integer splits of the lines and of the operator on the
+ *                           tensor cores (about 2^-48 of the line's largest value, rounded
+ *                           once to FP64); 1 runs the FFT line passes in double-float
+ *                           arithmetic (pairs of FP32 values, about 48 significant bits;
+ *                           GB300 issues FP32 operations at about 77x its FP64 rate); 0 runs
+ *                           them in FP64.  2 needs axis lengths in {8, 12, 16, 20, 24, 32}
+ *                           (the lengths the FP64 form accepts).  The FP32 forms accept 0 only
  * sky_tune_set returns SKY_EINVAL for a value outside these sets; sky_tune_get
  * returns the current value (-1 for an unknown knob or a NULL context). */
 typedef enum {

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libsky.so")
-SOURCES = ["sky_api.cu", "hamiltonian.cu", "fields.cu", "gemm.cu", "eigen.cu", "eigen_tridiag.cu", "overlap_noalloc.cu", "tc_ops.cu", "oz_ops.cu", "precond.cu", "probe.cu", "td.cu"]
+SOURCES = ["sky_api.cu", "hamiltonian.cu", "fields.cu", "gemm.cu", "eigen.cu", "eigen_tridiag.cu", "overlap_noalloc.cu", "tc_ops.cu", "oz_ops.cu", "oz_deriv.cu", "precond.cu", "probe.cu", "td.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -97,14 +97,16 @@ template <> const double* kt_of<double>(const Ctx* c, int axis) { return c->d_kt
 template <> const float* kt_of<float>(const Ctx* c, int axis) { return c->d_ktf[axis]; }
 
 // G_j = d_j src for the three axes; nb = number of 3D arrays.
-// One derivative pass d_axis src -> dst over nb arrays: FP64 arrays in
-// double-float arithmetic when the context asks for it (SKY_KNOB_LINE_ARITH).
+// One derivative pass d_axis src -> dst over nb arrays.  FP64 arrays
+// (SKY_KNOB_LINE_ARITH): 2 the digit-split operator on the tensor cores,
+// 1 the FFT line pass in double-float arithmetic, 0 the FFT in FP64.
 template <typename T>
 static cudaError_t deriv_pass(Ctx* c, int ax, const cx<T>* src, cx<T>* dst, long long nb) {
   const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
   const long long G = c->G;
   if constexpr (std::is_same<T, double>::value) {
-    if (c->line_dd) {
+    if (c->line_arith == 2 && c->d_dop[ax]) return deriv_tc(c, ax, src, dst, nb);
+    if (c->line_arith >= 1) {
       OpDerivDD op{src, dst, c->d_ktdd[ax], G};
       auto go = [&](auto NC) -> cudaError_t {
         constexpr int N = decltype(NC)::value;

@@ -1,0 +1,568 @@
+// Spectral derivative along one axis (Sec. 2.2: the derivatives are taken
+// with FFTs) as a dense contraction on the 5th-generation tensor cores, for
+// the FP64 form.
+//
+// Along axis j the FFT derivative d_j f = IFFT_j[i (k + theta/L) FFT_j[f]] is
+// one linear map applied to every line of n points: the circulant n x n
+// complex matrix
+//     D[m][q] = d[(m - q) mod n],  d[r] = (i / n) sum_a kappa_a e^{2 pi i a r / n},
+// kappa_a = (2 pi a' + theta) / L with a' = a or a - n (FFT order; the Nyquist
+// wavenumber kept, as in the line passes).  On the interleaved (re, im)
+// storage it is the real 2n x 2n matrix
+//     Dr[2m + c'][2q + c] = [[Re D, -Im D], [Im D, Re D]][c'][c],
+// so one pass over nb arrays is OUT = LINES Dr^T with one row per line
+// (nb G / n rows, K = N = 2n, padded to NC = a multiple of 16).  Both
+// operands are cut into six base-256 digits (oz_digits.cuh), each line scaled
+// by its own exponent and each row of Dr by its own; the 21 digit products of
+// weight g = s + t <= 5 are summed exactly in FP32 in TMEM (per K value
+// |G_g| <= (g + 3) 2^14, K <= 64), combined exactly in a 64-bit integer,
+// rounded once to FP64 and scaled by the two exponents.  The only error is the
+// truncated digit expansion, about 2^-48 of the line's and the row's largest
+// values.
+//
+// Persistent kernel, one CTA per SM, 128 lines per tile:
+//   warps 0-7   producers: warp w takes lines 16 w .. 16 w + 15 of the tile,
+//               lanes 0-15 the first half of each line's points and lanes
+//               16-31 the second; a thread loads its half line at once, the
+//               pair agrees on the line's exponent by one shuffle, and each
+//               writes its digits into a ring stage in the canonical
+//               no-swizzle K-major layout (8-row x 16-byte core matrices),
+//               fences the writes for the tensor core's proxy and arrives;
+//   warp 8      owns TMEM (6 groups x NC fp32 columns); one lane issues
+//               tcgen05.mma (M = 128, N = NC, K = 16) for every digit pair;
+//   warps 9-16  epilogue: two warps per TMEM lane quadrant, half the columns
+//               each; they drain the groups in order into 64-bit integers,
+//               round, scale and store the (re, im) pairs at the line's
+//               points (in place is allowed: tiles own disjoint lines).
+// The operator's digits, computed once per context on the host in long
+// double, stay in shared memory for the whole launch.  Every mbarrier wait is
+// bounded; a timeout sets SKY_ETIMEOUT, the kernel waits (bounded) for the
+// MMAs it issued, frees TMEM and returns.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "oz_digits.cuh"
+#include "oz_gemm.cuh"
+
+namespace sky {
+namespace ozd {
+
+using namespace ozdig;
+using tc::fence_after;
+using tc::fence_before;
+using tc::idesc_bf16;
+using tc::mbar_init;
+using tc::mbar_wait;
+using tc::mma_bf16;
+using tc::mma_commit;
+using tc::smem_u32;
+
+constexpr int S = 6;               // digits per operand (FP64 inputs)
+constexpr int BM = 128;            // lines per tile (MMA M)
+constexpr int kProd = 8, kEpi = 8;   // producer warps: two threads per line
+constexpr int THREADS = 32 * (kProd + 1 + kEpi);
+constexpr int kSmemMax = 232448;   // dynamic shared memory opt-in limit per CTA
+constexpr int kBars = 24;
+
+__host__ __device__ constexpr int nc_of(int n) { return ((2 * n + 15) / 16) * 16; }
+
+template <int N>
+struct Shape {
+  static constexpr int NC = nc_of(N);          // K and output columns (reals), padded
+  static constexpr int TILE_A = BM * NC * 2;   // one digit of a tile of lines
+  static constexpr int STAGE = S * TILE_A;
+  static constexpr int TILE_B = NC * NC * 2;   // one digit of the operator
+  static constexpr int OPB = S * TILE_B;
+  static constexpr int AUX = NC * 4 + 2 * BM * 4 + kBars * 8 + 16;
+  static constexpr int STAGES = (2 * STAGE + OPB + AUX + 1024 <= kSmemMax) ? 2 : 1;
+  static constexpr int SMEM = STAGES * STAGE + OPB + AUX + 1024;
+  static constexpr int HALF = NC / 2;          // columns per epilogue warp
+  static_assert(S * NC <= 512, "TMEM columns");
+  static_assert(SMEM <= kSmemMax, "shared memory");
+  static_assert(HALF % 8 == 0, "TMEM load blocks of 8 columns");
+};
+
+// Byte offset of element (r, k) of a K-major bf16 tile with nc columns in the
+// canonical no-swizzle layout: 8 x 8 core matrices of 128 contiguous bytes,
+// 128 bytes apart along K, 16 nc bytes apart along the rows.
+__host__ __device__ constexpr int cm_off(int r, int k, int nc) {
+  return (r >> 3) * (nc * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+// Shared-memory matrix descriptor of that layout: leading byte offset 128
+// (core matrices along K), stride byte offset 16 nc (8-row groups), version 1,
+// layout type 0 (no swizzle).
+__device__ __forceinline__ uint64_t ns_desc(uint32_t saddr, int nc) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)((nc * 16) >> 4) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// The six balanced base-256 digits of the signed integer Y = +-round(|x|
+// 2^{48 - E}) (|Y| <= 2^48), as floats: adding 128 to each of the five lower
+// byte positions (0x8080808080) turns every lower byte, minus 128, into a
+// digit in [-128, 127], with the carries propagated by the addition; the top
+// digit is the rest, an arithmetic shift (|digit 0| <= 256).  All exact in bf16.
+__device__ __forceinline__ void digits6f(double x, int E, float* d) {
+  long long Y = (long long)fixed_of<6>(x, E);
+  if (sign_of(x)) Y = -Y;
+  const long long Z = Y + 0x8080808080LL;
+  const unsigned lo = (unsigned)Z, hi = (unsigned)((unsigned long long)Z >> 32);
+  auto f = [](int v) { return __int_as_float(0x4B400000 + v) - 12582912.0f; };   // exact, |v| < 2^22
+  d[5] = f((int)(lo & 255u) - 128);
+  d[4] = f((int)((lo >> 8) & 255u) - 128);
+  d[3] = f((int)((lo >> 16) & 255u) - 128);
+  d[2] = f((int)(lo >> 24) - 128);
+  d[1] = f((int)(hi & 255u) - 128);
+  d[0] = f((int)(Z >> 40));
+}
+__device__ __forceinline__ unsigned bf16x2(float lo, float hi) {   // lo in the low half
+  unsigned r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+// v 2^sc rounded to the nearest double (halfway cases away from zero), by
+// integer operations on the bit pattern; results outside the normal range go
+// through ldexp.
+__device__ __forceinline__ double scaled_double(long long v, int sc) {
+  if (v == 0) return 0.0;
+  const unsigned long long neg = v < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long u = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int pb = 63 - __clzll((long long)u);   // position of the leading bit
+  const int be = pb + sc + 1023;               // biased exponent of the result
+  if (be < 1 || be > 2045) return ldexp((double)v, sc);
+  unsigned long long r;
+  if (pb > 52) {
+    const int sh = pb - 52;
+    r = ((u >> (sh - 1)) + 1ull) >> 1;           // 53 bits, rounded; 2^53 on carry
+  } else {
+    r = u << (52 - pb);
+  }
+  // r in [2^52, 2^53]: adding it to (be - 1) << 52 sets the implicit bit's
+  // exponent and carries a rounding overflow into the exponent.
+  return __longlong_as_double((long long)(neg | ((((unsigned long long)(be - 1)) << 52) + r)));
+}
+
+struct DerivArgs {
+  const double2* src;   // nb arrays of G complex points (may equal dst)
+  double2* dst;
+  const uint4* op;      // operator digits, S * TILE_B bytes in the canonical layout
+  const int* ope;       // operator row exponents [NC]
+  int nx, ny, nz;
+  long long G;
+  long long nlines;
+  int ntiles;
+  int* status;
+};
+
+// First point and stride of line l (lines of one axis, x fastest, then the
+// remaining axes in storage order, then the array).
+template <int N, int AXIS>
+__device__ __forceinline__ long long line_base(const DerivArgs& a, long long l, long long& stride) {
+  if constexpr (AXIS == 0) {
+    stride = 1;
+    return l * N;
+  } else if constexpr (AXIS == 1) {
+    const long long x = l % a.nx, t = l / a.nx, z = t % a.nz, b = t / a.nz;
+    stride = a.nx;
+    return b * a.G + z * (long long)a.ny * a.nx + x;
+  } else {
+    const long long x = l % a.nx, t = l / a.nx, y = t % a.ny, b = t / a.ny;
+    stride = (long long)a.nx * a.ny;
+    return b * a.G + y * (long long)a.nx + x;
+  }
+}
+
+template <int N, int AXIS>
+__global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
+  using Sh = Shape<N>;
+  constexpr int NC = Sh::NC, STAGES = Sh::STAGES, HALF = Sh::HALF;
+  constexpr int TILE_A = Sh::TILE_A, TILE_B = Sh::TILE_B, STAGE = Sh::STAGE;
+  constexpr uint32_t TMEM_COLS = 512;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((unsigned long long)smem_raw + 1023ull) & ~1023ull);
+  unsigned char* opb = base;                                  // operator digits
+  unsigned char* ring = base + Sh::OPB;                       // STAGES x STAGE
+  int* s_eb = (int*)(ring + STAGES * STAGE);                  // [NC]
+  int* s_ea = s_eb + NC;                                      // [2][BM]
+  unsigned long long* bars = (unsigned long long*)(s_ea + 2 * BM);
+  uint32_t* tmem_slot = (uint32_t*)(bars + kBars);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t bar0 = smem_u32(bars);
+  auto full = [&](int s) { return bar0 + 8u * s; };
+  auto empty = [&](int s) { return bar0 + 8u * (2 + s); };
+  auto acc_full = [&](int g) { return bar0 + 8u * (4 + g); };
+  auto acc_empty = [&](int g) { return bar0 + 8u * (4 + S + g); };
+  auto ea_full = [&](int j) { return bar0 + 8u * (4 + 2 * S + j); };
+  auto ea_empty = [&](int j) { return bar0 + 8u * (6 + 2 * S + j); };
+  const uint32_t drain = bar0 + 8u * (8 + 2 * S);
+
+  // the operator's digits and row exponents, for the whole launch
+  for (int i = threadIdx.x; i < Sh::OPB / 16; i += blockDim.x) ((uint4*)opb)[i] = a.op[i];
+  for (int i = threadIdx.x; i < NC; i += blockDim.x) s_eb[i] = a.ope[i];
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full(s), kProd * 32);
+      mbar_init(empty(s), 1);
+    }
+    for (int g = 0; g < S; ++g) {
+      mbar_init(acc_full(g), 1);
+      mbar_init(acc_empty(g), kEpi);
+    }
+    for (int j = 0; j < 2; ++j) {
+      mbar_init(ea_full(j), kProd * 32);
+      mbar_init(ea_empty(j), kEpi * 32);
+    }
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kProd) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp < kProd) {
+    // ---------------------------------------------------------------- producers
+    // half 0 takes points [0, H0), half 1 [H0, N): H0 a multiple of 4, so each
+    // half covers whole 16-byte chunks (8 reals) of the digit rows
+    constexpr int H0 = ((N / 2 + 3) / 4) * 4, H1 = N - H0;
+    static_assert(H1 > 0 && H1 <= H0 && H1 % 4 == 0, "line halves");
+    const int r = warp * 16 + (lane & 15);    // row (line) of the tile
+    const int hh = lane >> 4;                 // which half of the line
+    const int np = hh ? H1 : H0;              // points of this half
+    const int p0 = hh ? H0 : 0;               // first point
+    int it = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
+      const int s = it % STAGES, u = it / STAGES, slot = it & 1;
+      if (u > 0 && !mbar_wait(empty(s), (uint32_t)((u - 1) & 1))) {
+        flag_status(a.status, SKY_ETIMEOUT);
+        break;
+      }
+      if (it >= 2 && !mbar_wait(ea_empty(slot), (uint32_t)(((it >> 1) - 1) & 1))) {
+        flag_status(a.status, SKY_ETIMEOUT);
+        break;
+      }
+      const long long l = (long long)t * BM + r;
+      const bool valid = l < a.nlines;
+      long long stride = 0;
+      const long long lb = valid ? line_base<N, AXIS>(a, l, stride) : 0;
+      double2 v[H0];
+#pragma unroll
+      for (int j = 0; j < H0; ++j)
+        v[j] = (valid && j < np) ? a.src[lb + (long long)(p0 + j) * stride] : make_double2(0.0, 0.0);
+      int E = INT_MIN;
+#pragma unroll
+      for (int j = 0; j < H0; ++j) E = max(E, max(exp_of(v[j].x), exp_of(v[j].y)));
+      E = max(E, __shfl_xor_sync(0xffffffffu, E, 16));
+      if (E == INT_MIN) E = 0;
+      if (hh == 0) s_ea[slot * BM + r] = E;
+      unsigned char* ta = ring + s * STAGE;
+#pragma unroll
+      for (int c = 0; c < H0 / 4; ++c) {
+        if (c < np / 4) {
+          unsigned w[S][4];   // digit p of the chunk's 8 reals, as 4 bf16 pairs
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float dr[S], di[S];
+            digits6f(v[4 * c + j].x, E, dr);
+            digits6f(v[4 * c + j].y, E, di);
+#pragma unroll
+            for (int p = 0; p < S; ++p) w[p][j] = bf16x2(dr[p], di[p]);
+          }
+          const int k0 = 2 * p0 + 8 * c;
+#pragma unroll
+          for (int p = 0; p < S; ++p)
+            *(uint4*)(ta + p * TILE_A + cm_off(r, k0, NC)) =
+                make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+        }
+      }
+      // columns 2N .. NC - 1 (padding): zeros, from the second half
+      if (hh == 1) {
+#pragma unroll
+        for (int k = 2 * N; k < NC; k += 8)
+#pragma unroll
+          for (int p = 0; p < S; ++p)
+            *(uint4*)(ta + p * TILE_A + cm_off(r, k, NC)) = make_uint4(0u, 0u, 0u, 0u);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(full(s));
+      mbar_arrive(ea_full(slot));
+    }
+  } else if (warp == kProd) {
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(BM, NC);
+      const uint32_t sb = smem_u32(opb);
+      bool ok = true;
+      int it = 0;
+      for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++it) {
+        const int s = it % STAGES, u = it / STAGES;
+        if (!mbar_wait(full(s), (uint32_t)(u & 1))) {
+          flag_status(a.status, SKY_ETIMEOUT);
+          break;
+        }
+        fence_after();
+        const uint32_t sa = smem_u32(ring + s * STAGE);
+        for (int g = 0; g < S; ++g) {
+          if (it > 0) {
+            // the epilogue must have drained this group of the previous tile
+            if (!mbar_wait(acc_empty(g), (uint32_t)((it - 1) & 1))) {
+              flag_status(a.status, SKY_ETIMEOUT);
+              ok = false;
+              break;
+            }
+            fence_after();
+          }
+          const uint32_t acc = tmem + (uint32_t)(g * NC);
+          for (int p = 0; p <= g; ++p) {
+#pragma unroll
+            for (int ks = 0; ks < NC / 16; ++ks)   // 16 values of K = two core matrices
+              mma_bf16(acc, ns_desc(sa + p * TILE_A + ks * 256, NC),
+                       ns_desc(sb + (g - p) * TILE_B + ks * 256, NC), idesc,
+                       (p == 0 && ks == 0) ? 0u : 1u);
+          }
+          mma_commit(acc_full(g));   // arrives when this group's MMAs have completed
+        }
+        if (!ok) break;
+        mma_commit(empty(s));
+      }
+      // every MMA issued by this thread completes before TMEM is freed
+      mma_commit(drain);
+      if (!mbar_wait(drain, 0)) flag_status(a.status, SKY_ETIMEOUT);
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int w = warp - kProd - 1;            // 0 .. kEpi - 1
+    const int q = warp & 3, half = w >> 2;     // TMEM lane quadrant = warp id mod 4
+    const int row = q * 32 + lane;
+    bool ok = true;
+    int it = 0;
+    for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++it) {
+      const int slot = it & 1;
+      if (!mbar_wait(ea_full(slot), (uint32_t)((it >> 1) & 1))) {
+        if (lane == 0) flag_status(a.status, SKY_ETIMEOUT);
+        break;
+      }
+      const int E = s_ea[slot * BM + row];
+      mbar_arrive(ea_empty(slot));
+      const long long l = (long long)t * BM + row;
+      long long stride = 0;
+      const long long lb = l < a.nlines ? line_base<N, AXIS>(a, l, stride) : 0;
+      const int sc = E - 16 - 8 * (S - 1);
+      // columns in blocks of 8 (4 points): all groups of a block are combined
+      // before the next block; a group goes back to the MMA warp after its
+      // last block (waits on a completed phase return at once until then)
+#pragma unroll 1
+      for (int cb = 0; cb < HALF; cb += 8) {
+        long long acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = 0;
+#pragma unroll
+        for (int g = 0; g < S; ++g) {
+          if (!mbar_wait(acc_full(g), (uint32_t)(it & 1))) {
+            if (lane == 0) flag_status(a.status, SKY_ETIMEOUT);
+            ok = false;
+            break;
+          }
+          fence_after();
+          uint32_t v[8];
+          oz::tmem_ld<8>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * NC + half * HALF + cb), v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (cb + 8 == HALF) {
+            // this warp's lanes of the group are read: hand it back
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty(g));
+          }
+          const long long w8 = 1LL << (8 * (S - 1 - g));
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            acc[c] += (long long)__float2int_rn(__uint_as_float(v[c])) * w8;
+        }
+        if (!ok) break;
+        if (l < a.nlines) {
+#pragma unroll
+          for (int c = 0; c < 8; c += 2) {
+            const int o = half * HALF + cb + c;   // even: (re, im) of point o / 2
+            const int m = o >> 1;
+            if (m < N) {
+              double2 res;
+              res.x = scaled_double(acc[c], sc + s_eb[o]);
+              res.y = scaled_double(acc[c + 1], sc + s_eb[o + 1]);
+              a.dst[lb + m * stride] = res;
+            }
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == kProd) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------ host side
+bool supported(int n) { return n == 8 || n == 12 || n == 16 || n == 20 || n == 24 || n == 32; }
+
+// Digits [S][NC][NC] (canonical layout, bf16 bit patterns) and row exponents
+// [NC] of the real operator of one axis, built in long double.
+void build_operator(int n, double L, double theta, std::vector<unsigned short>& dig,
+                    std::vector<int>& ex) {
+  const int NC = nc_of(n);
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  std::vector<long double> dre(n), dim(n);
+  for (int r = 0; r < n; ++r) {
+    long double sr = 0.0L, si = 0.0L;
+    for (int a = 0; a < n; ++a) {
+      const int mm = a < (n + 1) / 2 ? a : a - n;
+      const long double kap = (two_pi * mm + (long double)theta) / (long double)L;
+      const long double ang = two_pi * (long double)(((long long)a * r) % n) / (long double)n;
+      sr -= kap * sinl(ang);   // Re of i kappa e^{i ang}
+      si += kap * cosl(ang);   // Im
+    }
+    dre[r] = sr / n;
+    dim[r] = si / n;
+  }
+  std::vector<double> B((size_t)NC * NC, 0.0);
+  for (int m = 0; m < n; ++m)
+    for (int q = 0; q < n; ++q) {
+      const int r = ((m - q) % n + n) % n;
+      const double re = (double)dre[r], im = (double)dim[r];
+      B[(size_t)(2 * m) * NC + 2 * q] = re;
+      B[(size_t)(2 * m) * NC + 2 * q + 1] = -im;
+      B[(size_t)(2 * m + 1) * NC + 2 * q] = im;
+      B[(size_t)(2 * m + 1) * NC + 2 * q + 1] = re;
+    }
+  dig.assign((size_t)S * NC * NC, 0);
+  ex.assign(NC, 0);
+  for (int o = 0; o < NC; ++o) {
+    int F = INT_MIN;
+    for (int k = 0; k < NC; ++k) {
+      const double x = B[(size_t)o * NC + k];
+      if (x != 0.0) {
+        int e;
+        std::frexp(x, &e);   // |x| < 2^e
+        F = e > F ? e : F;
+      }
+    }
+    if (F == INT_MIN) F = 0;
+    ex[o] = F;
+    for (int k = 0; k < NC; ++k) {
+      const double x = B[(size_t)o * NC + k];
+      // X = round(|x| 2^{8S - F}) < 2^48 + 1, exact (power-of-two scaling, then +0.5)
+      long long X = (long long)std::floor(std::ldexp(std::fabs(x), 8 * S - F) + 0.5);
+      int d[S];
+      for (int s = S - 1; s >= 1; --s) {
+        int v = (int)(X & 255);
+        X >>= 8;
+        if (v >= 128) { v -= 256; ++X; }
+        d[s] = v;
+      }
+      d[0] = (int)X;
+      for (int p = 0; p < S; ++p) {
+        const float f = (float)(x < 0.0 ? -d[p] : d[p]);   // |d| <= 256: exact in bf16
+        unsigned u;
+        std::memcpy(&u, &f, 4);
+        dig[((size_t)p * NC * NC * 2 + cm_off(o, k, NC)) / 2] = (unsigned short)(u >> 16);
+      }
+    }
+  }
+}
+
+template <int N, int AXIS>
+cudaError_t launch(const DerivArgs& a, const Ctx* c) {
+  using Sh = Shape<N>;
+  static bool set[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!set[dev]) {
+    e = cudaFuncSetAttribute(k_oz_deriv<N, AXIS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Sh::SMEM);
+    if (e != cudaSuccess) return e;
+    set[dev] = true;
+  }
+  const int grid = a.ntiles < c->num_sms ? a.ntiles : c->num_sms;
+  k_oz_deriv<N, AXIS><<<grid, THREADS, Sh::SMEM, c->stream>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace ozd
+
+sky_status deriv_tc_init(Ctx* c) {
+  for (int j = 0; j < 3; ++j) {
+    c->d_dop[j] = nullptr;
+    c->d_dope[j] = nullptr;
+  }
+  if (c->prec != SKY_F64) return SKY_OK;
+  for (int j = 0; j < 3; ++j) {
+    if (!ozd::supported(c->n[j])) continue;
+    std::vector<unsigned short> dig;
+    std::vector<int> ex;
+    ozd::build_operator(c->n[j], c->L[j], c->theta[j], dig, ex);
+    cudaError_t e = cudaMalloc(&c->d_dop[j], dig.size() * sizeof(unsigned short));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_dope[j], ex.size() * sizeof(int));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->d_dop[j], dig.data(), dig.size() * sizeof(unsigned short),
+                     cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->d_dope[j], ex.data(), ex.size() * sizeof(int), cudaMemcpyHostToDevice);
+    const sky_status s = cuda_check(c, e, "derivative operator upload");
+    if (s != SKY_OK) return s;
+  }
+  return SKY_OK;
+}
+
+// dst = d_ax src over nb arrays of G complex doubles (dst may equal src).
+cudaError_t deriv_tc(Ctx* c, int ax, const double2* src, double2* dst, long long nb) {
+  const int n = c->n[ax];
+  if (!c->d_dop[ax]) return cudaErrorInvalidValue;
+  ozd::DerivArgs a;
+  a.src = src;
+  a.dst = dst;
+  a.op = (const uint4*)c->d_dop[ax];
+  a.ope = c->d_dope[ax];
+  a.nx = c->n[0];
+  a.ny = c->n[1];
+  a.nz = c->n[2];
+  a.G = c->G;
+  a.nlines = nb * (c->G / n);
+  if (a.nlines == 0) return cudaSuccess;
+  const long long nt = (a.nlines + ozd::BM - 1) / ozd::BM;
+  if (nt > INT_MAX) return cudaErrorInvalidValue;
+  a.ntiles = (int)nt;
+  a.status = c->d_status;
+  auto go = [&](auto NC) -> cudaError_t {
+    constexpr int N = decltype(NC)::value;
+    if (ax == 0) return ozd::launch<N, 0>(a, c);
+    if (ax == 1) return ozd::launch<N, 1>(a, c);
+    return ozd::launch<N, 2>(a, c);
+  };
+  switch (n) {
+    case 8: return go(std::integral_constant<int, 8>{});
+    case 12: return go(std::integral_constant<int, 12>{});
+    case 16: return go(std::integral_constant<int, 16>{});
+    case 20: return go(std::integral_constant<int, 20>{});
+    case 24: return go(std::integral_constant<int, 24>{});
+    case 32: return go(std::integral_constant<int, 32>{});
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sky

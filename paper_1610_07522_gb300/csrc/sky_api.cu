@@ -89,7 +89,8 @@ static void free_all(Ctx* c) {
                   c->d_stats, c->d_tcA[0], c->d_tcA[1], c->d_tcA[2], c->d_tcB[0],
                   c->d_tcB[1], c->d_tcB[2], c->d_tcRotA[0], c->d_tcRotA[1], c->d_tcRotA[2],
                   c->d_tcPart, c->d_netpart, c->d_trid, c->d_ozA, c->d_ozB, c->d_ozE,
-                  c->d_ozP, c->d_trivec};
+                  c->d_ozP, c->d_trivec, c->d_dop[0], c->d_dop[1], c->d_dop[2],
+                  c->d_dope[0], c->d_dope[1], c->d_dope[2]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -239,7 +240,7 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   c->wait_spins = kBarrierSpins;
   c->jac_max_sweeps = kJacMaxSweeps;
   c->eig_method = SKY_EIG_AUTO;
-  c->line_dd = prec == SKY_F64 ? 1 : 0;
+  c->line_arith = prec == SKY_F64 ? 1 : 0;   // the tensor-core operator once built
   size_t gpart = 0;
   for (int I = 1; I <= Imax; ++I) {   // room for the largest tunable split count
     const size_t need = overlap_partial_elems(I, V, kMaxOverlapWaves * c->ov_slots);
@@ -339,6 +340,8 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   if (s == SKY_OK) s = cuda_check(c, cudaMemset(c->d_stats, 0, 8 * sizeof(long long)), "stats reset");
   if (s == SKY_OK) s = cuda_check(c, cudaMemset(c->d_bar, 0, 2 * sizeof(unsigned)), "barrier reset");
   if (s == SKY_OK) s = tri_init(c);
+  if (s == SKY_OK) s = deriv_tc_init(c);
+  if (s == SKY_OK && c->d_dop[0] && c->d_dop[1] && c->d_dop[2]) c->line_arith = 2;
   if (s == SKY_OK) s = upload_twiddles_hamiltonian(c);
   if (s == SKY_OK) s = upload_twiddles_fields(c);
   if (s == SKY_OK) s = build_coulomb_table(c);
@@ -609,9 +612,10 @@ sky_status sky_tune_set(sky_ctx* c, sky_knob knob, int value) {
       c->eig_method = value;
       return SKY_OK;
     case SKY_KNOB_LINE_ARITH:
-      if (value != 0 && value != 1) break;
-      if (value == 1 && c->prec != SKY_F64) break;
-      c->line_dd = value;
+      if (value < 0 || value > 2) break;
+      if (value >= 1 && c->prec != SKY_F64) break;
+      if (value == 2 && !(c->d_dop[0] && c->d_dop[1] && c->d_dop[2])) break;
+      c->line_arith = value;
       return SKY_OK;
     case SKY_KNOB_SPLIT_GEMM:
       if (value != 0 && value != 1) break;
@@ -643,7 +647,7 @@ int sky_tune_get(const sky_ctx* c, sky_knob knob) {
     case SKY_KNOB_JACOBI_MAX_SWEEPS: return c->jac_max_sweeps;
     case SKY_KNOB_EIGEN_METHOD: return c->eig_method;
     case SKY_KNOB_SPLIT_GEMM: return c->oz_on;
-    case SKY_KNOB_LINE_ARITH: return c->line_dd;
+    case SKY_KNOB_LINE_ARITH: return c->line_arith;
     default: return -1;
   }
 }

@@ -79,7 +79,10 @@ struct Ctx {
   float* d_ktf[3];                  // the same in FP32
   double* d_kp[3];                  // plain wavenumbers (real fields)
   float2* d_ktdd[3];                // (k + theta/L) / n as float pairs (double-float passes)
-  int line_dd;                      // 1: FP64 derivative passes in double-float arithmetic
+  int line_arith;                   // FP64 derivative passes: 0 FP64 FFT, 1 double-float FFT,
+                                    // 2 digit-split operator on the tensor cores
+  void* d_dop[3];                   // tensor-core derivative operators: digits, smem layout
+  int* d_dope[3];                   // their row exponents
   double* d_damp[2];                // 1 / (E0 + hb2m_q |k + theta/L|^2), [G]
   double damp_E0[2];                // E0 the tables were built for (NaN = none)
   double* d_coul;                   // 4 pi e^2 / |k|^2 (0 at k = 0), [G]
@@ -208,6 +211,11 @@ sky_status subspace_literal_batch(Ctx* c, int np, const double2* const* H,
 sky_status eigh_batch_tri(Ctx* c, int np, const double2* const* A, const int* n,
                           double* const* w, double2* const* Z, const int* run, int run_stride);
 sky_status tri_init(Ctx* c);
+// Derivative passes of the FP64 form as digit-split operator products on the
+// tensor cores (oz_deriv.cu): operators built at context creation for axis
+// lengths 8, 12, 16, 20, 24, 32; dst = d_ax src over nb arrays (dst may be src).
+sky_status deriv_tc_init(Ctx* c);
+cudaError_t deriv_tc(Ctx* c, int ax, const double2* src, double2* dst, long long nb);
 bool tri_vectors_global(int n);
 size_t tri_vec_elems(int m, int nb, int nsm);
 inline size_t tri_slot_doubles(int m) { return (size_t)m * m + 16 * (size_t)m; }

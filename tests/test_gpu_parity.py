@@ -514,11 +514,12 @@ def test_batched_loewdin_and_rayleigh_ritz():
             assert np.max(np.abs(Mg.conj().T @ Ss[b] @ Mg - np.eye(I[b]))) < 1e-11
 
 
-@pytest.mark.parametrize("case", [CASES[2], CASES[3]])
-def test_apply_h_and_densities_in_both_line_arithmetics(case):
-    """The FP64 form's derivative line passes in double-float arithmetic (the
-    default, SKY_KNOB_LINE_ARITH = 1) and in FP64 (0): both within the FP64
-    per-call tolerance of the oracle; FP32 contexts accept only 0."""
+@pytest.mark.parametrize("case", [CASES[2], CASES[3], CASES[4]])
+def test_apply_h_and_densities_in_every_line_arithmetic(case):
+    """The FP64 form's derivative passes as the digit-split operator on the
+    tensor cores (the default, SKY_KNOB_LINE_ARITH = 2), as FFT line passes in
+    double-float arithmetic (1) and in FP64 (0): all within the FP64 per-call
+    tolerance of the oracle; FP32 contexts accept only 0."""
     rng = np.random.default_rng(77)
     with Ctx(*case) as c:
         g = c.grid
@@ -527,8 +528,8 @@ def test_apply_h_and_densities_in_both_line_arithmetics(case):
         U, Bf, W = _fields(g, rng)
         want = O.apply_h(psi, U, Bf, W, g)
         rho_w, tau_w, J_w, dJ_w = O.densities(psi, g)
-        assert B.sky_tune_get(c.ctx, B.SKY_KNOB_LINE_ARITH) == 1
-        for arith in (1, 0):
+        assert B.sky_tune_get(c.ctx, B.SKY_KNOB_LINE_ARITH) == 2
+        for arith in (2, 1, 0):
             B.sky_tune_set(c.ctx, B.SKY_KNOB_LINE_ARITH, arith)
             d_h = torch.zeros(psi.shape, dtype=torch.complex128, device="cuda:0")
             B.sky_apply_h(c.ctx, dev(U), dev(Bf), dev(W), dev(psi), d_h, I)
@@ -541,8 +542,33 @@ def test_apply_h_and_densities_in_both_line_arithmetics(case):
             assert relerr(host(J), J_w.ravel()) < REL, arith
     with Ctx((16, 16, 16), prec=B.SKY_F32) as c32:
         assert B.sky_tune_get(c32.ctx, B.SKY_KNOB_LINE_ARITH) == 0
-        with pytest.raises(B.SkyError):
-            B.sky_tune_set(c32.ctx, B.SKY_KNOB_LINE_ARITH, 1)
+        for bad in (1, 2):
+            with pytest.raises(B.SkyError):
+                B.sky_tune_set(c32.ctx, B.SKY_KNOB_LINE_ARITH, bad)
+
+
+def test_tensor_core_derivative_many_tiles_ragged_and_in_place():
+    """The operator kernel on 24^3 with 37 spinors (74 arrays: 42 624 lines per
+    axis, 333 tiles of 128 with a ragged last tile; more tiles than SMs, so
+    every CTA loops), through apply_h (gradient out of place, divergence in
+    place) and against the FFT form in FP64 on the same context."""
+    rng = np.random.default_rng(5)
+    with Ctx((24, 24, 24), twist=(0.7, -0.3, 1.9)) as c:
+        g = c.grid
+        I = 37
+        psi = IN.random_spinors(g.n, I, rng)
+        U, Bf, W = _fields(g, rng)
+        d_psi, dU, dB, dW = dev(psi), dev(U), dev(Bf), dev(W)
+        out = {}
+        for arith in (2, 0):
+            B.sky_tune_set(c.ctx, B.SKY_KNOB_LINE_ARITH, arith)
+            d_h = torch.zeros(psi.shape, dtype=torch.complex128, device="cuda:0")
+            B.sky_apply_h(c.ctx, dU, dB, dW, d_psi, d_h, I)
+            out[arith] = host(d_h)
+        assert relerr(out[2], out[0]) < REL
+        idx = [0, 17, 36]
+        want = O.apply_h(psi[idx], U, Bf, W, g)
+        assert relerr(out[2][idx], want) < REL
 
 
 def test_apply_h_across_magnitudes():
