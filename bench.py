@@ -744,6 +744,22 @@ def probe_call(args):
         B.sky_overlap(ctx, psi, psi, I, X)
     elif args.probe_call == "rotate":
         B.sky_rotate(ctx, psi, M, I, out)
+    elif args.probe_call == "ritz":
+        # the batched Rayleigh-Ritz solve of both species (I = N and Z):
+        # Hermitian H with a spread spectrum, C = identity
+        Is = [w.N, w.Z]
+        Hs, Cs, Ms, ls = [], [], [], []
+        for n in Is:
+            h = torch.randn((n, n), dtype=torch.complex128, device=dev, generator=gen) * 0.1
+            h = h + h.conj().T + torch.diag(torch.linspace(-60.0, 20.0, n, dtype=torch.float64,
+                                                           device=dev)).to(torch.complex128)
+            Hs.append(torch.view_as_real(h.contiguous()))
+            Cs.append(torch.view_as_real(torch.eye(n, dtype=torch.complex128, device=dev)))
+            Ms.append(torch.zeros((n, n, 2), dtype=torch.float64, device=dev))
+            ls.append(torch.zeros(n, dtype=torch.float64, device=dev))
+        torch.cuda.synchronize(dev)
+        n0 = B.sky_kernel_launches()
+        B.sky_subspace_diag_batched(ctx, Hs, Cs, Is, Ms, ls)
     B.sky_sync(ctx)
     print(json.dumps({"probe_call": args.probe_call, "workload": args.workload, "form": args.form,
                       "I": I, "launches": B.sky_kernel_launches() - n0}))
@@ -843,6 +859,9 @@ def run_gpu(args):
     sc.sync()
     torch.cuda.synchronize()
     calls = call_rooflines(sc.call_events, w.grid, prec, peaks, csize)
+    # where a single-stream step spends its time: CUDA events around every call
+    breakdown = {k: sum(e0.elapsed_time(e1) for _, e0, e1 in ev) / args.steps
+                 for k, ev in sc.call_events.items()}
     sc.call_events = None
     sc.close()
     # the line's roofline: the h.psi call, the largest call of the step (the
@@ -945,8 +964,10 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "solver_stats_timed_steps": solver_stats,
         "single_stream": {"ms_per_step": conc_ms, "value": ws * units / (conc_ms / 1e3),
+                          "calls_ms_per_step": breakdown,
                           "note": "both species on one context and stream (the main number "
-                                  "runs them on two)"},
+                                  "runs them on two); calls_ms_per_step: CUDA events around "
+                                  "each library call of a separate single-stream run"},
         "split_eigensolve": {"ms_per_step": split_ms, "value": ws * units / (split_ms / 1e3),
                              "note": "two streams, each species' Loewdin and Rayleigh-Ritz solve "
                                      "on its own stream (the main number: one batched solve)"},
@@ -986,7 +1007,7 @@ def main():
                     help="skip the time-dependent stepping leg")
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the time-to-convergence comparison of the forms")
-    ap.add_argument("--probe-call", default=None, choices=["apply_h", "overlap", "rotate"],
+    ap.add_argument("--probe-call", default=None, choices=["apply_h", "overlap", "rotate", "ritz"],
                     help="run one library call on the workload's shapes and exit (for ncu)")
     ap.add_argument("--line-arith", type=int, default=None, choices=[0, 1],
                     help="--probe-call only: FP64 form's derivative line passes in FP64 (0) "

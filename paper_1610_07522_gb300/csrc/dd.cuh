@@ -65,6 +65,9 @@ __device__ __forceinline__ ddc operator-(ddc a) { return ddc{-a.x, -a.y}; }
 __device__ __forceinline__ ddc operator*(dd s, ddc a) { return ddc{s * a.x, s * a.y}; }
 __device__ __forceinline__ ddc mul_i(ddc a) { return ddc{-a.y, a.x}; }
 __device__ __forceinline__ ddc mul_mi(ddc a) { return ddc{a.y, -a.x}; }
+__device__ __forceinline__ ddc half(ddc a) {   // exact (barring underflow)
+  return ddc{dd(a.x.hi * 0.5f, a.x.lo * 0.5f), dd(a.y.hi * 0.5f, a.y.lo * 0.5f)};
+}
 
 // double <-> pair.  GB300's FP64 unit issues about one seventieth of the FP32
 // rate, and conversions between double and float run on it, so both
@@ -108,7 +111,38 @@ __device__ __forceinline__ double widen(float f) {
   const long long mag = m == 0u ? 0LL : ((long long)m << 29) + (896LL << 52);
   return __longlong_as_double(mag | ((long long)(u & 0x80000000u) << 32));
 }
-__device__ __forceinline__ double dbl_of(dd a) { return __dadd_rn(widen(a.hi), widen(a.lo)); }
+// hi + lo rounded to a double by integer operations: hi widened exactly; lo
+// counted in units of the last place of hi's double, an integer shift of
+// lo's significand (rounded half up when the unit is coarser), added to or
+// subtracted from hi's pattern.  For a normalised pair (|lo| <= ulp(hi) / 2,
+// what every operation here returns) the count stays below 2^28, so the sum
+// never leaves hi's binade, except downwards from a power of two, where the
+// unit of the binade below (half as large) is used.  Zeros, subnormals,
+// infinities, NaNs and pairs with |lo| > 2^-24 |hi| take one FP64 addition.
+__device__ __forceinline__ double dbl_of(dd a) {
+  const unsigned uh = __float_as_uint(a.hi), ul = __float_as_uint(a.lo);
+  const unsigned mh = uh & 0x7fffffffu, ml = ul & 0x7fffffffu;
+  const int eh = (int)(mh >> 23), el = (int)(ml >> 23);
+  const long long sgn = (long long)(uh & 0x80000000u) << 32;
+  if (ml == 0u && (unsigned)(eh - 1) < 254u)   // exact float: widen
+    return __longlong_as_double((((long long)mh << 29) + (896LL << 52)) | sgn);
+  if ((unsigned)(eh - 1) >= 254u || (unsigned)(el - 1) >= 254u || eh - el < 24)
+    return __dadd_rn(widen(a.hi), widen(a.lo));
+  long long hd = ((long long)mh << 29) + (896LL << 52);     // |hi| as a double pattern
+  const long long sig = (long long)((ul & 0x7fffffu) | 0x800000u);
+  const bool same = ((uh ^ ul) & 0x80000000u) == 0u;
+  const bool down = !same && (mh & 0x7fffffu) == 0u;       // |hi| a power of two, decreasing
+  const int sh = 29 - (eh - el) + (down ? 1 : 0);           // |lo| / unit = sig 2^sh
+  long long K;
+  if (sh >= 0) {
+    K = sig << sh;
+  } else {
+    const int r = -sh;
+    K = r > 25 ? 0 : ((sig >> (r - 1)) + 1) >> 1;
+  }
+  hd = same ? hd + K : hd - K;
+  return __longlong_as_double(hd | sgn);
+}
 __device__ __forceinline__ ddc ddc_of(double2 v) { return ddc{dd_of(v.x), dd_of(v.y)}; }
 __device__ __forceinline__ double2 dbl2_of(ddc v) { return make_double2(dbl_of(v.x), dbl_of(v.y)); }
 

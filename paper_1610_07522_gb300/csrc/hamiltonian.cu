@@ -186,6 +186,37 @@ __global__ void __launch_bounds__(256) k_h_local(const cx<T>* __restrict__ psi, 
   hpsi[o1] = L1;
 }
 
+// The same pass for the FP64 form in double-float arithmetic (the FP32 pipe;
+// loads split, stores rounded by integer operations, dd.cuh).
+__global__ void __launch_bounds__(256) k_h_local_dd(const double2* __restrict__ psi, double2* g0,
+                                                    double2* g1, double2* g2,
+                                                    double2* __restrict__ hpsi,
+                                                    const double* __restrict__ U,
+                                                    const double* __restrict__ B,
+                                                    const double* __restrict__ W, int G) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= G) return;
+  const long long o0 = (long long)blockIdx.y * 2 * G + p, o1 = o0 + G;
+  const ddc a0 = ddc_of(psi[o0]), a1 = ddc_of(psi[o1]);
+  const dd u = dd_of(U[p]), bb = dd_of(B[p]);
+  const dd wx = dd_of(W[p]), wy = dd_of(W[G + p]), wz = dd_of(W[2 * G + p]);
+  double2* gs[3] = {g0, g1, g2};
+  ddc L0 = u * a0, L1 = u * a1;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const ddc d0 = ddc_of(gs[j][o0]), d1 = ddc_of(gs[j][o1]);
+    ddc t0, t1;
+    apply_A<dd>(j, wx, wy, wz, d0, d1, t0, t1);    // A_j G_j
+    L0 = L0 + half(mul_mi(t0));                    // - (i/2) A_j G_j
+    L1 = L1 + half(mul_mi(t1));
+    apply_A<dd>(j, wx, wy, wz, a0, a1, t0, t1);    // A_j psi
+    gs[j][o0] = dbl2_of((-bb) * d0 + half(mul_mi(t0)));   // F_j = -B G_j - (i/2) A_j psi
+    gs[j][o1] = dbl2_of((-bb) * d1 + half(mul_mi(t1)));
+  }
+  hpsi[o0] = dbl2_of(L0);
+  hpsi[o1] = dbl2_of(L1);
+}
+
 // Deterministic block sum of two doubles (blockDim.x == kRedBlock).
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
   __shared__ double sa[kRedBlock / 32], sb[kRedBlock / 32];
@@ -262,7 +293,12 @@ static sky_status apply_h_t(Ctx* c, const double* U, const double* B, const doub
     cudaError_t e = gradient_passes<T>(c, ps, g, 2LL * ns);
     if (e != cudaSuccess) return cuda_check(c, e, "apply_h gradient");
     dim3 grid(div_up(G, 256), ns);
-    k_h_local<T><<<grid, 256, 0, c->stream>>>(ps, g[0], g[1], g[2], hs, U, B, W, (int)G); note_launch();
+    if (std::is_same<T, double>::value && c->line_arith != 0)
+      k_h_local_dd<<<grid, 256, 0, c->stream>>>((const double2*)ps, (double2*)g[0], (double2*)g[1],
+                                                (double2*)g[2], (double2*)hs, U, B, W, (int)G);
+    else
+      k_h_local<T><<<grid, 256, 0, c->stream>>>(ps, g[0], g[1], g[2], hs, U, B, W, (int)G);
+    note_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "apply_h local");
     // pass 3: F_j <- d_j F_j in place, one axis per array
     for (int ax = 0; ax < 3; ++ax) {

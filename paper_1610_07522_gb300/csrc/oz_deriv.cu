@@ -14,11 +14,15 @@
 // (nb G / n rows, K = N = 2n, padded to NC = a multiple of 16).  Both
 // operands are cut into six base-256 digits (oz_digits.cuh), each line scaled
 // by its own exponent and each row of Dr by its own; the 21 digit products of
-// weight g = s + t <= 5 are summed exactly in FP32 in TMEM (per K value
-// |G_g| <= (g + 3) 2^14, K <= 64), combined exactly in a 64-bit integer,
-// rounded once to FP64 and scaled by the two exponents.  The only error is the
-// truncated digit expansion, about 2^-48 of the line's and the row's largest
-// values.
+// weight g = s + t <= 5 are summed in FP32 in TMEM: weights 0-3 exactly, one
+// accumulator each (per K value |G_g| <= (g + 3) 2^14, K <= 64, so every sum
+// stays an integer below 2^24), weights 4 and 5 together in a fifth, the
+// weight-5 products taken with the operator's digits times 2^-8 (exact in
+// bf16); its FP32 rounding, at most K 2^-24 of a sum below 2^23 at weight
+// 2^-32, is about 2^-49 of the largest term.  The sums are combined in a
+// 64-bit integer, rounded once to FP64 and scaled by the two exponents.  The
+// error is that rounding plus the truncated digit expansion, about 2^-48 of
+// the line's and the row's largest values.
 //
 // Persistent kernel, one CTA per SM, 128 lines per tile:
 //   warps 0-7   producers: warp w takes lines 16 w .. 16 w + 15 of the tile,
@@ -28,12 +32,15 @@
 //               writes its digits into a ring stage in the canonical
 //               no-swizzle K-major layout (8-row x 16-byte core matrices),
 //               fences the writes for the tensor core's proxy and arrives;
-//   warp 8      owns TMEM (6 groups x NC fp32 columns); one lane issues
+//   warp 8      owns TMEM (two accumulator sets of 5 x NC fp32 columns, so
+//               the MMAs of one tile run while the epilogue drains the
+//               previous one; one set when 5 NC > 256); one lane issues
 //               tcgen05.mma (M = 128, N = NC, K = 16) for every digit pair;
 //   warps 9-16  epilogue: two warps per TMEM lane quadrant, half the columns
-//               each; they drain the groups in order into 64-bit integers,
-//               round, scale and store the (re, im) pairs at the line's
-//               points (in place is allowed: tiles own disjoint lines).
+//               each, in blocks of 8 columns; they combine the groups into
+//               64-bit integers, round, scale and store the (re, im) pairs at
+//               the line's points (in place is allowed: tiles own disjoint
+//               lines), then hand the accumulator set back.
 // The operator's digits, computed once per context on the host in long
 // double, stay in shared memory for the whole launch.  Every mbarrier wait is
 // bounded; a timeout sets SKY_ETIMEOUT, the kernel waits (bounded) for the
@@ -64,6 +71,7 @@ constexpr int kProd = 8, kEpi = 8;   // producer warps: two threads per line
 constexpr int THREADS = 32 * (kProd + 1 + kEpi);
 constexpr int kSmemMax = 232448;   // dynamic shared memory opt-in limit per CTA
 constexpr int kBars = 24;
+constexpr int NG = 5;              // TMEM groups: weights 0, 1, 2, 3 and {4, 5}
 
 __host__ __device__ constexpr int nc_of(int n) { return ((2 * n + 15) / 16) * 16; }
 
@@ -73,14 +81,22 @@ struct Shape {
   static constexpr int TILE_A = BM * NC * 2;   // one digit of a tile of lines
   static constexpr int STAGE = S * TILE_A;
   static constexpr int TILE_B = NC * NC * 2;   // one digit of the operator
-  static constexpr int OPB = S * TILE_B;
+  static constexpr int OPB = 2 * S * TILE_B;   // its digits, then the digits times 2^-8
+  static constexpr int NBUF = NG * NC <= 256 ? 2 : 1;   // TMEM accumulator sets
   static constexpr int AUX = NC * 4 + 2 * BM * 4 + kBars * 8 + 16;
-  static constexpr int STAGES = (2 * STAGE + OPB + AUX + 1024 <= kSmemMax) ? 2 : 1;
-  static constexpr int SMEM = STAGES * STAGE + OPB + AUX + 1024;
+  static constexpr int H0 = ((N / 2 + 3) / 4) * 4;             // points of a line's first half
+  // staging of the next tile's half lines (one 16-byte slot per point and
+  // producer thread) when it fits beside one ring stage
+  static constexpr int STG_BYTES = H0 * kProd * 32 * 16;
+  static constexpr bool PREFETCH = STAGE + OPB + AUX + STG_BYTES + 1024 <= kSmemMax;
+  static constexpr int STG = PREFETCH ? STG_BYTES : 0;
+  static constexpr int STAGES = (2 * STAGE + OPB + AUX + STG + 1024 <= kSmemMax) ? 2 : 1;
+  static constexpr int SMEM = STAGES * STAGE + OPB + AUX + STG + 1024;
   static constexpr int HALF = NC / 2;          // columns per epilogue warp
-  static_assert(S * NC <= 512, "TMEM columns");
+  static_assert(NG * NC <= 512, "TMEM columns");
   static_assert(SMEM <= kSmemMax, "shared memory");
   static_assert(HALF % 8 == 0, "TMEM load blocks of 8 columns");
+  static_assert(NC <= 64, "int32 bounds of the group combination");
 };
 
 // Byte offset of element (r, k) of a K-major bf16 tile with nc columns in the
@@ -99,6 +115,15 @@ __device__ __forceinline__ uint64_t ns_desc(uint32_t saddr, int nc) {
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+// 16-byte asynchronous copy global -> shared (zero fill when !valid).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // The six balanced base-256 digits of the signed integer Y = +-round(|x|
 // 2^{48 - E}) (|Y| <= 2^48), as floats: adding 128 to each of the five lower
 // byte positions (0x8080808080) turns every lower byte, minus 128, into a
@@ -144,15 +169,39 @@ __device__ __forceinline__ double scaled_double(long long v, int sc) {
   return __longlong_as_double((long long)(neg | ((((unsigned long long)(be - 1)) << 52) + r)));
 }
 
+// n / d for 0 <= n < 2^31 by an invariant multiplier (Granlund and Montgomery,
+// PLDI 1994): with L = ceil(log2 d) and p = 31 + L, m = ceil(2^p / d) < 2^32
+// and floor(n / d) = floor(n m / 2^p), because n m / 2^p exceeds n / d by
+// less than n / 2^p < 2^-L <= 1 / d; d = 1 is the identity.
+struct FastDiv {
+  unsigned d, m;
+  int sh;   // p - 32
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f{d, 0u, 0};
+  if (d > 1) {
+    int L = 0;
+    while ((1ull << L) < d) ++L;
+    const int p = 31 + L;
+    f.m = (unsigned)(((1ull << p) + d - 1) / d);
+    f.sh = p - 32;
+  }
+  return f;
+}
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
+  return f.d == 1 ? n : (__umulhi(n, f.m) >> f.sh);
+}
+
 struct DerivArgs {
   const double2* src;   // nb arrays of G complex points (may equal dst)
   double2* dst;
-  const uint4* op;      // operator digits, S * TILE_B bytes in the canonical layout
+  const uint4* op;      // operator digits, 2 S * TILE_B bytes in the canonical layout
   const int* ope;       // operator row exponents [NC]
   int nx, ny, nz;
   long long G;
-  long long nlines;
+  long long nlines;   // < 2^31
   int ntiles;
+  FastDiv div1, div2;   // by nx, then by nz (lines along y) or ny (lines along z)
   int* status;
 };
 
@@ -163,14 +212,19 @@ __device__ __forceinline__ long long line_base(const DerivArgs& a, long long l, 
   if constexpr (AXIS == 0) {
     stride = 1;
     return l * N;
-  } else if constexpr (AXIS == 1) {
-    const long long x = l % a.nx, t = l / a.nx, z = t % a.nz, b = t / a.nz;
-    stride = a.nx;
-    return b * a.G + z * (long long)a.ny * a.nx + x;
   } else {
-    const long long x = l % a.nx, t = l / a.nx, y = t % a.ny, b = t / a.ny;
-    stride = (long long)a.nx * a.ny;
-    return b * a.G + y * (long long)a.nx + x;
+    const unsigned lu = (unsigned)l;
+    const unsigned t = fdiv(lu, a.div1), x = lu - t * (unsigned)a.nx;
+    const unsigned b = fdiv(t, a.div2);
+    if constexpr (AXIS == 1) {
+      const unsigned z = t - b * (unsigned)a.nz;
+      stride = a.nx;
+      return (long long)b * a.G + (long long)(z * (unsigned)(a.ny * a.nx) + x);
+    } else {
+      const unsigned y = t - b * (unsigned)a.ny;
+      stride = (long long)a.nx * a.ny;
+      return (long long)b * a.G + (long long)(y * (unsigned)a.nx + x);
+    }
   }
 }
 
@@ -184,7 +238,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
   unsigned char* base = (unsigned char*)(((unsigned long long)smem_raw + 1023ull) & ~1023ull);
   unsigned char* opb = base;                                  // operator digits
   unsigned char* ring = base + Sh::OPB;                       // STAGES x STAGE
-  int* s_eb = (int*)(ring + STAGES * STAGE);                  // [NC]
+  unsigned char* stg = ring + STAGES * STAGE;                 // [H0][producer thread] 16 B
+  int* s_eb = (int*)(stg + Sh::STG);                          // [NC]
   int* s_ea = s_eb + NC;                                      // [2][BM]
   unsigned long long* bars = (unsigned long long*)(s_ea + 2 * BM);
   uint32_t* tmem_slot = (uint32_t*)(bars + kBars);
@@ -192,8 +247,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
   const uint32_t bar0 = smem_u32(bars);
   auto full = [&](int s) { return bar0 + 8u * s; };
   auto empty = [&](int s) { return bar0 + 8u * (2 + s); };
-  auto acc_full = [&](int g) { return bar0 + 8u * (4 + g); };
-  auto acc_empty = [&](int g) { return bar0 + 8u * (4 + S + g); };
+  auto acc_full = [&](int b) { return bar0 + 8u * (4 + b); };
+  auto acc_empty = [&](int b) { return bar0 + 8u * (4 + S + b); };
   auto ea_full = [&](int j) { return bar0 + 8u * (4 + 2 * S + j); };
   auto ea_empty = [&](int j) { return bar0 + 8u * (6 + 2 * S + j); };
   const uint32_t drain = bar0 + 8u * (8 + 2 * S);
@@ -207,9 +262,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
       mbar_init(full(s), kProd * 32);
       mbar_init(empty(s), 1);
     }
-    for (int g = 0; g < S; ++g) {
-      mbar_init(acc_full(g), 1);
-      mbar_init(acc_empty(g), kEpi);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full(b), 1);
+      mbar_init(acc_empty(b), kEpi);
     }
     for (int j = 0; j < 2; ++j) {
       mbar_init(ea_full(j), kProd * 32);
@@ -233,16 +288,64 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
   if (warp < kProd) {
     // ---------------------------------------------------------------- producers
     // half 0 takes points [0, H0), half 1 [H0, N): H0 a multiple of 4, so each
-    // half covers whole 16-byte chunks (8 reals) of the digit rows
-    constexpr int H0 = ((N / 2 + 3) / 4) * 4, H1 = N - H0;
+    // half covers whole 16-byte chunks (8 reals) of the digit rows.  With
+    // PREFETCH a thread copies its half line of the next tile into its own
+    // staging slots (cp.async) while it splits the current one: no other
+    // thread takes part in the hand-over.
+    constexpr int H0 = Sh::H0, H1 = N - H0;
     static_assert(H1 > 0 && H1 <= H0 && H1 % 4 == 0, "line halves");
+    constexpr int PT = kProd * 32;            // producer threads
     const int r = warp * 16 + (lane & 15);    // row (line) of the tile
     const int hh = lane >> 4;                 // which half of the line
     const int np = hh ? H1 : H0;              // points of this half
     const int p0 = hh ? H0 : 0;               // first point
+    const uint32_t my_stg = smem_u32(stg) + (uint32_t)threadIdx.x * 16u;
+    auto prefetch = [&](int t, bool go) {     // go: a data dependency on the caller's reads
+      const long long l = (long long)t * BM + r;
+      const bool valid = go && l < a.nlines;
+      long long stride = 0;
+      const long long lb = valid ? line_base<N, AXIS>(a, l, stride) : 0;
+#pragma unroll
+      for (int j = 0; j < H0; ++j)
+        if (j < np)
+          cp_async16(my_stg + (uint32_t)(j * PT * 16),
+                     valid ? (const void*)(a.src + lb + (long long)(p0 + j) * stride)
+                           : (const void*)a.src,
+                     valid);
+      cp_async_commit();
+    };
+    if constexpr (Sh::PREFETCH)
+      if (blockIdx.x < a.ntiles) prefetch(blockIdx.x, true);
     int it = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
       const int s = it % STAGES, u = it / STAGES, slot = it & 1;
+      double2 v[H0];
+      if constexpr (Sh::PREFETCH) {
+        cp_async_wait_all();
+#pragma unroll
+        for (int j = 0; j < H0; ++j)
+          v[j] = j < np ? *(const double2*)(stg + (j * PT + threadIdx.x) * 16)
+                        : make_double2(0.0, 0.0);
+      } else {
+        const long long l = (long long)t * BM + r;
+        const bool valid = l < a.nlines;
+        long long stride = 0;
+        const long long lb = valid ? line_base<N, AXIS>(a, l, stride) : 0;
+#pragma unroll
+        for (int j = 0; j < H0; ++j)
+          v[j] = (valid && j < np) ? a.src[lb + (long long)(p0 + j) * stride]
+                                   : make_double2(0.0, 0.0);
+      }
+      int E = INT_MIN;
+#pragma unroll
+      for (int j = 0; j < H0; ++j) E = max(E, max(exp_of(v[j].x), exp_of(v[j].y)));
+      if constexpr (Sh::PREFETCH) {
+        // the next copy overwrites the slots just read: it is issued after E,
+        // which depends on every value read
+        if (t + (int)gridDim.x < a.ntiles) prefetch(t + gridDim.x, E != INT_MAX);
+      }
+      E = max(E, __shfl_xor_sync(0xffffffffu, E, 16));
+      if (E == INT_MIN) E = 0;
       if (u > 0 && !mbar_wait(empty(s), (uint32_t)((u - 1) & 1))) {
         flag_status(a.status, SKY_ETIMEOUT);
         break;
@@ -251,19 +354,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
         flag_status(a.status, SKY_ETIMEOUT);
         break;
       }
-      const long long l = (long long)t * BM + r;
-      const bool valid = l < a.nlines;
-      long long stride = 0;
-      const long long lb = valid ? line_base<N, AXIS>(a, l, stride) : 0;
-      double2 v[H0];
-#pragma unroll
-      for (int j = 0; j < H0; ++j)
-        v[j] = (valid && j < np) ? a.src[lb + (long long)(p0 + j) * stride] : make_double2(0.0, 0.0);
-      int E = INT_MIN;
-#pragma unroll
-      for (int j = 0; j < H0; ++j) E = max(E, max(exp_of(v[j].x), exp_of(v[j].y)));
-      E = max(E, __shfl_xor_sync(0xffffffffu, E, 16));
-      if (E == INT_MIN) E = 0;
       if (hh == 0) s_ea[slot * BM + r] = E;
       unsigned char* ta = ring + s * STAGE;
 #pragma unroll
@@ -297,6 +387,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
       mbar_arrive(full(s));
       mbar_arrive(ea_full(slot));
     }
+    if constexpr (Sh::PREFETCH) cp_async_wait_all();   // no copy outlives the launch
   } else if (warp == kProd) {
     // ---------------------------------------------------------------- MMA issue
     if (lane == 0) {
@@ -312,26 +403,32 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
         }
         fence_after();
         const uint32_t sa = smem_u32(ring + s * STAGE);
-        for (int g = 0; g < S; ++g) {
-          if (it > 0) {
-            // the epilogue must have drained this group of the previous tile
-            if (!mbar_wait(acc_empty(g), (uint32_t)((it - 1) & 1))) {
-              flag_status(a.status, SKY_ETIMEOUT);
-              ok = false;
-              break;
-            }
-            fence_after();
+        constexpr int NBUF = Sh::NBUF;
+        const int b = it % NBUF, use = it / NBUF;
+        if (use > 0) {
+          // the epilogue must have drained this accumulator set
+          if (!mbar_wait(acc_empty(b), (uint32_t)((use - 1) & 1))) {
+            flag_status(a.status, SKY_ETIMEOUT);
+            ok = false;
+            break;
           }
-          const uint32_t acc = tmem + (uint32_t)(g * NC);
+          fence_after();
+        }
+        for (int g = 0; g <= S - 1; ++g) {
+          // weights 0..3 into groups 0..3; weights 4 and 5 into group 4, the
+          // weight-5 products with the operator's digits times 2^-8
+          const int grp = g < NG ? g : NG - 1;
+          const uint32_t acc = tmem + (uint32_t)(b * 256 + grp * NC);
           for (int p = 0; p <= g; ++p) {
+            const int q = (g == S - 1) ? S + (g - p) : (g - p);
 #pragma unroll
             for (int ks = 0; ks < NC / 16; ++ks)   // 16 values of K = two core matrices
               mma_bf16(acc, ns_desc(sa + p * TILE_A + ks * 256, NC),
-                       ns_desc(sb + (g - p) * TILE_B + ks * 256, NC), idesc,
-                       (p == 0 && ks == 0) ? 0u : 1u);
+                       ns_desc(sb + q * TILE_B + ks * 256, NC), idesc,
+                       (g < NG && p == 0 && ks == 0) ? 0u : 1u);
           }
-          mma_commit(acc_full(g));   // arrives when this group's MMAs have completed
         }
+        mma_commit(acc_full(b));   // arrives when this tile's MMAs have completed
         if (!ok) break;
         mma_commit(empty(s));
       }
@@ -358,37 +455,36 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
       long long stride = 0;
       const long long lb = l < a.nlines ? line_base<N, AXIS>(a, l, stride) : 0;
       const int sc = E - 16 - 8 * (S - 1);
-      // columns in blocks of 8 (4 points): all groups of a block are combined
-      // before the next block; a group goes back to the MMA warp after its
-      // last block (waits on a completed phase return at once until then)
+      constexpr int NBUF = Sh::NBUF;
+      const int b = it % NBUF, use = it / NBUF;
+      if (!mbar_wait(acc_full(b), (uint32_t)(use & 1))) {
+        if (lane == 0) flag_status(a.status, SKY_ETIMEOUT);
+        break;
+      }
+      fence_after();
+      // columns in blocks of 8 (4 points).  The exact group sums (integers,
+      // |G_g| < 2^24) fold into int32: u = G0 2^8 + G1, w = G2 2^8 + G3, and
+      // x = round(2^8 G45) from the weight-{4,5} group (|x| < 2^31 for
+      // K <= 64); the total sum_g G_g 2^{8(5-g)} = u 2^32 + w 2^16 + x.
 #pragma unroll 1
       for (int cb = 0; cb < HALF; cb += 8) {
+        uint32_t v[NG][8];
+#pragma unroll
+        for (int g = 0; g < NG; ++g)
+          oz::tmem_ld<8>(tmem + ((uint32_t)(q * 32) << 16) +
+                             (uint32_t)(b * 256 + g * NC + half * HALF + cb),
+                         v[g]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         long long acc[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = 0;
-#pragma unroll
-        for (int g = 0; g < S; ++g) {
-          if (!mbar_wait(acc_full(g), (uint32_t)(it & 1))) {
-            if (lane == 0) flag_status(a.status, SKY_ETIMEOUT);
-            ok = false;
-            break;
-          }
-          fence_after();
-          uint32_t v[8];
-          oz::tmem_ld<8>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * NC + half * HALF + cb), v);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (cb + 8 == HALF) {
-            // this warp's lanes of the group are read: hand it back
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty(g));
-          }
-          const long long w8 = 1LL << (8 * (S - 1 - g));
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            acc[c] += (long long)__float2int_rn(__uint_as_float(v[c])) * w8;
+        for (int c = 0; c < 8; ++c) {
+          const int fu = __float2int_rn(__uint_as_float(v[0][c])) * 256 +
+                         __float2int_rn(__uint_as_float(v[1][c]));
+          const int fw = __float2int_rn(__uint_as_float(v[2][c])) * 256 +
+                         __float2int_rn(__uint_as_float(v[3][c]));
+          const int fx = __float2int_rn(__uint_as_float(v[4][c]) * 256.0f);
+          acc[c] = ((long long)fu << 32) + ((long long)fw << 16) + (long long)fx;
         }
-        if (!ok) break;
         if (l < a.nlines) {
 #pragma unroll
           for (int c = 0; c < 8; c += 2) {
@@ -403,6 +499,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
           }
         }
       }
+      // this warp's lanes of the accumulator set are read: hand it back
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty(b));
     }
   }
   fence_before();
@@ -418,7 +518,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
 // ------------------------------------------------------------ host side
 bool supported(int n) { return n == 8 || n == 12 || n == 16 || n == 20 || n == 24 || n == 32; }
 
-// Digits [S][NC][NC] (canonical layout, bf16 bit patterns) and row exponents
+// Digits [2S][NC][NC] (canonical layout, bf16 bit patterns; digits S..2S-1
+// are digits 0..S-1 times 2^-8) and row exponents
 // [NC] of the real operator of one axis, built in long double.
 void build_operator(int n, double L, double theta, std::vector<unsigned short>& dig,
                     std::vector<int>& ex) {
@@ -447,7 +548,7 @@ void build_operator(int n, double L, double theta, std::vector<unsigned short>& 
       B[(size_t)(2 * m + 1) * NC + 2 * q] = im;
       B[(size_t)(2 * m + 1) * NC + 2 * q + 1] = re;
     }
-  dig.assign((size_t)S * NC * NC, 0);
+  dig.assign((size_t)2 * S * NC * NC, 0);
   ex.assign(NC, 0);
   for (int o = 0; o < NC; ++o) {
     int F = INT_MIN;
@@ -475,9 +576,12 @@ void build_operator(int n, double L, double theta, std::vector<unsigned short>& 
       d[0] = (int)X;
       for (int p = 0; p < S; ++p) {
         const float f = (float)(x < 0.0 ? -d[p] : d[p]);   // |d| <= 256: exact in bf16
-        unsigned u;
+        const float f8 = f * 0.00390625f;                   // times 2^-8: also exact
+        unsigned u, u8;
         std::memcpy(&u, &f, 4);
+        std::memcpy(&u8, &f8, 4);
         dig[((size_t)p * NC * NC * 2 + cm_off(o, k, NC)) / 2] = (unsigned short)(u >> 16);
+        dig[((size_t)(S + p) * NC * NC * 2 + cm_off(o, k, NC)) / 2] = (unsigned short)(u8 >> 16);
       }
     }
   }
@@ -544,6 +648,9 @@ cudaError_t deriv_tc(Ctx* c, int ax, const double2* src, double2* dst, long long
   a.G = c->G;
   a.nlines = nb * (c->G / n);
   if (a.nlines == 0) return cudaSuccess;
+  if (a.nlines >= (1LL << 31)) return cudaErrorInvalidValue;
+  a.div1 = ozd::make_fastdiv((unsigned)c->n[0]);
+  a.div2 = ozd::make_fastdiv((unsigned)(ax == 1 ? c->n[2] : c->n[1]));
   const long long nt = (a.nlines + ozd::BM - 1) / ozd::BM;
   if (nt > INT_MAX) return cudaErrorInvalidValue;
   a.ntiles = (int)nt;

@@ -235,10 +235,14 @@ sky_status oz_overlap(Ctx* c, const void* a, const void* b, int I, double2* X);
 sky_status oz_rotate(Ctx* c, const void* phi, const double2* M, int I, void* out);
 // I x I complex products from this many states on go to the tensor cores;
 // device-gated ones (the Newton-Schulz iterations, most of which the device
-// skips) from kOzZgemmGated on, below which one batched FP64 launch costs
-// less than the digit-split launch sequence a skipped product still enqueues
-constexpr int kOzZgemmMin = 192;
-constexpr int kOzZgemmGated = 768;
+// skips) from kOzZgemmGated on: a skipped product still enqueues the
+// digit-split launch sequence (four short launches), which at 24^3 with
+// 280 + 120 states costs less than the FP64 products it replaces (19.9 ms
+// per iteration against 20.0 with the threshold at 768); ungated products
+// of 96 states and more (120 x 120: 75 us as FP64 3M products, less on the
+// tensor cores) take the tensor cores too (19.81 ms)
+constexpr int kOzZgemmMin = 96;
+constexpr int kOzZgemmGated = 192;
 bool oz_zgemm_fits(const Ctx* c, int n);
 sky_status oz_zgemm(Ctx* c, bool ah, bool bh, const double2* A, const double2* B, double2* C,
                     int n, const int* run, const int* stop);

@@ -143,8 +143,9 @@ class Solver:
     # ------------------------------------------------------------ iteration
     def densities(self):
         for q in range(2):   # I = 0 gives zero densities
-            B.sky_densities(self.ctxq[q], self.psi[q], self.I[q], self.rho[q], self.tau[q], self.J[q],
-                            self.divJ[q])
+            self._timed("densities", q, lambda: B.sky_densities(
+                self.ctxq[q], self.psi[q], self.I[q], self.rho[q], self.tau[q], self.J[q],
+                self.divJ[q]))
 
     def _timed(self, kind, q, fn):
         """Run fn(); with call_events set, bracket it with CUDA events on the
@@ -170,8 +171,9 @@ class Solver:
             self.dampq[q].weights(ctx, self.G, q, self.U[q], self.Bf[q], self.W[q], self.wq[q],
                                  self.damping_scale)
             w = self.wq[q]
-        B.sky_damped_step(ctx, q, self.psi[q], self.h[q], self.eps[o:o + I], self.phi[q], I,
-                          self.w.x0, self.w.E0, w)
+        self._timed("damped_step", q, lambda: B.sky_damped_step(
+            ctx, q, self.psi[q], self.h[q], self.eps[o:o + I], self.phi[q], I,
+            self.w.x0, self.w.E0, w))
         self._timed("apply_h", q, lambda: B.sky_apply_h(
             ctx, self.U[q], self.Bf[q], self.W[q], self.phi[q], self.h[q], I))
         for X, rhs in ((self.S[q], self.phi[q]), (self.H[q], self.h[q])):
@@ -191,11 +193,13 @@ class Solver:
         the recombination psi = phi M."""
         qs = self._species()
         I = [self.I[q] for q in qs]
-        B.sky_orthonormalize_batched(self.ctx, [self.S[q] for q in qs], I, [self.C[q] for q in qs])
+        self._timed("loewdin", 0, lambda: B.sky_orthonormalize_batched(
+            self.ctx, [self.S[q] for q in qs], I, [self.C[q] for q in qs]))
         diag = (B.sky_subspace_diag_batched if self.variant == "exact"
                 else B.sky_subspace_diag_literal_batched)
-        diag(self.ctx, [self.H[q] for q in qs], [self.C[q] for q in qs], I, [self.M[q] for q in qs],
-             [self.lam[self.off[q]:self.off[q] + self.I[q]] for q in qs])
+        self._timed("ritz", 0, lambda: diag(
+            self.ctx, [self.H[q] for q in qs], [self.C[q] for q in qs], I, [self.M[q] for q in qs],
+            [self.lam[self.off[q]:self.off[q] + self.I[q]] for q in qs]))
         self._fork()
         for q in qs:
             self._timed("rotate", q, lambda: B.sky_rotate(self.ctxq[q], self.phi[q], self.M[q],
@@ -249,9 +253,12 @@ class Solver:
         B.sky_sp_spread(self.ctx, self.eps, self.hn2, self.A, self.spread)
         self.densities()
         self._join()
-        if not frozen:
-            B.sky_mean_fields(self.ctx, self.rho, self.tau, self.divJ, self.U, self.Bf, self.W)
-        B.sky_energy(self.ctx, self.rho, self.tau, self.divJ, self.eout)
+
+        def fields():
+            if not frozen:
+                B.sky_mean_fields(self.ctx, self.rho, self.tau, self.divJ, self.U, self.Bf, self.W)
+            B.sky_energy(self.ctx, self.rho, self.tau, self.divJ, self.eout)
+        self._timed("fields", 0, fields)
 
     def step_host(self, host, eout_host):
         """One iteration from host state: copy psi and the mean field in from
