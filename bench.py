@@ -221,11 +221,13 @@ def convergence_leg(dev, maxit=4000, nets_out=None):
     w = IN.WORKLOADS[CONV_WORKLOAD]
     inp = IN.make_inputs(w)
 
-    def solve(prec, net=None, escalate=None, variant="exact", wl=None):
+    def solve(prec, net=None, escalate=None, variant="exact", wl=None, const=None, plain_after=0):
         wl = w if wl is None else wl
         s = Solver(wl, prec=prec, device=dev, variant=variant, concurrent_species=True)
         if net is not None:
             s.set_damping(net)
+        if const is not None:
+            s.set_constant_weight(const)
         i_ = inp if wl is w else IN.make_inputs(wl)
         s.load(i_["psi0"], i_.get("rho0"), i_.get("tau0"))
         torch.cuda.synchronize(dev)
@@ -241,6 +243,20 @@ def convergence_leg(dev, maxit=4000, nets_out=None):
              "E_per_A": hist[-1]["E"] / s.A}
         if net is not None:
             r["fallbacks"] = s.damping_fallbacks
+        if plain_after and conv:
+            # is the stop point a fixed point of the plain method?  continue
+            # from it with the plain step and record the largest |dE/A|
+            s.set_damping(None)
+            s.set_constant_weight(None)
+            E0_ = hist[-1]["E"]
+            d = 0.0
+            for _ in range(plain_after):
+                s.step()
+                E1_ = s.energy()[0]
+                d = max(d, abs(E1_ - E0_) / s.A)
+                E0_ = E1_
+            r["plain_continuation"] = {"iterations": plain_after, "max_dE_per_A": d,
+                                       "E_per_A_end": E0_ / s.A}
         s.close()
         return r
 
@@ -276,9 +292,13 @@ def convergence_leg(dev, maxit=4000, nets_out=None):
     train_s = time.perf_counter() - t
     s.close()
     out["learned_train_seconds"] = round(train_s, 3)
-    out["learned_fp64"] = solve(B.SKY_F64, net)
-    out["learned_fp32"] = solve(B.SKY_F32, net)
-    out["learned_bf16x3_to_fp32"] = solve(B.SKY_F32_BF16X3, net, escalate=(2e-5, B.SKY_F32))
+    out["learned_fp64"] = solve(B.SKY_F64, net, plain_after=CONV_PLAIN_AFTER)
+    out["learned_fp32"] = solve(B.SKY_F32, net, plain_after=CONV_PLAIN_AFTER)
+    out["learned_bf16x3_to_fp32"] = solve(B.SKY_F32_BF16X3, net, escalate=(2e-5, B.SKY_F32),
+                                          plain_after=CONV_PLAIN_AFTER)
+    # the uniform step sizes a per-voxel weight has to beat (FP64 form)
+    for c in CONV_CONST_WEIGHTS:
+        out[f"const_w{c:g}_fp64"] = solve(B.SKY_F64, const=c, plain_after=CONV_PLAIN_AFTER)
     # the same network trained on trajectories of the 16^3 (FP64), 24^3 (FP64)
     # and 32^3 (split-BF16) workloads together
     t = time.perf_counter()
@@ -297,13 +317,14 @@ def convergence_leg(dev, maxit=4000, nets_out=None):
     for s in keep:
         s.close()
     out["learned_configs123_train_seconds"] = round(time.perf_counter() - t, 3)
-    out["learned_configs123_fp32"] = solve(B.SKY_F32, net3)
+    out["learned_configs123_fp32"] = solve(B.SKY_F32, net3, plain_after=CONV_PLAIN_AFTER)
     if nets_out is not None:
         nets_out["net_configs123"] = net3
     out["batched"] = batched_convergence(dev, net, maxit)
     base = out["fp64"]["seconds"]
     forms = ("fp64_paper_literal", "fp32", "bf16x3", "bf16x3_to_fp32", "learned_fp64", "learned_fp32",
-             "learned_bf16x3_to_fp32", "learned_configs123_fp32")
+             "learned_bf16x3_to_fp32", "learned_configs123_fp32") + tuple(
+                 f"const_w{c:g}_fp64" for c in CONV_CONST_WEIGHTS)
     # a form reaches the fixed point when its stop point is as close to it as
     # the plain FP64 method's own stop point, within 1e-4 MeV per nucleon
     gap = abs(out["fp64"]["E_per_A"] - E_star)
@@ -316,10 +337,18 @@ def convergence_leg(dev, maxit=4000, nets_out=None):
                                      abs(t_lit["E_per_A"] - t_ex["E_per_A"]) < 1e-4)
     out["speedup_vs_fp64"] = {k: (round(base / out[k]["seconds"], 3) if out[k]["seconds"] else None)
                               for k in forms}
+    consts = [k for k in forms if k.startswith("const_w") and out[k]["converged"]]
+    if consts:
+        best = min(consts, key=lambda k: out[k]["seconds"])
+        out["best_constant_weight"] = {"form": best, "seconds": out[best]["seconds"],
+                                       "iterations": out[best]["iterations"],
+                                       "same_fixed_point": out[best]["same_fixed_point"]}
     return out
 
 
 CONV_BOXES = 8
+CONV_CONST_WEIGHTS = (1.25, 1.5, 1.75, 2.0)
+CONV_PLAIN_AFTER = 20
 
 
 def batched_convergence(dev, net, maxit):

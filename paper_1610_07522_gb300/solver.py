@@ -86,6 +86,7 @@ class Solver:
         self.damping_on = False
         self.damping_fallbacks = 0
         self.wq = None
+        self.const_w = None          # [2, G] constant damping weight, or None
 
     def set_damping(self, net, rise_tol=1e-5, min_scale=1.0 / 16.0):
         """Use the learned per-voxel weight in the damped step,
@@ -108,6 +109,14 @@ class Solver:
             self.dampq[1].workspace(self.G)
         if net is not None:
             net.workspace(self.G)
+
+    def set_constant_weight(self, c):
+        """Scale the damped update of every voxel by the constant ``c``
+        (phi = psi - c (psi - phi_plain); c = 1 is the plain step, None turns it
+        off): the uniform step size a learned per-voxel weight has to beat.
+        Ignored while a learned weight is on."""
+        self.const_w = None if c is None else torch.full((2, self.G), float(c), dtype=torch.float32,
+                                                         device=self.device)
 
     # ------------------------------------------------------------ set-up
     def _species(self):
@@ -171,6 +180,8 @@ class Solver:
             self.dampq[q].weights(ctx, self.G, q, self.U[q], self.Bf[q], self.W[q], self.wq[q],
                                  self.damping_scale)
             w = self.wq[q]
+        elif self.const_w is not None:
+            w = self.const_w[q]
         self._timed("damped_step", q, lambda: B.sky_damped_step(
             ctx, q, self.psi[q], self.h[q], self.eps[o:o + I], self.phi[q], I,
             self.w.x0, self.w.E0, w))

@@ -308,6 +308,22 @@ def test_iterations_16cubed_16n16p():
     _compare_runs(_gpu_run(w, inp, 12), _oracle_run(w, inp, 12))
 
 
+def test_iterations_16cubed_16n16p_whole_run():
+    """The 16^3, 16 n + 16 p workload for its whole iteration budget (300)
+    against the oracle, iteration by iteration.  The two trajectories do not
+    part: measured over 800 iterations on a GB300, the total energies agree to
+    8.5e-13 relative and the Ritz values to 6e-11 MeV at worst (1.5e-13 and
+    2.1e-12 MeV within the first 300); the bounds below leave a factor 10-50.
+    The run does not meet the 1e-6 MeV stop rule within its budget (the gas
+    keeps clustering; |dE/A| has a minimum of 3.4e-6 MeV near iteration 60),
+    so the comparison covers the whole path the method takes."""
+    w = IN.WORKLOADS["sly4_16cubed_16n16p_fp64"]
+    inp = IN.make_inputs(w)
+    gpu = _gpu_run(w, inp, w.maxit)
+    ora = _oracle_run(w, inp, w.maxit)
+    _compare_runs(gpu, ora, e_rel=1e-11, lam_abs=1e-10, rho_rel=1e-10)
+
+
 def test_iterations_twisted_coulomb_small():
     w = IN.Workload(name="t", grid=(12, 16, 8), dx=(1.0, 0.9, 1.2), N=9, Z=7, coulomb=True,
                     twist=(1.0, -0.5, 2.2), init="blobs", seed=33)
