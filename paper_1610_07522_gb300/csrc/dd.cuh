@@ -69,6 +69,16 @@ __device__ __forceinline__ ddc half(ddc a) {   // exact (barring underflow)
   return ddc{dd(a.x.hi * 0.5f, a.x.lo * 0.5f), dd(a.y.hi * 0.5f, a.y.lo * 0.5f)};
 }
 
+// a / b: the quotient of the high parts (hardware reciprocal) corrected
+// once by the exact residual a - q1 b; relative error a few 2^-46.
+__device__ __forceinline__ dd ddiv(dd a, dd b) {
+  const float y = __fdividef(1.0f, b.hi);
+  const float q1 = __fmul_rn(a.hi, y);
+  const dd r = a - dd(q1, 0.0f) * b;
+  const float q2 = __fmul_rn(r.hi, y);
+  return fast_two_sum(q1, q2);
+}
+
 // double <-> pair.  GB300's FP64 unit issues about one seventieth of the FP32
 // rate, and conversions between double and float run on it, so both
 // directions work on the bit patterns with integer operations where the

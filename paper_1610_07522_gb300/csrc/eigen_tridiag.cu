@@ -17,9 +17,10 @@
 //     block recomputes the next column and reflector itself (the same
 //     arithmetic in every block), so each step costs one barrier.  The heads
 //     of up to four problems run side by side on separate warp groups.
-//  2. k_tri_bisect: eigenvalues of T by Sturm-count multisection (sign
-//     changes of the leading minors of T - x I, no divisions), kBisLanes
-//     points per eigenvalue and round.
+//  2. k_tri_bisect: eigenvalues of T by multisection on the count of
+//     negative LDL^T pivots of T - x I, one warp (kBisLanes points) per
+//     eigenvalue and round: FP32 counts first, then double-float ones (the
+//     chip's FP64 latency makes an FP64 count ~10 times slower).
 //  3. k_tri_vectors: eigenvectors of T by inverse iteration (Gaussian
 //     elimination with partial pivoting of T - lambda I, factored once, then
 //     kInvIters solves from a counter-based random start); eigenvalues closer
@@ -33,14 +34,16 @@
 //     order.
 //
 // Eigenvalues come out ascending, eigenvectors as the columns of Z.
+#include "dd.cuh"
 #include "eig_common.cuh"
 
 namespace sky {
 
 constexpr int kTriThreads = 512;
 constexpr int kTriWarps = kTriThreads / 32;
-constexpr int kBisLanes = 16;           // bisection points per eigenvalue and round
-constexpr int kBisMaxRounds = 96;       // ample for 2 eps ||T|| at 17x per round
+constexpr int kBisLanes = 32;           // bisection points per eigenvalue and round: one warp,
+                                        // so every eigenvalue has its own warp (one wave)
+constexpr int kBisMaxRounds = 96;       // ample for 2 eps ||T|| at 33x per round
 constexpr int kInvIters = 3;            // inverse-iteration solves per vector
 constexpr int kVecThreads = 8;          // eigenvectors per block of k_tri_vectors
 constexpr double kTightRel = 1e-9;      // cluster threshold relative to ||T||
@@ -89,6 +92,8 @@ struct TriPtrs {
   double *Y, *Y2, *U0, *U1, *U2;
   double2 *P0, *P1, *C0, *C1, *tau;
   double *d, *e, *e2, *lam;
+  float *df, *e2f;               // d and e^2 rounded to float (coarse bisection rounds)
+  dd *ddd, *e2dd;                // d and e^2 as float pairs (fine bisection rounds)
 };
 
 __device__ __forceinline__ TriPtrs tri_ptrs(const TriBatch& a, int b) {
@@ -106,6 +111,8 @@ __device__ __forceinline__ TriPtrs tri_ptrs(const TriBatch& a, int b) {
   p.P0 = vecs; p.P1 = vecs + m; p.C0 = vecs + 2 * m; p.C1 = vecs + 3 * m; p.tau = vecs + 4 * m;
   double* s = reinterpret_cast<double*>(vecs + 5 * m);
   p.d = s; p.e = s + m; p.e2 = s + 2 * m; p.lam = s + 3 * m;
+  p.ddd = reinterpret_cast<dd*>(s + 4 * m); p.e2dd = p.ddd + m;        // m doubles each
+  p.df = reinterpret_cast<float*>(s + 6 * m); p.e2f = p.df + m;        // m / 2 doubles each
   return p;
 }
 
@@ -280,12 +287,18 @@ __device__ void tri_heads(const TriBatch& a, int b0, int t, double2* dsm, HeadSh
         p.d[t] = bd.y;
         p.e[t] = bd.x;
         p.e2[t] = bd.x * bd.x;
+        p.ddd[t] = dd_of(bd.y);
+        p.e2dd[t] = dd_of(bd.x) * dd_of(bd.x);
+        p.df[t] = __double2float_rn(bd.y);
+        p.e2f[t] = __double2float_rn(bd.x * bd.x);
         p.tau[t] = s_tau[b];
       }
       double2* Vt = p.V + (size_t)t * n;
       for (int i = t + 1 + ht; i < n; i += kHeadThreads) Vt[i] = vn[i];
     } else if (ht == 0) {
       p.d[t] = vn[t].x;                     // t = n - 1
+      p.ddd[t] = dd_of(vn[t].x);
+      p.df[t] = __double2float_rn(vn[t].x);
     }
   }
 }
@@ -429,84 +442,85 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_hh_tridiag(TriBatch a) {
 }
 
 // ---- stage 2: eigenvalues of T -------------------------------------------------
-// Number of eigenvalues of T below x: the sign changes of the Sturm sequence
-// p_0 = 1, p_k = (d_k - x) p_{k-1} - e_{k-1}^2 p_{k-2} (leading minors of
-// T - x I), which equals the number of negative pivots of its LDL^T
-// factorisation.  Every computed p_k is exact for T with d_k - x and e_{k-1}^2
-// perturbed by a few ulps, so the count is backward stable like the pivot
-// recurrence, and needs no division.  The pair (p_k, p_{k-1}) is rescaled by a
-// power of two (exact) whenever it leaves [2^-500, 2^500]; an exact zero p_k
-// takes the sign opposite to p_{k-1}.
-__device__ __forceinline__ int exp_of(double x) {
-  return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+// Number of eigenvalues of T below x: the number of negative pivots of the
+// LDL^T factorisation of T - x I, q_0 = d_0 - x, q_k = (d_k - x) -
+// e_{k-1}^2 / q_{k-1} (Sylvester's law of inertia); a pivot of modulus below
+// pivmin is replaced by -pivmin.  The computed count is exact for T with
+// every d_k - x and e_k^2 perturbed by a few units of the arithmetic's last
+// place (Kahan; LAPACK's dstebz), so x is located to within that perturbation
+// of ||T||.  On this chip a dependent FP64 operation takes ~67 cycles and an
+// FP64 division ~670 (measured), FP32 ones ~5, so the count runs in FP32 to
+// about 2^-16 ||T|| and then in double-float arithmetic (about 2^-46 per
+// operation) to 2^-43 ||T||, no FP64 operation in the loops.
+constexpr float kPivMin32 = 0x1p-100f;
+constexpr double kBisF32Rel = 0x1p-16;   // FP32 rounds down to this width / ||T||
+constexpr double kBisF32Pad = 0x1p-17;   // then widened by this much / ||T|| on each side
+constexpr double kBisDDRel = 0x1p-43;    // double-float rounds down to this width / ||T||
+
+__device__ __forceinline__ int sturm_count32(const float* __restrict__ d,
+                                             const float* __restrict__ e2, int n, float x) {
+  float q = __ldg(d) - x;
+  int cnt = 0;
+  for (int i = 1;; ++i) {
+    if (fabsf(q) < kPivMin32) q = -kPivMin32;
+    cnt += q < 0.0f;
+    if (i >= n) break;
+    q = (__ldg(d + i) - x) - __fdividef(__ldg(e2 + i - 1), q);
+  }
+  return cnt;
 }
-__device__ __forceinline__ int sturm_count(const double* __restrict__ d,
-                                           const double* __restrict__ e2, int n, double x) {
-  double p2 = 1.0, p1 = __ldg(d) - x;
-  if ((__double_as_longlong(p1) << 1) == 0) p1 = -0x1p-600;
-  long long b1 = __double_as_longlong(p1);
-  int cnt = (int)((unsigned long long)b1 >> 63);
-#pragma unroll 2
-  for (int i = 1; i < n; ++i) {
-    double p = fma(__ldg(d + i) - x, p1, -(__ldg(e2 + i - 1) * p2));
-    long long bp = __double_as_longlong(p);
-    if ((bp << 1) == 0) {                      // exact zero: opposite sign to p_{k-1}
-      p = b1 < 0 ? 0x1p-600 * -p1 : -0x1p-600 * p1;
-      bp = __double_as_longlong(p);
-    }
-    cnt += (int)((unsigned long long)(bp ^ b1) >> 63);
-    p2 = p1;
-    p1 = p;
-    b1 = bp;
-    const int ex = max(exp_of(p1), exp_of(p2));
-    if ((ex > 1023 + 500 && ex < 2047) || ex < 1023 - 500) {
-      const double sc = __longlong_as_double((long long)(2046 - ex) << 52);   // 2^(1023 - ex)
-      p1 *= sc;
-      p2 *= sc;
-      b1 = __double_as_longlong(p1);
-    }
+__device__ __forceinline__ int sturm_count_dd(const dd* __restrict__ d, const dd* __restrict__ e2,
+                                              int n, dd x) {
+  dd q = d[0] - x;
+  int cnt = 0;
+  for (int i = 1;; ++i) {
+    if (fabsf(q.hi) < kPivMin32) q = dd(-kPivMin32, 0.0f);
+    cnt += q.hi < 0.0f;
+    if (i >= n) break;
+    q = (d[i] - x) - ddiv(e2[i - 1], q);
   }
   return cnt;
 }
 
-// kBisLanes lanes per eigenvalue; 32-thread blocks spread the work over the SMs.
+// One warp per eigenvalue (every eigenvalue its own warp: one wave).  The
+// lanes count at L points per round, so a round narrows the bracket L + 1
+// times; the bracket invariant is count(lo) <= j < count(hi).
 __global__ void __launch_bounds__(32) k_tri_bisect(TriBatch a) {
   constexpr int L = kBisLanes;
-  const int grp = threadIdx.x / L, l = threadIdx.x % L;
-  const unsigned mask = ((1u << L) - 1u) << (grp * L);
-  const int item = blockIdx.x * (32 / L) + grp;
-  if (item >= a.off[a.np]) return;          // whole groups leave together
+  static_assert(L == 32, "one warp per eigenvalue");
+  const int l = threadIdx.x;
+  const unsigned mask = 0xffffffffu;
+  const int item = blockIdx.x;
+  if (item >= a.off[a.np]) return;
   const int b = find_prob(a.off, a.np, item);
   if (!tri_run(a, b)) return;
   const int n = a.n[b], j = item - a.off[b];
   const TriPtrs p = tri_ptrs(a, b);
   // Gershgorin interval
-  double lo = INFINITY, hi = -INFINITY;
+  double glo = INFINITY, ghi = -INFINITY;
   for (int i = l; i < n; i += L) {
     const double r = (i > 0 ? fabs(p.e[i - 1]) : 0.0) + (i < n - 1 ? fabs(p.e[i]) : 0.0);
-    lo = fmin(lo, p.d[i] - r);
-    hi = fmax(hi, p.d[i] + r);
+    glo = fmin(glo, p.d[i] - r);
+    ghi = fmax(ghi, p.d[i] + r);
   }
 #pragma unroll
   for (int o = 1; o < L; o <<= 1) {
-    lo = fmin(lo, __shfl_xor_sync(mask, lo, o, L));
-    hi = fmax(hi, __shfl_xor_sync(mask, hi, o, L));
+    glo = fmin(glo, __shfl_xor_sync(mask, glo, o));
+    ghi = fmax(ghi, __shfl_xor_sync(mask, ghi, o));
   }
-  const double nrm = fmax(fabs(lo), fabs(hi));
+  const double nrm = fmax(fmax(fabs(glo), fabs(ghi)), 1e-290);
   const double pad = 2.0 * kEps * nrm + 1e-290;
-  lo -= pad;
-  hi += pad;
-  const double tol = 2.5 * kEps * nrm;
-  for (int round = 0; round < kBisMaxRounds; ++round) {
-    if (!(hi - lo > tol)) break;
-    const double x = lo + (hi - lo) * ((double)(l + 1) / (double)(L + 1));
-    const int cnt = sturm_count(p.d, p.e2, n, x);
+  glo -= pad;
+  ghi += pad;
+  // a round: counts at L interior points (or, with ends, at L points from lo
+  // to hi inclusive); returns false when the ends do not bracket j
+  auto narrow = [&](double& lo, double& hi, int cnt, double x) {
     double nlo = lo, nhi = hi;
     bool above = false;
-#pragma unroll
+#pragma unroll 4
     for (int k = 0; k < L; ++k) {
-      const double xk = __shfl_sync(mask, x, k, L);
-      const int ck = __shfl_sync(mask, cnt, k, L);
+      const double xk = __shfl_sync(mask, x, k);
+      const int ck = __shfl_sync(mask, cnt, k);
       if (!above) {
         if (ck <= j) nlo = xk;
         else { nhi = xk; above = true; }
@@ -514,6 +528,40 @@ __global__ void __launch_bounds__(32) k_tri_bisect(TriBatch a) {
     }
     lo = nlo;
     hi = nhi;
+  };
+  // FP32 rounds
+  double lo = glo, hi = ghi;
+  {
+    float lo32 = __double2float_rd(lo), hi32 = __double2float_ru(hi);
+    const float w32 = (float)(kBisF32Rel * nrm);
+    for (int round = 0; round < 12 && hi32 - lo32 > w32; ++round) {
+      const float x = lo32 + (hi32 - lo32) * ((float)(l + 1) / (float)(L + 1));
+      const int cnt = sturm_count32(p.df, p.e2f, n, x);
+      double dlo = lo32, dhi = hi32;
+      narrow(dlo, dhi, cnt, (double)x);
+      lo32 = (float)dlo;
+      hi32 = (float)dhi;
+    }
+    lo = fmax((double)lo32 - kBisF32Pad * nrm, glo);
+    hi = fmin((double)hi32 + kBisF32Pad * nrm, ghi);
+  }
+  // double-float rounds; the first one includes both ends as a check
+  {
+    const double x = lo + (hi - lo) * ((double)l / (double)(L - 1));
+    const int cnt = sturm_count_dd(p.ddd, p.e2dd, n, dd_of(x));
+    const int c0 = __shfl_sync(mask, cnt, 0), cL = __shfl_sync(mask, cnt, L - 1);
+    if (c0 <= j && cL > j) {
+      narrow(lo, hi, cnt, x);
+    } else {
+      lo = glo;                              // the FP32 bracket missed: start over
+      hi = ghi;
+    }
+  }
+  const double tol = kBisDDRel * nrm;
+  for (int round = 0; round < kBisMaxRounds && hi - lo > tol; ++round) {
+    const double x = lo + (hi - lo) * ((double)(l + 1) / (double)(L + 1));
+    const int cnt = sturm_count_dd(p.ddd, p.e2dd, n, dd_of(x));
+    narrow(lo, hi, cnt, x);
   }
   if (l == 0) {
     const double lam = 0.5 * (lo + hi);
@@ -834,8 +882,7 @@ static sky_status tri_group(Ctx* c, int np, const int* idx, const double2* const
   e = cudaLaunchCooperativeKernel((const void*)k_hh_tridiag, dim3(G), dim3(kTriThreads), args,
                                   used * sizeof(double2), c->stream);
   if (e != cudaSuccess) return cuda_check(c, e, "householder tridiagonalisation");
-  const int per = 32 / kBisLanes;
-  k_tri_bisect<<<div_up(ntot, per), 32, 0, c->stream>>>(a);
+  k_tri_bisect<<<(unsigned)ntot, 32, 0, c->stream>>>(a);
   k_tri_vectors<<<div_up(ntot, kVecThreads), kVecThreads, 0, c->stream>>>(a);
   k_tri_window<<<(unsigned)ntot, kWinThreads, 0, c->stream>>>(a, 0);
   k_tri_window<<<(unsigned)ntot, kWinThreads, 0, c->stream>>>(a, 1);

@@ -218,7 +218,7 @@ sky_status deriv_tc_init(Ctx* c);
 cudaError_t deriv_tc(Ctx* c, int ax, const double2* src, double2* dst, long long nb);
 bool tri_vectors_global(int n);
 size_t tri_vec_elems(int m, int nb, int nsm);
-inline size_t tri_slot_doubles(int m) { return (size_t)m * m + 16 * (size_t)m; }
+inline size_t tri_slot_doubles(int m) { return (size_t)m * m + 18 * (size_t)m; }
 sky_status eigh_impl(Ctx* c, const double2* A, int I, double* w, double2* Z,
                      const int* run = nullptr);
 sky_status lowdin_impl(Ctx* c, const double2* S, int I, double2* C);
