@@ -349,6 +349,12 @@ static sky_status damped_t(Ctx* c, int q, const cx<T>* psi, const cx<T>* hpsi,
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "damping table");
     c->damp_E0[q] = E0;
   }
+  if constexpr (std::is_same<T, double>::value) {
+    if (c->line_arith == 2 && damp_tc_available(c)) {
+      e = damp_tc(c, q, psi, hpsi, eps, phi, I, x0, w);
+      return e == cudaSuccess ? SKY_OK : cuda_check(c, e, "damped step");
+    }
+  }
   const long long nb = 2LL * I;
   OpDampZFwd<T> o1{psi, hpsi, eps, phi, G};
   OpPass<T, false> o2{phi, G};

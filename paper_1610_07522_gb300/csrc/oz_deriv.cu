@@ -75,6 +75,13 @@ constexpr int NG = 5;              // TMEM groups: weights 0, 1, 2, 3 and {4, 5}
 
 __host__ __device__ constexpr int nc_of(int n) { return ((2 * n + 15) / 16) * 16; }
 
+// Operators of an axis: the derivative, the forward and the inverse DFT.
+constexpr int kOpDeriv = 0, kOpFwd = 1, kOpInv = 2;
+// Producer input: the lines of src, or the residual src - eps psi (src = h psi).
+constexpr int kInPlain = 0, kInResidual = 1;
+// Epilogue output: the product; times P[point] scale; or psi - w[point] times it.
+constexpr int kOutPlain = 0, kOutScaleP = 1, kOutUpdate = 2;
+
 template <int N>
 struct Shape {
   static constexpr int NC = nc_of(N);          // K and output columns (reals), padded
@@ -202,6 +209,12 @@ struct DerivArgs {
   long long nlines;   // < 2^31
   int ntiles;
   FastDiv div1, div2;   // by nx, then by nz (lines along y) or ny (lines along z)
+  FastDiv div0;         // by ny nz (lines along x: the array of a line)
+  const double2* psi;   // kInResidual: psi (src is h psi); kOutUpdate: psi of the update
+  const double* eps;    // kInResidual: eps per state (array b is state b / 2)
+  const double* P;      // kOutScaleP: factor per point, times scale
+  double scale;
+  const float* w;       // kOutUpdate: weight per point, or null for 1
   int* status;
 };
 
@@ -228,7 +241,15 @@ __device__ __forceinline__ long long line_base(const DerivArgs& a, long long l, 
   }
 }
 
+// Index b of the array that line l belongs to.
 template <int N, int AXIS>
+__device__ __forceinline__ unsigned line_array(const DerivArgs& a, long long l) {
+  const unsigned lu = (unsigned)l;
+  if constexpr (AXIS == 0) return fdiv(lu, a.div0);
+  else return fdiv(fdiv(lu, a.div1), a.div2);
+}
+
+template <int N, int AXIS, int IN, int OUT>
 __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
   using Sh = Shape<N>;
   constexpr int NC = Sh::NC, STAGES = Sh::STAGES, HALF = Sh::HALF;
@@ -314,13 +335,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
                      valid);
       cp_async_commit();
     };
-    if constexpr (Sh::PREFETCH)
+    constexpr bool PF = Sh::PREFETCH && IN == kInPlain;
+    if constexpr (PF)
       if (blockIdx.x < a.ntiles) prefetch(blockIdx.x, true);
     int it = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
       const int s = it % STAGES, u = it / STAGES, slot = it & 1;
       double2 v[H0];
-      if constexpr (Sh::PREFETCH) {
+      if constexpr (PF) {
         cp_async_wait_all();
 #pragma unroll
         for (int j = 0; j < H0; ++j)
@@ -335,11 +357,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
         for (int j = 0; j < H0; ++j)
           v[j] = (valid && j < np) ? a.src[lb + (long long)(p0 + j) * stride]
                                    : make_double2(0.0, 0.0);
+        if constexpr (IN == kInResidual) {    // src - eps psi (src = h psi)
+          const double e = valid ? a.eps[line_array<N, AXIS>(a, l) >> 1] : 0.0;
+#pragma unroll
+          for (int j = 0; j < H0; ++j)
+            if (valid && j < np) {
+              const double2 ps = a.psi[lb + (long long)(p0 + j) * stride];
+              v[j] = make_double2(fma(-e, ps.x, v[j].x), fma(-e, ps.y, v[j].y));
+            }
+        }
       }
       int E = INT_MIN;
 #pragma unroll
       for (int j = 0; j < H0; ++j) E = max(E, max(exp_of(v[j].x), exp_of(v[j].y)));
-      if constexpr (Sh::PREFETCH) {
+      if constexpr (PF) {
         // the next copy overwrites the slots just read: it is issued after E,
         // which depends on every value read
         if (t + (int)gridDim.x < a.ntiles) prefetch(t + gridDim.x, E != INT_MAX);
@@ -387,7 +418,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
       mbar_arrive(full(s));
       mbar_arrive(ea_full(slot));
     }
-    if constexpr (Sh::PREFETCH) cp_async_wait_all();   // no copy outlives the launch
+    if constexpr (PF) cp_async_wait_all();   // no copy outlives the launch
   } else if (warp == kProd) {
     // ---------------------------------------------------------------- MMA issue
     if (lane == 0) {
@@ -454,6 +485,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
       const long long l = (long long)t * BM + row;
       long long stride = 0;
       const long long lb = l < a.nlines ? line_base<N, AXIS>(a, l, stride) : 0;
+      long long bG = 0;
+      if constexpr (OUT != kOutPlain) bG = l < a.nlines ? (long long)line_array<N, AXIS>(a, l) * a.G : 0;
       const int sc = E - 16 - 8 * (S - 1);
       constexpr int NBUF = Sh::NBUF;
       const int b = it % NBUF, use = it / NBUF;
@@ -494,7 +527,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
               double2 res;
               res.x = scaled_double(acc[c], sc + s_eb[o]);
               res.y = scaled_double(acc[c + 1], sc + s_eb[o + 1]);
-              a.dst[lb + m * stride] = res;
+              const long long at = lb + m * stride;
+              if constexpr (OUT == kOutScaleP) {
+                const double f = a.P[at - bG] * a.scale;
+                res = make_double2(res.x * f, res.y * f);
+              } else if constexpr (OUT == kOutUpdate) {
+                const double2 ps = a.psi[at];
+                if (a.w) {
+                  const double f = (double)a.w[at - bG];
+                  res = make_double2(fma(-f, res.x, ps.x), fma(-f, res.y, ps.y));
+                } else {
+                  res = make_double2(ps.x - res.x, ps.y - res.y);
+                }
+              }
+              a.dst[at] = res;
             }
           }
         }
@@ -519,30 +565,46 @@ __global__ void __launch_bounds__(THREADS, 1) k_oz_deriv(const DerivArgs a) {
 bool supported(int n) { return n == 8 || n == 12 || n == 16 || n == 20 || n == 24 || n == 32; }
 
 // Digits [2S][NC][NC] (canonical layout, bf16 bit patterns; digits S..2S-1
-// are digits 0..S-1 times 2^-8) and row exponents
-// [NC] of the real operator of one axis, built in long double.
-void build_operator(int n, double L, double theta, std::vector<unsigned short>& dig,
+// are digits 0..S-1 times 2^-8) and row exponents [NC] of the real operator
+// of one axis, built in long double.  kind: kOpDeriv the derivative, the
+// circulant D[m][q] = d[(m - q) mod n], d[r] = (i/n) sum_a kappa_a
+// e^{2 pi i a r / n}; kOpFwd / kOpInv the unnormalised DFT, D[m][q] =
+// e^{-+2 pi i (m q mod n) / n}.
+void build_operator(int n, double L, double theta, int kind, std::vector<unsigned short>& dig,
                     std::vector<int>& ex) {
   const int NC = nc_of(n);
   const long double two_pi = 6.283185307179586476925286766559005768L;
   std::vector<long double> dre(n), dim(n);
-  for (int r = 0; r < n; ++r) {
-    long double sr = 0.0L, si = 0.0L;
-    for (int a = 0; a < n; ++a) {
-      const int mm = a < (n + 1) / 2 ? a : a - n;
-      const long double kap = (two_pi * mm + (long double)theta) / (long double)L;
-      const long double ang = two_pi * (long double)(((long long)a * r) % n) / (long double)n;
-      sr -= kap * sinl(ang);   // Re of i kappa e^{i ang}
-      si += kap * cosl(ang);   // Im
+  if (kind == kOpDeriv) {
+    for (int r = 0; r < n; ++r) {
+      long double sr = 0.0L, si = 0.0L;
+      for (int a = 0; a < n; ++a) {
+        const int mm = a < (n + 1) / 2 ? a : a - n;
+        const long double kap = (two_pi * mm + (long double)theta) / (long double)L;
+        const long double ang = two_pi * (long double)(((long long)a * r) % n) / (long double)n;
+        sr -= kap * sinl(ang);   // Re of i kappa e^{i ang}
+        si += kap * cosl(ang);   // Im
+      }
+      dre[r] = sr / n;
+      dim[r] = si / n;
     }
-    dre[r] = sr / n;
-    dim[r] = si / n;
   }
+  auto entry = [&](int m, int q, double& re, double& im) {
+    if (kind == kOpDeriv) {
+      const int r = ((m - q) % n + n) % n;
+      re = (double)dre[r];
+      im = (double)dim[r];
+    } else {
+      const long double ang = two_pi * (long double)(((long long)m * q) % n) / (long double)n;
+      re = (double)cosl(ang);
+      im = (double)(kind == kOpFwd ? -sinl(ang) : sinl(ang));
+    }
+  };
   std::vector<double> B((size_t)NC * NC, 0.0);
   for (int m = 0; m < n; ++m)
     for (int q = 0; q < n; ++q) {
-      const int r = ((m - q) % n + n) % n;
-      const double re = (double)dre[r], im = (double)dim[r];
+      double re, im;
+      entry(m, q, re, im);
       B[(size_t)(2 * m) * NC + 2 * q] = re;
       B[(size_t)(2 * m) * NC + 2 * q + 1] = -im;
       B[(size_t)(2 * m + 1) * NC + 2 * q] = im;
@@ -587,7 +649,7 @@ void build_operator(int n, double L, double theta, std::vector<unsigned short>& 
   }
 }
 
-template <int N, int AXIS>
+template <int N, int AXIS, int IN, int OUT>
 cudaError_t launch(const DerivArgs& a, const Ctx* c) {
   using Sh = Shape<N>;
   static bool set[64] = {false};
@@ -596,72 +658,99 @@ cudaError_t launch(const DerivArgs& a, const Ctx* c) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   if (!set[dev]) {
-    e = cudaFuncSetAttribute(k_oz_deriv<N, AXIS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Sh::SMEM);
+    e = cudaFuncSetAttribute(k_oz_deriv<N, AXIS, IN, OUT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
     if (e != cudaSuccess) return e;
     set[dev] = true;
   }
   const int grid = a.ntiles < c->num_sms ? a.ntiles : c->num_sms;
-  k_oz_deriv<N, AXIS><<<grid, THREADS, Sh::SMEM, c->stream>>>(a);
+  k_oz_deriv<N, AXIS, IN, OUT><<<grid, THREADS, Sh::SMEM, c->stream>>>(a);
   note_launch();
   return cudaGetLastError();
 }
 
 }  // namespace ozd
 
+static sky_status upload_operator(Ctx* c, int n, double L, double theta, int kind, void** dig_out,
+                                  int** ex_out) {
+  std::vector<unsigned short> dig;
+  std::vector<int> ex;
+  ozd::build_operator(n, L, theta, kind, dig, ex);
+  cudaError_t e = cudaMalloc(dig_out, dig.size() * sizeof(unsigned short));
+  if (e == cudaSuccess) e = cudaMalloc(ex_out, ex.size() * sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(*dig_out, dig.data(), dig.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(*ex_out, ex.data(), ex.size() * sizeof(int), cudaMemcpyHostToDevice);
+  return cuda_check(c, e, "operator upload");
+}
+
 sky_status deriv_tc_init(Ctx* c) {
   for (int j = 0; j < 3; ++j) {
     c->d_dop[j] = nullptr;
     c->d_dope[j] = nullptr;
+    for (int k = 0; k < 2; ++k) {
+      c->d_dft[j][k] = nullptr;
+      c->d_dfte[j][k] = nullptr;
+    }
   }
   if (c->prec != SKY_F64) return SKY_OK;
   for (int j = 0; j < 3; ++j) {
     if (!ozd::supported(c->n[j])) continue;
-    std::vector<unsigned short> dig;
-    std::vector<int> ex;
-    ozd::build_operator(c->n[j], c->L[j], c->theta[j], dig, ex);
-    cudaError_t e = cudaMalloc(&c->d_dop[j], dig.size() * sizeof(unsigned short));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_dope[j], ex.size() * sizeof(int));
-    if (e == cudaSuccess)
-      e = cudaMemcpy(c->d_dop[j], dig.data(), dig.size() * sizeof(unsigned short),
-                     cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(c->d_dope[j], ex.data(), ex.size() * sizeof(int), cudaMemcpyHostToDevice);
-    const sky_status s = cuda_check(c, e, "derivative operator upload");
+    sky_status s = upload_operator(c, c->n[j], c->L[j], c->theta[j], ozd::kOpDeriv, &c->d_dop[j],
+                                   &c->d_dope[j]);
+    for (int k = 0; k < 2 && s == SKY_OK; ++k)
+      s = upload_operator(c, c->n[j], c->L[j], c->theta[j], k == 0 ? ozd::kOpFwd : ozd::kOpInv,
+                          &c->d_dft[j][k], &c->d_dfte[j][k]);
     if (s != SKY_OK) return s;
   }
   return SKY_OK;
 }
 
-// dst = d_ax src over nb arrays of G complex doubles (dst may equal src).
-cudaError_t deriv_tc(Ctx* c, int ax, const double2* src, double2* dst, long long nb) {
-  const int n = c->n[ax];
-  if (!c->d_dop[ax]) return cudaErrorInvalidValue;
-  ozd::DerivArgs a;
+namespace {
+
+ozd::DerivArgs op_args(const Ctx* c, int ax, const double2* src, double2* dst, long long nb,
+                       const void* op, const int* ope) {
+  ozd::DerivArgs a{};
   a.src = src;
   a.dst = dst;
-  a.op = (const uint4*)c->d_dop[ax];
-  a.ope = c->d_dope[ax];
+  a.op = (const uint4*)op;
+  a.ope = ope;
   a.nx = c->n[0];
   a.ny = c->n[1];
   a.nz = c->n[2];
   a.G = c->G;
-  a.nlines = nb * (c->G / n);
-  if (a.nlines == 0) return cudaSuccess;
-  if (a.nlines >= (1LL << 31)) return cudaErrorInvalidValue;
+  a.nlines = nb * (c->G / c->n[ax]);
   a.div1 = ozd::make_fastdiv((unsigned)c->n[0]);
   a.div2 = ozd::make_fastdiv((unsigned)(ax == 1 ? c->n[2] : c->n[1]));
+  a.div0 = ozd::make_fastdiv((unsigned)(c->n[1] * c->n[2]));
   const long long nt = (a.nlines + ozd::BM - 1) / ozd::BM;
-  if (nt > INT_MAX) return cudaErrorInvalidValue;
-  a.ntiles = (int)nt;
+  a.ntiles = nt > INT_MAX ? INT_MAX : (int)nt;
   a.status = c->d_status;
+  return a;
+}
+
+// One operator pass along ax with the given modes (only the combinations
+// the library uses are instantiated).
+template <int IN, int OUT>
+cudaError_t op_pass(const Ctx* c, int ax, const ozd::DerivArgs& a) {
+  if (a.nlines == 0) return cudaSuccess;
+  if (a.nlines >= (1LL << 31)) return cudaErrorInvalidValue;
   auto go = [&](auto NC) -> cudaError_t {
     constexpr int N = decltype(NC)::value;
-    if (ax == 0) return ozd::launch<N, 0>(a, c);
-    if (ax == 1) return ozd::launch<N, 1>(a, c);
-    return ozd::launch<N, 2>(a, c);
+    if constexpr (IN == ozd::kInResidual) {
+      return ax == 2 ? ozd::launch<N, 2, IN, OUT>(a, c) : cudaErrorInvalidValue;
+    } else if constexpr (OUT == ozd::kOutScaleP) {
+      return ax == 0 ? ozd::launch<N, 0, IN, OUT>(a, c) : cudaErrorInvalidValue;
+    } else if constexpr (OUT == ozd::kOutUpdate) {
+      return ax == 2 ? ozd::launch<N, 2, IN, OUT>(a, c) : cudaErrorInvalidValue;
+    } else {
+      if (ax == 0) return ozd::launch<N, 0, IN, OUT>(a, c);
+      if (ax == 1) return ozd::launch<N, 1, IN, OUT>(a, c);
+      return ozd::launch<N, 2, IN, OUT>(a, c);
+    }
   };
-  switch (n) {
+  switch (c->n[ax]) {
     case 8: return go(std::integral_constant<int, 8>{});
     case 12: return go(std::integral_constant<int, 12>{});
     case 16: return go(std::integral_constant<int, 16>{});
@@ -670,6 +759,53 @@ cudaError_t deriv_tc(Ctx* c, int ax, const double2* src, double2* dst, long long
     case 32: return go(std::integral_constant<int, 32>{});
     default: return cudaErrorInvalidValue;
   }
+}
+
+}  // namespace
+
+// dst = d_ax src over nb arrays of G complex doubles (dst may equal src).
+cudaError_t deriv_tc(Ctx* c, int ax, const double2* src, double2* dst, long long nb) {
+  if (!c->d_dop[ax]) return cudaErrorInvalidValue;
+  return op_pass<ozd::kInPlain, ozd::kOutPlain>(
+      c, ax, op_args(c, ax, src, dst, nb, c->d_dop[ax], c->d_dope[ax]));
+}
+
+bool damp_tc_available(const Ctx* c) {
+  for (int j = 0; j < 3; ++j)
+    if (!c->d_dft[j][0] || !c->d_dft[j][1]) return false;
+  return true;
+}
+
+// The damped step's 3D transform pair as six operator passes over the 2I
+// arrays (the damping table P must be current): phi = F_z F_y F_x of
+// (h psi - eps psi), times P x0 / G in the last forward pass, the inverse
+// passes, phi = psi - w (result) in the last.
+cudaError_t damp_tc(Ctx* c, int q, const double2* psi, const double2* hpsi, const double* eps,
+                    double2* phi, int I, double x0, const float* w) {
+  const long long nb = 2LL * I;
+  auto args = [&](int ax, int k, const double2* src) {
+    return op_args(c, ax, src, phi, nb, c->d_dft[ax][k], c->d_dfte[ax][k]);
+  };
+  ozd::DerivArgs a = args(2, 0, hpsi);
+  a.psi = psi;
+  a.eps = eps;
+  cudaError_t e = op_pass<ozd::kInResidual, ozd::kOutPlain>(c, 2, a);
+  if (e == cudaSuccess) e = op_pass<ozd::kInPlain, ozd::kOutPlain>(c, 1, args(1, 0, phi));
+  if (e == cudaSuccess) {
+    ozd::DerivArgs b = args(0, 0, phi);
+    b.P = c->d_damp[q];
+    b.scale = x0 / (double)c->G;
+    e = op_pass<ozd::kInPlain, ozd::kOutScaleP>(c, 0, b);
+  }
+  if (e == cudaSuccess) e = op_pass<ozd::kInPlain, ozd::kOutPlain>(c, 0, args(0, 1, phi));
+  if (e == cudaSuccess) e = op_pass<ozd::kInPlain, ozd::kOutPlain>(c, 1, args(1, 1, phi));
+  if (e == cudaSuccess) {
+    ozd::DerivArgs d = args(2, 1, phi);
+    d.psi = psi;
+    d.w = w;
+    e = op_pass<ozd::kInPlain, ozd::kOutUpdate>(c, 2, d);
+  }
+  return e;
 }
 
 }  // namespace sky

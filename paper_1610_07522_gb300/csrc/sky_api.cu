@@ -90,7 +90,10 @@ static void free_all(Ctx* c) {
                   c->d_tcB[1], c->d_tcB[2], c->d_tcRotA[0], c->d_tcRotA[1], c->d_tcRotA[2],
                   c->d_tcPart, c->d_netpart, c->d_trid, c->d_ozA, c->d_ozB, c->d_ozE,
                   c->d_ozP, c->d_trivec, c->d_dop[0], c->d_dop[1], c->d_dop[2],
-                  c->d_dope[0], c->d_dope[1], c->d_dope[2]};
+                  c->d_dope[0], c->d_dope[1], c->d_dope[2],
+                  c->d_dft[0][0], c->d_dft[0][1], c->d_dft[1][0], c->d_dft[1][1],
+                  c->d_dft[2][0], c->d_dft[2][1], c->d_dfte[0][0], c->d_dfte[0][1],
+                  c->d_dfte[1][0], c->d_dfte[1][1], c->d_dfte[2][0], c->d_dfte[2][1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }

@@ -83,6 +83,8 @@ struct Ctx {
                                     // 2 digit-split operator on the tensor cores
   void* d_dop[3];                   // tensor-core derivative operators: digits, smem layout
   int* d_dope[3];                   // their row exponents
+  void* d_dft[3][2];                // forward / inverse DFT operators of each axis (same form)
+  int* d_dfte[3][2];
   double* d_damp[2];                // 1 / (E0 + hb2m_q |k + theta/L|^2), [G]
   double damp_E0[2];                // E0 the tables were built for (NaN = none)
   double* d_coul;                   // 4 pi e^2 / |k|^2 (0 at k = 0), [G]
@@ -216,6 +218,9 @@ sky_status tri_init(Ctx* c);
 // lengths 8, 12, 16, 20, 24, 32; dst = d_ax src over nb arrays (dst may be src).
 sky_status deriv_tc_init(Ctx* c);
 cudaError_t deriv_tc(Ctx* c, int ax, const double2* src, double2* dst, long long nb);
+bool damp_tc_available(const Ctx* c);
+cudaError_t damp_tc(Ctx* c, int q, const double2* psi, const double2* hpsi, const double* eps,
+                    double2* phi, int I, double x0, const float* w);
 bool tri_vectors_global(int n);
 size_t tri_vec_elems(int m, int nb, int nsm);
 inline size_t tri_slot_doubles(int m) { return (size_t)m * m + 18 * (size_t)m; }

@@ -609,3 +609,29 @@ def test_apply_h_across_magnitudes():
         got = host(d_h)
         for a in range(psi.shape[0]):
             assert relerr(got[a], want[a]) < REL, a
+
+
+@pytest.mark.parametrize("case", [CASES[2], CASES[3], CASES[4]])
+def test_damped_step_correction_in_every_arithmetic(case):
+    """The damped step's correction psi - phi (the preconditioned residual,
+    small beside psi) against the oracle's, with and without a per-voxel
+    weight, in the three arithmetics of the FP64 form: the 3D transform pair
+    as six DFT operator products on the tensor cores (default), FFT line
+    passes in FP64 (0) -- (1) keeps the FFT passes as well."""
+    rng = np.random.default_rng(17)
+    with Ctx(*case) as c:
+        g = c.grid
+        I = 5
+        psi = IN.random_spinors(g.n, I, rng)
+        hpsi = IN.random_spinors(g.n, I, rng) * 30.0
+        eps = rng.uniform(-40, 10, I)
+        wv = (0.5 + rng.uniform(0.0, 1.5, g.shape)).astype(np.float32)
+        base = O.damped_step(psi, hpsi, eps, g, P["hb2m_n"], 0.45, 100.0)
+        for arith in (2, 1, 0):
+            B.sky_tune_set(c.ctx, B.SKY_KNOB_LINE_ARITH, arith)
+            for w in (None, wv):
+                want = (psi - base) * (1.0 if w is None else w.astype(np.float64)[None, None])
+                phi = torch.zeros(psi.shape, dtype=torch.complex128, device="cuda:0")
+                B.sky_damped_step(c.ctx, 0, dev(psi), dev(hpsi), dev(eps), phi, I, 0.45, 100.0,
+                                  None if w is None else dev(w))
+                assert relerr(psi - host(phi), want) < REL, (arith, w is None)

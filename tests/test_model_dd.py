@@ -209,3 +209,24 @@ def test_circulant_operator_is_the_fft_derivative(shape, dx, twist):
         out = inter @ R.T
         outc = (out[:, 0::2] + 1j * out[:, 1::2]).reshape(np.moveaxis(f, ax, -1).shape)
         assert np.max(np.abs(np.moveaxis(outc, -1, ax) - want)) < 1e-12 * np.max(np.abs(want))
+
+
+def dft_operator(n, inverse):
+    """The unnormalised DFT of a line as the operator matrix the kernels use:
+    D[m][q] = e^{-+2 pi i (m q mod n) / n} (not circulant: it depends on m q)."""
+    mq = np.outer(np.arange(n), np.arange(n)) % n
+    return np.exp((2j if inverse else -2j) * np.pi * mq / n)
+
+
+@pytest.mark.parametrize("n", [8, 12, 20, 24, 32])
+def test_dft_operators_are_the_fft(n):
+    rng = np.random.default_rng(n)
+    f = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    assert np.allclose(dft_operator(n, False) @ f, np.fft.fft(f), rtol=0, atol=1e-12 * n)
+    assert np.allclose(dft_operator(n, True) @ f, n * np.fft.ifft(f), rtol=0, atol=1e-12 * n)
+    # the derivative's circulant form is F^-1 diag(i kappa) F
+    D, _ = circulant_operator(n, 7.0, 0.4)
+    a = np.arange(n)
+    kap = (2 * np.pi * np.where(a < (n + 1) // 2, a, a - n) + 0.4) / 7.0
+    want = dft_operator(n, True) @ np.diag(1j * kap) @ dft_operator(n, False) / n
+    assert np.max(np.abs(D - want)) < 1e-12 * np.max(np.abs(want))
