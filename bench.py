@@ -821,6 +821,22 @@ def run_gpu(args):
     for _ in range(args.warmup):
         s.step()
     s.sync()
+    eager_ms = None
+    if args.graph:
+        # the same steps enqueued call by call, for the record; then the
+        # iteration captured once as a CUDA graph and replayed
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        for _ in range(args.steps):
+            s.step()
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        eager_ms = e0.elapsed_time(e1) / args.steps
+        s.capture()
+        for _ in range(args.warmup):
+            s.step()
+        s.sync()
     sampler = ClockSampler(_gpu_smi_id(local))
     B.sky_stats(s.ctx, reset=True)
     _barrier(dist)
@@ -835,6 +851,9 @@ def run_gpu(args):
     t1.record(s.stream)
     torch.cuda.synchronize()
     launches = B.sky_kernel_launches() - launches0
+    graphed = s.graph is not None
+    if graphed:                  # replays launch no kernels from the host
+        launches = s.launches_per_step * args.steps
     solver_stats = B.sky_stats(s.ctx)
     _barrier(dist)
     clocks = sampler.stop()
@@ -992,6 +1011,11 @@ def run_gpu(args):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "solver_stats_timed_steps": solver_stats,
+        "graph": {"captured": graphed,
+                  "eager_ms_per_step": eager_ms,
+                  "note": "the timed steps replay one CUDA graph of the iteration (captured "
+                          "after the warm-up); eager_ms_per_step: the same steps enqueued call "
+                          "by call"},
         "single_stream": {"ms_per_step": conc_ms, "value": ws * units / (conc_ms / 1e3),
                           "calls_ms_per_step": breakdown,
                           "note": "both species on one context and stream (the main number "
@@ -1026,6 +1050,8 @@ def main():
     ap.add_argument("--form", default="fp64", choices=sorted(FORMS),
                     help="spinor precision form (fp64: the paper's FP64 method)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="time the steps enqueued call by call instead of as a CUDA graph")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-box batched (CUDA graph) form")
     ap.add_argument("--no-config5", action="store_true",

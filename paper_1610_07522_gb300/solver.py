@@ -82,6 +82,7 @@ class Solver:
         # dict to collect (I, start, end) per call of sky_apply_h / sky_overlap / sky_rotate
         # (keys "apply_h", "overlap", "rotate"), events on the species' stream, or None
         self.call_events = None
+        self.graph = None            # CUDA graph of one step (capture()), replayed by step()
         self.damping = None          # learned.DampingNet giving the per-voxel step weight, or None
         self.damping_on = False
         self.damping_fallbacks = 0
@@ -95,6 +96,7 @@ class Solver:
         ``rise_tol`` MeV in one iteration (the damped gradient step lowers the
         energy) ``run`` halves s, and below ``min_scale`` it returns to the
         plain step for good."""
+        self.graph = None
         self.damping = net
         self.damping_on = net is not None
         self.damping_scale = 1.0
@@ -115,6 +117,7 @@ class Solver:
         (phi = psi - c (psi - phi_plain); c = 1 is the plain step, None turns it
         off): the uniform step size a learned per-voxel weight has to beat.
         Ignored while a learned weight is on."""
+        self.graph = None
         self.const_w = None if c is None else torch.full((2, self.G), float(c), dtype=torch.float32,
                                                          device=self.device)
 
@@ -241,8 +244,49 @@ class Solver:
              [self.lam[self.off[q]:self.off[q] + I]])
         self._timed("rotate", q, lambda: B.sky_rotate(ctx, self.phi[q], self.M[q], I, self.psi[q]))
 
+    def _set_main_stream(self, st):
+        self.stream = st
+        self.streamq[0] = st
+        if not self.concurrent:
+            self.streamq[1] = st
+        B.sky_set_stream(self.ctx, st.cuda_stream)
+
+    def capture(self, frozen=False):
+        """Record one iteration into a CUDA graph; ``step()`` then replays it
+        (the ~300 launches of an iteration as one graph launch).  Call after at
+        least one eager iteration (first-use allocations and attributes happen
+        there) and again after anything that changes the launch sequence
+        (precision, damping, eigensolver route)."""
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        old = self.stream
+        cap = torch.cuda.Stream(device=self.device)
+        n0 = B.sky_kernel_launches()
+        try:
+            with torch.cuda.graph(g, stream=cap):
+                self._set_main_stream(cap)
+                self.step_eager(frozen)
+        finally:
+            self._set_main_stream(old)
+        self.launches_per_step = B.sky_kernel_launches() - n0
+        self.graph = g
+        self.graph_frozen = frozen
+        torch.cuda.synchronize(self.device)
+
+    def release_graph(self):
+        self.graph = None
+
     def step(self, frozen=False):
-        """One full iteration (Fig. 1 steps 2-5); enqueued, not synchronised."""
+        """One full iteration (Fig. 1 steps 2-5); enqueued, not synchronised:
+        the captured graph when there is one, else the calls one by one."""
+        if self.graph is not None and frozen == self.graph_frozen and self.call_events is None:
+            with torch.cuda.stream(self.stream):
+                self.graph.replay()
+            return
+        self.step_eager(frozen)
+
+    def step_eager(self, frozen=False):
+        """One full iteration enqueued call by call."""
         self._fork()
         if self.split_eig:
             # two independent chains (neutrons on the main stream, protons on the
@@ -299,6 +343,7 @@ class Solver:
 
     def set_prec(self, prec):
         """Switch the GEMM form of an FP32-spinor solver (sky_set_prec)."""
+        self.graph = None
         B.sky_set_prec(self.ctx, prec)
         if self.concurrent:
             B.sky_set_prec(self.ctxq[1], prec)
@@ -307,6 +352,7 @@ class Solver:
     def set_eigen_method(self, method):
         """Choose the FP64 eigensolver of the diagonalisations
         (B.SKY_EIG_AUTO, B.SKY_EIG_JACOBI or B.SKY_EIG_TRIDIAGONAL)."""
+        self.graph = None
         for c in {id(x): x for x in self.ctxq}.values():
             B.sky_tune_set(c, B.SKY_KNOB_EIGEN_METHOD, method)
 
@@ -342,6 +388,7 @@ class Solver:
             else:
                 below = 0
             if self.damping_on and E_prev is not None and (E - E_prev) / self.A > self.rise_tol:
+                self.graph = None            # the scale is a launch argument
                 self.damping_scale *= 0.5
                 self.damping_fallbacks += 1
                 hist[-1]["fallback"] = self.damping_scale
