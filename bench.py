@@ -644,9 +644,61 @@ NPROD = {0: 21, 1: 10, 2: 3, 3: 6}
 # apply_h; profiles/), divided by its I.  Keyed by (workload, form); absent
 # until captured for the current kernels.
 HPSI_TRAFFIC_PER_SPINOR = {
-    # 2.780 GB over the 8 kernels of one I = 280 call (profiles/sky_apply_h_sly4_24cubed_280n_fp64.md)
-    ("sly4_24cubed_280n120p_coulomb_fp64", "fp64"): 2780380928.0 / 280,
+    # 2.784 GB over the 8 kernels of one I = 280 call (profiles/sky_apply_h_sly4_24cubed_280n_fp64.md)
+    ("sly4_24cubed_280n120p_coulomb_fp64", "fp64"): 2784466176.0 / 280,
 }
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_oz_deriv launch
+# along y over the 560 neutron spin components of the 24^3 workload
+# (profiles/k_oz_deriv_sly4_24cubed_280n_fp64.md): 124.2 + 71.5 MB
+DERIV_TRAFFIC = {("sly4_24cubed_280n120p_coulomb_fp64", "fp64"): 195.7e6}
+
+
+def derivative_roofline(dev, w, prec, peaks, form, reps=20):
+    """The dominant kernel of the step, live: one spectral derivative pass
+    (sky_derivative along y, the digit-split operator product on the tensor
+    cores in the FP64 form) over the 2N spin components of the workload's
+    neutrons, CUDA events on the context stream around reps launches.
+    Algorithmic bytes per launch: every complex point read once and written
+    once; bound: HBM (the operator work, 21 digit products of a 2n x 2n
+    operator per line, runs on the tensor cores)."""
+    import torch
+    from paper_1610_07522_gb300 import binding as B
+    st = torch.cuda.current_stream(dev)
+    ctx = B.sky_init(w.grid, w.dx, w.params, w.coulomb, w.twist, prec, w.N, st.cuda_stream)
+    nx, ny, nz = w.grid
+    G = nx * ny * nz
+    nb = 2 * w.N
+    cd = torch.complex128 if prec == 0 else torch.complex64
+    gen = torch.Generator(device=dev).manual_seed(3)
+    src = torch.randn((nb, G), dtype=cd, device=dev, generator=gen)
+    dst = torch.zeros_like(src)
+    for _ in range(3):
+        B.sky_derivative(ctx, 1, src, dst, nb)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        B.sky_derivative(ctx, 1, src, dst, nb)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    B.sky_destroy(ctx)
+    ms = e0.elapsed_time(e1) / reps
+    byt = 2.0 * nb * G * src.element_size()
+    ach = byt / (ms / 1e3) / 1e9
+    tr = DERIV_TRAFFIC.get((w.name, form))
+    return {"kernel": "k_oz_deriv (sky_derivative along y: the spectral derivative as a "
+                      "digit-split operator product on the tensor cores)" if prec == 0 else
+                      "k_line_yz (sky_derivative along y: FFT line pass)",
+            "bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": peaks["hbm_gbs"],
+            "frac": ach / peaks["hbm_gbs"], "avg_launch_ms": ms, "launches_timed": reps,
+            "arrays": nb, "algorithmic_bytes_per_launch": byt,
+            "work": "per launch: read and write every complex point of the 2N arrays once",
+            "traffic": tr,
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of "
+                               "the same shapes (writes still dirty in L2 at the kernel's end are "
+                               "written back later)") if tr else "not captured for this workload "
+                                                                 "and form",
+            "peak_source": "measured HBM copy bandwidth (MEASURED_PEAKS.json, burst)"}
 
 
 def fma_peaks(dev):
@@ -710,8 +762,9 @@ def call_rooflines(events, grid, prec, peaks, csize):
             "achieved": fl / (ms / 1e3) / 1e12, "peak": pk,
             "frac": fl / (ms / 1e3) / 1e12 / pk,
             "peak_source": (f"measured {'FP64' if prec == 0 else 'FP32'} FMA rate (sky_fma_probe, this run)"
-                            + ("; the derivative line passes run in double-float arithmetic on the "
-                               "FP32 pipe, so this is an FP64-equivalent rate" if prec == 0 else "")),
+                            + ("; in the FP64 form the derivative passes are tensor-core operator "
+                               "products and the pointwise terms double-float FP32 work, so this "
+                               "is an FP64-equivalent rate, not a pipe fraction" if prec == 0 else "")),
             "hbm_algorithmic_GBps": by / (ms / 1e3) / 1e9,
             "hbm_frac": by / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
             "work": "per spinor: 40 G sum_j log2 n_j + 150 G flops, 2 x 2G complex values moved"}
@@ -912,16 +965,19 @@ def run_gpu(args):
                  for k, ev in sc.call_events.items()}
     sc.call_events = None
     sc.close()
-    # the line's roofline: the h.psi call, the largest call of the step (the
-    # FP64 FFT line passes are FP64-pipe work); the contractions beside it
-    roof = dict(calls.get("apply_h", {}))
+    # the h.psi call beside the contractions (call-level), and the line's
+    # roofline: the dominant kernel of the step, timed live on its own
+    ah = dict(calls.get("apply_h", {}))
     tps = HPSI_TRAFFIC_PER_SPINOR.get((args.workload, args.form))
-    roof["traffic"] = tps * roof["mean_I"] if (tps and roof) else None
-    roof["traffic_source"] = (
-        "ncu dram__bytes_read.sum + dram__bytes_write.sum over the kernels of one sky_apply_h "
-        "call (bench.py --probe-call apply_h) per spinor, times this run's mean I per call"
-        if roof["traffic"] is not None else "not captured for this workload and form")
-    roof["fma_peaks_tflops"] = probe
+    if ah:
+        ah["traffic"] = tps * ah["mean_I"] if tps else None
+        ah["traffic_source"] = (
+            "ncu dram__bytes_read.sum + dram__bytes_write.sum over the kernels of one sky_apply_h "
+            "call (bench.py --probe-call apply_h) per spinor, times this run's mean I per call"
+            if ah["traffic"] is not None else "not captured for this workload and form")
+        ah["fma_peaks_tflops"] = probe
+        calls["apply_h"] = ah
+    roof = derivative_roofline(dev, w, prec, peaks, args.form)
 
     # end to end through the public API with pinned host buffers
     host = {
@@ -1005,7 +1061,7 @@ def run_gpu(args):
                    "parallelism": f"replicas x{ws}",
                    "l2": f"working set (psi, phi, h psi: {3 * s.psi[0].element_size() * V * (w.N + w.Z) / 1e9:.2f} GB) exceeds L2 (129 MB), no flush"},
         "roofline": roof,
-        "roofline_calls": {k: v for k, v in calls.items() if k != "apply_h"},
+        "roofline_calls": calls,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "spinor-applies/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

@@ -135,6 +135,17 @@ unsigned long long sky_kernel_launches(void);
 sky_status sky_apply_h(sky_ctx* ctx, const double* U, const double* B, const double* W,
                        const void* psi, void* hpsi, int I, double* eps, double* hnorm2);
 
+/* ---- Spectral derivative along one axis (Sec. 2.2: the derivatives of the
+ * method are taken with FFTs) ------------------------------------------------
+ * dst = d_axis src for n arrays of G complex points each ([n][G], x fastest,
+ * complex128 in the FP64 form, complex64 in the FP32 forms), with the
+ * wavenumbers k + theta/L of the spinor derivatives (Nyquist kept): the
+ * derivative every h psi and density call applies, one axis at a time
+ * (axis 0 = x, 1 = y, 2 = z).  dst may equal src (in place), otherwise the
+ * two must not overlap.  Arithmetic as SKY_KNOB_LINE_ARITH selects.
+ * SKY_EINVAL for a bad axis, n < 0 or null pointers with n > 0. */
+sky_status sky_derivative(sky_ctx* ctx, int axis, const void* src, void* dst, int n);
+
 /* ---- Step 2: damped gradient step (Eq. dampstep) ---------------------------
  * phi = psi - x0 * P (hpsi - eps psi), P = 1/(E0 + hb2m_q |k + theta/L|^2)
  * diagonal in momentum space (hb2m_q of species q = 0 neutrons, 1 protons).

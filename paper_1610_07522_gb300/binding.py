@@ -52,6 +52,7 @@ _SIGNATURES = {
     "sky_kernel_launches": (ctypes.c_ulonglong, []),
     "sky_stats": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), _I]),
     "sky_apply_h": (_I, [_P, _P, _P, _P, _P, _P, _I, _P, _P]),
+    "sky_derivative": (_I, [_P, _I, _P, _P, _I]),
     "sky_damped_step": (_I, [_P, _I, _P, _P, _P, _P, _I, _D, _D, _P]),
     "sky_overlap": (_I, [_P, _P, _P, _I, _P]),
     "sky_orthonormalize": (_I, [_P, _P, _I, _P]),
@@ -181,6 +182,10 @@ def sky_kernel_launches():
 def sky_apply_h(ctx, U, B, W, psi, hpsi, I, eps=None, hnorm2=None):
     _check(ctx, lib().sky_apply_h(ctx, _ptr(U), _ptr(B), _ptr(W), _ptr(psi), _ptr(hpsi), int(I),
                                   _ptr(eps), _ptr(hnorm2)))
+
+
+def sky_derivative(ctx, axis, src, dst, n):
+    _check(ctx, lib().sky_derivative(ctx, int(axis), _ptr(src), _ptr(dst), int(n)))
 
 
 def sky_damped_step(ctx, q, psi, hpsi, eps, phi, I, x0, E0, w=None):

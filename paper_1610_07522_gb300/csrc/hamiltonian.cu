@@ -326,6 +326,15 @@ sky_status apply_h_impl(Ctx* c, const double* U, const double* B, const double* 
   return apply_h_t<float>(c, U, B, W, (const float2*)psi, (float2*)hpsi, I, eps, hn2);
 }
 
+sky_status derivative_impl(Ctx* c, int axis, const void* src, void* dst, int n) {
+  cudaError_t e;
+  if (c->prec == SKY_F64)
+    e = deriv_pass<double>(c, axis, (const double2*)src, (double2*)dst, n);
+  else
+    e = deriv_pass<float>(c, axis, (const float2*)src, (float2*)dst, n);
+  return e == cudaSuccess ? SKY_OK : cuda_check(c, e, "derivative");
+}
+
 // ------------------------------------------------------------ damped step
 __global__ void k_damp_table(double* P, const double* kx, const double* ky, const double* kz,
                              int nx, int ny, int nz, double hb2m, double E0) {

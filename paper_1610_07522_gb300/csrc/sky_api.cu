@@ -443,6 +443,14 @@ sky_status sky_td_taylor(sky_ctx* c, const double* U, const double* B, const dou
   return td_taylor_impl(c, U, B, W, psi, out, work, I, tau, order);
 }
 
+sky_status sky_derivative(sky_ctx* c, int axis, const void* src, void* dst, int n) {
+  if (!c) return SKY_EINVAL;
+  if (axis < 0 || axis > 2 || n < 0) return set_err(c, SKY_EINVAL, "derivative: axis %d, n %d", axis, n);
+  if (n == 0) return SKY_OK;
+  if (!src || !dst) return set_err(c, SKY_EINVAL, "derivative: null pointer");
+  return derivative_impl(c, axis, src, dst, n);
+}
+
 sky_status sky_damped_step(sky_ctx* c, int q, const void* psi, const void* hpsi, const double* eps,
                            void* phi, int I, double x0, double E0, const float* w) {
   CHECK_CTX();

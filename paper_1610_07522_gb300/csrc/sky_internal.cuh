@@ -216,6 +216,7 @@ sky_status tri_init(Ctx* c);
 // Derivative passes of the FP64 form as digit-split operator products on the
 // tensor cores (oz_deriv.cu): operators built at context creation for axis
 // lengths 8, 12, 16, 20, 24, 32; dst = d_ax src over nb arrays (dst may be src).
+sky_status derivative_impl(Ctx* c, int axis, const void* src, void* dst, int n);
 sky_status deriv_tc_init(Ctx* c);
 cudaError_t deriv_tc(Ctx* c, int ax, const double2* src, double2* dst, long long nb);
 bool damp_tc_available(const Ctx* c);

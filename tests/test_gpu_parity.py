@@ -635,3 +635,33 @@ def test_damped_step_correction_in_every_arithmetic(case):
                 B.sky_damped_step(c.ctx, 0, dev(psi), dev(hpsi), dev(eps), phi, I, 0.45, 100.0,
                                   None if w is None else dev(w))
                 assert relerr(psi - host(phi), want) < REL, (arith, w is None)
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[3], CASES[4]])
+def test_derivative_every_axis(case):
+    """sky_derivative against the oracle's spectral derivative (twisted
+    wavenumbers, Nyquist kept), every axis, out of place and in place, in the
+    three arithmetics of the FP64 form; the FP32 form within its bound."""
+    rng = np.random.default_rng(23)
+    with Ctx(*case) as c:
+        g = c.grid
+        n = 7
+        f = IN.random_spinors(g.n, n, rng).reshape((2 * n,) + g.shape)[:n]
+        for arith in (2, 1, 0):
+            B.sky_tune_set(c.ctx, B.SKY_KNOB_LINE_ARITH, arith)
+            for ax in range(3):
+                want = np.stack([O.deriv(f[k], ax, g) for k in range(n)])
+                out = torch.zeros(f.shape, dtype=torch.complex128, device="cuda:0")
+                B.sky_derivative(c.ctx, ax, dev(f), out, n)
+                assert relerr(host(out), want) < REL, (arith, ax)
+                inp = dev(f)
+                B.sky_derivative(c.ctx, ax, inp, inp, n)
+                assert relerr(host(inp), want) < REL, (arith, ax, "in place")
+    with Ctx(case[0], case[1], case[2], prec=B.SKY_F32) as c32:
+        g = c32.grid
+        f = IN.random_spinors(g.n, 2, rng).reshape((4,) + g.shape)
+        for ax in range(3):
+            want = np.stack([O.deriv(f[k], ax, g) for k in range(4)])
+            out = torch.zeros(f.shape, dtype=torch.complex64, device="cuda:0")
+            B.sky_derivative(c32.ctx, ax, dev(f.astype(np.complex64)), out, 4)
+            assert relerr(host(out), want) < 4e-6, ax
