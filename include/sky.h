@@ -225,9 +225,11 @@ sky_status sky_subspace_diag_literal_batched(sky_ctx* ctx, int nb, const double*
 
 /* Raise the batch capacity of the batched calls to nb problems of up to
  * max_states each (1 <= nb <= 128).  Allocates device memory (about
- * 9.5 max_states^2 complex doubles per problem) and synchronises the context
- * stream; call it outside stream capture.  SKY_ENOMEM leaves the context as
- * it was. */
+ * 9.5 max_states^2 complex doubles per problem; for nb > 8 also the digit
+ * buffers of the grouped tensor-core I x I products, about 72 max_states
+ * bytes per problem and state plus partials, capped at 2 GiB each) and
+ * synchronises the context stream; call it outside stream capture.
+ * SKY_ENOMEM leaves the context as it was. */
 sky_status sky_reserve_batch(sky_ctx* ctx, int nb);
 sky_status sky_subspace_diag_batched(sky_ctx* ctx, int nb, const double* const* H,
                                      const double* const* C, const int* I, double* const* M,
@@ -302,9 +304,12 @@ sky_status sky_set_prec(sky_ctx* ctx, sky_prec prec);
  *                           (Householder reduction to real tridiagonal form, bisection,
  *                           inverse iteration, back-transformation: the paper's route
  *                           through ScaLAPACK, Sec. 3.3.2) or SKY_EIG_AUTO (default:
- *                           tridiagonal for batches of at most 8 problems of 64 states or
- *                           more, Jacobi otherwise; the tridiagonal route falls back to
- *                           Jacobi when its work vectors exceed shared memory)
+ *                           tridiagonal for batches with a problem of 64 states or more,
+ *                           Jacobi for batches of smaller problems only; a batch of more
+ *                           than 8 problems splits the reduction's blocks into teams, one
+ *                           per large problem and shared ones for small problems; the
+ *                           tridiagonal route falls back to Jacobi when its work vectors
+ *                           exceed shared memory)
  *   SKY_KNOB_SPLIT_GEMM     FP64 and FP32 forms: 1 (default) computes sky_overlap and
  *                           sky_rotate on the tensor cores as exact-integer split products
  *                           (each row scaled by a power of two and cut into signed 8-bit

@@ -25,17 +25,18 @@ __device__ __forceinline__ double rcp_refined(double x) {
   return r;
 }
 
-// Grid barrier over all blocks of a cooperative launch: a monotonic arrival
-// counter (reset before the launch); barrier number e completes when it
-// reaches e * gridDim.x.  Release-add to arrive, acquire loads to wait, with
-// a bounded spin: on timeout it flags SKY_ETIMEOUT and returns false.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, int* status,
-                                             long long max_spins) {
+// Barrier over `count` blocks of a cooperative launch that share the arrival
+// counter `bar` (reset before the launch): barrier number e completes when
+// the counter reaches e * count.  Release-add to arrive, acquire loads to
+// wait, with a bounded spin: on timeout it flags SKY_ETIMEOUT and returns
+// false.  The whole grid is count = gridDim.x.
+__device__ __forceinline__ bool blocks_barrier(unsigned* bar, unsigned& epoch, unsigned count,
+                                               int* status, long long max_spins) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ++epoch;
-    const unsigned target = epoch * gridDim.x;
+    const unsigned target = epoch * count;
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
     int ok = 1;
     long long spins = 0;
@@ -54,6 +55,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, int
   }
   __syncthreads();
   return s_ok != 0;
+}
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, int* status,
+                                             long long max_spins) {
+  return blocks_barrier(bar, epoch, gridDim.x, status, max_spins);
 }
 
 // Problem of item w: the last b with off[b] <= w (off ascending, off[np] > w).

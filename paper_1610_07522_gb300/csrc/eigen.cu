@@ -516,12 +516,12 @@ static sky_status eigh_batch_jacobi(Ctx* c, int np, const double2* const* A, con
   return cuda_check(c, cudaGetLastError(), "jacobi finish");
 }
 
-// Until the method is set, problems of kTriAutoMin states and more in batches of
-// at most kTriAutoBatch take the tridiagonal route (O(n^3) once instead of per
-// Jacobi sweep); many small problems stay with the batched Jacobi solver,
-// whose rounds serve the whole batch at once.
+// Until the method is set, batches with a problem of kTriAutoMin states or more
+// take the tridiagonal route (O(n^3) once instead of per Jacobi sweep; a batch
+// of many problems splits its blocks into teams); batches of small problems
+// only stay with the batched Jacobi solver, whose rounds serve the whole
+// batch at once.
 constexpr int kTriAutoMin = 64;
-constexpr int kTriAutoBatch = 8;
 
 // Eigendecomposition of np Hermitian matrices A[b] (n[b] x n[b]) into ascending
 // w[b] and eigenvector columns Z[b]; problem b is skipped when run[b*stride] == 0.
@@ -532,7 +532,7 @@ sky_status eigh_batch(Ctx* c, int np, const double2* const* A, const int* n, dou
   int nmax = 0;
   for (int b = 0; b < np; ++b) nmax = n[b] > nmax ? n[b] : nmax;
   const bool tri = c->eig_method == SKY_EIG_TRIDIAGONAL ||
-                   (c->eig_method == SKY_EIG_AUTO && nmax >= kTriAutoMin && np <= kTriAutoBatch);
+                   (c->eig_method == SKY_EIG_AUTO && nmax >= kTriAutoMin);
   if (tri) {
     const sky_status s = eigh_batch_tri(c, np, A, n, w, Z, run, run_stride);
     if (s != SKY_EUNSUPPORTED) return s;

@@ -34,6 +34,9 @@
 //     order.
 //
 // Eigenvalues come out ascending, eigenvectors as the columns of Z.
+#include <algorithm>
+#include <cmath>
+
 #include "dd.cuh"
 #include "eig_common.cuh"
 
@@ -54,6 +57,7 @@ constexpr int kWinChunks = (2 * kWinMax + 1 + 31) / 32;
 constexpr int kBackWarps = 16;
 constexpr size_t kTriSmemMax = 200 * 1024;   // dynamic shared memory of k_hh_tridiag / k_hh_back
 constexpr double kEps = 2.220446049250313e-16;
+constexpr int kTeamBarStride = 32;     // unsigned between team barrier counters (128 bytes)
 
 struct TriBatch {
   const double2* A[kMaxBatch];   // input matrices, row-major n x n
@@ -84,6 +88,21 @@ struct TriBatch {
   int* status;
   long long spins;
   long long* stats;
+  // Teams (stage 1): the blocks tg0[k] .. tg0[k+1]-1 reduce the problems
+  // tmem[tp0[k]] .. tmem[tp0[k+1]-1] by themselves, with their own barrier
+  // counter tbar[kTeamBarStride k]; one team of all blocks when nteam = 1.
+  int nteam;
+  int tmem[kMaxBatch];
+  int tp0[kMaxBatch + 1];
+  int tg0[kMaxBatch + 1];
+  unsigned* tbar;
+};
+
+// This block's team: its size G, the block's rank gb in it, its problems
+// (positions p0 .. p1-1 of tmem) and its barrier counter.
+struct TeamView {
+  int G, gb, p0, p1;
+  unsigned* bar;
 };
 
 struct TriPtrs {
@@ -145,10 +164,23 @@ constexpr int kHeadWarps = 4;
 constexpr int kHeadThreads = kHeadWarps * 32;
 constexpr int kHeadGroups = kTriWarps / kHeadWarps;
 
-// First own column of block g for problem b and the number of own columns.
-__device__ __forceinline__ void own_range(const TriBatch& a, int b, int& j0, int& ns) {
-  const int G = gridDim.x, n = a.n[b];
-  j0 = (((int)blockIdx.x - a.rot[b]) % G + G) % G;
+__device__ __forceinline__ TeamView team_view(const TriBatch& a) {
+  const int k = find_prob(a.tg0, a.nteam, (int)blockIdx.x);
+  TeamView v;
+  v.G = a.tg0[k + 1] - a.tg0[k];
+  v.gb = (int)blockIdx.x - a.tg0[k];
+  v.p0 = a.tp0[k];
+  v.p1 = a.tp0[k + 1];
+  v.bar = a.tbar + (size_t)kTeamBarStride * k;
+  return v;
+}
+
+// First own column of this block for problem b and the number of own columns
+// (columns are dealt cyclically over the team's blocks).
+__device__ __forceinline__ void own_range(const TriBatch& a, const TeamView& tv, int b, int& j0,
+                                          int& ns) {
+  const int G = tv.G, n = a.n[b];
+  j0 = ((tv.gb - a.rot[b]) % G + G) % G;
   ns = j0 < n ? (n - 1 - j0) / G + 1 : 0;
 }
 
@@ -168,19 +200,21 @@ struct HeadShared {
   double2 sc[kHeadGroups][2];
 };
 
-// Step t of the problems b0 .. b0 + kHeadGroups - 1 (group q serves b0 + q),
-// every block alike: column t of the trailing matrix (updated by reflector
+// Step t of the team's problems tmem[k0 .. k0 + kHeadGroups - 1] (group q
+// serves tmem[k0 + q]), every block of the team alike: column t of the trailing matrix (updated by reflector
 // t-1 from the published copy), d_t, and reflector t.  Work vectors: vn = v_t
 // (built in place from the column), vo = v_{t-1}, w.  v_{t-1}^H p_{t-1} is the
 // sum of the owners' published per-block partials (the same order in every
 // block); beta, tau and 1/(alpha - beta) are formed once per problem by the
 // group's first thread and passed on in shared memory.  The published p and
 // column are loaded in one pass (one L2 round trip per step).
-__device__ void tri_heads(const TriBatch& a, int b0, int t, double2* dsm, HeadShared& hs,
-                          double2* s_tau, const unsigned char* s_run) {
+__device__ void tri_heads(const TriBatch& a, const TeamView& tv, int k0, int t, double2* dsm,
+                          HeadShared& hs, double2* s_tau, const unsigned char* s_run) {
   const int q = threadIdx.x / kHeadThreads, ht = threadIdx.x % kHeadThreads;
-  const int b = b0 + q, lane = threadIdx.x & 31, hwarp = ht >> 5;
-  const bool on = b < a.np && s_run[b] && t <= a.n[b] - 1;
+  const int lane = threadIdx.x & 31, hwarp = ht >> 5;
+  const bool has = k0 + q < tv.p1;
+  const int b = has ? a.tmem[k0 + q] : 0;
+  const bool on = has && s_run[b] && t <= a.n[b] - 1;
   const int n = on ? a.n[b] : 0;
   double2* vb = on ? vec_base(a, b, dsm) : dsm;
   double2* vn = vb + (size_t)(t & 1) * n;
@@ -212,7 +246,7 @@ __device__ void tri_heads(const TriBatch& a, int b0, int t, double2* dsm, HeadSh
       if (hwarp == 0) {
         const double* ps = sp_row(a, b, t - 1);
         double S = 0.0;
-        for (int g = lane; g < (int)gridDim.x; g += 32) S += __ldcg(ps + g);
+        for (int g = lane; g < tv.G; g += 32) S += __ldcg(ps + g);
         S = warp_sum(S);
         if (lane == 0) {
           const double2 tau = s_tau[b];
@@ -280,7 +314,7 @@ __device__ void tri_heads(const TriBatch& a, int b0, int t, double2* dsm, HeadSh
     }
   }
   __syncthreads();
-  if (on && blockIdx.x == 0) {
+  if (on && tv.gb == 0) {
     if (refl) {
       if (ht == 0) {
         const double2 bd = hs.sc[q][1];
@@ -304,11 +338,11 @@ __device__ void tri_heads(const TriBatch& a, int b0, int t, double2* dsm, HeadSh
 }
 
 // Own columns of problem b active at step t (j >= t+1): first slot and count.
-__device__ __forceinline__ void active_own(const TriBatch& a, int b, int t, int& j0, int& smin,
-                                           int& cb) {
-  const int G = gridDim.x;
+__device__ __forceinline__ void active_own(const TriBatch& a, const TeamView& tv, int b, int t,
+                                           int& j0, int& smin, int& cb) {
+  const int G = tv.G;
   int ns;
-  own_range(a, b, j0, ns);
+  own_range(a, tv, b, j0, ns);
   smin = t + 1 > j0 ? (t + 1 - j0 + G - 1) / G : 0;
   cb = ns > smin ? ns - smin : 0;
 }
@@ -316,24 +350,26 @@ __device__ __forceinline__ void active_own(const TriBatch& a, int b, int t, int&
 // Own columns j >= t+1, one warp per column: update by reflector t-1 (rows
 // > t), p_j = col_j^H v_t, publication of p_j and of column t+1, and the
 // block's partial of Re(v_t^H p_t) per problem (over its own columns, in
-// column order).
-__device__ void tri_body(const TriBatch& a, int t, double2* dsm, double* contrib,
-                         const unsigned char* s_run) {
-  const int G = gridDim.x, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+// column order), for the team's problems.
+__device__ void tri_body(const TriBatch& a, const TeamView& tv, int t, double2* dsm,
+                         double* contrib, const unsigned char* s_run) {
+  const int G = tv.G, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int C = 0;
-  for (int b = 0; b < a.np; ++b) {
+  for (int k = tv.p0; k < tv.p1; ++k) {
+    const int b = a.tmem[k];
     if (!s_run[b] || t > a.n[b] - 2) continue;
     int j0, smin, cb;
-    active_own(a, b, t, j0, smin, cb);
+    active_own(a, tv, b, t, j0, smin, cb);
     C += cb;
   }
   for (int ci = wid; ci < C; ci += kTriWarps) {
     // column ci -> problem b, column j, slot s
     int b = 0, j = 0, s = 0, rest = ci;
-    for (; b < a.np; ++b) {
+    for (int k = tv.p0; k < tv.p1; ++k) {
+      b = a.tmem[k];
       if (!s_run[b] || t > a.n[b] - 2) continue;
       int j0, smin, cb;
-      active_own(a, b, t, j0, smin, cb);
+      active_own(a, tv, b, t, j0, smin, cb);
       if (rest < cb) {
         s = smin + rest;
         j = j0 + s * G;
@@ -376,20 +412,22 @@ __device__ void tri_body(const TriBatch& a, int t, double2* dsm, double* contrib
   }
   __syncthreads();
   // per-problem partials, one thread per problem, own columns in order
-  for (int b = threadIdx.x; b < a.np; b += blockDim.x) {
+  for (int k = tv.p0 + (int)threadIdx.x; k < tv.p1; k += blockDim.x) {
+    const int b = a.tmem[k];
     if (!s_run[b] || t > a.n[b] - 2) continue;
     int first = 0;
-    for (int q = 0; q < b; ++q) {
+    for (int kq = tv.p0; kq < k; ++kq) {
+      const int q = a.tmem[kq];
       if (!s_run[q] || t > a.n[q] - 2) continue;
       int j0, smin, cb;
-      active_own(a, q, t, j0, smin, cb);
+      active_own(a, tv, q, t, j0, smin, cb);
       first += cb;
     }
     int j0, smin, cb;
-    active_own(a, b, t, j0, smin, cb);
+    active_own(a, tv, b, t, j0, smin, cb);
     double acc = 0.0;
-    for (int k = 0; k < cb; ++k) acc += contrib[first + k];
-    sp_row(a, b, t)[blockIdx.x] = acc;
+    for (int i = 0; i < cb; ++i) acc += contrib[first + i];
+    sp_row(a, b, t)[tv.gb] = acc;
   }
 }
 
@@ -400,9 +438,11 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_hh_tridiag(TriBatch a) {
   __shared__ unsigned char s_run[kMaxBatch];
   const int tid = threadIdx.x, nt = blockDim.x;
   double* contrib = reinterpret_cast<double*>(dsm + a.coff);
+  const TeamView tv = team_view(a);
   unsigned epoch = 0;
   int nrun = 0;
-  for (int b = 0; b < a.np; ++b) {
+  for (int k = tv.p0; k < tv.p1; ++k) {
+    const int b = a.tmem[k];
     const bool r = tri_run(a, b);
     if (tid == 0) {
       s_run[b] = r;
@@ -412,14 +452,15 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_hh_tridiag(TriBatch a) {
   }
   __syncthreads();
   // own columns: column j = conj(row j) of the Hermitian input
-  for (int b = 0; b < a.np; ++b) {
+  for (int k = tv.p0; k < tv.p1; ++k) {
+    const int b = a.tmem[k];
     if (!s_run[b]) continue;
     int j0, ns;
-    own_range(a, b, j0, ns);
+    own_range(a, tv, b, j0, ns);
     const int n = a.n[b];
     const double2* A = a.A[b];
     for (int s = 0; s < ns; ++s) {
-      const int j = j0 + s * (int)gridDim.x;
+      const int j = j0 + s * tv.G;
       double2* col = own_col(a, b, dsm, j, s);
       for (int i = tid; i < n; i += nt) {
         double2 x = A[(size_t)j * n + i];
@@ -430,14 +471,21 @@ __global__ void __launch_bounds__(kTriThreads, 1) k_hh_tridiag(TriBatch a) {
   }
   __syncthreads();
   for (int t = 0; t < nrun; ++t) {
-    for (int b0 = 0; b0 < a.np; b0 += kHeadGroups) tri_heads(a, b0, t, dsm, hs, s_tau, s_run);
-    tri_body(a, t, dsm, contrib, s_run);
-    if (t + 1 < nrun && !grid_barrier(a.bar, epoch, a.status, a.spins)) return;
+    for (int k0 = tv.p0; k0 < tv.p1; k0 += kHeadGroups)
+      tri_heads(a, tv, k0, t, dsm, hs, s_tau, s_run);
+    tri_body(a, tv, t, dsm, contrib, s_run);
+    if (t + 1 < nrun) {
+      if (tv.G == 1) {
+        __syncthreads();
+      } else if (!blocks_barrier(tv.bar, epoch, (unsigned)tv.G, a.status, a.spins)) {
+        return;
+      }
+    }
   }
-  if (blockIdx.x == 0 && tid == 0) {
+  if (tv.gb == 0 && tid == 0) {
     long long k = 0;
-    for (int b = 0; b < a.np; ++b) k += s_run[b];
-    a.stats[6] += k;
+    for (int q = tv.p0; q < tv.p1; ++q) k += s_run[a.tmem[q]];
+    atomicAdd(reinterpret_cast<unsigned long long*>(a.stats + 6), (unsigned long long)k);
   }
 }
 
@@ -784,7 +832,7 @@ __global__ void __launch_bounds__(kBackWarps * 32) k_hh_back(TriBatch a, int zst
   }
 }
 
-__global__ void k_tri_reset(unsigned* bar) { bar[0] = 0u; }
+__global__ void k_tri_reset(unsigned* bar) { bar[(size_t)kTeamBarStride * threadIdx.x] = 0u; }
 
 // A problem of n states keeps its work vectors in global memory when they
 // alone (with the per-column partials) exceed the shared-memory budget.
@@ -812,6 +860,136 @@ sky_status tri_init(Ctx* c) {
   return cuda_check(c, e, "tridiagonal solver attributes");
 }
 
+// ---- teams of blocks for batches of many problems ----------------------------------
+// With one team, every block takes part in every problem's steps and the
+// slowest problem sets the pace of all: n_max steps, each with the head work
+// of every problem.  A batch of more than kTeamMin problems (the many boxes of
+// twist-averaged runs) is split instead: a problem whose work needs several
+// blocks gets a team of its own, smaller ones share one-block teams (no
+// barrier at all), each team stepping at its own pace.  The split minimises
+// the largest estimated team time
+//   steps x (per-step latency) + sum over its problems of 4 n^3 FMAs / rate,
+// by bisection on the time target: problems are taken largest first, teams
+// of several blocks sized to the target, the rest packed first-fit into
+// one-block teams whose work vectors fit in shared memory.
+constexpr int kTeamMin = 8;
+constexpr double kTeamFma = 3.4e9;      // FP64 FMAs per second of one block (one per SM)
+constexpr double kTeamStep1 = 1.5e-6;   // seconds per step of a one-block team
+constexpr double kTeamStepG = 5.0e-6;   // seconds per step of a team with a barrier
+constexpr double kTeamHead = 1.0e-6;    // per step and further group of kHeadGroups problems
+constexpr int kTeamMinCols = 4;         // own columns per block of a team at least
+
+struct TeamPlan {
+  int nteam;
+  int mem[kMaxBatch];
+  int p0[kMaxBatch + 1];
+  int g0[kMaxBatch + 1];
+};
+
+static double team_work(int n) { return 4.0 * (double)n * n * n / kTeamFma; }
+static size_t team_vec(int n) { return 3 * (size_t)n + (size_t)(n + 1) / 2 + 1; }   // double2
+
+// Estimated time of a team of g blocks for problems mem[k0 .. k1).
+static double team_time(const int* n, const int* mem, int k0, int k1, int g) {
+  int nmax = 0;
+  double w = 0.0;
+  for (int k = k0; k < k1; ++k) {
+    nmax = n[mem[k]] > nmax ? n[mem[k]] : nmax;
+    w += team_work(n[mem[k]]);
+  }
+  const int groups = (k1 - k0 + kHeadGroups - 1) / kHeadGroups;
+  const double step = (g > 1 ? kTeamStepG : kTeamStep1) + kTeamHead * (groups - 1);
+  return nmax * step + w / g;
+}
+
+// Teams for the target time T (problems in `order`, largest first); returns
+// the blocks used, or a number above `blocks` when T cannot be met.
+static int plan_at(int np, const int* n, const int* order, double T, size_t budget, TeamPlan& p) {
+  int used = 0, k = 0;
+  p.nteam = 0;
+  bool packed[kMaxBatch];
+  for (int i = 0; i < np; ++i) {
+    const int b = order[i];
+    packed[b] = team_work(n[b]) + n[b] * kTeamStep1 <= T;
+    if (packed[b]) continue;
+    const double room = T - n[b] * kTeamStepG;
+    const int gmax = n[b] / kTeamMinCols > 2 ? n[b] / kTeamMinCols : 2;
+    if (room <= 0.0) return 1 << 30;
+    const double gf = team_work(n[b]) / room;
+    if (gf > gmax) return 1 << 30;
+    int g = (int)std::ceil(gf);
+    g = g < 2 ? 2 : g;
+    p.p0[p.nteam] = k;
+    p.g0[p.nteam] = used;
+    p.mem[k++] = b;
+    used += g;
+    ++p.nteam;
+  }
+  // first fit, largest first, into one-block teams
+  int bin_of[kMaxBatch], nbin = 0;
+  double bw[kMaxBatch];
+  int bn[kMaxBatch], bk[kMaxBatch];
+  size_t bv[kMaxBatch];
+  for (int i = 0; i < np; ++i) {
+    const int b = order[i];
+    if (!packed[b]) continue;
+    int f = -1;
+    for (int q = 0; q < nbin && f < 0; ++q) {
+      const int groups = (bk[q] + 1 + kHeadGroups - 1) / kHeadGroups;
+      const double t = bn[q] * (kTeamStep1 + kTeamHead * (groups - 1)) + bw[q] + team_work(n[b]);
+      if (t <= T && bv[q] + team_vec(n[b]) <= budget) f = q;
+    }
+    if (f < 0) {
+      if (team_vec(n[b]) > budget) return 1 << 30;
+      f = nbin++;
+      bw[f] = 0.0; bn[f] = n[b]; bk[f] = 0; bv[f] = 0;
+    }
+    bw[f] += team_work(n[b]);
+    bk[f] += 1;
+    bv[f] += team_vec(n[b]);
+    bin_of[b] = f;
+  }
+  for (int q = 0; q < nbin; ++q) {
+    p.p0[p.nteam] = k;
+    p.g0[p.nteam] = used++;
+    for (int i = 0; i < np; ++i)
+      if (packed[order[i]] && bin_of[order[i]] == q) p.mem[k++] = order[i];
+    ++p.nteam;
+  }
+  p.p0[p.nteam] = k;
+  p.g0[p.nteam] = used;
+  return used;
+}
+
+// The team split of np problems over `blocks` blocks (false if none fits).
+static bool plan_teams(int np, const int* n, int blocks, size_t budget, TeamPlan& p) {
+  int order[kMaxBatch];
+  for (int b = 0; b < np; ++b) order[b] = b;
+  std::sort(order, order + np, [&](int x, int y) { return n[x] != n[y] ? n[x] > n[y] : x < y; });
+  double hi = 1.0, lo = 0.0;
+  if (plan_at(np, n, order, hi, budget, p) > blocks) return false;
+  for (int it = 0; it < 48; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (plan_at(np, n, order, mid, budget, p) <= blocks) hi = mid; else lo = mid;
+  }
+  int used = plan_at(np, n, order, hi, budget, p);
+  // spare blocks to the slowest single-problem teams
+  while (used < blocks) {
+    int best = -1;
+    double bt = 0.0;
+    for (int t = 0; t < p.nteam; ++t) {
+      const int g = p.g0[t + 1] - p.g0[t];
+      if (p.p0[t + 1] - p.p0[t] != 1 || g + 1 > n[p.mem[p.p0[t]]] / kTeamMinCols) continue;
+      const double tt = team_time(n, p.mem, p.p0[t], p.p0[t + 1], g);
+      if (tt > bt) { bt = tt; best = t; }
+    }
+    if (best < 0) break;
+    for (int t = best + 1; t <= p.nteam; ++t) p.g0[t] += 1;
+    ++used;
+  }
+  return true;
+}
+
 // One launch sequence for the problems idx[0..np) of a batch (their vectors fit).
 static sky_status tri_group(Ctx* c, int np, const int* idx, const double2* const* A, const int* n,
                             double* const* w, double2* const* Z, const int* run, int run_stride,
@@ -829,35 +1007,91 @@ static sky_status tri_group(Ctx* c, int np, const int* idx, const double2* const
     if (n[b] > nmax) nmax = n[b];
   }
   if (ntot == 0) return SKY_OK;
-  const int G = (int)(ntot < c->num_sms ? ntot : c->num_sms);
-  // shared memory: three work vectors per problem (in global memory for a
-  // problem whose vectors alone exceed it), then own columns while they fit
+  int G = (int)(ntot < c->num_sms ? ntot : c->num_sms);
   size_t used = 0;
-  int maxown = 0;
-  for (int q = 0; q < np; ++q) {
-    if (gvec[idx[q]]) {
-      a.voff[q] = -1;
-    } else {
-      a.voff[q] = (int)used;
-      used += 3 * (size_t)a.n[q];
-    }
-    maxown += (a.n[q] + G - 1) / G;
-  }
   a.gvec = c->d_trivec;
   a.gvec_stride = 3 * (size_t)c->tri_m;
-  a.coff = (int)used;
-  used += (size_t)(maxown + 1) / 2;
-  int rot = 0;
-  for (int q = 0; q < np; ++q) {
-    const size_t need = (size_t)((a.n[q] + G - 1) / G) * a.n[q];
-    if ((used + need) * sizeof(double2) <= kTriSmemMax) {
-      a.soff[q] = (int)used;
-      used += need;
-    } else {
-      a.soff[q] = -1;
+  if (np > kTeamMin) {
+    // teams: the per-column partials first (one region for every team), then
+    // each team's work vectors and own columns while they fit
+    TeamPlan tp;
+    const size_t budget = kTriSmemMax / sizeof(double2);
+    G = c->num_sms;
+    if (!plan_teams(np, a.n, G, budget - 64, tp)) return SKY_EUNSUPPORTED;
+    G = tp.g0[tp.nteam];
+    a.nteam = tp.nteam;
+    size_t cmax = 0;
+    for (int t = 0; t <= tp.nteam; ++t) {
+      a.tp0[t] = tp.p0[t];
+      a.tg0[t] = tp.g0[t];
     }
-    a.rot[q] = rot;
-    rot = (rot + a.n[q]) % G;
+    for (int k = 0; k < np; ++k) a.tmem[k] = tp.mem[k];
+    for (int t = 0; t < tp.nteam; ++t) {
+      const int g = tp.g0[t + 1] - tp.g0[t];
+      size_t own = 0;
+      for (int k = tp.p0[t]; k < tp.p0[t + 1]; ++k) own += (a.n[tp.mem[k]] + g - 1) / g;
+      cmax = own > cmax ? own : cmax;
+    }
+    a.coff = 0;
+    const size_t base = (cmax + 1) / 2 + 1;
+    used = base;
+    for (int t = 0; t < tp.nteam; ++t) {
+      const int g = tp.g0[t + 1] - tp.g0[t];
+      size_t u = base;
+      for (int k = tp.p0[t]; k < tp.p0[t + 1]; ++k) {
+        const int q = tp.mem[k];
+        if (gvec[idx[q]]) return SKY_EUNSUPPORTED;
+        a.voff[q] = (int)u;
+        u += 3 * (size_t)a.n[q];
+        a.rot[q] = 0;
+      }
+      if (u > budget) return SKY_EUNSUPPORTED;
+      for (int k = tp.p0[t]; k < tp.p0[t + 1]; ++k) {
+        const int q = tp.mem[k];
+        const size_t need = (size_t)((a.n[q] + g - 1) / g) * a.n[q];
+        if (u + need <= budget) {
+          a.soff[q] = (int)u;
+          u += need;
+        } else {
+          a.soff[q] = -1;
+        }
+      }
+      used = u > used ? u : used;
+    }
+    a.tbar = c->d_tbar;
+  } else {
+    // one team of all blocks.  Shared memory: three work vectors per problem
+    // (in global memory for a problem whose vectors alone exceed it), then own
+    // columns while they fit
+    int maxown = 0;
+    for (int q = 0; q < np; ++q) {
+      if (gvec[idx[q]]) {
+        a.voff[q] = -1;
+      } else {
+        a.voff[q] = (int)used;
+        used += 3 * (size_t)a.n[q];
+      }
+      maxown += (a.n[q] + G - 1) / G;
+    }
+    a.coff = (int)used;
+    used += (size_t)(maxown + 1) / 2;
+    int rot = 0;
+    for (int q = 0; q < np; ++q) {
+      const size_t need = (size_t)((a.n[q] + G - 1) / G) * a.n[q];
+      if ((used + need) * sizeof(double2) <= kTriSmemMax) {
+        a.soff[q] = (int)used;
+        used += need;
+      } else {
+        a.soff[q] = -1;
+      }
+      a.rot[q] = rot;
+      rot = (rot + a.n[q]) % G;
+    }
+    a.nteam = 1;
+    a.tp0[0] = 0; a.tp0[1] = np;
+    a.tg0[0] = 0; a.tg0[1] = G;
+    for (int q = 0; q < np; ++q) a.tmem[q] = q;
+    a.tbar = c->d_bar;
   }
   const int zstride = nmax + (nmax & 1);
   int back_warps = kBackWarps;
@@ -874,7 +1108,7 @@ static sky_status tri_group(Ctx* c, int np, const int* idx, const double2* const
     if (!ident) return SKY_EUNSUPPORTED;
   }
   cudaError_t e;
-  k_tri_reset<<<1, 1, 0, c->stream>>>(c->d_bar);
+  k_tri_reset<<<1, a.nteam, 0, c->stream>>>(a.tbar);
   note_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(c, e, "tridiagonal reset");
   void* args[] = {&a};
@@ -908,6 +1142,15 @@ sky_status eigh_batch_tri(Ctx* c, int np, const double2* const* A, const int* n,
   int ng = 0;
   size_t used = 0;
   groups[0] = 0;
+  if (np > kTeamMin) {
+    // one launch sequence, the blocks split into teams (tri_group)
+    for (int b = 0; b < np; ++b) {
+      gvec[b] = false;
+      order[b] = b;
+      if (tri_vectors_global(n[b]) || n[b] > c->tri_m) return SKY_EUNSUPPORTED;
+    }
+    return tri_group(c, np, order, A, n, w, Z, run, run_stride, gvec);
+  }
   // work vectors in global memory for problems too large for shared memory,
   // and, when the global buffer has room, for the largest problems until the
   // whole batch fits one launch sequence (a device-gated batch must: it

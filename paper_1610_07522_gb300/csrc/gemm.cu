@@ -279,6 +279,9 @@ static void launch_zgemm(Ctx* c, const ZJobs& j, int nmax) {
 }
 
 sky_status zgemm_batch(Ctx* c, const ZJobs& jin) {
+  // a batch of many problems: every product in one grouped tensor-core launch
+  // sequence (oz_zgemm_group), when its buffers hold them
+  if (jin.np > kOzGroupMin && oz_zgemm_group_fits(c, jin.np, jin.n)) return oz_zgemm_group(c, jin);
   // problems of kOzZgemmMin states or more: tensor-core digit-split products
   // (one launch sequence each, gated like the rest); the others in one
   // batched FP64 launch

@@ -194,6 +194,71 @@ __host__ __device__ inline void item_of(const OzArgs& a, int bnt, int t, int& m0
   if (nkb < 0) nkb = 0;
 }
 
+// Grouped products: np independent n x n complex products in one launch
+// (the many small problems of a batched eigensolve).  Problem b's operand
+// rows are stacked in the two maps (A rows ra[b] .. ra[b] + n - 1, B rows
+// rb[b] .. rb[b] + 2n - 1, K = 2n digits per row, zero beyond); its items
+// are the output tiles tile0[b] .. tile0[b+1] - 1 (one K range each); its
+// partials go to P + po[b], rows of 2n.  A tile that runs past the problem's
+// rows reads the next problem's rows, whose results are not stored.
+struct OzGroup {
+  int np;
+  int tile0[kMaxBatch + 1];
+  int n[kMaxBatch];
+  int ra[kMaxBatch];
+  int rb[kMaxBatch];
+  long long po[kMaxBatch];
+  const double2* A[kMaxBatch];
+  const double2* B[kMaxBatch];
+  double2* C[kMaxBatch];
+  const int* run[kMaxBatch];
+  const int* stop[kMaxBatch];
+};
+
+__host__ __device__ inline bool group_gated(const OzGroup& G, int b) {
+  return (G.run[b] && *G.run[b] == 0) || (G.stop[b] && *G.stop[b] != 0);
+}
+
+// One work item: global map rows m0 (A) and n0 (B), K blocks kb0 .. kb0 +
+// nkb - 1, output rows / columns from (mloc, nloc) within an M x N result
+// (of problem b in a grouped launch).
+struct OzItem {
+  int m0, n0, kb0, nkb, b, mloc, nloc, M, N;
+};
+
+template <bool GROUP>
+__device__ __forceinline__ bool item_at(const OzArgs& a, const OzGroup* G, int bnt, int t,
+                                        OzItem& it) {
+  if constexpr (GROUP) {
+    int lo = 0, hi = G->np - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (G->tile0[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int b = lo, n = G->n[b];
+    if (group_gated(*G, b)) return false;
+    const int mt = (n + BM - 1) / BM, tt = t - G->tile0[b];
+    const int mi = tt % mt, nj = tt / mt;
+    it.b = b;
+    it.mloc = mi * BM;
+    it.nloc = nj * bnt;
+    it.m0 = G->ra[b] + it.mloc;
+    it.n0 = G->rb[b] + it.nloc;
+    it.kb0 = 0;
+    it.nkb = (2 * n + BK - 1) / BK;
+    it.M = n;
+    it.N = 2 * n;
+  } else {
+    item_of(a, bnt, t, it.m0, it.n0, it.kb0, it.nkb);
+    it.b = t / a.ntiles;   // the K split
+    it.mloc = it.m0;
+    it.nloc = it.n0;
+    it.M = a.M;
+    it.N = a.N;
+  }
+  return true;
+}
+
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float y) {
   const float s = hi + y;
   const float bp = s - hi;
@@ -207,10 +272,9 @@ __device__ __forceinline__ double pow2d(int k) {
   return __longlong_as_double((long long)(1023 + k) << 52);
 }
 
-template <int S, int BNT>
-__global__ void __launch_bounds__(THREADS, 1)
-    k_oz_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
-              OzArgs a) {
+template <int S, int BNT, bool GROUP>
+__device__ __forceinline__ void oz_gemm_body(const CUtensorMap* pA, const CUtensorMap* pB,
+                                             const OzArgs& a, const OzGroup* grp) {
   if ((a.run && *a.run == 0) || (a.stop && *a.stop != 0)) return;   // uniform in the CTA
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((unsigned long long)smem_raw + 1023ull) & ~1023ull);
@@ -227,7 +291,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   unsigned long long* bars = (unsigned long long*)(base + STAGES * STAGE);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kMaxStages + 2 * kMaxS + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nitems = a.ntiles * a.nsplit;
+  const int nitems = GROUP ? grp->tile0[grp->np] : a.ntiles * a.nsplit;
   const uint32_t bar0 = smem_u32(bars);
   auto full = [&](int s) { return bar0 + 8u * s; };
   auto empty = [&](int s) { return bar0 + 8u * (kMaxStages + s); };
@@ -266,8 +330,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       long long g = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
-        int m0, n0, kb0, nkb;
-        item_of(a, BNT, t, m0, n0, kb0, nkb);
+        OzItem it;
+        if (!item_at<GROUP>(a, grp, BNT, t, it)) continue;
+        const int m0 = it.m0, n0 = it.n0, kb0 = it.kb0, nkb = it.nkb;
         for (int j = 0; j < nkb; ++j, ++g) {
           const int s = (int)(g % STAGES);
           const long long u = g / STAGES;
@@ -280,8 +345,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           mbar_expect_tx(full(s), STAGE);
           const int kc = (kb0 + j) * BK;
           for (int p = 0; p < S; ++p) {
-            tma_load_3d(sa + p * TILE_A, &mA, kc, m0, p, full(s));
-            tma_load_3d(sa + S * TILE_A + p * TILE_B, &mB, kc, n0, p, full(s));
+            tma_load_3d(sa + p * TILE_A, pA, kc, m0, p, full(s));
+            tma_load_3d(sa + S * TILE_A + p * TILE_B, pB, kc, n0, p, full(s));
           }
         }
       }
@@ -295,8 +360,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       long long gpos = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
-        int m0, n0, kb0, nkb;
-        item_of(a, BNT, t, m0, n0, kb0, nkb);
+        OzItem it;
+        if (!item_at<GROUP>(a, grp, BNT, t, it)) continue;
+        const int nkb = it.nkb;
         for (int j = 0; j < nkb && ok; ++j, ++gpos) {
           const int s = (int)(gpos % STAGES);
           const long long u = gpos / STAGES;
@@ -352,8 +418,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int g = 0; g < S; ++g) efl[g] = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < nitems && ok; t += gridDim.x) {
-      int m0, n0, kb0, nkb;
-      item_of(a, BNT, t, m0, n0, kb0, nkb);
+      OzItem it;
+      if (!item_at<GROUP>(a, grp, BNT, t, it)) continue;
+      const int nkb = it.nkb;
       float hi[HALF], lo[HALF];
 #pragma unroll
       for (int c = 0; c < HALF; ++c) hi[c] = lo[c] = 0.0f;
@@ -382,14 +449,15 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
       if (!ok) break;
-      const int row = m0 + q * 32 + lane;
-      const int col0 = n0 + half * HALF;
-      if (row < a.M) {
-        if (a.mode == 0) {
-          float2* prow = a.P + (long long)(t / a.ntiles) * a.sp + (long long)row * a.ldp;
+      const int row = it.mloc + q * 32 + lane;
+      const int col0 = it.nloc + half * HALF;
+      if (row < it.M) {
+        if (GROUP || a.mode == 0) {
+          float2* prow = GROUP ? a.P + grp->po[it.b] + (long long)row * it.N
+                               : a.P + (long long)it.b * a.sp + (long long)row * a.ldp;
 #pragma unroll
           for (int c = 0; c < HALF; ++c)
-            if (col0 + c < a.N) prow[col0 + c] = make_float2(hi[c], lo[c]);
+            if (col0 + c < it.N) prow[col0 + c] = make_float2(hi[c], lo[c]);
         } else {
           const int er = a.ea[row] - 16;
           if (a.out_f32) {
@@ -421,6 +489,20 @@ __global__ void __launch_bounds__(THREADS, 1)
                  "r"(TMEM_COLS)
                  : "memory");
   }
+}
+
+template <int S, int BNT>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_oz_gemm(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+              OzArgs a) {
+  oz_gemm_body<S, BNT, false>(&mA, &mB, a, nullptr);
+}
+
+template <int S, int BNT>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_oz_gemm_group(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+                    OzArgs a, const __grid_constant__ OzGroup grp) {
+  oz_gemm_body<S, BNT, true>(&mA, &mB, a, &grp);
 }
 
 template <int S, int BNT>
@@ -511,6 +593,40 @@ inline cudaError_t oz_gemm(const void* A, long long lda, long long sa, int M, co
   k_oz_gemm<S, BNT><<<grid, THREADS, smem_bytes<S, BNT>(), s>>>(ma, mb, g);
   note_launch();
   *splits = z;
+  return cudaGetLastError();
+}
+
+// Launch the grouped form over grp's problems: A holds rowsA stacked rows,
+// B rowsB, both of row stride ld (bf16 elements, a multiple of 8; each
+// problem's digits zero from K = 2n on), slice strides sa, sb.
+template <int S, int BNT>
+inline cudaError_t oz_gemm_group(const void* A, long long sa, int rowsA, const void* B,
+                                 long long sb, int rowsB, long long ld, const OzGroup& grp,
+                                 OzArgs g, cudaStream_t s) {
+  if (grp.np <= 0 || grp.tile0[grp.np] == 0) return cudaSuccess;
+  if ((ld & 7) || (sa & 7) || (sb & 7) || rowsA <= 0 || rowsB <= 0) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  cudaError_t e;
+  if ((e = make_map3(&ma, A, S, rowsA, (int)ld, ld, sa, BM)) != cudaSuccess) return e;
+  if ((e = make_map3(&mb, B, S, rowsB, (int)ld, ld, sb, BNT)) != cudaSuccess) return e;
+  static bool smem_set[64] = {false};
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!smem_set[dev]) {
+    e = cudaFuncSetAttribute(k_oz_gemm_group<S, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_bytes<S, BNT>());
+    if (e != cudaSuccess) return e;
+    smem_set[dev] = true;
+  }
+  int nsm = 0;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int items = grp.tile0[grp.np];
+  const int grid = items < nsm ? items : nsm;
+  g.mode = 0;
+  g.run = g.stop = nullptr;
+  k_oz_gemm_group<S, BNT><<<grid, THREADS, smem_bytes<S, BNT>(), s>>>(ma, mb, g, grp);
+  note_launch();
   return cudaGetLastError();
 }
 

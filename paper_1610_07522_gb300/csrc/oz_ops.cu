@@ -245,6 +245,64 @@ __global__ void k_oz_zgemm_reduce(const float2* __restrict__ P, int nz, long lon
   C[e] = make_double2(sc * re, -sc * im);
 }
 
+// Grouped form of the two kernels above (blockIdx.y = problem b of the
+// group; rows stacked at G.ra / G.rb, exponents indexed by stacked row).
+// Operand B (second) adds the (Im, -Re) rows n .. 2n - 1 of its problem.
+// Every row is written up to ld (zeros from K = 2n on), so a K block that
+// runs past 2n reads zeros.
+template <int S>
+__global__ void __launch_bounds__(256) k_oz_split_group(oz::OzGroup G, int second, int trans,
+                                                        int* E, unsigned short* dst, long long ld,
+                                                        long long ss) {
+  const int b = blockIdx.y, r = blockIdx.x;
+  const int n = G.n[b];
+  if (r >= n || oz::group_gated(G, b)) return;
+  const double2* __restrict__ src = second ? G.B[b] : G.A[b];
+  auto at = [&](int k) {
+    return trans ? conjx(src[(long long)k * n + r]) : src[(long long)r * n + k];
+  };
+  int m = INT_MIN;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double2 v = at(k);
+    m = max(m, max(exp_of(v.x), exp_of(v.y)));
+  }
+  m = block_max<double>(m);
+  const int Er = m == INT_MIN ? 0 : m;
+  const long long row = (second ? G.rb[b] : G.ra[b]) + r;
+  if (threadIdx.x == 0) E[row] = Er;
+  unsigned* d32 = reinterpret_cast<unsigned*>(dst);
+  const long long kh = ld / 2;   // complex entries per row, padding included
+  for (int k = threadIdx.x; k < kh; k += blockDim.x) {
+    unsigned short dr[S], di[S];
+    if (k < n) {
+      const double2 v = at(k);
+      digits<S>(v.x, Er, dr);
+      digits<S>(v.y, Er, di);
+    } else {
+#pragma unroll
+      for (int s = 0; s < S; ++s) dr[s] = di[s] = 0;
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      d32[(s * ss + row * ld) / 2 + k] = pack2(dr[s], di[s]);
+      if (second) d32[(s * ss + (row + n) * ld) / 2 + k] = pack2(di[s], neg_bf16(dr[s]));
+    }
+  }
+}
+
+__global__ void k_oz_reduce_group(const float2* __restrict__ P, oz::OzGroup G,
+                                  const int* __restrict__ Ea, const int* __restrict__ Eb) {
+  const int b = blockIdx.y, n = G.n[b];
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n || oz::group_gated(G, b)) return;
+  const int m = (int)(e / n), c = (int)(e % n);
+  const float2* Pm = P + G.po[b] + (long long)m * 2 * n;
+  const float2 r = Pm[c], i = Pm[n + c];
+  const double re = (double)r.x + (double)r.y, im = (double)i.x + (double)i.y;
+  const double sc = oz::pow2d(Ea[G.ra[b] + m] + Eb[G.rb[b] + c] - 16);
+  G.C[b][e] = make_double2(sc * re, -sc * im);
+}
+
 // X[a][b] (+)= dV 2^{Ea[a] + Eb[b] - 16} sum_z (P_z[a][b] + i P_z[a][I + b]) for a >= b
 // (each P entry an unevaluated pair hi + lo), mirrored.
 __global__ void k_oz_overlap_reduce(const float2* __restrict__ P, int nz, long long sp,
@@ -466,6 +524,65 @@ sky_status oz_zgemm(Ctx* c, bool ah, bool bh, const double2* A, const double2* B
                                                       run, stop);
   note_launch();
   return cuda_check(c, cudaGetLastError(), "oz zgemm reduce");
+}
+
+// The products C_b = opA(A_b) opB(B_b) of every problem of a batch (n_b <=
+// the context's state count) in one grouped launch sequence: two digit
+// splits, one tensor-core launch over all problems' tiles, one reduction
+// (the per-problem form above, stacked; gates per problem).
+int oz_group_slices() { return oz::kS64; }
+
+bool oz_zgemm_group_fits(const Ctx* c, int np, const int* n) {
+  if (!c->d_ozgA || np > c->ozg_np) return false;
+  long long rows = 0;
+  long long p = 0;
+  for (int b = 0; b < np; ++b) {
+    if (n[b] > c->max_states) return false;
+    rows += n[b];
+    p += 2LL * n[b] * n[b];
+  }
+  return rows <= c->ozg_rows && p <= (long long)c->ozg_p_elems;
+}
+
+sky_status oz_zgemm_group(Ctx* c, const ZJobs& j) {
+  constexpr int S = oz::kS64, BN = oz::kBN64;
+  cudaStream_t st = c->stream;
+  oz::OzGroup G;
+  G.np = j.np;
+  G.tile0[0] = 0;
+  int ra = 0, nmax = 0;
+  long long po = 0;
+  for (int b = 0; b < j.np; ++b) {
+    const int n = j.n[b];
+    G.n[b] = n; G.ra[b] = ra; G.rb[b] = 2 * ra; G.po[b] = po;
+    G.A[b] = j.A[b]; G.B[b] = j.B[b]; G.C[b] = j.C[b];
+    G.run[b] = j.run[b]; G.stop[b] = j.stop[b];
+    G.tile0[b + 1] = G.tile0[b] + (n > 0 ? ((n + oz::BM - 1) / oz::BM) * ((2 * n + BN - 1) / BN) : 0);
+    ra += n;
+    po += 2LL * n * n;
+    nmax = n > nmax ? n : nmax;
+  }
+  if (nmax == 0) return SKY_OK;
+  const long long ld = c->ozg_ld;
+  const long long sa = (long long)c->ozg_rows * ld, sb = 2 * sa;
+  int* Ea = c->d_ozgE;
+  int* Eb = c->d_ozgE + c->ozg_rows;
+  unsigned short* Ap = (unsigned short*)c->d_ozgA;
+  unsigned short* Bp = (unsigned short*)c->d_ozgB;
+  k_oz_split_group<S><<<dim3(nmax, j.np), 256, 0, st>>>(G, 0, j.ah ? 1 : 0, Ea, Ap, ld, sa);
+  k_oz_split_group<S><<<dim3(nmax, j.np), 256, 0, st>>>(G, 1, j.bh ? 0 : 1, Eb, Bp, ld, sb);
+  note_launch(2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(c, e, "grouped zgemm split");
+  oz::OzArgs g{};
+  g.P = c->d_ozgP;
+  g.status = c->d_status;
+  e = oz::oz_gemm_group<S, BN>(Ap, sa, ra, Bp, sb, 2 * ra, ld, G, g, st);
+  if (e != cudaSuccess) return cuda_check(c, e, "grouped zgemm");
+  k_oz_reduce_group<<<dim3(div_up((long long)nmax * nmax, 256), j.np), 256, 0, st>>>(
+      c->d_ozgP, G, Ea, Eb);
+  note_launch();
+  return cuda_check(c, cudaGetLastError(), "grouped zgemm reduce");
 }
 
 sky_status oz_overlap(Ctx* c, const void* a, const void* b, int I, double2* X) {

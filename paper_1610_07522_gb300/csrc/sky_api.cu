@@ -83,13 +83,13 @@ static void free_all(Ctx* c) {
                   c->d_ktdd[2], c->d_ktf[0], c->d_ktf[1],
                   c->d_ktf[2], c->d_kp[0], c->d_kp[1], c->d_kp[2], c->d_damp[0], c->d_damp[1],
                   c->d_coul, c->d_gscr, c->d_red, c->d_dpart, c->d_ftmp, c->d_fcx, c->d_gpart,
-                  c->d_eigA[0], c->d_eigA[1], c->d_eigV, c->d_eigw, c->d_eigpart, c->d_bar,
+                  c->d_eigA[0], c->d_eigA[1], c->d_eigV, c->d_eigw, c->d_eigpart, c->d_bar, c->d_tbar,
                   c->d_eigres, c->d_eigrot, c->d_small[0], c->d_small[1], c->d_small[2],
                   c->d_small[3], c->d_small[4], c->d_small[5], c->d_gate,
                   c->d_stats, c->d_tcA[0], c->d_tcA[1], c->d_tcA[2], c->d_tcB[0],
                   c->d_tcB[1], c->d_tcB[2], c->d_tcRotA[0], c->d_tcRotA[1], c->d_tcRotA[2],
                   c->d_tcPart, c->d_netpart, c->d_trid, c->d_ozA, c->d_ozB, c->d_ozE,
-                  c->d_ozP, c->d_trivec, c->d_dop[0], c->d_dop[1], c->d_dop[2],
+                  c->d_ozP, c->d_trivec, c->d_ozgA, c->d_ozgB, c->d_ozgP, c->d_ozgE, c->d_dop[0], c->d_dop[1], c->d_dop[2],
                   c->d_dope[0], c->d_dope[1], c->d_dope[2],
                   c->d_dft[0][0], c->d_dft[0][1], c->d_dft[1][0], c->d_dft[1][1],
                   c->d_dft[2][0], c->d_dft[2][1], c->d_dfte[0][0], c->d_dfte[0][1],
@@ -285,6 +285,7 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
   ALLOC(c->d_eigV, c->eig_slot * c->eig_batch);
   ALLOC(c->d_eigw, (2 * c->eig_slot_rot + 2) * c->eig_batch);
   ALLOC(c->d_bar, 2);
+  ALLOC(c->d_tbar, (size_t)32 * kMaxBatch);
   ALLOC(c->d_eigres, kMaxBatch);
   if (s == SKY_OK) {
     char* p = nullptr;
@@ -689,12 +690,51 @@ sky_status sky_reserve_batch(sky_ctx* c, int nb) {
       if (p) cudaFree(p);
     return s;
   }
+  // grouped I x I products for batches of many problems: digits of every
+  // problem's rows stacked (up to nb x Imax rows, capped at about 2 GiB)
+  void *ga = nullptr, *gb = nullptr;
+  float2* gp = nullptr;
+  int* ge = nullptr;
+  long long grows = 0, gld = 0;
+  size_t gpe = 0;
+  if (s == SKY_OK && nb > kOzGroupMin) {
+    gld = (2LL * Imax + 7) / 8 * 8;
+    const long long per_row = (long long)oz_group_slices() * 3 * gld * 2;   // A + B bytes
+    const long long cap = 2LL << 30;
+    grows = (long long)nb * Imax;
+    if (grows * per_row > cap) grows = cap / per_row;
+    gpe = (size_t)nb * 2 * (size_t)Imax * (size_t)Imax;
+    if (gpe * sizeof(float2) > (size_t)cap) gpe = (size_t)cap / sizeof(float2);
+    if (grows >= Imax) {
+      unsigned short *pa = nullptr, *pb = nullptr;
+      s = dalloc(c, &pa, (size_t)oz_group_slices() * grows * gld);
+      if (s == SKY_OK) s = dalloc(c, &pb, (size_t)oz_group_slices() * 2 * grows * gld);
+      if (s == SKY_OK) s = dalloc(c, &gp, gpe);
+      if (s == SKY_OK) s = dalloc(c, &ge, (size_t)3 * grows);
+      ga = pa;
+      gb = pb;
+      if (s != SKY_OK) {
+        void* ptrs[] = {a0, a1, v, w, rot, sm[0], sm[1], sm[2], sm[3], sm[4], sm[5], trid, tvec,
+                        ga, gb, gp, ge};
+        for (void* p : ptrs)
+          if (p) cudaFree(p);
+        return s;
+      }
+    }
+  }
   cudaStreamSynchronize(c->stream);   // no queued work may still use the old buffers
   void* old[] = {c->d_eigA[0], c->d_eigA[1], c->d_eigV, c->d_eigw, c->d_eigrot, c->d_small[0],
                  c->d_small[1], c->d_small[2], c->d_small[3], c->d_small[4], c->d_small[5],
                  c->d_trid, c->d_trivec};
   for (void* p : old)
     if (p) cudaFree(p);
+  if (ga) {
+    void* og[] = {c->d_ozgA, c->d_ozgB, c->d_ozgP, c->d_ozgE};
+    for (void* p : og)
+      if (p) cudaFree(p);
+    c->d_ozgA = ga; c->d_ozgB = gb; c->d_ozgP = gp; c->d_ozgE = ge;
+    c->ozg_rows = (int)grows; c->ozg_ld = gld; c->ozg_p_elems = gpe; c->ozg_np = nb;
+  }
   c->d_trivec = tvec;
   c->tri_vec_slots = tvec ? (nb < 8 ? nb : 8) : 0;
   c->d_eigA[0] = a0; c->d_eigA[1] = a1; c->d_eigV = v; c->d_eigw = w; c->d_eigrot = rot;

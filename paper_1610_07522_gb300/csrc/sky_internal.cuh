@@ -103,6 +103,7 @@ struct Ctx {
   double* d_eigw;                   // eigenvalues [m]
   double* d_eigpart;                // per-block partial norms
   unsigned* d_bar;                  // grid barrier {count, generation}
+  unsigned* d_tbar;                 // team barrier counters of the tridiagonal reduction
   int* d_eigres;                    // which ping-pong buffer holds each result [kMaxBatch]
   int eig_batch;                    // problems a batched eigensolve may hold
   size_t eig_slot;                  // elements per problem in d_eigA / d_eigV
@@ -140,6 +141,17 @@ struct Ctx {
   int* d_ozE;                       // row exponents
   float2* d_ozP;                    // split-K partials (hi, lo)
   size_t oz_a_elems, oz_b_elems, oz_p_elems;
+  // grouped I x I products of a batched eigensolve (oz_zgemm_group): digits of
+  // up to ozg_rows stacked rows (A; B twice as many) of row stride ozg_ld,
+  // partials, row exponents; allocated by sky_reserve_batch for batches of
+  // more than kOzGroupMin problems
+  void* d_ozgA;
+  void* d_ozgB;
+  float2* d_ozgP;
+  int* d_ozgE;
+  int ozg_rows, ozg_np;
+  long long ozg_ld;
+  size_t ozg_p_elems;
   char err[256];
 };
 
@@ -250,6 +262,10 @@ sky_status oz_rotate(Ctx* c, const void* phi, const double2* M, int I, void* out
 constexpr int kOzZgemmMin = 96;
 constexpr int kOzZgemmGated = 192;
 bool oz_zgemm_fits(const Ctx* c, int n);
+bool oz_zgemm_group_fits(const Ctx* c, int np, const int* n);
+sky_status oz_zgemm_group(Ctx* c, const ZJobs& j);
+int oz_group_slices();               // digits of the grouped products
+constexpr int kOzGroupMin = 8;      // batches of more problems take the grouped products
 sky_status oz_zgemm(Ctx* c, bool ah, bool bh, const double2* A, const double2* B, double2* C,
                     int n, const int* run, const int* stop);
 sky_status tc_rotate(Ctx* c, const void* phi, const double2* M, int I, void* out);

@@ -131,6 +131,65 @@ def test_batched_tridiagonal_route_uneven_sizes():
         _check(Hs[b], M[b].cpu().numpy(), lam[b].cpu().numpy(), f"batched b={b} n={sizes[b]}")
 
 
+def test_batched_tridiagonal_teams_many_uneven_problems():
+    """Forty problems of the sizes of the twist-averaged batch (both species of
+    16^3, 20^3 and 24^3 boxes, plus a few others) in one batched solve: more
+    than eight problems, so the reduction's blocks split into teams (several
+    blocks for a large problem, small ones sharing a block); the automatic
+    method must take the tridiagonal route, and every problem agrees with the
+    oracle."""
+    rng = np.random.default_rng(19)
+    sizes = [290, 125, 168, 72, 86, 37] * 6 + [300, 17, 64, 3]
+    kinds = ["random", "pairs", "degenerate"]
+    Hs = [_matrix(kinds[b % 3], n, rng) for b, n in enumerate(sizes)]
+    c = _ctx(300)
+    B.sky_reserve_batch(c, len(sizes))
+    B.sky_stats(c, reset=True)
+    dH = [_dev(h) for h in Hs]
+    dC = [_dev(np.eye(n, dtype=np.complex128)) for n in sizes]
+    M = [torch.zeros((n, n), dtype=torch.complex128, device="cuda:0") for n in sizes]
+    lam = [torch.zeros(n, dtype=torch.float64, device="cuda:0") for n in sizes]
+    B.sky_subspace_diag_batched(c, dH, dC, sizes, M, lam)
+    B.sky_sync(c)
+    st = B.sky_stats(c)
+    B.sky_destroy(c)
+    assert st["tridiagonal_solves"] == len(sizes) and st["jacobi_solves"] == 0
+    for b, n in enumerate(sizes):
+        _check(Hs[b], M[b].cpu().numpy(), lam[b].cpu().numpy(),
+               f"teams b={b} {kinds[b % 3]} n={n}")
+
+
+def test_gated_loewdin_many_problems_by_teams():
+    """Twelve overlaps, every third far from the identity: Newton-Schulz for
+    the others, the eigendecomposition route (gated on the device) for those,
+    all in one batched call whose tridiagonal launch runs only the gated
+    problems' teams; every factor against the oracle's S^{-1/2}."""
+    rng = np.random.default_rng(23)
+    sizes = [150, 90, 64, 120, 70, 100, 66, 130, 80, 96, 110, 75]
+    S = []
+    for b, n in enumerate(sizes):
+        if b % 3 == 0:
+            X = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+            S.append(X @ X.conj().T / n + 0.05 * np.eye(n))
+        else:
+            E = 1e-3 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+            S.append(np.eye(n) + 0.5 * (E + E.conj().T))
+    c = _ctx(150)
+    B.sky_reserve_batch(c, len(sizes))
+    B.sky_stats(c, reset=True)
+    dS = [_dev(s_) for s_ in S]
+    C = [torch.zeros((n, n), dtype=torch.complex128, device="cuda:0") for n in sizes]
+    B.sky_orthonormalize_batched(c, dS, sizes, C)
+    B.sky_sync(c)
+    st = B.sky_stats(c)
+    B.sky_destroy(c)
+    assert st["tridiagonal_solves"] == 4 and st["jacobi_solves"] == 0
+    for b in range(len(sizes)):
+        Cw = O.loewdin(S[b])
+        Cg = C[b].cpu().numpy()
+        assert np.max(np.abs(Cg - Cw)) < 1e-10 * np.max(np.abs(Cw)), b
+
+
 def test_loewdin_eigen_route_by_tridiagonal_solver():
     """An overlap far from the identity (S^{-1/2} from the eigendecomposition,
     Eq. Loewedin) at a size the tridiagonal route serves."""
