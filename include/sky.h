@@ -290,7 +290,12 @@ sky_status sky_set_prec(sky_ctx* ctx, sky_prec prec);
  *   SKY_KNOB_LINE_YZ        threads per block of the y/z FFT line passes: 32, 64, 128
  *   SKY_KNOB_LINE_X         lines per block of the x FFT line passes: 16, 32, 64
  *   SKY_KNOB_OVERLAP_WAVES  FMA overlap: K splits filling 1 or 2 waves of blocks
- *   SKY_KNOB_TC_WAVES       split-BF16 overlap: K splits filling 1, 2 or 4 waves of SMs
+ *   SKY_KNOB_TC_WAVES       split-BF16 overlap: K splits filling 1, 2 or 4 waves of SMs,
+ *                           or 0: the fewest splits the FP32 accumulation bound allows
+ *                           (2048 values of K each; for contexts that share the GPU with
+ *                           other boxes' work)
+ *   SKY_KNOB_TC_TILE_N      split-BF16 overlap and recombination GEMM tiles: 128 x 256
+ *                           (256), 128 x 128 (128) or 0 (default: 256 for x3 when N allows)
  *   SKY_KNOB_JACOBI_BLOCKS  blocks of the cooperative eigensolver: 1..JACOBI_BLOCKS_MAX
  *                           (until set: one per SM, two per SM for problems >= 512)
  *   SKY_KNOB_JACOBI_BLOCKS_MAX  (read only) co-resident blocks of that kernel
@@ -343,7 +348,8 @@ typedef enum {
   SKY_KNOB_JACOBI_MAX_SWEEPS = 7,
   SKY_KNOB_EIGEN_METHOD = 8,
   SKY_KNOB_SPLIT_GEMM = 9,
-  SKY_KNOB_LINE_ARITH = 10
+  SKY_KNOB_LINE_ARITH = 10,
+  SKY_KNOB_TC_TILE_N = 11
 } sky_knob;
 enum { SKY_EIG_AUTO = 0, SKY_EIG_JACOBI = 1, SKY_EIG_TRIDIAGONAL = 2 };
 sky_status sky_tune_set(sky_ctx* ctx, sky_knob knob, int value);

@@ -22,10 +22,14 @@ CANDIDATES = {
     B.SKY_KNOB_LINE_X: (16, 32, 64),
     B.SKY_KNOB_OVERLAP_WAVES: (1, 2),
     B.SKY_KNOB_TC_WAVES: (1, 2, 4),
+    B.SKY_KNOB_TC_TILE_N: (128, 256),
 }
+# boxes that share the GPU (a batch) may also take the fewest K splits
+BATCH_CANDIDATES = dict(CANDIDATES)
+BATCH_CANDIDATES[B.SKY_KNOB_TC_WAVES] = (0, 1, 2, 4)
 NAMES = {B.SKY_KNOB_LINE_YZ: "line_yz", B.SKY_KNOB_LINE_X: "line_x",
          B.SKY_KNOB_OVERLAP_WAVES: "overlap_waves", B.SKY_KNOB_TC_WAVES: "tc_waves",
-         B.SKY_KNOB_JACOBI_BLOCKS: "jacobi_blocks"}
+         B.SKY_KNOB_TC_TILE_N: "tc_tile_n", B.SKY_KNOB_JACOBI_BLOCKS: "jacobi_blocks"}
 TC_FORMS = (B.SKY_F32_BF16X3, B.SKY_F32_BF16X6)
 
 
@@ -77,8 +81,16 @@ def tune_box(solver, reps=5, cache=None):
     res = {}
     for knob in (B.SKY_KNOB_LINE_YZ, B.SKY_KNOB_LINE_X):
         res[NAMES[knob]] = _pick(ctx, knob, CANDIDATES[knob], h, st, reps)
-    knob = B.SKY_KNOB_TC_WAVES if solver.prec in TC_FORMS else B.SKY_KNOB_OVERLAP_WAVES
-    res[NAMES[knob]] = _pick(ctx, knob, CANDIDATES[knob], ov, st, reps)
+    if solver.prec in TC_FORMS:
+        rot = lambda: B.sky_rotate(ctx, solver.phi[q], solver.M[q], I, solver.h[q])
+        res[NAMES[B.SKY_KNOB_TC_TILE_N]] = _pick(ctx, B.SKY_KNOB_TC_TILE_N,
+                                                 CANDIDATES[B.SKY_KNOB_TC_TILE_N],
+                                                 lambda: (ov(), rot()), st, reps)
+        res[NAMES[B.SKY_KNOB_TC_WAVES]] = _pick(ctx, B.SKY_KNOB_TC_WAVES,
+                                                CANDIDATES[B.SKY_KNOB_TC_WAVES], ov, st, reps)
+    else:
+        knob = B.SKY_KNOB_OVERLAP_WAVES
+        res[NAMES[knob]] = _pick(ctx, knob, CANDIDATES[knob], ov, st, reps)
     torch.cuda.synchronize(solver.device)
     if cache:
         data = {}
@@ -106,21 +118,84 @@ def tune_eigensolver(eig_ctx, run_solve, stream, reps=3):
     return _pick(eig_ctx, B.SKY_KNOB_JACOBI_BLOCKS, values, run_solve, stream, reps)
 
 
+def _concurrent(boxes, main, fn):
+    """fn(box) for every box on its own stream, forked from and joined to
+    ``main`` (how the boxes of a batch run)."""
+    ev = torch.cuda.Event()
+    ev.record(main)
+    for s in boxes:
+        s.stream.wait_event(ev)
+        fn(s)
+    for s in boxes:
+        e = torch.cuda.Event()
+        e.record(s.stream)
+        main.wait_event(e)
+
+
+def _pick_batch(boxes, knob, values, fn, main, reps):
+    """Like _pick, with the knob set on every box of ``boxes`` and fn run on
+    all of them at once (each box on its own stream), timed on ``main``."""
+    times = {}
+    for v in values:
+        for s in boxes:
+            B.sky_tune_set(s.ctx, knob, v)
+        times[v] = _time(lambda: _concurrent(boxes, main, fn), main, reps)
+    best = min(times, key=times.get)
+    for s in boxes:
+        B.sky_tune_set(s.ctx, knob, best)
+    return best, times
+
+
 def tune_batch(bs, reps=5, cache=None):
-    """Tune a BatchSolver: the box knobs once per distinct box shape (grid,
-    particle numbers, precision), applied to every box of that shape, then the
-    shared eigensolver's block count on the whole batch (needs one iteration
-    done, so that its matrices are valid).  Returns the choices."""
+    """Tune a BatchSolver.  The boxes of one shape (grid, particle numbers,
+    precision) share their knobs, and each candidate is timed on all boxes of
+    that shape running together, each on its own stream, since that is how
+    they run in the batch: FFT line-pass block shapes on h psi, then for the
+    split-BF16 forms the GEMM tile width (128 x 128 or 128 x 256, on the
+    overlap and the recombination) and the overlap's K splits (down to the
+    fewest the accumulation bound allows), else the FMA overlap's splits.
+    The shared eigensolver's Jacobi block count is tuned only when the batch
+    takes the Jacobi route (needs one iteration done).  Returns the choices."""
     shapes = {}
     for s in bs.boxes:
         shapes.setdefault((tuple(s.w.grid), s.I, s.prec), []).append(s)
+    main = torch.cuda.current_stream(bs.device)
     out = {}
     for shape, boxes in shapes.items():
-        res = tune_box(boxes[0], reps, cache)
-        settings = {k: v[0] for k, v in res.items()}
-        for s in boxes[1:]:
-            apply(s.ctx, settings)
+        def q_of(s):
+            return 0 if s.I[0] >= s.I[1] else 1
+
+        def h(s):
+            q = q_of(s)
+            B.sky_apply_h(s.ctx, s.U[q], s.Bf[q], s.W[q], s.psi[q], s.h[q], s.I[q])
+
+        def ov(s):
+            q = q_of(s)
+            B.sky_overlap(s.ctx, s.psi[q], s.h[q], s.I[q], s.H[q])
+
+        def ovrot(s):
+            q = q_of(s)
+            B.sky_overlap(s.ctx, s.psi[q], s.h[q], s.I[q], s.H[q])
+            B.sky_rotate(s.ctx, s.phi[q], s.M[q], s.I[q], s.h[q])
+
+        res = {}
+        for knob in (B.SKY_KNOB_LINE_YZ, B.SKY_KNOB_LINE_X):
+            res[NAMES[knob]] = _pick_batch(boxes, knob, BATCH_CANDIDATES[knob], h, main, reps)
+        if boxes[0].prec in TC_FORMS:
+            res[NAMES[B.SKY_KNOB_TC_TILE_N]] = _pick_batch(
+                boxes, B.SKY_KNOB_TC_TILE_N, BATCH_CANDIDATES[B.SKY_KNOB_TC_TILE_N], ovrot, main, reps)
+            res[NAMES[B.SKY_KNOB_TC_WAVES]] = _pick_batch(
+                boxes, B.SKY_KNOB_TC_WAVES, BATCH_CANDIDATES[B.SKY_KNOB_TC_WAVES], ov, main, reps)
+        else:
+            knob = B.SKY_KNOB_OVERLAP_WAVES
+            res[NAMES[knob]] = _pick_batch(boxes, knob, BATCH_CANDIDATES[knob], ov, main, reps)
         out[str(shape)] = res
-    main = torch.cuda.current_stream(bs.device)
-    out["jacobi_blocks"] = tune_eigensolver(bs.eig, bs.eigensolve, main, reps=max(1, reps // 2))
+    torch.cuda.synchronize(bs.device)
+    B.sky_stats(bs.eig, reset=True)
+    bs.eigensolve()
+    torch.cuda.synchronize(bs.device)
+    if B.sky_stats(bs.eig)["jacobi_solves"] > 0:
+        out["jacobi_blocks"] = tune_eigensolver(bs.eig, bs.eigensolve, main, reps=max(1, reps // 2))
+    else:
+        out["eigensolver"] = ("tridiagonal, teams", None)
     return out

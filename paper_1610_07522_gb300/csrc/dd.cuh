@@ -154,6 +154,33 @@ __device__ __forceinline__ double dbl_of(dd a) {
   return __longlong_as_double(hd | sgn);
 }
 __device__ __forceinline__ ddc ddc_of(double2 v) { return ddc{dd_of(v.x), dd_of(v.y)}; }
+
+// A sum of products of floats in a float pair (the FP32 forms' reductions):
+// a b = p + e exactly (e from an FMA); p joins the high part by TwoSum and
+// both errors collect in the low part, so each term costs a few FP32
+// operations instead of FP64 ones, about 2^-48 of the running sum per term.
+struct AccF {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+  }
+  // sign * Re(conj(a) d) and sign * Im(conj(a) d) (sign +-1: exact)
+  __device__ __forceinline__ void re_cj(float sg, float2 a, float2 d) {
+    add_prod(a.x, sg * d.x);
+    add_prod(a.y, sg * d.y);
+  }
+  __device__ __forceinline__ void im_cj(float sg, float2 a, float2 d) {
+    add_prod(a.x, sg * d.y);
+    add_prod(a.y, -sg * d.x);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 __device__ __forceinline__ double2 dbl2_of(ddc v) { return make_double2(dbl_of(v.x), dbl_of(v.y)); }
 
 }  // namespace sky

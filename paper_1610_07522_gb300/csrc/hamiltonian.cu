@@ -249,13 +249,30 @@ __global__ void __launch_bounds__(kRedBlock) k_h_sum(const cx<T>* __restrict__ p
                                                      double* part, int nblk, int state0) {
   const long long base = (long long)blockIdx.y * 2 * G;
   double e = 0.0, n2 = 0.0;
-  for (int p = blockIdx.x * kRedBlock + threadIdx.x; p < 2 * G; p += nblk * kRedBlock) {
-    const long long o = base + p;
-    const cx<T> h = hpsi[o] + g0[o] + g1[o] + g2[o];
-    hpsi[o] = h;
-    const double2 hd = to_d2(h), pd = to_d2(psi[o]);
-    e += pd.x * hd.x + pd.y * hd.y;
-    n2 += hd.x * hd.x + hd.y * hd.y;
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32 arrays: exact products summed in float pairs (AccF), FP32 pipe
+    AccF ae, an;
+    for (int p = blockIdx.x * kRedBlock + threadIdx.x; p < 2 * G; p += nblk * kRedBlock) {
+      const long long o = base + p;
+      const cx<T> h = hpsi[o] + g0[o] + g1[o] + g2[o];
+      hpsi[o] = h;
+      const cx<T> ps = psi[o];
+      ae.add_prod(ps.x, h.x);
+      ae.add_prod(ps.y, h.y);
+      an.add_prod(h.x, h.x);
+      an.add_prod(h.y, h.y);
+    }
+    e = ae.value();
+    n2 = an.value();
+  } else {
+    for (int p = blockIdx.x * kRedBlock + threadIdx.x; p < 2 * G; p += nblk * kRedBlock) {
+      const long long o = base + p;
+      const cx<T> h = hpsi[o] + g0[o] + g1[o] + g2[o];
+      hpsi[o] = h;
+      const double2 hd = to_d2(h), pd = to_d2(psi[o]);
+      e += pd.x * hd.x + pd.y * hd.y;
+      n2 += hd.x * hd.x + hd.y * hd.y;
+    }
   }
   block_sum2(e, n2);
   if (threadIdx.x == 0) {
@@ -409,6 +426,38 @@ __global__ void __launch_bounds__(128) k_dens_accum(const cx<T>* __restrict__ ps
   const int s_end = (s_beg + per_split) < ns ? (s_beg + per_split) : ns;
   double rho = 0, tau = 0, jx = 0, jy = 0, jz = 0;
   const cx<T>* gs[3] = {g0, g1, g2};
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32 arrays: every product exact as a float pair, the sums in float
+    // pairs (AccF) on the FP32 pipe; the same terms as the FP64 loop below,
+    // with X(s, t, j) = conj(a_s) d_t along j:
+    //   Im M_xj = Im X(0,1,j) + Im X(1,0,j), Im M_yj = Re X(1,0,j) - Re X(0,1,j),
+    //   Im M_zj = Im X(0,0,j) - Im X(1,1,j)
+    AccF r, ta, ax, ay, az;
+    for (int s = s_beg; s < s_end; ++s) {
+      const long long o0 = (long long)s * 2 * G + p, o1 = o0 + G;
+      const float2 a0 = psi[o0], a1 = psi[o1];
+      r.add_prod(a0.x, a0.x); r.add_prod(a0.y, a0.y);
+      r.add_prod(a1.x, a1.x); r.add_prod(a1.y, a1.y);
+      float2 d0[3], d1[3];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        d0[j] = gs[j][o0];
+        d1[j] = gs[j][o1];
+        ta.add_prod(d0[j].x, d0[j].x); ta.add_prod(d0[j].y, d0[j].y);
+        ta.add_prod(d1[j].x, d1[j].x); ta.add_prod(d1[j].y, d1[j].y);
+      }
+      // J_x = Im M_zy - Im M_yz
+      ax.im_cj(1.0f, a0, d0[1]); ax.im_cj(-1.0f, a1, d1[1]);
+      ax.re_cj(-1.0f, a1, d0[2]); ax.re_cj(1.0f, a0, d1[2]);
+      // J_y = Im M_xz - Im M_zx
+      ay.im_cj(1.0f, a0, d1[2]); ay.im_cj(1.0f, a1, d0[2]);
+      ay.im_cj(-1.0f, a0, d0[0]); ay.im_cj(1.0f, a1, d1[0]);
+      // J_z = Im M_yx - Im M_xy
+      az.re_cj(1.0f, a1, d0[0]); az.re_cj(-1.0f, a0, d1[0]);
+      az.im_cj(-1.0f, a0, d1[1]); az.im_cj(-1.0f, a1, d0[1]);
+    }
+    rho = r.value(); tau = ta.value(); jx = ax.value(); jy = ay.value(); jz = az.value();
+  } else {
   for (int s = s_beg; s < s_end; ++s) {
     const long long o0 = (long long)s * 2 * G + p, o1 = o0 + G;
     const double2 a0 = to_d2(psi[o0]), a1 = to_d2(psi[o1]);
@@ -427,6 +476,7 @@ __global__ void __launch_bounds__(128) k_dens_accum(const cx<T>* __restrict__ ps
     jx += imz[1] - imy[2];
     jy += imx[2] - imz[0];
     jz += imy[0] - imx[1];
+  }
   }
   double* dst = part + (long long)blockIdx.y * 5 * G;
   dst[p] = rho;

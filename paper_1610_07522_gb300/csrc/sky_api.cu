@@ -603,8 +603,12 @@ sky_status sky_tune_set(sky_ctx* c, sky_knob knob, int value) {
       c->ov_waves = value;
       return SKY_OK;
     case SKY_KNOB_TC_WAVES:
-      if (value != 1 && value != 2 && value != 4) break;
+      if (value != 0 && value != 1 && value != 2 && value != 4) break;
       c->tc_waves = value;
+      return SKY_OK;
+    case SKY_KNOB_TC_TILE_N:
+      if (value != 0 && value != 128 && value != 256) break;
+      c->tc_tile_n = value;
       return SKY_OK;
     case SKY_KNOB_JACOBI_BLOCKS:
       if (value < 1 || value > c->eig_grid_max) break;
@@ -653,6 +657,7 @@ int sky_tune_get(const sky_ctx* c, sky_knob knob) {
     case SKY_KNOB_LINE_X: return c->line_x;
     case SKY_KNOB_OVERLAP_WAVES: return c->ov_waves;
     case SKY_KNOB_TC_WAVES: return c->tc_waves;
+    case SKY_KNOB_TC_TILE_N: return c->tc_tile_n;
     case SKY_KNOB_JACOBI_BLOCKS: return c->eig_grid;
     case SKY_KNOB_JACOBI_BLOCKS_MAX: return c->eig_grid_max;
     case SKY_KNOB_WAIT_SPINS: return (int)(c->wait_spins / 1000);

@@ -119,6 +119,7 @@ struct Ctx {
   long long wait_spins;             // spin budget of the eigensolver's grid-barrier waits
   int jac_max_sweeps;               // Jacobi sweeps before SKY_ENOCONV
   int tc_waves;                     // K-split waves of the tensor-core overlap (tunable)
+  int tc_tile_n;                    // N width of the split-BF16 GEMM tiles: 0 auto, 128, 256
   double2* d_small[6];              // I x I temporaries
   void* d_tcA[3];                   // split-BF16 operand pieces (tensor-core forms)
   void* d_tcB[3];

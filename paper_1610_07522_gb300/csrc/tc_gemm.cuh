@@ -382,14 +382,15 @@ inline Phases phases_for_split(int nsplit) {
 inline cudaError_t gemm_bf16(const void* const* A, long long lda, const void* const* B,
                              long long ldb, int nsplit, int M, int N, int K, int* splits,
                              float* D, long long ldd, long long sstride, int* status,
-                             cudaStream_t s) {
+                             cudaStream_t s, int tile_n = 0) {
   if (M <= 0 || N <= 0 || K <= 0) { *splits = 0; return cudaSuccess; }
   // TMA needs 16-byte row strides; columns past K read as zeros
   if ((lda & 7) || (ldb & 7) || (ldd & 3) || lda < K || ldb < K || nsplit < 1 || nsplit > 3)
     return cudaErrorInvalidValue;
   // 128 x 256 tiles when the pieces of one K block still fit twice in the ring
-  // (x3: 96 KiB per stage), else 128 x 128 (x6: 96 KiB per stage)
-  const int bnt = (nsplit <= 2 && (long long)N >= 256) ? 256 : 128;
+  // (x3: 96 KiB per stage), else 128 x 128 (x6: 96 KiB per stage); tile_n
+  // 128 asks for the narrow tiles (more tiles, for products that share the GPU)
+  const int bnt = (nsplit <= 2 && (long long)N >= 256 && tile_n != 128) ? 256 : 128;
   CUtensorMap ma[3], mb[3];
   cudaError_t e;
   for (int i = 0; i < 3; ++i) {

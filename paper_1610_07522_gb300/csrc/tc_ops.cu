@@ -186,6 +186,8 @@ sky_status tc_overlap(Ctx* c, const void* a, const void* b, int I, double2* X) {
   if (e != cudaSuccess) return cuda_check(c, e, "tc split");
   const long long ldd = (2LL * I + 3) / 4 * 4;
   const int tiles = ((I + tc::BM - 1) / tc::BM) * ((2 * I + tc::BN - 1) / tc::BN);
+  // tc_waves 0: the fewest splits the accumulation bound allows (for boxes
+  // that share the GPU with others), else about that many waves of SMs
   int z = c->tc_waves * c->num_sms / tiles;
   if (z < tc_min_splits(K)) z = tc_min_splits(K);   // bounded FP32 accumulation length
   if (z < 1) z = 1;
@@ -194,7 +196,7 @@ sky_status tc_overlap(Ctx* c, const void* a, const void* b, int I, double2* X) {
   const void* pa[3] = {A[0], A[1], A[2]};
   const void* pb[3] = {Bp[0], Bp[1], Bp[2]};
   e = tc::gemm_bf16(pa, K, pb, K, n, I, 2 * I, (int)K, &z, c->d_tcPart, ldd, sstride,
-                    c->d_status, c->stream);
+                    c->d_status, c->stream, c->tc_tile_n);
   if (e != cudaSuccess) return cuda_check(c, e, "tc overlap gemm");
   k_tc_overlap_reduce<<<div_up((long long)I * I, 256), 256, 0, c->stream>>>(
       c->d_tcPart, z, sstride, ldd, I, c->dV, X);
@@ -223,7 +225,7 @@ sky_status tc_rotate(Ctx* c, const void* phi, const double2* M, int I, void* out
   const void* pa[3] = {Ra[0], Ra[1], Ra[2]};
   const void* pb[3] = {Bp[0], Bp[1], Bp[2]};
   e = tc::gemm_bf16(pa, ldk, pb, ldk, n, I, (int)K2V, 2 * Ipad, &z, (float*)out, K2V, 0,
-                    c->d_status, c->stream);
+                    c->d_status, c->stream, c->tc_tile_n);
   return cuda_check(c, e, "tc rotate gemm");
 }
 

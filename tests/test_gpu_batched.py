@@ -120,6 +120,46 @@ def test_batched_boxes_match_single_boxes_and_oracle():
     bs.close()
 
 
+def test_batch_of_many_problems_matches_single_boxes():
+    """Five boxes (ten species problems, the largest of 66 states): more than
+    eight problems with one of 64 states or more, so the shared eigensolve
+    takes the tridiagonal route with its blocks in teams and every I x I
+    product of the batch in one grouped tensor-core launch; each box against
+    the same box iterated alone (two problems, one team, per-problem
+    products) over three iterations of the FP64 form."""
+    ws = [IN.Workload(name=f"many_{i}", grid=g, dx=(1.0, 1.0, 1.0), N=n, Z=z,
+                      twist=tw, init="blobs", seed=90 + i)
+          for i, (g, n, z, tw) in enumerate([
+              ((12, 12, 12), 66, 30, (0.4, -1.2, 2.0)),
+              ((8, 8, 8), 20, 9, (1.1, 0.3, -0.6)),
+              ((12, 12, 12), 40, 17, (-2.5, 0.9, 0.2)),
+              ((8, 8, 8), 14, 6, (0.0, 0.0, 0.0)),
+              ((12, 12, 12), 52, 22, (2.9, -0.1, -1.7))])]
+    bs = BatchSolver(ws, prec=B.SKY_F64)
+    bs.load()
+    singles = []
+    for w in ws:
+        s = Solver(w, prec=B.SKY_F64)
+        inp = IN.make_inputs(w)
+        s.load(inp["psi0"], inp.get("rho0"), inp.get("tau0"))
+        singles.append(s)
+    B.sky_stats(bs.eig, reset=True)
+    for k in range(3):
+        bs.step_eager()
+        for s in singles:
+            s.step()
+        en = bs.energies()
+        for b, s in enumerate(singles):
+            E, _, _ = s.energy()
+            assert abs(en[b][0] - E) <= 1e-10 * abs(E), (k, b)
+            assert np.max(np.abs(host(bs.boxes[b].lam) - host(s.lam))) < 1e-9, (k, b)
+    st = B.sky_stats(bs.eig)
+    assert st["jacobi_solves"] == 0 and st["tridiagonal_solves"] >= 3 * len(bs.problems)
+    for s in singles:
+        s.close()
+    bs.close()
+
+
 @pytest.mark.parametrize("prec", [B.SKY_F64, B.SKY_F32_BF16X3])
 def test_graph_replay_equals_eager_iteration(prec):
     ws = _boxes()
@@ -151,7 +191,8 @@ def test_tunable_knobs_keep_the_results():
     ctx = B.sky_init((12, 16, 20), (1.0, 1.0, 1.0), P, False, (0.3, -0.8, 1.7), B.SKY_F64, 40,
                      torch.cuda.current_stream().cuda_stream)
     for knob, bad in ((B.SKY_KNOB_LINE_YZ, 96), (B.SKY_KNOB_LINE_X, 128), (B.SKY_KNOB_OVERLAP_WAVES, 3),
-                      (B.SKY_KNOB_TC_WAVES, 3), (B.SKY_KNOB_JACOBI_BLOCKS, 0)):
+                      (B.SKY_KNOB_TC_WAVES, 3), (B.SKY_KNOB_TC_TILE_N, 64),
+                      (B.SKY_KNOB_JACOBI_BLOCKS, 0)):
         with pytest.raises(B.SkyError):
             B.sky_tune_set(ctx, knob, bad)
     assert 1 <= B.sky_tune_get(ctx, B.SKY_KNOB_JACOBI_BLOCKS) <= B.sky_tune_get(ctx, B.SKY_KNOB_JACOBI_BLOCKS_MAX)
@@ -199,10 +240,10 @@ def test_autotuned_graph_batch_matches_untuned():
     a.step_eager()
     b.step_eager()
     res = b.tune(reps=2)
-    assert "jacobi_blocks" in res
+    assert "jacobi_blocks" in res or "eigensolver" in res
     for box in b.boxes:
-        assert B.sky_tune_get(box.ctx, B.SKY_KNOB_LINE_YZ) in autotune.CANDIDATES[B.SKY_KNOB_LINE_YZ]
-        assert B.sky_tune_get(box.ctx, B.SKY_KNOB_TC_WAVES) in autotune.CANDIDATES[B.SKY_KNOB_TC_WAVES]
+        for knob in (B.SKY_KNOB_LINE_YZ, B.SKY_KNOB_TC_WAVES, B.SKY_KNOB_TC_TILE_N):
+            assert B.sky_tune_get(box.ctx, knob) in autotune.BATCH_CANDIDATES[knob]
     b.capture()
     for _ in range(3):
         a.step_eager()
