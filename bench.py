@@ -790,6 +790,35 @@ def call_rooflines(events, grid, prec, peaks, csize):
     return out
 
 
+def probe_batched(args):
+    """One eager iteration of the 64-box batched form (after loading, two
+    iterations and the batch autotuner), inside the NVTX range "probe", for
+    an ncu launch list of exactly that iteration (ncu --nvtx --nvtx-include
+    "probe/")."""
+    import torch
+    from paper_1610_07522_gb300 import binding as B
+    from paper_1610_07522_gb300 import inputs as IN
+    from paper_1610_07522_gb300.batched import BatchSolver
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    bs = BatchSolver(IN.batched_workloads(64), prec=FORMS[args.form], device=dev)
+    bs.load()
+    bs.step_eager()
+    bs.step_eager()
+    bs.tune(reps=2)
+    bs.step_eager()
+    torch.cuda.synchronize(dev)
+    n0 = B.sky_kernel_launches()
+    torch.cuda.nvtx.range_push("probe")
+    bs.step_eager()
+    torch.cuda.synchronize(dev)
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"probe_call": "batched", "form": args.form, "instances": len(bs.boxes),
+                      "launches": B.sky_kernel_launches() - n0}))
+    bs.close()
+    return 0
+
+
 def probe_call(args):
     """One library call on the workload's shapes (random states), for an ncu
     capture of exactly that call's kernels; prints the number of library
@@ -797,6 +826,8 @@ def probe_call(args):
     import torch
     from paper_1610_07522_gb300 import binding as B
     from paper_1610_07522_gb300 import inputs as IN
+    if args.probe_call == "batched":
+        return probe_batched(args)
     w = IN.WORKLOADS[args.workload]
     prec = FORMS[args.form]
     torch.cuda.set_device(0)
@@ -1118,7 +1149,7 @@ def main():
                     help="skip the time-dependent stepping leg")
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the time-to-convergence comparison of the forms")
-    ap.add_argument("--probe-call", default=None, choices=["apply_h", "overlap", "rotate", "ritz"],
+    ap.add_argument("--probe-call", default=None, choices=["apply_h", "overlap", "rotate", "ritz", "batched"],
                     help="run one library call on the workload's shapes and exit (for ncu)")
     ap.add_argument("--line-arith", type=int, default=None, choices=[0, 1],
                     help="--probe-call only: FP64 form's derivative line passes in FP64 (0) "

@@ -296,6 +296,12 @@ sky_status sky_set_prec(sky_ctx* ctx, sky_prec prec);
  *                           other boxes' work)
  *   SKY_KNOB_TC_TILE_N      split-BF16 overlap and recombination GEMM tiles: 128 x 256
  *                           (256), 128 x 128 (128) or 0 (default: 256 for x3 when N allows)
+ *   SKY_KNOB_FUSED_H        FP32 forms with every axis length in {8, 12, 16, 20, 24, 32}:
+ *                           1 applies h psi in one pass per axis (each line's derivative,
+ *                           spin-orbit and flux terms and the flux derivative in registers,
+ *                           h psi read and written once per pass), 0 the general gradient /
+ *                           local / divergence passes; default 1 when every axis is at most
+ *                           24, else 0
  *   SKY_KNOB_JACOBI_BLOCKS  blocks of the cooperative eigensolver: 1..JACOBI_BLOCKS_MAX
  *                           (until set: one per SM, two per SM for problems >= 512)
  *   SKY_KNOB_JACOBI_BLOCKS_MAX  (read only) co-resident blocks of that kernel
@@ -349,7 +355,8 @@ typedef enum {
   SKY_KNOB_EIGEN_METHOD = 8,
   SKY_KNOB_SPLIT_GEMM = 9,
   SKY_KNOB_LINE_ARITH = 10,
-  SKY_KNOB_TC_TILE_N = 11
+  SKY_KNOB_TC_TILE_N = 11,
+  SKY_KNOB_FUSED_H = 12
 } sky_knob;
 enum { SKY_EIG_AUTO = 0, SKY_EIG_JACOBI = 1, SKY_EIG_TRIDIAGONAL = 2 };
 sky_status sky_tune_set(sky_ctx* ctx, sky_knob knob, int value);

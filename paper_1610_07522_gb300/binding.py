@@ -20,7 +20,7 @@ SKY_F64, SKY_F32, SKY_F32_BF16X3, SKY_F32_BF16X6 = 0, 1, 2, 3
 (SKY_KNOB_LINE_YZ, SKY_KNOB_LINE_X, SKY_KNOB_OVERLAP_WAVES, SKY_KNOB_TC_WAVES,
  SKY_KNOB_JACOBI_BLOCKS, SKY_KNOB_JACOBI_BLOCKS_MAX, SKY_KNOB_WAIT_SPINS,
  SKY_KNOB_JACOBI_MAX_SWEEPS, SKY_KNOB_EIGEN_METHOD, SKY_KNOB_SPLIT_GEMM,
- SKY_KNOB_LINE_ARITH, SKY_KNOB_TC_TILE_N) = range(12)
+ SKY_KNOB_LINE_ARITH, SKY_KNOB_TC_TILE_N, SKY_KNOB_FUSED_H) = range(13)
 SKY_EIG_AUTO, SKY_EIG_JACOBI, SKY_EIG_TRIDIAGONAL = range(3)
 
 _P = ctypes.c_void_p

@@ -296,6 +296,312 @@ __global__ void k_state_totals(const double* part, int nblk, int I, double dV,
   if (hn2) hn2[s] = dV * b;
 }
 
+// ------------------------------------------------------------ fused FP32 h psi
+// For FP32 arrays with every axis length up to 32, one pass per axis j
+// computes that axis's whole share of h psi for a line of both spin
+// components of one state:
+//   G = d_j psi (the line in registers: forward transform, x i(k + theta/L)/N,
+//   inverse), then point by point L_j = -(i/2) A_j G and F_j = -B G - (i/2)
+//   A_j psi (F in place of G), then D_j = d_j F_j, and h psi += L_j + D_j
+//   (h psi = U psi + L_x + D_x in the first pass);
+// the last pass also forms <psi|h psi> and |h psi|^2.  The sum of the three
+// passes is the rearranged h psi of the general path (identical terms, other
+// rounding order), with h psi read and written once per pass and psi read
+// once, instead of the gradient, local and divergence passes that write and
+// re-read three scratch arrays.  States go in chunks whose psi and h psi stay
+// in L2 across the passes.  Fields as floats (one conversion per call).
+constexpr int kHaxLinesX = 32;      // lines per block along x (staged in shared memory)
+constexpr int kHaxMaxN = 32;        // longest axis of the fused path
+constexpr double kHaxL2Bytes = 48.0 * 1024 * 1024;   // psi + h psi of one chunk
+
+struct HFields {
+  const float* u;
+  const float* b;
+  const float* w;   // wx, wy, wz at w, w + G, w + 2 G
+};
+
+__global__ void k_fields_f32(const double* __restrict__ U, const double* __restrict__ B,
+                             const double* __restrict__ W, int G, float* out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= G) return;
+  out[p] = (float)U[p];
+  out[G + p] = (float)B[p];
+  out[2 * G + p] = (float)W[p];
+  out[3 * G + p] = (float)W[G + p];
+  out[4 * G + p] = (float)W[2 * G + p];
+}
+
+// d_j of a line in place: forward transform, x i k_m / N, inverse.
+template <int N>
+__device__ __forceinline__ void deriv_line(float2 (&v)[N], const float* __restrict__ kt,
+                                           float inv_n) {
+  Fft<float, N, false>::run(v);
+#pragma unroll
+  for (int m = 0; m < N; ++m) {
+    const float kk = __ldg(kt + m) * inv_n;
+    v[m] = make_float2(-kk * v[m].y, kk * v[m].x);
+  }
+  Fft<float, N, true>::run(v);
+}
+
+// Point idx of the line: a = psi (both components), g = d_j psi -> F_j;
+// returns L_j = -(i/2) A_j G in l0, l1.
+template <int AXIS>
+__device__ __forceinline__ void h_point(const HFields& f, int G, int idx, float2 a0, float2 a1,
+                                        float2& g0, float2& g1, float2& l0, float2& l1) {
+  const float bb = __ldg(f.b + idx);
+  const float wx = __ldg(f.w + idx), wy = __ldg(f.w + G + idx), wz = __ldg(f.w + 2 * G + idx);
+  float2 t0, t1;
+  apply_A<float>(AXIS, wx, wy, wz, g0, g1, t0, t1);     // A_j G_j
+  l0 = 0.5f * mul_mi(t0);
+  l1 = 0.5f * mul_mi(t1);
+  apply_A<float>(AXIS, wx, wy, wz, a0, a1, t0, t1);     // A_j psi
+  g0 = (-bb) * g0 + 0.5f * mul_mi(t0);                  // F_j = -B G_j - (i/2) A_j psi
+  g1 = (-bb) * g1 + 0.5f * mul_mi(t1);
+}
+
+// x pass (first): h psi = U psi + L_x + D_x.  A block stages nl <= kHaxLinesX
+// consecutive x lines of both components of state blockIdx.y through shared
+// memory (coalesced loads and stores; rows padded to N + 1).  One component's
+// line at a time is transformed in registers; G, then F, of both components
+// wait in gs[m][c][thread].
+template <int N>
+__global__ void __launch_bounds__(kHaxLinesX) k_h_axis_x(const float2* __restrict__ psi,
+                                                         float2* __restrict__ hpsi, HFields f,
+                                                         const float* __restrict__ kt,
+                                                         float inv_n, int G, int rows) {
+  __shared__ float2 tile[2][kHaxLinesX][N + 1];
+  __shared__ float2 gs[N][2][kHaxLinesX];
+  const int l0 = blockIdx.x * kHaxLinesX;
+  const int nl = rows - l0 < kHaxLinesX ? rows - l0 : kHaxLinesX;
+  const long long sb = (long long)blockIdx.y * 2 * G;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 2 * nl * N; e += kHaxLinesX) {
+    const int c = e / (nl * N), r = e - c * nl * N;
+    const int ll = r / N, m = r - ll * N;
+    tile[c][ll][m] = psi[sb + (long long)c * G + (long long)(l0 + ll) * N + m];
+  }
+  __syncthreads();
+  if (tid < nl) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float2 v[N];
+#pragma unroll
+      for (int m = 0; m < N; ++m) v[m] = tile[c][tid][m];
+      deriv_line<N>(v, kt, inv_n);
+#pragma unroll
+      for (int m = 0; m < N; ++m) gs[m][c][tid] = v[m];
+    }
+    const int base = (l0 + tid) * N;
+#pragma unroll 4
+    for (int m = 0; m < N; ++m) {
+      const float2 a0 = tile[0][tid][m], a1 = tile[1][tid][m];
+      float2 g0 = gs[m][0][tid], g1 = gs[m][1][tid], L0, L1;
+      h_point<0>(f, G, base + m, a0, a1, g0, g1, L0, L1);
+      gs[m][0][tid] = g0;
+      gs[m][1][tid] = g1;
+      const float u = __ldg(f.u + base + m);
+      tile[0][tid][m] = u * a0 + L0;
+      tile[1][tid][m] = u * a1 + L1;
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float2 v[N];
+#pragma unroll
+      for (int m = 0; m < N; ++m) v[m] = gs[m][c][tid];
+      deriv_line<N>(v, kt, inv_n);
+#pragma unroll
+      for (int m = 0; m < N; ++m) tile[c][tid][m] = tile[c][tid][m] + v[m];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < 2 * nl * N; e += kHaxLinesX) {
+    const int c = e / (nl * N), r = e - c * nl * N;
+    const int ll = r / N, m = r - ll * N;
+    hpsi[sb + (long long)c * G + (long long)(l0 + ll) * N + m] = tile[c][ll][m];
+  }
+}
+
+// Threads (lines) per block of the y / z pass: two shared arrays of N x 2
+// values per thread (32 KiB at most).
+__host__ __device__ constexpr int hax_threads(int N) { return N <= 16 ? 64 : 32; }
+
+// y (AXIS 1) or z (AXIS 2) pass: one thread per line (consecutive threads on
+// consecutive x: coalesced).  The line's G, then F, of both components wait in
+// gs[m][c][thread] while one component's line is transformed in registers;
+// L_j waits in ls.  Loads never follow a store to global memory within a
+// phase (the pointwise phase stores to shared memory only; the last phase
+// loads a component's old h psi values before storing any), so each thread's
+// loads overlap instead of forming a chain of round trips.  The z pass (LAST)
+// also adds this block's <psi|h psi> and |h psi|^2 (float-pair sums of exact
+// products) to part[(state0 + state) * nblk + block].
+template <int N, int AXIS, bool LAST>
+__global__ void __launch_bounds__(hax_threads(N)) k_h_axis_yz(const float2* __restrict__ psi,
+                                                              float2* __restrict__ hpsi,
+                                                              HFields f,
+                                                              const float* __restrict__ kt,
+                                                              float inv_n, int nx, int ny, int G,
+                                                              int lines, double* part, int nblk,
+                                                              int state0) {
+  constexpr int T = hax_threads(N);
+  __shared__ float2 gs[N][2][T];
+  __shared__ float2 ls[N][2][T];
+  const int tid = threadIdx.x;
+  const int l = blockIdx.x * T + tid;
+  const long long sb = (long long)blockIdx.y * 2 * G;
+  const float2* __restrict__ p0 = psi + sb;
+  float2* __restrict__ h0 = hpsi + sb;
+  const float* __restrict__ fb = f.b;
+  const float* __restrict__ fw = f.w;
+  AccF ae, an;
+  if (l < lines) {
+    const int x = l % nx, t = l / nx;
+    const int base = AXIS == 1 ? t * ny * nx + x : t * nx + x;
+    const int stride = AXIS == 1 ? nx : nx * ny;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float2 v[N];
+#pragma unroll
+      for (int m = 0; m < N; ++m) v[m] = p0[(long long)c * G + base + m * stride];
+      deriv_line<N>(v, kt, inv_n);
+#pragma unroll
+      for (int m = 0; m < N; ++m) gs[m][c][tid] = v[m];
+    }
+#pragma unroll 8
+    for (int m = 0; m < N; ++m) {
+      const int idx = base + m * stride;
+      const float2 a0 = p0[idx], a1 = p0[G + idx];
+      const float bb = fb[idx];
+      const float wx = fw[idx], wy = fw[G + idx], wz = fw[2 * G + idx];
+      float2 g0 = gs[m][0][tid], g1 = gs[m][1][tid], t0, t1;
+      apply_A<float>(AXIS, wx, wy, wz, g0, g1, t0, t1);     // A_j G_j
+      ls[m][0][tid] = 0.5f * mul_mi(t0);                     // L_j = -(i/2) A_j G_j
+      ls[m][1][tid] = 0.5f * mul_mi(t1);
+      apply_A<float>(AXIS, wx, wy, wz, a0, a1, t0, t1);     // A_j psi
+      gs[m][0][tid] = (-bb) * g0 + 0.5f * mul_mi(t0);       // F_j = -B G_j - (i/2) A_j psi
+      gs[m][1][tid] = (-bb) * g1 + 0.5f * mul_mi(t1);
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float2 v[N];
+#pragma unroll
+      for (int m = 0; m < N; ++m) v[m] = gs[m][c][tid];
+      deriv_line<N>(v, kt, inv_n);
+      float2 hv[N];
+#pragma unroll
+      for (int m = 0; m < N; ++m) hv[m] = h0[(long long)c * G + base + m * stride];
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        v[m] = hv[m] + ls[m][c][tid] + v[m];
+        h0[(long long)c * G + base + m * stride] = v[m];
+      }
+      if constexpr (LAST) {
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          const float2 a = p0[(long long)c * G + base + m * stride];
+          ae.add_prod(a.x, v[m].x);
+          ae.add_prod(a.y, v[m].y);
+          an.add_prod(v[m].x, v[m].x);
+          an.add_prod(v[m].y, v[m].y);
+        }
+      }
+    }
+  }
+  if constexpr (LAST) {
+    __shared__ double red[2][T / 32];
+    double e = ae.value(), n2 = an.value();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_down_sync(0xffffffffu, e, o);
+      n2 += __shfl_down_sync(0xffffffffu, n2, o);
+    }
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = e;
+      red[1][tid >> 5] = n2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double se = 0.0, sn = 0.0;
+      for (int w = 0; w < T / 32; ++w) {
+        se += red[0][w];
+        sn += red[1][w];
+      }
+      double* dst = part + ((long long)(state0 + blockIdx.y) * nblk + blockIdx.x) * 2;
+      dst[0] = se;
+      dst[1] = sn;
+    }
+  }
+}
+
+bool fused_h_ok(const Ctx* c) {
+  if (!c->d_hf) return false;
+  if (c->prec == SKY_F64) return false;
+  for (int j = 0; j < 3; ++j) {
+    const int n = c->n[j];
+    if (n != 8 && n != 12 && n != 16 && n != 20 && n != 24 && n != 32) return false;
+  }
+  return true;
+}
+int fused_h_blocks(const Ctx* c) {
+  return (int)div_up((long long)c->n[0] * c->n[1], c->n[2] <= 16 ? 64 : 32);
+}
+
+// The three passes over states s0 .. s0 + ns - 1 (ps, hs: their arrays).
+static cudaError_t fused_h_chunk(Ctx* c, const float2* ps, float2* hs, const HFields& f, int ns,
+                                 int s0, int nblk) {
+  const int nx = c->n[0], ny = c->n[1], nz = c->n[2], G = (int)c->G;
+  cudaError_t e = dispatch_n<false>(nx, [&](auto Nc) -> cudaError_t {
+    constexpr int N = decltype(Nc)::value;
+    k_h_axis_x<N><<<dim3(div_up(ny * nz, kHaxLinesX), ns), kHaxLinesX, 0, c->stream>>>(
+        ps, hs, f, c->d_ktf[0], 1.0f / nx, G, ny * nz);
+    return cudaGetLastError();
+  });
+  if (e != cudaSuccess) return e;
+  e = dispatch_n<false>(ny, [&](auto Nc) -> cudaError_t {
+    constexpr int N = decltype(Nc)::value;
+    constexpr int T = hax_threads(N);
+    k_h_axis_yz<N, 1, false><<<dim3(div_up(nx * nz, T), ns), T, 0, c->stream>>>(
+        ps, hs, f, c->d_ktf[1], 1.0f / ny, nx, ny, G, nx * nz, nullptr, 0, 0);
+    return cudaGetLastError();
+  });
+  if (e != cudaSuccess) return e;
+  e = dispatch_n<false>(nz, [&](auto Nc) -> cudaError_t {
+    constexpr int N = decltype(Nc)::value;
+    k_h_axis_yz<N, 2, true><<<dim3(nblk, ns), hax_threads(N), 0, c->stream>>>(
+        ps, hs, f, c->d_ktf[2], 1.0f / nz, nx, ny, G, nx * ny, c->d_red, nblk, s0);
+    return cudaGetLastError();
+  });
+  note_launch(3);
+  return e;
+}
+
+static sky_status apply_h_fused(Ctx* c, const double* U, const double* B, const double* W,
+                                const float2* psi, float2* hpsi, int I, double* eps, double* hn2) {
+  const long long G = c->G, V = 2 * G;
+  float* ff = c->d_hf;   // U, B, W as floats
+  k_fields_f32<<<div_up(G, 256), 256, 0, c->stream>>>(U, B, W, (int)G, ff);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(c, e, "fused h psi fields");
+  const HFields f{ff, ff + G, ff + 2 * G};
+  const int nblk = fused_h_blocks(c);
+  long long chunk = (long long)(kHaxL2Bytes / (2.0 * V * sizeof(float2)));
+  if (chunk < 1) chunk = 1;
+  for (int s0 = 0; s0 < I; s0 += (int)chunk) {
+    const int ns = (I - s0) < chunk ? (I - s0) : (int)chunk;
+    const float2* ps = psi + (long long)s0 * V;
+    float2* hs = hpsi + (long long)s0 * V;
+    e = fused_h_chunk(c, ps, hs, f, ns, s0, nblk);
+    if (e != cudaSuccess) return cuda_check(c, e, "fused h psi");
+  }
+  if (eps || hn2) {
+    k_state_totals<<<div_up(I, 128), 128, 0, c->stream>>>(c->d_red, nblk, I, c->dV, eps, hn2);
+    note_launch();
+    return cuda_check(c, cudaGetLastError(), "fused h psi totals");
+  }
+  return SKY_OK;
+}
+
 template <typename T>
 static sky_status apply_h_t(Ctx* c, const double* U, const double* B, const double* W,
                             const cx<T>* psi, cx<T>* hpsi, int I, double* eps, double* hn2) {
@@ -340,6 +646,8 @@ sky_status apply_h_impl(Ctx* c, const double* U, const double* B, const double* 
                         const void* psi, void* hpsi, int I, double* eps, double* hn2) {
   if (c->prec == SKY_F64)
     return apply_h_t<double>(c, U, B, W, (const double2*)psi, (double2*)hpsi, I, eps, hn2);
+  if (c->fused_h && fused_h_ok(c))
+    return apply_h_fused(c, U, B, W, (const float2*)psi, (float2*)hpsi, I, eps, hn2);
   return apply_h_t<float>(c, U, B, W, (const float2*)psi, (float2*)hpsi, I, eps, hn2);
 }
 

@@ -82,7 +82,7 @@ static void free_all(Ctx* c) {
   void* ptrs[] = {c->d_status, c->d_kt[0], c->d_kt[1], c->d_kt[2], c->d_ktdd[0], c->d_ktdd[1],
                   c->d_ktdd[2], c->d_ktf[0], c->d_ktf[1],
                   c->d_ktf[2], c->d_kp[0], c->d_kp[1], c->d_kp[2], c->d_damp[0], c->d_damp[1],
-                  c->d_coul, c->d_gscr, c->d_red, c->d_dpart, c->d_ftmp, c->d_fcx, c->d_gpart,
+                  c->d_coul, c->d_gscr, c->d_red, c->d_dpart, c->d_ftmp, c->d_fcx, c->d_hf, c->d_gpart,
                   c->d_eigA[0], c->d_eigA[1], c->d_eigV, c->d_eigw, c->d_eigpart, c->d_bar, c->d_tbar,
                   c->d_eigres, c->d_eigrot, c->d_small[0], c->d_small[1], c->d_small[2],
                   c->d_small[3], c->d_small[4], c->d_small[5], c->d_gate,
@@ -270,7 +270,20 @@ sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const 
     if (e != cudaSuccess) { cudaGetLastError(); s = set_err(c, SKY_ENOMEM, "scratch allocation failed"); }
     c->d_gscr = p;
   }
-  ALLOC(c->d_red, (size_t)Imax * c->red_nblk * 2);
+  {
+    // per-state reduction partials of h psi: the general path's blocks or the
+    // fused FP32 path's (one per 32 lines along z at most)
+    const long long fz = ((long long)grid[0] * grid[1] + 31) / 32;
+    const long long nb = fz > c->red_nblk ? fz : c->red_nblk;
+    ALLOC(c->d_red, (size_t)Imax * nb * 2);
+  }
+  if (prec != SKY_F64) {
+    // fused h psi by default up to axis length 24 (measured faster there on
+    // GB300: 16^3 1.6x, 24^3 1.3x); at 32 its per-line state limits the warps
+    // per SM and the general passes are faster (the knob still selects it)
+    ALLOC(c->d_hf, (size_t)5 * G);
+    c->fused_h = grid[0] <= 24 && grid[1] <= 24 && grid[2] <= 24 ? 1 : 0;
+  }
   ALLOC(c->d_dpart, (size_t)kDensSplits * 5 * G);
   ALLOC(c->d_ftmp, (size_t)16 * G);
   ALLOC(c->d_fcx, G);
@@ -610,6 +623,11 @@ sky_status sky_tune_set(sky_ctx* c, sky_knob knob, int value) {
       if (value != 0 && value != 128 && value != 256) break;
       c->tc_tile_n = value;
       return SKY_OK;
+    case SKY_KNOB_FUSED_H:
+      if (value != 0 && value != 1) break;
+      if (value == 1 && !fused_h_ok(c)) break;
+      c->fused_h = value;
+      return SKY_OK;
     case SKY_KNOB_JACOBI_BLOCKS:
       if (value < 1 || value > c->eig_grid_max) break;
       c->eig_grid = value;
@@ -658,6 +676,7 @@ int sky_tune_get(const sky_ctx* c, sky_knob knob) {
     case SKY_KNOB_OVERLAP_WAVES: return c->ov_waves;
     case SKY_KNOB_TC_WAVES: return c->tc_waves;
     case SKY_KNOB_TC_TILE_N: return c->tc_tile_n;
+    case SKY_KNOB_FUSED_H: return c->fused_h && fused_h_ok(c) ? 1 : 0;
     case SKY_KNOB_JACOBI_BLOCKS: return c->eig_grid;
     case SKY_KNOB_JACOBI_BLOCKS_MAX: return c->eig_grid_max;
     case SKY_KNOB_WAIT_SPINS: return (int)(c->wait_spins / 1000);

@@ -95,6 +95,8 @@ struct Ctx {
   double* d_dpart;                  // density partials [kDensSplits][5][G]
   double* d_ftmp;                   // field temporaries [16][G]
   double2* d_fcx;                   // complex field scratch [G]
+  float* d_hf;                      // FP32 forms: U, B, W of one species as floats [5][G]
+  int fused_h;                      // FP32 forms: one fused pass per axis for h psi (tunable)
   double2* d_gpart;                 // split-K partials of sky_overlap
   size_t gpart_elems;
   int ov_slots;                     // resident CTAs of the overlap kernel
@@ -265,7 +267,9 @@ constexpr int kOzZgemmGated = 192;
 bool oz_zgemm_fits(const Ctx* c, int n);
 bool oz_zgemm_group_fits(const Ctx* c, int np, const int* n);
 sky_status oz_zgemm_group(Ctx* c, const ZJobs& j);
-int oz_group_slices();               // digits of the grouped products
+int oz_group_slices();
+bool fused_h_ok(const Ctx* c);      // the fused FP32 h psi applies to this context
+int fused_h_blocks(const Ctx* c);   // its reduction blocks per state               // digits of the grouped products
 constexpr int kOzGroupMin = 8;      // batches of more problems take the grouped products
 sky_status oz_zgemm(Ctx* c, bool ah, bool bh, const double2* A, const double2* B, double2* C,
                     int n, const int* run, const int* stop);

@@ -407,6 +407,42 @@ def test_fp32_apply_h_damped_densities(case):
         assert relerr(host(J), Jw.ravel()) < REL32
 
 
+@pytest.mark.parametrize("grid,twist,I", [((12, 16, 20), (0.3, -0.8, 1.7), 37),
+                                           ((24, 24, 24), (0.0, 0.0, 0.0), 5),
+                                           ((32, 8, 12), (-2.1, 0.4, 3.0), 9)])
+def test_fp32_fused_h_matches_general_path_and_oracle(grid, twist, I):
+    """The FP32 forms' h psi in one fused pass per axis (the default for axis
+    lengths up to 32) against the general gradient / local / divergence
+    passes (knob 0) and the oracle, with <psi|h psi> and |h psi|^2; uneven
+    axes and twists, so that every axis has its own transform length and
+    wavenumbers."""
+    rng = np.random.default_rng(23 + I)
+    with Ctx(grid, twist=twist, prec=B.SKY_F32, max_states=I) as c:
+        g = c.grid
+        psi = _r32(IN.random_spinors(g.n, I, rng))
+        U, Bf, W = _fields(g, rng)
+        want = O.apply_h(psi, U, Bf, W, g)
+        e_w, n_w = O.sp_energies(psi, want, g)
+        assert B.sky_tune_get(c.ctx, B.SKY_KNOB_FUSED_H) == (1 if max(grid) <= 24 else 0)
+        out = {}
+        for fused in (1, 0):
+            B.sky_tune_set(c.ctx, B.SKY_KNOB_FUSED_H, fused)
+            assert B.sky_tune_get(c.ctx, B.SKY_KNOB_FUSED_H) == fused
+            d_h = torch.zeros(psi.shape, dtype=torch.complex64, device="cuda:0")
+            eps = torch.zeros(I, dtype=torch.float64, device="cuda:0")
+            hn2 = torch.zeros(I, dtype=torch.float64, device="cuda:0")
+            B.sky_apply_h(c.ctx, dev(U), dev(Bf), dev(W), dev32(psi), d_h, I, eps, hn2)
+            out[fused] = host(d_h)
+            assert relerr(out[fused], want) < REL32, fused
+            assert relerr(host(eps), e_w) < REL32, fused
+            assert relerr(host(hn2), n_w) < REL32, fused
+        assert relerr(out[1], out[0]) < REL32
+    with Ctx((64, 48, 16), prec=B.SKY_F32, max_states=2) as c64:
+        assert B.sky_tune_get(c64.ctx, B.SKY_KNOB_FUSED_H) == 0   # axes beyond 32: general path
+        with pytest.raises(B.SkyError):
+            B.sky_tune_set(c64.ctx, B.SKY_KNOB_FUSED_H, 1)
+
+
 def test_fp32_overlap_and_rotate():
     rng = np.random.default_rng(22)
     with Ctx((32, 32, 32), prec=B.SKY_F32, max_states=70) as c:
