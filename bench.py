@@ -592,6 +592,7 @@ def batched_leg(dev, form="bf16x3", count=64, steps=10):
     replayed as one CUDA graph.  Compared with the same boxes stepped one at a
     time (each box's own solver) and with the eager (not captured) batch."""
     import torch
+    from paper_1610_07522_gb300 import binding as B
     from paper_1610_07522_gb300 import inputs as IN
     from paper_1610_07522_gb300.batched import BatchSolver
 
@@ -615,18 +616,28 @@ def batched_leg(dev, form="bf16x3", count=64, steps=10):
     tuned = bs.tune(reps=3)
     bs.step_eager()
     eager_ms = timed(bs.step_eager, 3)
+    bs.capture()
+    for _ in range(3):
+        bs.step()
+    graph_ms = timed(bs.step, steps)
+    try:
+        bs.sync()
+        status = "ok"
+    except B.SkyError as e:
+        status = str(e)
 
+    # last: the same boxes one at a time (each its own two-problem eigensolve);
+    # timed after the batch numbers, since a captured batch graph replayed after
+    # the boxes were stepped alone has been seen to go non-finite (not yet
+    # explained; eager-only sequences stay finite)
     def one_at_a_time():
         for s in bs.boxes:
             s.step()
             torch.cuda.synchronize(dev)
     seq_ms = timed(one_at_a_time, 2)
-    bs.capture()
-    for _ in range(3):
-        bs.step()
-    graph_ms = timed(bs.step, steps)
     out = {"instances": count, "form": form, "grids": sorted({w.grid[0] for w in ws}),
            "units_per_step": bs.units, "graph_ms_per_step": graph_ms, "eager_ms_per_step": eager_ms,
+           "status_after_graph_steps": status,
            "one_box_at_a_time_ms_per_step": seq_ms,
            "value": bs.units / (graph_ms / 1e3), "unit": "spinor-applies/s",
            "launches_per_step": bs.launches_per_step,
