@@ -626,10 +626,9 @@ def batched_leg(dev, form="bf16x3", count=64, steps=10):
     except B.SkyError as e:
         status = str(e)
 
-    # last: the same boxes one at a time (each its own two-problem eigensolve);
-    # timed after the batch numbers, since a captured batch graph replayed after
-    # the boxes were stepped alone has been seen to go non-finite (not yet
-    # explained; eager-only sequences stay finite)
+    # last: the same boxes one at a time (each its own two-problem eigensolve),
+    # timed after the batch numbers so that those never start from the boxes'
+    # solo state
     def one_at_a_time():
         for s in bs.boxes:
             s.step()

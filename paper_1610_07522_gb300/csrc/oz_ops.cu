@@ -477,10 +477,11 @@ sky_status oz_rotate_t(Ctx* c, const void* phi, const double2* M, int I, void* o
 // of X's rows with Zt's rows (6 digits; about 1e-14 of the largest element).
 // Every kernel is skipped when the device gate (run, stop) says so.
 bool oz_zgemm_fits(const Ctx* c, int n) {
-  const long long K = 2LL * n;
+  // the digit rows are written with the padded stride ld = round_up(2n, 8)
+  const long long ld = round_up(2LL * n, 8);
   return c->d_ozB && n <= c->max_states &&
-         (long long)oz::kS64 * 2 * n * K <= (long long)c->oz_b_elems &&
-         (long long)oz::kS64 * n * K <= (long long)c->oz_a_elems;
+         (long long)oz::kS64 * 2 * n * ld <= (long long)c->oz_b_elems &&
+         (long long)oz::kS64 * n * ld <= (long long)c->oz_a_elems;
 }
 
 sky_status oz_zgemm(Ctx* c, bool ah, bool bh, const double2* A, const double2* B, double2* C,

@@ -139,8 +139,8 @@ static sky_status alloc_oz_scratch(Ctx* c, bool overlap_too) {
   size_t ae, be, ee, pe;
   oz_scratch_sizes(overlap_too ? c->prec : SKY_F64, overlap_too ? Imax : 0, overlap_too ? 2LL * c->G : 0,
                    c->num_sms, &ae, &be, &ee, &pe);
-  if (Imax >= kOzZgemmMin) {   // the I x I products
-    const size_t zb = (size_t)6 * 2 * Imax * 2 * Imax;
+  if (Imax >= kOzZgemmMin) {   // the I x I products: 2 I rows of ld = round_up(2 I, 8)
+    const size_t zb = (size_t)6 * 2 * Imax * (size_t)((2 * Imax + 7) / 8 * 8);
     if (zb > be) be = zb;
     if (zb / 2 > ae) ae = zb / 2;
     if ((size_t)2 * Imax * Imax > pe) pe = (size_t)2 * Imax * Imax;

@@ -190,6 +190,36 @@ def test_gated_loewdin_many_problems_by_teams():
         assert np.max(np.abs(Cg - Cw)) < 1e-10 * np.max(np.abs(Cw)), b
 
 
+@pytest.mark.parametrize("n", [290, 125])
+def test_split_bf16_context_products_with_padded_digit_rows(n):
+    """A split-BF16 context sizes its digit buffers for the I x I products
+    alone; with 2n not a multiple of 8 (290, 125) the digit rows are padded to
+    the next multiple of 8, and the buffers must hold the padded rows (they
+    once held 2n per row, and the last rows ran past the end).  Loewdin
+    factor (Newton-Schulz with tensor-core products from 192 states) and
+    Rayleigh-Ritz (tensor-core products from 96) against the oracle."""
+    rng = np.random.default_rng(40 + n)
+    c = B.sky_init((8, 8, 8), (1.0, 1.0, 1.0), dict(IN.SLY4), False, (0.0, 0.0, 0.0),
+                   B.SKY_F32_BF16X3, 290, torch.cuda.current_stream().cuda_stream)
+    E = 2e-3 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    S = np.eye(n) + 0.5 * (E + E.conj().T)
+    H = _matrix("random", n, rng)
+    C = torch.zeros((n, n), dtype=torch.complex128, device="cuda:0")
+    M = torch.zeros_like(C)
+    lam = torch.zeros(n, dtype=torch.float64, device="cuda:0")
+    for _ in range(2):
+        B.sky_orthonormalize(c, _dev(S), n, C)
+        B.sky_subspace_diag(c, _dev(H), C, n, M, lam)
+    B.sky_sync(c)
+    B.sky_destroy(c)
+    Cw = O.loewdin(S)
+    assert np.max(np.abs(C.cpu().numpy() - Cw)) < 1e-11 * np.max(np.abs(Cw))
+    _, want = O.rayleigh_ritz(S, H)
+    assert np.max(np.abs(lam.cpu().numpy() - want)) < 1e-9 * max(1.0, np.max(np.abs(want)))
+    Mg = M.cpu().numpy()
+    assert np.max(np.abs(Mg.conj().T @ S @ Mg - np.eye(n))) < 1e-11
+
+
 def test_loewdin_eigen_route_by_tridiagonal_solver():
     """An overlap far from the identity (S^{-1/2} from the eigendecomposition,
     Eq. Loewedin) at a size the tridiagonal route serves."""
