@@ -92,6 +92,18 @@ def test_binding_eigen_knob_matches_header():
                                                      binding.SKY_EIG_TRIDIAGONAL)
 
 
+def test_binding_knobs_match_header():
+    """Every tunable knob the header enumerates has the same value in the
+    binding (the knobs travel as plain ints across the C ABI)."""
+    from paper_1610_07522_gb300 import binding
+    src = open(os.path.join(ROOT, "include", "sky.h")).read()
+    body = re.search(r"typedef enum \{([^}]*)\} sky_knob;", src).group(1)
+    knobs = dict((k, int(v)) for k, v in re.findall(r"(SKY_KNOB_[A-Z0-9_]+)\s*=\s*(\d+)", body))
+    assert len(knobs) >= 13
+    for k, v in knobs.items():
+        assert getattr(binding, k) == v, k
+
+
 def test_solver_eigen_method_sets_every_context(monkeypatch):
     """Solver.set_eigen_method and bench.py --eigen set the knob once on each
     distinct context (host logic only: the contexts are stand-ins)."""
