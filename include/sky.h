@@ -124,6 +124,18 @@ int sky_supported_size(int n, sky_prec prec);
  * (all contexts); for launch accounting by callers. */
 unsigned long long sky_kernel_launches(void);
 
+/* The team split the batched tridiagonal eigensolver uses for a batch of more
+ * than 8 problems (Sec. 3.3.2; the blocks of its cooperative Householder
+ * reduction split into teams with their own barriers): np problems of n[b]
+ * states on `blocks` blocks (the GPU's SM count).  Writes team[b] (the team of
+ * problem b), first[t] and count[t] (team t's blocks, contiguous, in order)
+ * and returns the number of teams; 0 when the batch cannot be split (a
+ * problem's work vectors exceed shared memory: the solver then takes Jacobi)
+ * or an argument is invalid (np outside [1, 128], blocks < 1, n[b] < 1, null
+ * pointers).  team holds np entries, first and count np each (at most np
+ * teams).  Host only: needs no GPU and no context. */
+int sky_tri_team_plan(int np, const int* n, int blocks, int* team, int* first, int* count);
+
 /* ---- Step 2: single-particle Hamiltonian (Sec. 2.1-2.2, Eq. Schroedinger) --
  * hpsi = h psi for I states, h = U - sum_j d_j B d_j
  *        - (i/2) sum_ijk eps_ijk [W_i sigma_k d_j + d_j W_i sigma_k],

@@ -50,6 +50,8 @@ _SIGNATURES = {
     "sky_last_error": (ctypes.c_char_p, [_P]),
     "sky_supported_size": (_I, [_I, _I]),
     "sky_kernel_launches": (ctypes.c_ulonglong, []),
+    "sky_tri_team_plan": (_I, [_I, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                               ctypes.POINTER(_I)]),
     "sky_stats": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), _I]),
     "sky_apply_h": (_I, [_P, _P, _P, _P, _P, _P, _I, _P, _P]),
     "sky_derivative": (_I, [_P, _I, _P, _P, _I]),
@@ -177,6 +179,19 @@ def sky_stats(ctx, reset=False):
 
 def sky_kernel_launches():
     return int(lib().sky_kernel_launches())
+
+
+def sky_tri_team_plan(n, blocks):
+    """The batched eigensolver's team split for problems of sizes n on
+    ``blocks`` blocks (host only): (team of each problem, [(first block,
+    block count) per team]), or None when the batch cannot be split."""
+    np_ = len(n)
+    arr = (_I * max(np_, 1))
+    team, first, count = arr(), arr(), arr()
+    k = lib().sky_tri_team_plan(np_, arr(*[int(x) for x in n]), int(blocks), team, first, count)
+    if k <= 0:
+        return None
+    return [int(team[b]) for b in range(np_)], [(int(first[t]), int(count[t])) for t in range(k)]
 
 
 def sky_apply_h(ctx, U, B, W, psi, hpsi, I, eps=None, hnorm2=None):

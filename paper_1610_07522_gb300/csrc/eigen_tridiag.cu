@@ -966,8 +966,14 @@ static bool plan_teams(int np, const int* n, int blocks, size_t budget, TeamPlan
   int order[kMaxBatch];
   for (int b = 0; b < np; ++b) order[b] = b;
   std::sort(order, order + np, [&](int x, int y) { return n[x] != n[y] ? n[x] > n[y] : x < y; });
+  // an upper time bound that fits (1 s covers the usual batches on a full GPU;
+  // larger batches on fewer blocks need longer), then bisection
   double hi = 1.0, lo = 0.0;
-  if (plan_at(np, n, order, hi, budget, p) > blocks) return false;
+  while (plan_at(np, n, order, hi, budget, p) > blocks) {
+    lo = hi;
+    hi *= 2.0;
+    if (hi > 1e7) return false;   // no split fits (shared memory bounds the packing)
+  }
   for (int it = 0; it < 48; ++it) {
     const double mid = 0.5 * (lo + hi);
     if (plan_at(np, n, order, mid, budget, p) <= blocks) hi = mid; else lo = mid;
@@ -988,6 +994,22 @@ static bool plan_teams(int np, const int* n, int blocks, size_t budget, TeamPlan
     ++used;
   }
   return true;
+}
+
+// The team split of a batch on `blocks` blocks for callers (sky_tri_team_plan):
+// the number of teams, 0 if it cannot be split.
+int tri_team_plan(int np, const int* n, int blocks, int* team, int* first, int* count) {
+  if (np < 1 || np > kMaxBatch || blocks < 1 || !n || !team || !first || !count) return 0;
+  for (int b = 0; b < np; ++b)
+    if (n[b] < 1 || tri_vectors_global(n[b])) return 0;
+  TeamPlan tp;
+  if (!plan_teams(np, n, blocks, kTriSmemMax / sizeof(double2) - 64, tp)) return 0;
+  for (int t = 0; t < tp.nteam; ++t) {
+    first[t] = tp.g0[t];
+    count[t] = tp.g0[t + 1] - tp.g0[t];
+    for (int k = tp.p0[t]; k < tp.p0[t + 1]; ++k) team[tp.mem[k]] = t;
+  }
+  return tp.nteam;
 }
 
 // One launch sequence for the problems idx[0..np) of a batch (their vectors fit).

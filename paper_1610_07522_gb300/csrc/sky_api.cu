@@ -188,6 +188,10 @@ int sky_supported_size(int n, sky_prec prec) { return size_ok(n, prec) ? 1 : 0; 
 
 unsigned long long sky_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int sky_tri_team_plan(int np, const int* n, int blocks, int* team, int* first, int* count) {
+  return tri_team_plan(np, n, blocks, team, first, count);
+}
+
 sky_status sky_init(sky_ctx** out, const int grid[3], const double dx[3], const sky_skyrme* params,
                     const double twist[3], sky_prec prec, int max_states, void* stream) {
   if (!out) return SKY_EINVAL;

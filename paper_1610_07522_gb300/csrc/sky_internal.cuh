@@ -269,6 +269,7 @@ bool oz_zgemm_group_fits(const Ctx* c, int np, const int* n);
 sky_status oz_zgemm_group(Ctx* c, const ZJobs& j);
 int oz_group_slices();
 bool fused_h_ok(const Ctx* c);      // the fused FP32 h psi applies to this context
+int tri_team_plan(int np, const int* n, int blocks, int* team, int* first, int* count);
 int fused_h_blocks(const Ctx* c);   // its reduction blocks per state               // digits of the grouped products
 constexpr int kOzGroupMin = 8;      // batches of more problems take the grouped products
 sky_status oz_zgemm(Ctx* c, bool ah, bool bh, const double2* A, const double2* B, double2* C,
