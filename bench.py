@@ -634,9 +634,17 @@ def batched_leg(dev, form="bf16x3", count=64, steps=10):
             s.step()
             torch.cuda.synchronize(dev)
     seq_ms = timed(one_at_a_time, 2)
+    sizes = [bs.boxes[i].I[q] for i, q in bs.problems]
+    plan = B.sky_tri_team_plan(sizes, torch.cuda.get_device_properties(dev).multi_processor_count)
+    teams = None
+    if plan is not None:
+        team, tb = plan
+        teams = {"problems": len(sizes), "teams": len(tb), "blocks": sum(c for _, c in tb),
+                 "blocks_of_the_largest_problem": tb[team[sizes.index(max(sizes))]][1],
+                 "one_block_teams": sum(1 for _, c in tb if c == 1)}
     out = {"instances": count, "form": form, "grids": sorted({w.grid[0] for w in ws}),
            "units_per_step": bs.units, "graph_ms_per_step": graph_ms, "eager_ms_per_step": eager_ms,
-           "status_after_graph_steps": status,
+           "status_after_graph_steps": status, "eigensolver_teams": teams,
            "one_box_at_a_time_ms_per_step": seq_ms,
            "value": bs.units / (graph_ms / 1e3), "unit": "spinor-applies/s",
            "launches_per_step": bs.launches_per_step,
