@@ -409,13 +409,15 @@ def test_fp32_apply_h_damped_densities(case):
 
 @pytest.mark.parametrize("grid,twist,I", [((12, 16, 20), (0.3, -0.8, 1.7), 37),
                                            ((24, 24, 24), (0.0, 0.0, 0.0), 5),
+                                           ((24, 24, 24), (1.3, -0.2, 0.9), 120),
                                            ((32, 8, 12), (-2.1, 0.4, 3.0), 9)])
 def test_fp32_fused_h_matches_general_path_and_oracle(grid, twist, I):
     """The FP32 forms' h psi in one fused pass per axis (the default for axis
-    lengths up to 32) against the general gradient / local / divergence
+    lengths up to 24) against the general gradient / local / divergence
     passes (knob 0) and the oracle, with <psi|h psi> and |h psi|^2; uneven
     axes and twists, so that every axis has its own transform length and
-    wavenumbers."""
+    wavenumbers; 120 states at 24^3 take two chunks (about 108 states of psi
+    and h psi per 48 MB)."""
     rng = np.random.default_rng(23 + I)
     with Ctx(grid, twist=twist, prec=B.SKY_F32, max_states=I) as c:
         g = c.grid
