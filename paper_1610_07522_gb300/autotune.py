@@ -29,7 +29,8 @@ BATCH_CANDIDATES = dict(CANDIDATES)
 BATCH_CANDIDATES[B.SKY_KNOB_TC_WAVES] = (0, 1, 2, 4)
 NAMES = {B.SKY_KNOB_LINE_YZ: "line_yz", B.SKY_KNOB_LINE_X: "line_x",
          B.SKY_KNOB_OVERLAP_WAVES: "overlap_waves", B.SKY_KNOB_TC_WAVES: "tc_waves",
-         B.SKY_KNOB_TC_TILE_N: "tc_tile_n", B.SKY_KNOB_JACOBI_BLOCKS: "jacobi_blocks"}
+         B.SKY_KNOB_TC_TILE_N: "tc_tile_n", B.SKY_KNOB_FUSED_H: "fused_h",
+         B.SKY_KNOB_JACOBI_BLOCKS: "jacobi_blocks"}
 TC_FORMS = (B.SKY_F32_BF16X3, B.SKY_F32_BF16X6)
 
 
@@ -118,6 +119,17 @@ def tune_eigensolver(eig_ctx, run_solve, stream, reps=3):
     return _pick(eig_ctx, B.SKY_KNOB_JACOBI_BLOCKS, values, run_solve, stream, reps)
 
 
+def _settable(ctx, knob, value):
+    """Whether the context accepts the value (leaving the knob as it was)."""
+    old = B.sky_tune_get(ctx, knob)
+    try:
+        B.sky_tune_set(ctx, knob, value)
+    except B.SkyError:
+        return False
+    B.sky_tune_set(ctx, knob, old)
+    return True
+
+
 def _concurrent(boxes, main, fn):
     """fn(box) for every box on its own stream, forked from and joined to
     ``main`` (how the boxes of a batch run)."""
@@ -150,8 +162,9 @@ def tune_batch(bs, reps=5, cache=None):
     """Tune a BatchSolver.  The boxes of one shape (grid, particle numbers,
     precision) share their knobs, and each candidate is timed on all boxes of
     that shape running together, each on its own stream, since that is how
-    they run in the batch: FFT line-pass block shapes on h psi, then for the
-    split-BF16 forms the GEMM tile width (128 x 128 or 128 x 256, on the
+    they run in the batch: FFT line-pass block shapes on h psi, the FP32 h psi
+    as fused per-axis passes or general passes (where both exist), then for
+    the split-BF16 forms the GEMM tile width (128 x 128 or 128 x 256, on the
     overlap and the recombination) and the overlap's K splits (down to the
     fewest the accumulation bound allows), else the FMA overlap's splits.
     The shared eigensolver's Jacobi block count is tuned only when the batch
@@ -179,8 +192,17 @@ def tune_batch(bs, reps=5, cache=None):
             B.sky_rotate(s.ctx, s.phi[q], s.M[q], s.I[q], s.h[q])
 
         res = {}
+        fusable = _settable(boxes[0].ctx, B.SKY_KNOB_FUSED_H, 1)
+        if fusable:
+            # line-pass shapes on the general h psi passes, which use them
+            for s in boxes:
+                B.sky_tune_set(s.ctx, B.SKY_KNOB_FUSED_H, 0)
         for knob in (B.SKY_KNOB_LINE_YZ, B.SKY_KNOB_LINE_X):
             res[NAMES[knob]] = _pick_batch(boxes, knob, BATCH_CANDIDATES[knob], h, main, reps)
+        if fusable:
+            # the FP32 h psi as fused per-axis passes or as the general passes
+            res[NAMES[B.SKY_KNOB_FUSED_H]] = _pick_batch(boxes, B.SKY_KNOB_FUSED_H, (0, 1), h,
+                                                         main, reps)
         if boxes[0].prec in TC_FORMS:
             res[NAMES[B.SKY_KNOB_TC_TILE_N]] = _pick_batch(
                 boxes, B.SKY_KNOB_TC_TILE_N, BATCH_CANDIDATES[B.SKY_KNOB_TC_TILE_N], ovrot, main, reps)
