@@ -32,6 +32,18 @@ def test_header_declares_the_hot_path():
         assert n in names
 
 
+def test_header_is_plain_c(tmp_path):
+    """The boundary is a C ABI: the header compiles as strict C99 on its own."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "uses_sky.c"
+    src.write_text('#include "sky.h"\nint main(void) { return sky_supported_size(16, SKY_F64) != 1; }\n')
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o",
+                        str(tmp_path / "uses_sky.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_library_exports_every_declared_symbol(libpath):
     out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True).stdout
     exported = set(re.findall(r"\bT\s+(sky_[a-z_0-9]+)\b", out))
