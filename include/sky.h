@@ -143,7 +143,9 @@ int sky_tri_team_plan(int np, const int* n, int blocks, int* team, int* first, i
  * U, B: [G]; W: [3][G] (one species' mean field).  psi, hpsi: [I][2][G]
  * spinors, must not overlap.  eps (nullable, [I]) receives <psi|h|psi>,
  * hnorm2 (nullable, [I]) receives <h psi|h psi> (= <psi|h^2|psi>), both
- * with the volume element dx^3.  Stored as the paper's hampsi (Sec. 3.4). */
+ * with the volume element dx^3 (FP32 forms: sums of exact float products kept
+ * in float pairs, about 2^-48 of the sum per term, totals in FP64).  Stored as
+ * the paper's hampsi (Sec. 3.4). */
 sky_status sky_apply_h(sky_ctx* ctx, const double* U, const double* B, const double* W,
                        const void* psi, void* hpsi, int I, double* eps, double* hnorm2);
 
@@ -256,7 +258,9 @@ sky_status sky_rotate(sky_ctx* ctx, const void* phi, const double* M, int I, voi
 /* ---- Step 4a: densities (Eqs. rho, curr, tau; all v^2 = 1) -----------------
  * For the I states of one species: rho = sum |psi|^2, tau = sum |d psi|^2,
  * J_i = sum Re[-i eps_ijk psi^+ sigma_k d_j psi], divJ = sum_i d_i J_i
- * (spectral, real part).  rho, tau, divJ: [G]; J: [3][G] or NULL. */
+ * (spectral, real part).  rho, tau, divJ: [G]; J: [3][G] or NULL.  FP32 forms:
+ * the sums over states of exact float products are kept in float pairs (about
+ * 2^-48 of the sum per term), the splits added in FP64. */
 sky_status sky_densities(sky_ctx* ctx, const void* psi, int I, double* rho, double* tau,
                          double* J, double* divJ);
 
